@@ -1,0 +1,158 @@
+/*
+ * fmm.h -- C ABI of the GB300 (sm_103a) shift-free 2D FMM library (libfmm.so).
+ *
+ * The library evaluates the 2D log potential of N charges in the square
+ * [0, box]^2,
+ *
+ *     phi(z_i) = sum_{j != i} q_j log|z_i - z_j|,
+ *
+ * with the shift-free Fast Multipole Method of Kajima, "Summation of certain
+ * locally bilinear forms and its applications to the Fast Multipole Method"
+ * (arXiv 2009.00767):
+ *   - the computation box is split into a uniform quadtree of depth `levels`
+ *     (Sec. 2.1 items 1-4);
+ *   - for EVERY level k = 2..levels the multipole moments of every square are
+ *     formed directly from the particles (the upward pass U-bar of Sec. 2.2.1,
+ *     with no multipole-to-multipole shift);
+ *   - each square's interaction list (Sec. 2.1 item 5) is converted into a
+ *     local expansion (D-bar-1 of Sec. 2.2.1);
+ *   - each level's local expansion is evaluated directly at the particles and
+ *     the levels are summed (D-bar-2 of Sec. 2.2.1 by linearity, with no
+ *     local-to-local shift);
+ *   - the near field of the own and eight adjacent finest squares is summed
+ *     directly (Sec. 2.1 E-2).
+ * The vectors and bilinear forms of Sec. 2.2.1 are realised as complex
+ * multipole moments of order p (coefficients 0..p) and the multipole-to-local
+ * conversion of Greengard's 2D expansions (the paper's ref. [101]); the
+ * conversion operators depend only on the relative offset of two squares
+ * (40 offsets) and are built once per plan in FP64 (Sec. 4, Discussions (2)
+ * and (3)).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA global-memory pointers on the plan's device;
+ *     the caller owns them.  Host pointers are ordinary host memory.
+ *   - Arrays are dense and C-ordered.  xy is [N][2] (x then y), FP64.
+ *   - Work is enqueued on the plan's CUDA stream and returns without waiting
+ *     unless the entry point says otherwise.  Errors that only the device can
+ *     see (a particle outside the box, a non-finite value) are latched in the
+ *     plan and returned by fmm_sync; phi is then left unwritten for that call.
+ *   - A plan is not thread-safe: calls on one plan must not overlap.
+ *   - fmm_status values are returned; no entry point aborts or prints.
+ */
+#ifndef FMM_H_
+#define FMM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_plan_s* fmm_plan_t;
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_INVALID_ARG = 1,   /* a host-side argument check failed */
+    FMM_ERR_OUT_OF_BOX = 2,    /* a particle lies outside [0, box]^2 (device check) */
+    FMM_ERR_NONFINITE = 3,     /* a coordinate or charge is NaN or infinite (device check) */
+    FMM_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    FMM_ERR_OOM = 5,           /* device memory allocation failed in fmm_plan */
+    FMM_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
+    FMM_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+} fmm_status;
+
+/* Arithmetic of the hot path.  FMM_FP64 runs every stage in FP64.  The mixed
+ * modes run particle-side stages (P2M, L2P, P2P) in FP32 on coordinates local
+ * to each square, keep the cross-level sum and the final phi in FP64, and run
+ * M2L as stated: FP32 on the CUDA cores, or on the tensor cores (tcgen05) in
+ * TF32 / BF16 with FP32 accumulation, where the x3 forms split each operand
+ * into a high and a low part to recover FP32-level accuracy. */
+typedef enum {
+    FMM_FP64 = 0,
+    FMM_MIXED_FP32 = 1,
+    FMM_MIXED_TF32 = 2,
+    FMM_MIXED_3XTF32 = 3,
+    FMM_MIXED_BF16 = 4,
+    FMM_MIXED_BF16X3 = 5
+} fmm_precision;
+
+/* Per-call statistics of the last completed fmm_potential (valid after fmm_sync). */
+typedef struct {
+    int64_t n;                 /* particles */
+    int levels, p, precision;
+    double ms_total;           /* enqueue of the first stage to the end of the last, CUDA events */
+    double ms_sort;            /* bin + scan + scatter */
+    double ms_p2m;             /* moments of levels 2..levels */
+    double ms_m2l;             /* interaction-list conversion of levels 2..levels */
+    double ms_l2p;             /* local evaluation of levels 2..levels */
+    double ms_p2p;             /* near field + final phi in input order */
+    int64_t p2p_pairs;         /* ordered source-target pairs of the near field (counted on device) */
+    int64_t max_leaf;          /* largest finest-square population */
+    int kernel_launches;       /* kernels the library launched for that call */
+    uint64_t workspace_bytes;  /* device memory the plan owns */
+} fmm_stats;
+
+/* Create a plan for exactly n particles, a quadtree of depth `levels` over
+ * [0, box]^2 and expansion order p (coefficients 0..p).
+ *   out        receives the plan; unchanged on error.
+ *   n          1 <= n <= 2^31 - 1.
+ *   levels     0 <= levels <= 12 (levels 0 and 1 have no far field: the
+ *              interaction list exists from level 2, Sec. 2.1 item 5).
+ *   p          1 <= p <= 40 (FP64 and mixed modes alike).
+ *   box        side of the computation box (the paper's 5), > 0 and finite.
+ *   precision  an fmm_precision value.
+ *   stream     cudaStream_t to enqueue on (NULL = legacy default stream).
+ * The plan allocates all device workspaces and builds the 40 M2L operators in
+ * FP64 on the host (uploaded once); this cost is not part of fmm_potential.
+ * Returns FMM_ERR_INVALID_ARG, FMM_ERR_UNSUPPORTED, FMM_ERR_OOM or
+ * FMM_ERR_CUDA on failure. */
+fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box,
+                    int precision, void* stream);
+
+/* Change the stream later calls enqueue on. */
+fmm_status fmm_set_stream(fmm_plan_t plan, void* stream);
+
+/* phi[i] = potential at particle i, in input order (the whole method above).
+ *   xy   device, const double[n][2]; every point must lie in [0, box]^2.
+ *   q    device, const double[n].
+ *   phi  device, double[n]; written only if the device checks pass.
+ * Asynchronous on the plan's stream; allocates nothing.  Device-detected
+ * errors are reported by fmm_sync.  Coincident particles (r = 0) contribute 0. */
+fmm_status fmm_potential(fmm_plan_t plan, const double* xy, const double* q, double* phi);
+
+/* As fmm_potential, with HOST arrays: copies xy and q to plan-owned device
+ * buffers, runs the method and copies phi back, then waits for the stream.
+ * Host arrays may be pageable or pinned (pinned is faster).  Returns the
+ * device-detected status, like fmm_sync. */
+fmm_status fmm_potential_host(fmm_plan_t plan, const double* xy_host, const double* q_host,
+                              double* phi_host);
+
+/* Wait for the plan's stream; return the first device-detected error of the
+ * calls since the previous fmm_sync (FMM_OK if none) and clear it. */
+fmm_status fmm_sync(fmm_plan_t plan);
+
+/* Copy the statistics of the last synced call into *out (host struct). */
+fmm_status fmm_plan_stats(fmm_plan_t plan, fmm_stats* out);
+
+/* Free the plan and every device buffer it owns.  NULL is ignored. */
+void fmm_plan_destroy(fmm_plan_t plan);
+
+/* Static English text for a status code; never NULL. */
+const char* fmm_status_string(int status);
+
+/* FP64 direct sum at selected targets (the judge of every accuracy figure):
+ *   phi_t[t] = sum_{j != targets[t], r > 0} q_j log|z_targets[t] - z_j|.
+ *   xy, q      device, the n particles as in fmm_potential.
+ *   targets    device, const int64_t[n_targets], each in [0, n).
+ *   phi_t      device, double[n_targets].
+ *   stream     cudaStream_t (NULL = default stream).
+ * Asynchronous; allocates nothing; returns FMM_ERR_INVALID_ARG for n < 0,
+ * n_targets < 0 or null pointers with nonzero sizes. */
+fmm_status fmm_direct_targets(int64_t n, const double* xy, const double* q, int64_t n_targets,
+                              const int64_t* targets, double* phi_t, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif  /* FMM_H_ */

@@ -92,6 +92,9 @@ int oracle_get_threads(void) {
 static double binom_table[ORACLE_MAXBINOM + 1][ORACLE_MAXBINOM + 1];
 static int binom_ready = 0;
 
+/* The table is filled once, serially, before any OpenMP region can read it: every public
+ * entry point that reaches an expansion calls binom_init() first, and the library
+ * constructor fills it at load time. */
 static void binom_init(void) {
     if (binom_ready) return;
     for (int n = 0; n <= ORACLE_MAXBINOM; ++n) {
@@ -102,6 +105,8 @@ static void binom_init(void) {
     }
     binom_ready = 1;
 }
+
+__attribute__((constructor)) static void oracle_init(void) { binom_init(); }
 
 double oracle_binom(int n, int r) {
     binom_init();
@@ -139,7 +144,6 @@ static double multipole_eval(const cplx *a, int p, cplx c, cplx z) {
  *   b_l = -a_0 / (l z0^l) + z0^-l sum_{k>=1} a_k (-1)^k z0^-k C(l+k-1, k-1)   (l >= 1)
  * The result is ADDED to b[]. */
 static void m2l_accumulate(const cplx *a, int p, cplx z0, cplx *b) {
-    binom_init();
     cplx inv = 1.0 / z0;
     cplx ak_over[ORACLE_MAXP + 1];          /* a_k (-1)^k z0^-k */
     cplx ip = 1.0;
@@ -170,7 +174,6 @@ static double local_eval(const cplx *b, int p, cplx c, cplx z) {
 /* M2M: child moments a[] about c_c to parent moments about c_p, z0 = c_c - c_p (U-2).
  *   b_0 = a_0,  b_l = -a_0 z0^l / l + sum_{k=1}^{l} a_k z0^(l-k) C(l-1, k-1).  Added to b[]. */
 static void m2m_accumulate(const cplx *a, int p, cplx z0, cplx *b) {
-    binom_init();
     cplx zp[ORACLE_MAXP + 1];
     zp[0] = 1.0;
     for (int m = 1; m <= p; ++m) zp[m] = zp[m - 1] * z0;
@@ -185,7 +188,6 @@ static void m2m_accumulate(const cplx *a, int p, cplx z0, cplx *b) {
 /* L2L: parent local a[] about c_p re-centred at the child centre c_c, z0 = c_c - c_p (D-2).
  * sum_k a_k (u + z0)^k with u = z - c_c gives b_l = sum_{k>=l} a_k C(k, l) z0^(k-l).  Added to b[]. */
 static void l2l_accumulate(const cplx *a, int p, cplx z0, cplx *b) {
-    binom_init();
     cplx zp[ORACLE_MAXP + 1];
     zp[0] = 1.0;
     for (int m = 1; m <= p; ++m) zp[m] = zp[m - 1] * z0;
@@ -218,6 +220,7 @@ double oracle_multipole_eval(const double *a_in, int p, double cx, double cy, do
 }
 
 void oracle_m2l(const double *a_in, int p, double z0x, double z0y, double *b_out) {
+    binom_init();
     cplx a[ORACLE_MAXP + 1], b[ORACLE_MAXP + 1];
     unpack(a_in, p, a);
     for (int m = 0; m <= p; ++m) b[m] = 0.0;
@@ -232,6 +235,7 @@ double oracle_local_eval(const double *b_in, int p, double cx, double cy, double
 }
 
 void oracle_m2m(const double *a_in, int p, double z0x, double z0y, double *b_out) {
+    binom_init();
     cplx a[ORACLE_MAXP + 1], b[ORACLE_MAXP + 1];
     unpack(a_in, p, a);
     for (int m = 0; m <= p; ++m) b[m] = 0.0;
@@ -240,6 +244,7 @@ void oracle_m2m(const double *a_in, int p, double z0x, double z0y, double *b_out
 }
 
 void oracle_l2l(const double *a_in, int p, double z0x, double z0y, double *b_out) {
+    binom_init();
     cplx a[ORACLE_MAXP + 1], b[ORACLE_MAXP + 1];
     unpack(a_in, p, a);
     for (int m = 0; m <= p; ++m) b[m] = 0.0;
@@ -438,6 +443,7 @@ static void near_field(const tree_t *t, const double *xy, const double *q, doubl
 /* phi_far_level (optional, may be NULL): [levels+1][n] far field per level. */
 int oracle_shiftfree_levels(int64_t n, const double *xy, const double *q, int levels, int p, double box,
                             double *phi, double *phi_far_level) {
+    binom_init();
     tree_t t;
     int rc = tree_build(&t, n, xy, levels, p, box);
     if (rc) return rc;
@@ -478,6 +484,7 @@ int oracle_shiftfree(int64_t n, const double *xy, const double *q, int levels, i
 /* ------------------------------------------------------------------------ */
 
 int oracle_classical(int64_t n, const double *xy, const double *q, int levels, int p, double box, double *phi) {
+    binom_init();
     tree_t t;
     int rc = tree_build(&t, n, xy, levels, p, box);
     if (rc) return rc;

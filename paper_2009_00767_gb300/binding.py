@@ -1,0 +1,212 @@
+"""ctypes binding of include/fmm.h (libfmm.so): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: all of it runs in the CUDA kernels of libfmm.so.
+There is no fallback: if the library is missing or fails to load, importing
+this module raises.  PyTorch tensors are accepted for device buffers (their
+``data_ptr()`` is passed) and the current torch stream is used by default.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfmm.so")
+
+FMM_OK = 0
+FMM_ERR_INVALID_ARG = 1
+FMM_ERR_OUT_OF_BOX = 2
+FMM_ERR_NONFINITE = 3
+FMM_ERR_CUDA = 4
+FMM_ERR_OOM = 5
+FMM_ERR_TIMEOUT = 6
+FMM_ERR_UNSUPPORTED = 7
+
+FMM_FP64 = 0
+FMM_MIXED_FP32 = 1
+FMM_MIXED_TF32 = 2
+FMM_MIXED_3XTF32 = 3
+FMM_MIXED_BF16 = 4
+FMM_MIXED_BF16X3 = 5
+
+PRECISIONS = {"fp64": FMM_FP64, "fp32": FMM_MIXED_FP32, "tf32": FMM_MIXED_TF32, "3xtf32": FMM_MIXED_3XTF32,
+              "bf16": FMM_MIXED_BF16, "bf16x3": FMM_MIXED_BF16X3}
+
+# Every entry point include/fmm.h declares, with (restype, argtypes).
+_vp, _i64, _i32, _d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+
+
+class fmm_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("levels", ctypes.c_int), ("p", ctypes.c_int), ("precision", ctypes.c_int),
+                ("ms_total", ctypes.c_double), ("ms_sort", ctypes.c_double), ("ms_p2m", ctypes.c_double),
+                ("ms_m2l", ctypes.c_double), ("ms_l2p", ctypes.c_double), ("ms_p2p", ctypes.c_double),
+                ("p2p_pairs", ctypes.c_int64), ("max_leaf", ctypes.c_int64), ("kernel_launches", ctypes.c_int),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+SIGNATURES = {
+    "fmm_plan": (_i32, [ctypes.POINTER(_vp), _i64, _i32, _i32, _d, _i32, _vp]),
+    "fmm_set_stream": (_i32, [_vp, _vp]),
+    "fmm_potential": (_i32, [_vp, _vp, _vp, _vp]),
+    "fmm_potential_host": (_i32, [_vp, _vp, _vp, _vp]),
+    "fmm_sync": (_i32, [_vp]),
+    "fmm_plan_stats": (_i32, [_vp, ctypes.POINTER(fmm_stats)]),
+    "fmm_plan_destroy": (None, [_vp]),
+    "fmm_status_string": (ctypes.c_char_p, [_i32]),
+    "fmm_direct_targets": (_i32, [_i64, _vp, _vp, _i64, _vp, _vp, _vp]),
+}
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfmm.so is not built ({LIB_PATH}); run paper_2009_00767_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return _lib.fmm_status_string(int(status)).decode()
+
+
+fmm_status_string = status_string
+
+
+def _check(status: int, where: str):
+    if status != FMM_OK:
+        raise FmmError(status, where)
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array / int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def fmm_plan(n: int, levels: int, p: int, box: float = 5.0, precision="fp64", stream=None) -> int:
+    """Create a plan (see include/fmm.h); returns the opaque handle as an int."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    h = _vp()
+    _check(_lib.fmm_plan(ctypes.byref(h), int(n), int(levels), int(p), float(box), prec, _stream_handle(stream)),
+           "fmm_plan")
+    return h.value
+
+
+def fmm_set_stream(plan: int, stream=None):
+    _check(_lib.fmm_set_stream(plan, _stream_handle(stream)), "fmm_set_stream")
+
+
+def fmm_potential(plan: int, xy, q, phi):
+    """Enqueue phi = potential(xy, q) on the plan's stream; device buffers (float64)."""
+    _check(_lib.fmm_potential(plan, _ptr(xy), _ptr(q), _ptr(phi)), "fmm_potential")
+
+
+def fmm_potential_host(plan: int, xy, q, phi):
+    """Host buffers (numpy float64 or pinned CPU tensors); waits and returns the device status."""
+    _check(_lib.fmm_potential_host(plan, _ptr(xy), _ptr(q), _ptr(phi)), "fmm_potential_host")
+
+
+def fmm_sync(plan: int, check: bool = True) -> int:
+    s = _lib.fmm_sync(plan)
+    if check:
+        _check(s, "fmm_sync")
+    return s
+
+
+def fmm_plan_stats(plan: int) -> dict:
+    st = fmm_stats()
+    _check(_lib.fmm_plan_stats(plan, ctypes.byref(st)), "fmm_plan_stats")
+    return st.as_dict()
+
+
+def fmm_plan_destroy(plan: int):
+    _lib.fmm_plan_destroy(plan)
+
+
+def fmm_direct_targets(xy, q, targets, phi_t, stream=None):
+    n = int(q.shape[0])
+    nt = int(targets.shape[0])
+    _check(_lib.fmm_direct_targets(n, _ptr(xy), _ptr(q), nt, _ptr(targets), _ptr(phi_t), _stream_handle(stream)),
+           "fmm_direct_targets")
+
+
+class Plan:
+    """Owner of one fmm_plan handle; frees it on close / garbage collection."""
+
+    def __init__(self, n, levels, p, box=5.0, precision="fp64", stream=None):
+        self.n, self.levels, self.p, self.box, self.precision = int(n), int(levels), int(p), float(box), precision
+        self.handle = fmm_plan(n, levels, p, box, precision, stream)
+
+    def potential(self, xy, q, phi=None, sync=True):
+        import torch
+        if phi is None:
+            phi = torch.empty(self.n, dtype=torch.float64, device=xy.device)
+        fmm_potential(self.handle, xy, q, phi)
+        if sync:
+            fmm_sync(self.handle)
+        return phi
+
+    def potential_host(self, xy, q, phi=None):
+        if phi is None:
+            phi = np.empty(self.n)
+        fmm_potential_host(self.handle, xy, q, phi)
+        return phi
+
+    def sync(self, check=True):
+        return fmm_sync(self.handle, check)
+
+    def stats(self):
+        return fmm_plan_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fmm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,296 @@
+// api.cu -- the C ABI of include/fmm.h: plans, the FP64 operator build, dispatch and status.
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+namespace {
+
+using cd = std::complex<double>;
+
+// Scale-free M2L operators on power-sum moments (D-bar-1 of Sec. 2.2.1 realised with Greengard's
+// 2D multipole-to-local conversion, the paper's ref. [101]).  For a source square at offset
+// w0 = dx + i dy (in units of the side s) from the target, with moments M_0 = sum q,
+// M_k = sum q w^k and local coefficients b'_l of (z - c_t)/s:
+//   b'_0 = M_0 log(-w0)       + sum_k M_k (-1)^(k+1) / k  w0^-k                (+ M_0 ln s)
+//   b'_l = -M_0 / (l w0^l)    + sum_k M_k (-1)^(k+1) / k  C(l+k-1, k-1) w0^-(l+k)
+// Built in FP64 (Sec. 4, Discussion (3): the entries come from large binomials times small powers).
+// Layout [d][k][l], d = (dx + 3) + 7 (dy + 3); the nine adjacent offsets stay zero.
+void build_operators(int p, std::vector<cd>& T) {
+    const int p1 = p + 1;
+    T.assign((size_t)49 * p1 * p1, cd(0.0, 0.0));
+    std::vector<std::vector<double>> C(2 * p + 2, std::vector<double>(2 * p + 2, 0.0));
+    for (int nn = 0; nn < 2 * p + 2; ++nn) {
+        C[nn][0] = 1.0;
+        for (int r = 1; r <= nn; ++r) C[nn][r] = C[nn - 1][r - 1] + (r <= nn - 1 ? C[nn - 1][r] : 0.0);
+    }
+    for (int dy = -3; dy <= 3; ++dy)
+        for (int dx = -3; dx <= 3; ++dx) {
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+            const cd w0((double)dx, (double)dy);
+            const cd inv = 1.0 / w0;
+            std::vector<cd> ip(2 * p + 2);
+            ip[0] = 1.0;
+            for (int m = 1; m < 2 * p + 2; ++m) ip[m] = ip[m - 1] * inv;
+            cd* Td = &T[(size_t)((dx + 3) + 7 * (dy + 3)) * p1 * p1];
+            auto at = [&](int k, int l) -> cd& { return Td[(size_t)k * p1 + l]; };
+            at(0, 0) = std::log(-w0);
+            for (int l = 1; l <= p; ++l) at(0, l) = -ip[l] / (double)l;
+            for (int k = 1; k <= p; ++k) {
+                const double sgn = (k & 1) ? 1.0 : -1.0;   // (-1)^(k+1)
+                at(k, 0) = sgn / (double)k * ip[k];
+                for (int l = 1; l <= p; ++l) at(k, l) = sgn / (double)k * C[l + k - 1][k - 1] * ip[l + k];
+            }
+        }
+}
+
+bool valid_precision(int v) { return v >= FMM_FP64 && v <= FMM_MIXED_BF16X3; }
+
+template <class T>
+fmm_status dev_alloc(fmm_plan_s* pl, T** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA;
+    }
+    pl->workspace_bytes += bytes;
+    return FMM_OK;
+}
+
+void free_plan(fmm_plan_s* pl) {
+    if (!pl) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(pl->device);
+    void* bufs[] = {pl->keys, pl->rank, pl->counts, pl->leaf_start, pl->block_sums, pl->sorted_key,
+                    pl->sorted64, pl->sorted32, pl->phi_far, pl->T64, pl->T32, pl->d_status,
+                    pl->d_counters, pl->d_xy_stage, pl->d_q_stage, pl->d_phi_stage};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    for (int k = 0; k <= FMM_MAX_LEVELS; ++k) {
+        if (pl->grids.A[k]) cudaFree(pl->grids.A[k]);
+        if (pl->grids.B[k]) cudaFree(pl->grids.B[k]);
+    }
+    if (pl->h_status) cudaFreeHost(pl->h_status);
+    if (pl->h_counters) cudaFreeHost(pl->h_counters);
+    for (int e = 0; e < 6; ++e)
+        if (pl->ev[e]) cudaEventDestroy(pl->ev[e]);
+    cudaSetDevice(prev);
+    delete pl;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* phi) {
+    cudaStream_t st = pl->stream;
+    if (cudaMemsetAsync(pl->d_counters, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return FMM_ERR_CUDA;
+    cudaEventRecord(pl->ev[0], st);
+    int launches = fmm_launch_sort(pl, xy, q);
+    if (launches < 0) return FMM_ERR_CUDA;
+    int more = pl->precision == FMM_FP64 ? fmm_launch_fp64(pl, phi) : fmm_launch_mixed(pl, phi);
+    if (more == -2) return FMM_ERR_UNSUPPORTED;
+    if (more < 0) return FMM_ERR_CUDA;
+    pl->launches = launches + more;
+    pl->events_recorded = 1;
+    return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fmm_status_string(int status) {
+    switch (status) {
+        case FMM_OK: return "ok";
+        case FMM_ERR_INVALID_ARG: return "invalid argument";
+        case FMM_ERR_OUT_OF_BOX: return "a particle lies outside the computation box";
+        case FMM_ERR_NONFINITE: return "a coordinate or charge is not finite";
+        case FMM_ERR_CUDA: return "CUDA runtime error";
+        case FMM_ERR_OOM: return "out of device memory";
+        case FMM_ERR_TIMEOUT: return "a bounded device-side wait timed out";
+        case FMM_ERR_UNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, int precision, void* stream) {
+    if (!out) return FMM_ERR_INVALID_ARG;
+    if (n < 1 || n > 2147483647LL || levels < 0 || levels > FMM_MAX_LEVELS || p < 1 || p > FMM_MAX_P ||
+        !(box > 0.0) || !std::isfinite(box) || !valid_precision(precision))
+        return FMM_ERR_INVALID_ARG;
+    fmm_plan_s* pl = new (std::nothrow) fmm_plan_s();
+    if (!pl) return FMM_ERR_OOM;
+    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+        delete pl;
+        return FMM_ERR_CUDA;
+    }
+    pl->n = n;
+    pl->levels = levels;
+    pl->p = p;
+    pl->box = box;
+    pl->precision = precision;
+    pl->stream = static_cast<cudaStream_t>(stream);
+    const int64_t m = (int64_t)1 << (2 * levels);
+    const int p1 = p + 1;
+    fmm_status s = FMM_OK;
+#define FMM_TRY(expr)                \
+    do {                             \
+        s = (expr);                  \
+        if (s != FMM_OK) {           \
+            free_plan(pl);           \
+            return s;                \
+        }                            \
+    } while (0)
+    FMM_TRY(dev_alloc(pl, &pl->keys, sizeof(uint32_t) * n));
+    FMM_TRY(dev_alloc(pl, &pl->rank, sizeof(uint32_t) * n));
+    FMM_TRY(dev_alloc(pl, &pl->counts, sizeof(uint32_t) * m));
+    FMM_TRY(dev_alloc(pl, &pl->leaf_start, sizeof(uint32_t) * (m + 1)));
+    pl->scan_blocks = fmm_scan_blocks(m);
+    FMM_TRY(dev_alloc(pl, &pl->block_sums, sizeof(uint32_t) * pl->scan_blocks));
+    FMM_TRY(dev_alloc(pl, &pl->sorted_key, sizeof(uint32_t) * n));
+    if (precision == FMM_FP64)
+        FMM_TRY(dev_alloc(pl, &pl->sorted64, sizeof(fmm_p64) * n));
+    else
+        FMM_TRY(dev_alloc(pl, &pl->sorted32, sizeof(float4) * n));
+    FMM_TRY(dev_alloc(pl, &pl->phi_far, sizeof(double) * n));
+    const size_t cplx = precision == FMM_FP64 ? sizeof(double2) : sizeof(float2);
+    for (int k = 2; k <= levels; ++k) {
+        const size_t W = (size_t)fmm_grid_width(k);
+        pl->a_bytes[k] = W * W * p1 * cplx;
+        FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.A[k]), pl->a_bytes[k]));
+        FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.B[k]), ((size_t)1 << (2 * k)) * p1 * cplx));
+    }
+    std::vector<cd> T;
+    build_operators(p, T);
+    FMM_TRY(dev_alloc(pl, &pl->T64, sizeof(double2) * T.size()));
+    if (cudaMemcpy(pl->T64, T.data(), sizeof(double2) * T.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        FMM_TRY(FMM_ERR_CUDA);
+    if (precision != FMM_FP64) {
+        std::vector<float2> T32(T.size());
+        for (size_t i = 0; i < T.size(); ++i) T32[i] = make_float2((float)T[i].real(), (float)T[i].imag());
+        FMM_TRY(dev_alloc(pl, &pl->T32, sizeof(float2) * T32.size()));
+        if (cudaMemcpy(pl->T32, T32.data(), sizeof(float2) * T32.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            FMM_TRY(FMM_ERR_CUDA);
+    }
+    FMM_TRY(dev_alloc(pl, &pl->d_status, sizeof(unsigned int)));
+    FMM_TRY(dev_alloc(pl, &pl->d_counters, 2 * sizeof(unsigned long long)));
+    if (cudaMemset(pl->d_status, 0, sizeof(unsigned int)) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
+    if (cudaMallocHost(reinterpret_cast<void**>(&pl->h_status), sizeof(unsigned int)) != cudaSuccess)
+        FMM_TRY(FMM_ERR_OOM);
+    if (cudaMallocHost(reinterpret_cast<void**>(&pl->h_counters), 2 * sizeof(unsigned long long)) != cudaSuccess)
+        FMM_TRY(FMM_ERR_OOM);
+    FMM_TRY(dev_alloc(pl, &pl->d_xy_stage, sizeof(double) * 2 * n));
+    FMM_TRY(dev_alloc(pl, &pl->d_q_stage, sizeof(double) * n));
+    FMM_TRY(dev_alloc(pl, &pl->d_phi_stage, sizeof(double) * n));
+    for (int e = 0; e < 6; ++e)
+        if (cudaEventCreate(&pl->ev[e]) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
+#undef FMM_TRY
+    pl->last.n = n;
+    pl->last.levels = levels;
+    pl->last.p = p;
+    pl->last.precision = precision;
+    pl->last.workspace_bytes = pl->workspace_bytes;
+    *out = pl;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_stream(fmm_plan_t plan, void* stream) {
+    if (!plan) return FMM_ERR_INVALID_ARG;
+    plan->stream = static_cast<cudaStream_t>(stream);
+    return FMM_OK;
+}
+
+fmm_status fmm_potential(fmm_plan_t plan, const double* xy, const double* q, double* phi) {
+    if (!plan || !xy || !q || !phi) return FMM_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    return enqueue(plan, xy, q, phi);
+}
+
+fmm_status fmm_potential_host(fmm_plan_t plan, const double* xy_host, const double* q_host, double* phi_host) {
+    if (!plan || !xy_host || !q_host || !phi_host) return FMM_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    cudaStream_t st = plan->stream;
+    const size_t n = (size_t)plan->n;
+    if (cudaMemcpyAsync(plan->d_xy_stage, xy_host, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(plan->d_q_stage, q_host, sizeof(double) * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    fmm_status s = enqueue(plan, plan->d_xy_stage, plan->d_q_stage, plan->d_phi_stage);
+    if (s != FMM_OK) return s;
+    if (cudaMemcpyAsync(phi_host, plan->d_phi_stage, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    return fmm_sync(plan);
+}
+
+fmm_status fmm_sync(fmm_plan_t plan) {
+    if (!plan) return FMM_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    cudaStream_t st = plan->stream;
+    if (cudaMemcpyAsync(plan->h_status, plan->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(plan->h_counters, plan->d_counters, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaMemsetAsync(plan->d_status, 0, sizeof(unsigned int), st) != cudaSuccess)
+        return FMM_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (plan->events_recorded) {
+        float ms[5] = {0, 0, 0, 0, 0};
+        for (int e = 0; e < 5; ++e) cudaEventElapsedTime(&ms[e], plan->ev[e], plan->ev[e + 1]);
+        float tot = 0;
+        cudaEventElapsedTime(&tot, plan->ev[0], plan->ev[5]);
+        plan->last.ms_sort = ms[0];
+        plan->last.ms_p2m = ms[1];
+        plan->last.ms_m2l = ms[2];
+        plan->last.ms_l2p = ms[3];
+        plan->last.ms_p2p = ms[4];
+        plan->last.ms_total = tot;
+        plan->last.p2p_pairs = (int64_t)plan->h_counters[0];
+        plan->last.max_leaf = (int64_t)plan->h_counters[1];
+        plan->last.kernel_launches = plan->launches;
+        plan->events_recorded = 0;
+    }
+    const unsigned int f = *plan->h_status;
+    if (f & FMM_FLAG_NONFINITE) return FMM_ERR_NONFINITE;
+    if (f & FMM_FLAG_OUT_OF_BOX) return FMM_ERR_OUT_OF_BOX;
+    if (f & FMM_FLAG_TIMEOUT) return FMM_ERR_TIMEOUT;
+    return FMM_OK;
+}
+
+fmm_status fmm_plan_stats(fmm_plan_t plan, fmm_stats* out) {
+    if (!plan || !out) return FMM_ERR_INVALID_ARG;
+    *out = plan->last;
+    return FMM_OK;
+}
+
+void fmm_plan_destroy(fmm_plan_t plan) {
+    if (!plan) return;
+    cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+}
+
+fmm_status fmm_direct_targets(int64_t n, const double* xy, const double* q, int64_t n_targets,
+                              const int64_t* targets, double* phi_t, void* stream) {
+    if (n < 0 || n_targets < 0 || n_targets > 2147483647LL) return FMM_ERR_INVALID_ARG;
+    if (n_targets > 0 && (!targets || !phi_t || n == 0 || !xy || !q)) return FMM_ERR_INVALID_ARG;
+    int r = fmm_launch_direct_f64(n, xy, q, n_targets, targets, phi_t, static_cast<cudaStream_t>(stream));
+    return r < 0 ? FMM_ERR_CUDA : FMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+// sort.cu -- binning of the particles into the finest squares and the box-sorted copy.
+//
+// The tree is the uniform quadtree of Sec. 2.1 items 1-4: the square [0, box]^2 at level 0,
+// each level-k square split into four at level k+1, down to `levels`.  A particle's finest
+// square is (floor(x 2^l / box), floor(y 2^l / box)) in FP64, clamped to [0, 2^l - 1]; its
+// level-k square is the finest one shifted right by l - k.  Keys are Morton-interleaved, so
+// after a counting sort the particles of any square at any level form one contiguous range.
+//
+// Stages (HBM-bound gathers and scatters):
+//   k_bin      key + rank-in-square (atomic histogram) + device-side input checks
+//   k_scan_*   exclusive scan of the 4^l square populations -> CSR leaf_start
+//   k_scatter  box-sorted copy (FP64 absolute, or FP32 relative to the square centre)
+#include "fmm_internal.cuh"
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void k_bin(const double2* __restrict__ xy, const double* __restrict__ q, int64_t n, int levels,
+                      double box, uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
+                      uint32_t* __restrict__ counts, unsigned int* __restrict__ status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 p = xy[i];
+    double qq = q[i];
+    const double scale = (double)(1 << levels);
+    const int side = 1 << levels;
+    uint32_t key = 0;
+    if (!(isfinite(p.x) && isfinite(p.y) && isfinite(qq))) {
+        atomicOr(status, FMM_FLAG_NONFINITE);
+    } else {
+        if (!(p.x >= 0.0 && p.x <= box && p.y >= 0.0 && p.y <= box)) atomicOr(status, FMM_FLAG_OUT_OF_BOX);
+        double fx = floor(p.x * scale / box);
+        double fy = floor(p.y * scale / box);
+        int ix = fx < 0.0 ? 0 : (fx > (double)(side - 1) ? side - 1 : (int)fx);
+        int iy = fy < 0.0 ? 0 : (fy > (double)(side - 1) ? side - 1 : (int)fy);
+        key = fmm_morton((uint32_t)ix, (uint32_t)iy);
+    }
+    keys[i] = key;
+    rank[i] = atomicAdd(&counts[key], 1u);
+}
+
+// block-wide exclusive scan of kScanItems values per thread; returns the block total
+__device__ uint32_t block_exclusive_scan(uint32_t (&v)[kScanItems], uint32_t* warp_tot) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) { uint32_t t = v[j]; v[j] = s; s += t; }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (kScanThreads / 32) ? warp_tot[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < (kScanThreads / 32)) warp_tot[lane] = wi - w;   // exclusive warp offsets
+        if (lane == (kScanThreads / 32) - 1) warp_tot[kScanThreads / 32] = wi;
+    }
+    __syncthreads();
+    uint32_t base = warp_tot[warp] + inc - s;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) v[j] += base;
+    uint32_t total = warp_tot[kScanThreads / 32];
+    __syncthreads();
+    return total;
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, int64_t m, uint32_t* __restrict__ sums) {
+    __shared__ uint32_t wt[kScanThreads / 32 + 1];
+    uint32_t v[kScanItems];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) v[j] = (base + j < m) ? in[base + j] : 0u;
+    uint32_t tot = block_exclusive_scan(v, wt);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(uint32_t* __restrict__ sums, int nb) {
+    // one block of kScanThreads scans up to kScanTile block sums; larger counts loop in tiles
+    __shared__ uint32_t wt[kScanThreads / 32 + 1];
+    uint32_t carry = 0;
+    for (int t0 = 0; t0 < nb; t0 += kScanTile) {
+        uint32_t v[kScanItems];
+        int base = t0 + threadIdx.x * kScanItems;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) v[j] = (base + j < nb) ? sums[base + j] : 0u;
+        uint32_t tot = block_exclusive_scan(v, wt);
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j)
+            if (base + j < nb) sums[base + j] = v[j] + carry;
+        carry += tot;
+    }
+}
+
+__global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t m, const uint32_t* __restrict__ sums,
+                            uint32_t* __restrict__ out, uint32_t n_total) {
+    __shared__ uint32_t wt[kScanThreads / 32 + 1];
+    uint32_t v[kScanItems];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) v[j] = (base + j < m) ? in[base + j] : 0u;
+    block_exclusive_scan(v, wt);
+    uint32_t off = sums[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (base + j < m) out[base + j] = v[j] + off;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[m] = n_total;
+}
+
+template <bool kMixed>
+__global__ void k_scatter(const double2* __restrict__ xy, const double* __restrict__ q, int64_t n, int levels,
+                          double box, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank,
+                          const uint32_t* __restrict__ leaf_start, uint32_t* __restrict__ sorted_key,
+                          fmm_p64* __restrict__ s64, float4* __restrict__ s32) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t key = keys[i];
+    uint32_t pos = leaf_start[key] + rank[i];
+    double2 p = xy[i];
+    double qq = q[i];
+    sorted_key[pos] = key;
+    if (kMixed) {
+        // coordinates relative to the finest-square centre: FP32 keeps ~1e-7 of the square side
+        const double s = box / (double)(1 << levels);
+        double cx = ((double)fmm_compact2(key) + 0.5) * s;
+        double cy = ((double)fmm_compact2(key >> 1) + 0.5) * s;
+        s32[pos] = make_float4((float)(p.x - cx), (float)(p.y - cy), (float)qq, __int_as_float((int)i));
+    } else {
+        s64[pos] = fmm_p64{p.x, p.y, qq, (double)i};
+    }
+}
+
+}  // namespace
+
+int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
+    const int64_t n = pl->n;
+    const int64_t m = (int64_t)1 << (2 * pl->levels);
+    cudaStream_t st = pl->stream;
+    int launches = 0;
+    if (cudaMemsetAsync(pl->counts, 0, sizeof(uint32_t) * m, st) != cudaSuccess) return -1;
+    const int tb = 256;
+    const unsigned nblk = (unsigned)((n + tb - 1) / tb);
+    k_bin<<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, pl->box, pl->keys,
+                               pl->rank, pl->counts, pl->d_status);
+    ++launches;
+    const int nb = pl->scan_blocks;
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(pl->counts, m, pl->block_sums);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(pl->block_sums, nb);
+    k_scan_down<<<nb, kScanThreads, 0, st>>>(pl->counts, m, pl->block_sums, pl->leaf_start, (uint32_t)n);
+    launches += 3;
+    if (pl->precision == FMM_FP64)
+        k_scatter<false><<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, pl->box,
+                                              pl->keys, pl->rank, pl->leaf_start, pl->sorted_key, pl->sorted64,
+                                              pl->sorted32);
+    else
+        k_scatter<true><<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, pl->box,
+                                             pl->keys, pl->rank, pl->leaf_start, pl->sorted_key, pl->sorted64,
+                                             pl->sorted32);
+    ++launches;
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return launches;
+}
+
+int fmm_scan_blocks(int64_t m) { return (int)((m + kScanTile - 1) / kScanTile); }
