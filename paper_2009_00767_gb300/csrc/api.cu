@@ -76,6 +76,7 @@ void free_plan(fmm_plan_s* pl) {
     for (int k = 0; k <= FMM_MAX_LEVELS; ++k) {
         if (pl->grids.A[k]) cudaFree(pl->grids.A[k]);
         if (pl->grids.B[k]) cudaFree(pl->grids.B[k]);
+        if (pl->grids.B0[k]) cudaFree(pl->grids.B0[k]);
     }
     if (pl->h_status) cudaFreeHost(pl->h_status);
     if (pl->h_counters) cudaFreeHost(pl->h_counters);
@@ -170,12 +171,14 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     else
         FMM_TRY(dev_alloc(pl, &pl->sorted32, sizeof(float4) * n));
     FMM_TRY(dev_alloc(pl, &pl->phi_far, sizeof(double) * n));
-    const size_t cplx = precision == FMM_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t bcplx = precision == FMM_FP64 ? sizeof(double2) : sizeof(float2);
     for (int k = 2; k <= levels; ++k) {
         const size_t W = (size_t)fmm_grid_width(k);
-        pl->a_bytes[k] = W * W * p1 * cplx;
+        pl->a_bytes[k] = W * W * p1 * sizeof(double2);
         FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.A[k]), pl->a_bytes[k]));
-        FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.B[k]), ((size_t)1 << (2 * k)) * p1 * cplx));
+        FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.B[k]), ((size_t)1 << (2 * k)) * p1 * bcplx));
+        if (precision != FMM_FP64)
+            FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.B0[k]), ((size_t)1 << (2 * k)) * sizeof(double)));
     }
     std::vector<cd> T;
     build_operators(p, T);
@@ -183,8 +186,17 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     if (cudaMemcpy(pl->T64, T.data(), sizeof(double2) * T.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         FMM_TRY(FMM_ERR_CUDA);
     if (precision != FMM_FP64) {
-        std::vector<float2> T32(T.size());
-        for (size_t i = 0; i < T.size(); ++i) T32[i] = make_float2((float)T[i].real(), (float)T[i].imag());
+        pl->p1b = fmm_m2l_bucket(p1);
+        if (pl->p1b < 0) FMM_TRY(FMM_ERR_UNSUPPORTED);
+        const int pb = pl->p1b;
+        std::vector<float2> T32((size_t)49 * pb * pb, make_float2(0.f, 0.f));
+        for (int d = 0; d < 49; ++d)
+            for (int k = 0; k < p1; ++k)
+                for (int l = 0; l < p1; ++l) {
+                    if (k == 0 && l == 0) continue;   // the monopole-log term runs in FP64
+                    const cd v = T[((size_t)d * p1 + k) * p1 + l];
+                    T32[((size_t)d * pb + k) * pb + l] = make_float2((float)v.real(), (float)v.imag());
+                }
         FMM_TRY(dev_alloc(pl, &pl->T32, sizeof(float2) * T32.size()));
         if (cudaMemcpy(pl->T32, T32.data(), sizeof(float2) * T32.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             FMM_TRY(FMM_ERR_CUDA);

@@ -10,6 +10,7 @@
 //   A[k]  (k = 2..levels)    multipole moments of level k on a (2^k + 6)^2 grid with a 3-square
 //                            zero halo, row-major, p+1 complex coefficients per square
 //   B[k]                     local coefficients of level k, (2^k)^2 row-major, p+1 complex each
+//   B0[k]                    (mixed) Re b'_0 of each level-k square in FP64
 //   phi_far[n]               far field summed over levels, FP64, box-sorted order
 //   T64                      49 x (p+1) x (p+1) complex FP64 M2L operators, layout [d][k][l],
 //                            d = (dx + 3) + 7 (dy + 3), zero for the 9 adjacent offsets
@@ -37,8 +38,9 @@ struct __align__(32) fmm_p64 {
 #define FMM_FLAG_TIMEOUT 4u
 
 struct FmmLevelPtrs {
-    void* A[FMM_MAX_LEVELS + 1];
-    void* B[FMM_MAX_LEVELS + 1];
+    void* A[FMM_MAX_LEVELS + 1];    // FP64 moments (both paths), double2 [cell][p+1]
+    void* B[FMM_MAX_LEVELS + 1];    // local coefficients: double2 (FP64 path) or float2 (mixed)
+    void* B0[FMM_MAX_LEVELS + 1];   // mixed path: Re b'_0 in FP64, one per square
 };
 
 struct fmm_plan_s {
@@ -63,7 +65,8 @@ struct fmm_plan_s {
     double* phi_far;
 
     double2* T64;       // FP64 operators [49][p+1][p+1]
-    float2* T32;        // FP32 copy of T64 (mixed SIMT M2L)
+    float2* T32;        // FP32 operators [49][p1b][p1b], zero-padded, [d][0][0] = 0 (mixed SIMT M2L)
+    int p1b;            // padded coefficient count of the FP32 M2L kernel instance
 
     unsigned int* d_status;
     unsigned long long* d_counters;   // [0] = near-field pairs, [1] = max leaf population
@@ -109,5 +112,6 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q);
 int fmm_scan_blocks(int64_t m);
 int fmm_launch_fp64(fmm_plan_s* pl, double* phi);
 int fmm_launch_mixed(fmm_plan_s* pl, double* phi);
+int fmm_m2l_bucket(int p1);
 int fmm_launch_direct_f64(int64_t n, const double* xy, const double* q, int64_t nt, const int64_t* targets,
                           double* phi_t, cudaStream_t stream);

@@ -1,0 +1,60 @@
+"""Accuracy of the mixed-precision CUDA path against the FP64 CPU oracle (through the C ABI).
+
+The mixed path rounds the particle stages and M2L to FP32, so it is not
+bit-comparable with FP64: each case states its relative L2 error against the
+oracle's shift-free FMM at the same (levels, p), and the bar is 1e-6, the
+accuracy at which the benchmark's throughput is quoted.
+"""
+import numpy as np
+import pytest
+
+from conftest import rel_l2
+from paper_2009_00767_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("case", [
+    (4096, 4, 16, "uniform", 0),
+    (1000, 3, 8, "uniform", 1),
+    (20000, 6, 12, "gmm", 3),
+    (5000, 2, 30, "annulus", 4),
+    (33, 4, 40, "uniform", 5),
+    (100000, 7, 20, "uniform", 6),
+])
+def test_mixed_fp32_matches_oracle(oracle_mod, case):
+    from gpu_util import run_fmm
+    n, lev, p, fam, seed = case
+    xy, q = getattr(inputs, fam)(n, inputs.config_seed(0, 200 + seed))
+    phi, st = run_fmm(xy, q, lev, p, precision="fp32")
+    ref = oracle_mod.shiftfree(xy, q, lev, p)
+    err = rel_l2(phi, ref)
+    print(f"mixed fp32 N={n} levels={lev} p={p} {fam}: rel L2 vs oracle {err:.3e}")
+    assert err < MIXED_TOL
+
+
+def test_mixed_levels_0_1(oracle_mod):
+    from gpu_util import run_fmm
+    xy, q = inputs.uniform(700, 91)
+    for lev in (0, 1):
+        phi, _ = run_fmm(xy, q, lev, 6, precision="fp32")
+        assert rel_l2(phi, oracle_mod.direct(xy, q)) < MIXED_TOL
+
+
+def test_mixed_full_size_uniform_1m(oracle_mod):
+    """N = 1,048,576 uniform, levels 8, p = 20: every element against the oracle, error stated."""
+    from gpu_util import run_fmm
+    xy, q = inputs.uniform(1 << 20, inputs.config_seed(1))
+    phi, st = run_fmm(xy, q, 8, 20, precision="fp32")
+    ref = oracle_mod.shiftfree(xy, q, 8, 20)
+    err = rel_l2(phi, ref)
+    print(f"mixed fp32 N=2^20 levels=8 p=20: rel L2 vs oracle {err:.3e}")
+    assert err < MIXED_TOL
