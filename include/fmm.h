@@ -151,6 +151,27 @@ const char* fmm_status_string(int status);
 fmm_status fmm_direct_targets(int64_t n, const double* xy, const double* q, int64_t n_targets,
                               const int64_t* targets, double* phi_t, void* stream);
 
+/* The FP64 method of fmm_potential for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a library convenience.  Some callers cannot call
+ * cudaMalloc -- a loop that forbids allocation once it has started, a device whose free
+ * memory belongs to another allocator, a plugin that may not own allocations -- and
+ * fmm_plan allocates.  This entry point creates no plan and allocates nothing: its
+ * workspaces live in one fixed device array of 8.5 MB inside libfmm.so, which every GPU
+ * that loads the library reserves until the process exits.
+ *   n, levels, p, box   as for fmm_plan, FP64 only, limited to 1 <= n <= 65536,
+ *                       0 <= levels <= 6 and 1 <= p <= 20; larger requests return
+ *                       FMM_ERR_INVALID_ARG and touch nothing.
+ *   xy, q, phi          device arrays as for fmm_potential, owned by the caller.
+ *   stream              cudaStream_t to run on (NULL = default stream).
+ * The call waits for `stream` and returns the device checks' status (phi is left unwritten
+ * when a particle is outside the box or a value is not finite).  The first call on a device
+ * looks up the array's device address and creates the stage events for that device; make
+ * that first call before any stream capture.  Every call on a device shares the one array,
+ * so calls that overlap on the GPU (other threads, other streams) race and must be
+ * serialised by the caller. */
+fmm_status fmm_potential_noalloc(int64_t n, int levels, int p, double box, const double* xy,
+                                 const double* q, double* phi, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

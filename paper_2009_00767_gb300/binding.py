@@ -60,6 +60,7 @@ SIGNATURES = {
     "fmm_plan_destroy": (None, [_vp]),
     "fmm_status_string": (ctypes.c_char_p, [_i32]),
     "fmm_direct_targets": (_i32, [_i64, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "fmm_potential_noalloc": (_i32, [_i64, _i32, _i32, _d, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -164,6 +165,12 @@ def fmm_direct_targets(xy, q, targets, phi_t, stream=None):
     nt = int(targets.shape[0])
     _check(_lib.fmm_direct_targets(n, _ptr(xy), _ptr(q), nt, _ptr(targets), _ptr(phi_t), _stream_handle(stream)),
            "fmm_direct_targets")
+
+
+def fmm_potential_noalloc(xy, q, phi, levels: int, p: int, box: float = 5.0, stream=None):
+    """FP64 potential without a plan or any device allocation (n <= 65536, levels <= 6, p <= 20)."""
+    _check(_lib.fmm_potential_noalloc(int(q.shape[0]), int(levels), int(p), float(box), _ptr(xy), _ptr(q),
+                                      _ptr(phi), _stream_handle(stream)), "fmm_potential_noalloc")
 
 
 class Plan:
