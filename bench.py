@@ -107,6 +107,16 @@ def roofline_for(stage, stats, ms, w, peaks, sm_clock_mhz, precision, traffic):
     n = w["n"]
     if stage == "m2l":
         flops = m2l_pairs(w["levels"]) * 8 * p1 * p1
+        if precision in ("tf32", "3xtf32"):
+            # the stage runs levels >= 8 on the tensor cores and the coarser ones on the CUDA cores;
+            # algorithmic flops of all levels over the stage time, against the TF32 tensor peak
+            # (measured dense bf16 x the nominal TF32/BF16 ratio of 1/2)
+            peak = peaks.get("bf16_tflops", 1939.8) / 2.0
+            ach = flops / (ms * 1e-3) / 1e12
+            return {"kernel": "m2l", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": traffic,
+                    "peak_basis": "measured bf16 dense (MEASURED_PEAKS.json) x 1/2 for TF32",
+                    "work_per_launch": f"{flops:.4g} flop = IL pairs x 8 (p+1)^2 (split products not counted)"}
         if precision in ("fp32", "fp64"):
             lanes = FP32_LANES_PER_SM if precision == "fp32" else None
             if lanes is None:

@@ -6,7 +6,7 @@
 #include <new>
 #include <vector>
 
-#include "fmm_internal.cuh"
+#include "mixed_common.cuh"
 
 namespace {
 
@@ -76,8 +76,9 @@ void free_plan(fmm_plan_s* pl) {
     for (int k = 0; k <= FMM_MAX_LEVELS; ++k) {
         if (pl->grids.A[k]) cudaFree(pl->grids.A[k]);
         if (pl->grids.B[k]) cudaFree(pl->grids.B[k]);
-        if (pl->grids.B0[k]) cudaFree(pl->grids.B0[k]);
+        if (pl->grids.A32[k]) cudaFree(pl->grids.A32[k]);
     }
+    fmm_tc_destroy(pl);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     if (pl->h_counters) cudaFreeHost(pl->h_counters);
     for (int e = 0; e < 6; ++e)
@@ -101,7 +102,8 @@ struct DeviceGuard {
 
 fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* phi) {
     cudaStream_t st = pl->stream;
-    if (cudaMemsetAsync(pl->d_counters, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (cudaMemsetAsync(pl->d_counters, 0, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long), st) != cudaSuccess)
+        return FMM_ERR_CUDA;
     cudaEventRecord(pl->ev[0], st);
     int launches = fmm_launch_sort(pl, xy, q);
     if (launches < 0) return FMM_ERR_CUDA;
@@ -178,13 +180,24 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
         FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.A[k]), pl->a_bytes[k]));
         FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.B[k]), ((size_t)1 << (2 * k)) * p1 * bcplx));
         if (precision != FMM_FP64)
-            FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.B0[k]), ((size_t)1 << (2 * k)) * sizeof(double)));
+            FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.A32[k]), W * W * p1 * sizeof(float2)));
     }
     std::vector<cd> T;
     build_operators(p, T);
     FMM_TRY(dev_alloc(pl, &pl->T64, sizeof(double2) * T.size()));
     if (cudaMemcpy(pl->T64, T.data(), sizeof(double2) * T.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         FMM_TRY(FMM_ERR_CUDA);
+    if (precision == FMM_MIXED_BF16 || precision == FMM_MIXED_BF16X3) FMM_TRY(FMM_ERR_UNSUPPORTED);
+    if (precision == FMM_MIXED_TF32 || precision == FMM_MIXED_3XTF32) {
+        std::vector<double> tre(T.size()), tim(T.size());
+        for (size_t i = 0; i < T.size(); ++i) {
+            tre[i] = T[i].real();
+            tim[i] = T[i].imag();
+        }
+        const int r = fmm_tc_create(pl, tre, tim);
+        if (r == -2) FMM_TRY(FMM_ERR_UNSUPPORTED);
+        if (r < 0) FMM_TRY(FMM_ERR_CUDA);
+    }
     if (precision != FMM_FP64) {
         pl->p1b = fmm_m2l_bucket(p1);
         if (pl->p1b < 0) FMM_TRY(FMM_ERR_UNSUPPORTED);
@@ -202,11 +215,12 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
             FMM_TRY(FMM_ERR_CUDA);
     }
     FMM_TRY(dev_alloc(pl, &pl->d_status, sizeof(unsigned int)));
-    FMM_TRY(dev_alloc(pl, &pl->d_counters, 2 * sizeof(unsigned long long)));
+    FMM_TRY(dev_alloc(pl, &pl->d_counters, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long)));
     if (cudaMemset(pl->d_status, 0, sizeof(unsigned int)) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
     if (cudaMallocHost(reinterpret_cast<void**>(&pl->h_status), sizeof(unsigned int)) != cudaSuccess)
         FMM_TRY(FMM_ERR_OOM);
-    if (cudaMallocHost(reinterpret_cast<void**>(&pl->h_counters), 2 * sizeof(unsigned long long)) != cudaSuccess)
+    if (cudaMallocHost(reinterpret_cast<void**>(&pl->h_counters), 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long)) !=
+        cudaSuccess)
         FMM_TRY(FMM_ERR_OOM);
     FMM_TRY(dev_alloc(pl, &pl->d_xy_stage, sizeof(double) * 2 * n));
     FMM_TRY(dev_alloc(pl, &pl->d_q_stage, sizeof(double) * n));
@@ -257,8 +271,8 @@ fmm_status fmm_sync(fmm_plan_t plan) {
     cudaStream_t st = plan->stream;
     if (cudaMemcpyAsync(plan->h_status, plan->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
-        cudaMemcpyAsync(plan->h_counters, plan->d_counters, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                        st) != cudaSuccess ||
+        cudaMemcpyAsync(plan->h_counters, plan->d_counters, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemsetAsync(plan->d_status, 0, sizeof(unsigned int), st) != cudaSuccess)
         return FMM_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
@@ -273,8 +287,13 @@ fmm_status fmm_sync(fmm_plan_t plan) {
         plan->last.ms_l2p = ms[3];
         plan->last.ms_p2p = ms[4];
         plan->last.ms_total = tot;
-        plan->last.p2p_pairs = (int64_t)plan->h_counters[0];
-        plan->last.max_leaf = (int64_t)plan->h_counters[1];
+        unsigned long long pairs = 0, mx = 0;
+        for (int c = 0; c < FMM_COUNTER_SLOTS; ++c) {
+            pairs += plan->h_counters[c];
+            mx = plan->h_counters[FMM_COUNTER_SLOTS + c] > mx ? plan->h_counters[FMM_COUNTER_SLOTS + c] : mx;
+        }
+        plan->last.p2p_pairs = (int64_t)pairs;
+        plan->last.max_leaf = (int64_t)mx;
         plan->last.kernel_launches = plan->launches;
         plan->events_recorded = 0;
     }

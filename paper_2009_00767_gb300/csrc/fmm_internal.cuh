@@ -10,7 +10,8 @@
 //   A[k]  (k = 2..levels)    multipole moments of level k on a (2^k + 6)^2 grid with a 3-square
 //                            zero halo, row-major, p+1 complex coefficients per square
 //   B[k]                     local coefficients of level k, (2^k)^2 row-major, p+1 complex each
-//   B0[k]                    (mixed) Re b'_0 of each level-k square in FP64
+//   A32[k]                   (mixed) FP32 copy of A[k]; slot 0 holds M_0 as a float-float pair
+//   (mixed) B[k] slot 0 holds Re b'_0 as a float-float pair; phi_far holds float-float pairs
 //   phi_far[n]               far field summed over levels, FP64, box-sorted order
 //   T64                      49 x (p+1) x (p+1) complex FP64 M2L operators, layout [d][k][l],
 //                            d = (dx + 3) + 7 (dy + 3), zero for the 9 adjacent offsets
@@ -37,11 +38,45 @@ struct __align__(32) fmm_p64 {
 #define FMM_FLAG_NONFINITE 2u
 #define FMM_FLAG_TIMEOUT 4u
 
+// Near-field statistics are spread over this many counter slots (one update per CTA each) so
+// that no single L2 address serialises the updates.
+#define FMM_COUNTER_SLOTS 64
+
+// Conversions between FP32 and FP64 by integer bit operations, so that they do not occupy
+// GB300's narrow FP64 pipe.  Zero, subnormal and out-of-range inputs flush to zero (their
+// magnitudes are below 2^-126, far under the rounding of the results they feed).
+__device__ __forceinline__ double fmm_f2d_bits(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return 0.0;
+    const uint32_t m = u & 0x7fffffu;
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)((m & 7u) << 29));
+}
+// double -> (hi, lo) float pair with hi = the double truncated to 24 bits and lo the rest
+// (rounded to FP32); hi + lo carries about 48 bits of the double.
+__device__ __forceinline__ float2 fmm_d2ff_bits(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    if (e <= 896 || e >= 1151) return make_float2(0.f, 0.f);
+    const uint32_t sign = (uint32_t)(b >> 63) << 31;
+    const unsigned long long m = b & 0xfffffffffffffull;
+    const float hi = __uint_as_float(sign | ((uint32_t)(e - 896) << 23) | (uint32_t)(m >> 29));
+    float lo = 0.f;
+    if (e > 948) {   // 2^(e - 1075) is a normal float
+        lo = (float)(uint32_t)(m & 0x1fffffffu) * __uint_as_float((uint32_t)(e - 948) << 23);
+        if (sign) lo = -lo;
+    }
+    return make_float2(hi, lo);
+}
+
 struct FmmLevelPtrs {
     void* A[FMM_MAX_LEVELS + 1];    // FP64 moments (both paths), double2 [cell][p+1]
     void* B[FMM_MAX_LEVELS + 1];    // local coefficients: double2 (FP64 path) or float2 (mixed)
-    void* B0[FMM_MAX_LEVELS + 1];   // mixed path: Re b'_0 in FP64, one per square
+    void* A32[FMM_MAX_LEVELS + 1];  // mixed path: float2 copy of A, coefficient 0 as (hi, lo) of M_0
 };
+
+struct FmmTc;   // tensor-core M2L state (m2l_tc.cu)
 
 struct fmm_plan_s {
     int device;
@@ -67,11 +102,12 @@ struct fmm_plan_s {
     double2* T64;       // FP64 operators [49][p+1][p+1]
     float2* T32;        // FP32 operators [49][p1b][p1b], zero-padded, [d][0][0] = 0 (mixed SIMT M2L)
     int p1b;            // padded coefficient count of the FP32 M2L kernel instance
+    FmmTc* tc;          // tensor-core M2L state (TF32 modes), or null
 
     unsigned int* d_status;
-    unsigned long long* d_counters;   // [0] = near-field pairs, [1] = max leaf population
+    unsigned long long* d_counters;   // [0..63] near-field pair partials, [64..127] max leaf population
     unsigned int* h_status;           // pinned
-    unsigned long long* h_counters;   // pinned [2]
+    unsigned long long* h_counters;   // pinned [128]
 
     double* d_xy_stage;
     double* d_q_stage;

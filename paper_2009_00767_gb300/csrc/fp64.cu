@@ -190,8 +190,9 @@ k_p2p_f64(const fmm_p64* __restrict__ sp, const uint32_t* __restrict__ leaf_star
             ++nn;
         }
     if (lane == 0) {
-        atomicAdd(&counters[0], (unsigned long long)T * nsrc - (unsigned long long)T);
-        atomicMax(&counters[1], (unsigned long long)T);
+        const unsigned slot = blockIdx.x % FMM_COUNTER_SLOTS;
+        atomicAdd(&counters[slot], (unsigned long long)T * nsrc - (unsigned long long)T);
+        atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)T);
     }
     int tp = 1;
     while (tp < T && tp < 32) tp <<= 1;

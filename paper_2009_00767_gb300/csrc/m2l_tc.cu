@@ -1,0 +1,503 @@
+// m2l_tc.cu -- M2L (D-bar-1 of Sec. 2.2.1) on the 5th-generation tensor cores (tcgen05) for the
+// finest levels, in TF32 or in split 3xTF32 with FP32 accumulation in tensor memory.
+//
+// For one level k and one parity class c = (px, py) of target squares, the conversion of the
+// interaction list is a real GEMM
+//     D[t][n] = sum_d sum_kk  S[t + d][kk] * Op_d[n][kk]
+// with t the targets (M = 128 consecutive targets of one row of the class's sub-grid), n the
+// outputs (N = 2H: Re b'_0..b'_p then Im b'_0..b'_p, each padded to H) and kk the inputs
+// (K = 2H per offset: Re M_0..M_p then Im M_0..M_p).  The 27 offsets of the class fall into 12
+// groups that share one source window: the source parity (qx, qy) and the source row shift sy.
+// One TMA load brings a window of 130 source cells (128 targets plus one on each side) into
+// shared memory in the canonical no-swizzle K-major layout (16-byte core-matrix rows, K-chunk
+// stride LBO = 130 x 16 B); the three column shifts of a group are then the same window read
+// from a descriptor start moved by 16 B per cell.  The operators of a group arrive by one bulk
+// copy.  A single thread issues the MMAs; the accumulator lives in tensor memory and the
+// epilogue reads it back with tcgen05.ld.
+//
+// 3xTF32 (Ootomo & Yokota, 2022): x = x_hi + x_lo with x_hi rounded to TF32, and
+// D += A_hi B_hi + A_hi B_lo + A_lo B_hi, dropping A_lo B_lo, recovers about FP32 accuracy.
+//
+// The monopole-log term of b'_0, sum_d M_0 (log|w0| + ln s), is not in the GEMM: the epilogue
+// sums it in float-float from the FP32 moment grid.  Every wait on an mbarrier is bounded and
+// sets a status flag when it runs out.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <vector>
+
+#include "mixed_common.cuh"
+
+namespace {
+
+constexpr int kTile = 128;        // targets per tile (MMA M)
+constexpr int kWin = kTile + 2;   // source cells per window
+constexpr int kThreads = 128;
+constexpr int kMinLevel = 8;      // sub-grid rows of at least 128 targets
+constexpr unsigned kSpin = 1u << 24;
+
+struct TcGroup {
+    int qx, qy, sy, nops, slot0;
+    int sx[3];
+    int d[3];
+};
+
+struct TcArgs {
+    CUtensorMap tmap[2][FMM_MAX_LEVELS + 1];   // [part][level]
+    const float* ops[2];                       // [part] -> [class][27 slots][KC][N][4]
+    const float2* a32[FMM_MAX_LEVELS + 1];     // FP32 moment grids (3-cell halo) for the monopole term
+    float2* B[FMM_MAX_LEVELS + 1];
+    TcGroup groups[4][12];
+    float2 logc[FMM_MAX_LEVELS + 1][49];
+    int cta_base[FMM_MAX_LEVELS + 2];
+    int levels, p;
+    unsigned int* status;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
+    for (unsigned it = 0; it < kSpin; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, P;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major core matrices (8 rows x 16 B).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int KC, int NP, int NS>
+__global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ TcArgs a) {
+    constexpr int N = 4 * KC, H = 2 * KC;
+    constexpr uint32_t A_BYTES = KC * kWin * 16;
+    constexpr uint32_t OP_BYTES = KC * N * 16;
+    constexpr uint32_t STAGE = NP * (A_BYTES + 3 * OP_BYTES);
+    constexpr uint32_t TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * STAGE);   // full[NS], empty[NS], done
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * NS + 1);
+
+    // ---- which tile
+    const int cta = blockIdx.x;
+    int k = kMinLevel;
+    while (cta >= a.cta_base[k + 1]) ++k;
+    const int w2 = 1 << (k - 1);
+    const int tiles_per_row = w2 / kTile;
+    const int per_class = w2 * tiles_per_row;
+    const int rel = cta - a.cta_base[k];
+    const int cls = rel / per_class;
+    const int rr = rel - cls * per_class;
+    const int y = rr / tiles_per_row;
+    const int u0 = (rr - y * tiles_per_row) * kTile;
+    const int px = cls & 1, py = cls >> 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2 * NS + 1; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[b])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+
+    // ---- producer + MMA issuer: one thread
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        for (int g = 0; g < 12 && ok; ++g) {
+            const int s = g % NS, use = g / NS;
+            const TcGroup& G = a.groups[cls][g];
+            const uint32_t full = su32(&bars[s]), empty = su32(&bars[NS + s]);
+            if (g >= NS) ok = wait_bar(empty, (uint32_t)((use - 1) & 1));
+            if (!ok) break;
+            const uint32_t bytes = NP * (A_BYTES + (uint32_t)G.nops * OP_BYTES);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(bytes) : "memory");
+            const int q = G.qx + 2 * G.qy;
+            for (int part = 0; part < NP; ++part) {
+                const uint32_t dstA = su32(smem + s * STAGE + part * A_BYTES);
+                asm volatile(
+                    "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dstA),
+                    "l"(reinterpret_cast<uint64_t>(&a.tmap[part][k])), "r"(0), "r"(u0 - 1), "r"(y + G.sy), "r"(0),
+                    "r"(q), "r"(full)
+                    : "memory");
+                const uint32_t dstB = su32(smem + s * STAGE + NP * A_BYTES + part * 3 * OP_BYTES);
+                const float* srcB = a.ops[part] + ((size_t)cls * 27 + G.slot0) * (OP_BYTES / 4);
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        dstB),
+                    "l"(srcB), "r"((uint32_t)G.nops * OP_BYTES), "r"(full)
+                    : "memory");
+            }
+            ok = wait_bar(full, (uint32_t)(use & 1));
+            if (!ok) {
+                wait_bar(full, (uint32_t)(use & 1));   // give copies still in flight a second bounded wait
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t aBase = su32(smem + s * STAGE);
+            const uint32_t bBase = su32(smem + s * STAGE + NP * A_BYTES);
+            for (int o = 0; o < G.nops; ++o) {
+                const uint32_t aoff = (uint32_t)(1 + G.sx[o]) * 16u;
+#pragma unroll
+                for (int ks = 0; ks < KC / 2; ++ks) {
+                    const uint32_t acc = (g | o | ks) != 0;
+                    const uint64_t ah = smem_desc(aBase + aoff + ks * 2 * (kWin * 16), kWin * 16, 128);
+                    const uint64_t bh = smem_desc(bBase + o * OP_BYTES + ks * 2 * (N * 16), N * 16, 128);
+                    mma_tf32(tmem, ah, bh, IDESC, acc);
+                    if (NP == 2) {
+                        const uint64_t al =
+                            smem_desc(aBase + A_BYTES + aoff + ks * 2 * (kWin * 16), kWin * 16, 128);
+                        const uint64_t bl = smem_desc(bBase + 3 * OP_BYTES + o * OP_BYTES + ks * 2 * (N * 16),
+                                                      N * 16, 128);
+                        mma_tf32(tmem, ah, bl, IDESC, 1u);
+                        mma_tf32(tmem, al, bh, IDESC, 1u);
+                    }
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty)
+                         : "memory");
+        }
+        // the final commit tracks every MMA issued above
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         su32(&bars[2 * NS]))
+                     : "memory");
+        if (!ok) atomicOr(a.status, FMM_FLAG_TIMEOUT);
+    }
+    __syncwarp();
+    const bool done = wait_bar(su32(&bars[2 * NS]), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // ---- epilogue: warp w reads accumulator rows (targets) 32w..32w+31
+    float v[N];
+#pragma unroll
+    for (int c = 0; c < N; c += 16) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v + c);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (done) {
+        const int i = 32 * warp + lane;
+        const int tx = 2 * (u0 + i) + px, ty = 2 * y + py;
+        const int W = fmm_grid_width(k), p1 = a.p + 1;
+        const float2* A32 = a.a32[k];
+        float2 mono = make_float2(0.f, 0.f);
+        for (int dy = -2 - py; dy <= 3 - py; ++dy)
+            for (int dx = -2 - px; dx <= 3 - px; ++dx) {
+                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+                const float2 m0 = A32[((size_t)(ty + dy + FMM_HALO) * W + (tx + dx + FMM_HALO)) * p1];
+                mono = ff_add(mono, ff_mul(m0, a.logc[k][(dx + 3) + 7 * (dy + 3)]));
+            }
+        float2* B = a.B[k] + ((size_t)ty * (1u << k) + tx) * p1;
+        B[0] = ff_add_f(mono, v[0]);
+#pragma unroll
+        for (int l = 1; l < H; ++l)
+            if (l < p1) B[l] = make_float2(v[l], v[H + l]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// FP32 moment grid (3-cell halo) -> the GEMM's source layout, one thread per cell of a parity
+// sub-grid: out[part][q][KC][w2][w2][4] with the K index Re M_0..M_p, pad, Im M_0..M_p, pad.
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int KC, int NP>
+__global__ void k_prep_tc(const float2* __restrict__ a32, int k, int p1, float4* __restrict__ hi,
+                          float4* __restrict__ lo) {
+    constexpr int H = 2 * KC;
+    const int w2 = 1 << (k - 1);
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 4ll * w2 * w2) return;
+    const int col = (int)(e % w2), row = (int)((e / w2) % w2), q = (int)(e / ((int64_t)w2 * w2));
+    const int x = 2 * col + (q & 1), y = 2 * row + (q >> 1);
+    const int W = fmm_grid_width(k);
+    const float2* src = a32 + ((size_t)(y + FMM_HALO) * W + (x + FMM_HALO)) * p1;
+    float vals[2 * H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const float2 m = (j < p1) ? src[j] : make_float2(0.f, 0.f);
+        vals[j] = m.x;                     // coefficient 0 holds M_0's high word: M_0 is real
+        vals[H + j] = (j == 0) ? 0.f : m.y;
+    }
+    const size_t plane = (size_t)w2 * w2;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+        float h[4], l[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float v = vals[4 * c + t];
+            h[t] = tf32_rna(v);
+            l[t] = v - h[t];
+        }
+        const size_t off = ((size_t)q * KC + c) * plane + (size_t)row * w2 + col;
+        hi[off] = make_float4(h[0], h[1], h[2], h[3]);
+        if (NP == 2) lo[off] = make_float4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// host-side round to nearest TF32 (ties away), the rounding cvt.rna.tf32.f32 does on the device
+float host_tf32(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x;
+    u = (u + 0x1000u) & 0xffffe000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+template <int KC, int NP>
+size_t smem_bytes() {
+    constexpr int N = 4 * KC;
+    constexpr size_t stage = (size_t)NP * (KC * kWin * 16 + 3 * KC * N * 16);
+    const int ns = (2 * stage + 1024 + 256 <= 227 * 1024) ? 2 : 1;
+    return ns * stage + 1024 + 256;
+}
+
+template <int KC, int NP>
+int stages() {
+    constexpr int N = 4 * KC;
+    constexpr size_t stage = (size_t)NP * (KC * kWin * 16 + 3 * KC * N * 16);
+    return (2 * stage + 1024 + 256 <= 227 * 1024) ? 2 : 1;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- plan-side state
+struct FmmTc {
+    int kc, np;
+    float* ops[2];
+    float4* src[2][FMM_MAX_LEVELS + 1];
+    TcArgs args;   // tensor maps and tables, filled at plan time
+};
+
+int fmm_tc_kmin() { return kMinLevel; }
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+// Allocate and build the tensor-core M2L state.  Returns 0, or a negative value on failure
+// (-1 CUDA error, -2 unsupported p).
+int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vector<double>& Tim) {
+    const int p1 = pl->p + 1;
+    const int H = ((p1 + 7) / 8) * 8;
+    const int kc = H / 2;
+    if (kc != 4 && kc != 8 && kc != 12 && kc != 16) return -2;
+    const int np = pl->precision == FMM_MIXED_3XTF32 ? 2 : 1;
+    FmmTc* tc = new FmmTc();
+    memset(tc, 0, sizeof(FmmTc));
+    tc->kc = kc;
+    tc->np = np;
+    pl->tc = tc;
+    const int N = 4 * kc, K = 4 * kc;
+
+    // class tables: 12 groups (source parity qx, qy and row shift sy) of 1..3 offsets each
+    int slots[4] = {0, 0, 0, 0};
+    for (int cls = 0; cls < 4; ++cls) {
+        const int px = cls & 1, py = cls >> 1;
+        int g = 0;
+        for (int qy = 0; qy < 2; ++qy)
+            for (int qx = 0; qx < 2; ++qx)
+                for (int sy = -1; sy <= 1; ++sy, ++g) {
+                    TcGroup& G = tc->args.groups[cls][g];
+                    G.qx = qx;
+                    G.qy = qy;
+                    G.sy = sy;
+                    G.nops = 0;
+                    G.slot0 = slots[cls];
+                    const int dy = 2 * sy + qy - py;
+                    for (int sx = -1; sx <= 1; ++sx) {
+                        const int dx = 2 * sx + qx - px;
+                        if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+                        G.sx[G.nops] = sx;
+                        G.d[G.nops] = (dx + 3) + 7 * (dy + 3);
+                        ++G.nops;
+                    }
+                    slots[cls] += G.nops;
+                }
+        if (slots[cls] != 27) return -1;
+    }
+    // operators, real block form, [part][class][slot][KC][N][4]
+    const size_t opsz = (size_t)4 * 27 * kc * N * 4;
+    std::vector<float> hostops[2];
+    for (int part = 0; part < np; ++part) hostops[part].assign(opsz, 0.f);
+    for (int cls = 0; cls < 4; ++cls)
+        for (int g = 0; g < 12; ++g) {
+            const TcGroup& G = tc->args.groups[cls][g];
+            for (int o = 0; o < G.nops; ++o) {
+                const int d = G.d[o];
+                const size_t base = ((size_t)cls * 27 + G.slot0 + o) * kc * N * 4;
+                for (int n = 0; n < N; ++n)
+                    for (int kk = 0; kk < K; ++kk) {
+                        // input kk: Re M_j (kk < H) or Im M_j; output n: Re b_l (n < H) or Im b_l
+                        const int j = kk < H ? kk : kk - H, l = n < H ? n : n - H;
+                        double val = 0.0;
+                        if (j < p1 && l < p1 && !(j == 0 && l == 0)) {
+                            const double tr = Tre[((size_t)d * p1 + j) * p1 + l];
+                            const double ti = Tim[((size_t)d * p1 + j) * p1 + l];
+                            if (n < H && kk < H) val = tr;
+                            else if (n < H) val = -ti;
+                            else if (kk < H) val = ti;
+                            else val = tr;
+                        }
+                        const float v = (float)val;
+                        const float h = host_tf32(v);
+                        const size_t at = base + ((size_t)(kk / 4) * N + n) * 4 + (kk % 4);
+                        hostops[0][at] = h;
+                        if (np == 2) hostops[1][at] = v - h;
+                    }
+            }
+        }
+    for (int part = 0; part < np; ++part) {
+        if (cudaMalloc(&tc->ops[part], opsz * 4) != cudaSuccess) return -1;
+        pl->workspace_bytes += opsz * 4;
+        if (cudaMemcpy(tc->ops[part], hostops[part].data(), opsz * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return -1;
+        tc->args.ops[part] = tc->ops[part];
+    }
+    // source buffers and their tensor maps, levels kMinLevel..L
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encoder();
+    if (!enc) return -1;
+    for (int k = kMinLevel; k <= pl->levels; ++k) {
+        const uint64_t w2 = 1ull << (k - 1);
+        const size_t bytes = (size_t)4 * kc * w2 * w2 * 16;
+        for (int part = 0; part < np; ++part) {
+            if (cudaMalloc(&tc->src[part][k], bytes) != cudaSuccess) return -1;
+            pl->workspace_bytes += bytes;
+            cuuint64_t dims[5] = {4, w2, w2, (cuuint64_t)kc, 4};
+            cuuint64_t strides[4] = {16, 16 * w2, 16 * w2 * w2, 16 * w2 * w2 * (cuuint64_t)kc};
+            cuuint32_t box[5] = {4, (cuuint32_t)kWin, 1, (cuuint32_t)kc, 1};
+            cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+            if (enc(&tc->args.tmap[part][k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, tc->src[part][k], dims, strides, box,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return -1;
+        }
+    }
+    return 0;
+}
+
+void fmm_tc_destroy(fmm_plan_s* pl) {
+    FmmTc* tc = pl->tc;
+    if (!tc) return;
+    for (int part = 0; part < 2; ++part) {
+        if (tc->ops[part]) cudaFree(tc->ops[part]);
+        for (int k = 0; k <= FMM_MAX_LEVELS; ++k)
+            if (tc->src[part][k]) cudaFree(tc->src[part][k]);
+    }
+    delete tc;
+    pl->tc = nullptr;
+}
+
+template <int KC, int NP>
+static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
+    FmmTc* tc = pl->tc;
+    cudaStream_t st = pl->stream;
+    const int L = pl->levels, p1 = pl->p + 1;
+    int launches = 0;
+    for (int k = kMinLevel; k <= L; ++k) {
+        const int64_t cells = 4ll << (2 * (k - 1));
+        k_prep_tc<KC, NP><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(
+            reinterpret_cast<const float2*>(pl->grids.A32[k]), k, p1, tc->src[0][k], tc->src[1][k]);
+        ++launches;
+    }
+    TcArgs& a = tc->args;
+    for (int k = 0; k <= FMM_MAX_LEVELS; ++k) {
+        a.a32[k] = reinterpret_cast<const float2*>(pl->grids.A32[k]);
+        a.B[k] = reinterpret_cast<float2*>(pl->grids.B[k]);
+    }
+    memcpy(a.logc, lv.logc, sizeof(a.logc));
+    a.levels = L;
+    a.p = pl->p;
+    a.status = pl->d_status;
+    int acc = 0;
+    for (int k = 0; k <= FMM_MAX_LEVELS + 1; ++k) a.cta_base[k] = 0;
+    for (int k = kMinLevel; k <= L; ++k) {
+        a.cta_base[k] = acc;
+        const int w2 = 1 << (k - 1);
+        acc += 4 * w2 * (w2 / kTile);
+    }
+    for (int k = L + 1; k <= FMM_MAX_LEVELS + 1; ++k) a.cta_base[k] = acc;
+    const size_t shm = smem_bytes<KC, NP>();
+    if (stages<KC, NP>() == 2) {
+        auto kern = k_m2l_tc<KC, NP, 2>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
+        kern<<<acc, kThreads, shm, st>>>(a);
+    } else {
+        auto kern = k_m2l_tc<KC, NP, 1>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
+        kern<<<acc, kThreads, shm, st>>>(a);
+    }
+    ++launches;
+    return launches;
+}
+
+// Launch prep + tensor-core M2L for levels kMinLevel..L; returns kernels launched or -1.
+int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv) {
+    const FmmTc* tc = pl->tc;
+    if (!tc || pl->levels < kMinLevel) return 0;
+    const bool x3 = tc->np == 2;
+    switch (tc->kc) {
+        case 4: return x3 ? launch_tc_kc<4, 2>(pl, lv) : launch_tc_kc<4, 1>(pl, lv);
+        case 8: return x3 ? launch_tc_kc<8, 2>(pl, lv) : launch_tc_kc<8, 1>(pl, lv);
+        case 12: return x3 ? launch_tc_kc<12, 2>(pl, lv) : launch_tc_kc<12, 1>(pl, lv);
+        case 16: return x3 ? launch_tc_kc<16, 2>(pl, lv) : launch_tc_kc<16, 1>(pl, lv);
+        default: return -1;
+    }
+}

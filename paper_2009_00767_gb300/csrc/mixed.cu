@@ -1,40 +1,37 @@
-// mixed.cu -- the mixed-precision path: FP32 particle stages, FP32 M2L on the CUDA cores,
-// FP64 where magnitudes are large (moment accumulation, the monopole-log part of b'_0, the
-// cross-level sum of phi).
+// mixed.cu -- the mixed-precision path: FP32 particle stages and FP32 M2L on the CUDA cores,
+// with float-float (two FP32 words) wherever magnitudes are large.  GB300's FP64 pipe is far
+// narrower than its FP32 pipe, so no FP64 arithmetic runs inside the hot loops: FP64 appears
+// only in the atomic moment sums (executed in L2), in the one-off conversion of each moment
+// cell, and in the final phi written for the caller.
 //
 // Scaled form as in fp64.cu (w = (z - c) / s, power-sum moments M_m = sum q w^m):
-//   P2M  every level straight from the particles (U-bar of Sec. 2.2.1): w is formed in FP32
-//        from the particle's offset to its finest-square centre (exact dyadic square offsets
-//        plus an FP32 product), q w^m in FP32, warp-segmented FP32 sums of at most 32 terms,
-//        then FP64 atomics into the level's grid.
+//   P2M  every level straight from the particles (U-bar of Sec. 2.2.1): w in FP32 from the
+//        particle's offset to its finest-square centre (an exact dyadic square offset plus an
+//        FP32 product), q w^m in FP32, warp-segmented FP32 sums of at most 32 terms, then FP64
+//        atomics into the level's grid.
+//   prep each moment cell once to FP32; the total charge M_0 (real) is kept as a float-float
+//        pair (hi, lo) in the slot of coefficient 0.
 //   M2L  (D-bar-1) per target: b'_l = sum_d sum_k T_d[k][l] M[t+d][k] in FP32 (k, l = 0..p),
-//        except the monopole-log term M_0 (log|w0| + ln s) of b'_0, which is summed in FP64
-//        (it dominates the magnitude of phi for random-sign charges).
+//        except the monopole-log term sum_d M_0 (log|w0| + ln s) of b'_0, summed in
+//        float-float; Re b'_0 is stored as a float-float pair in the slot of coefficient 0.
 //   L2P  (D-bar-2 by linearity) per particle and level: Re sum_{l>=1} b'_l w^l by Horner in
-//        FP32, plus the FP64 b'_0; levels summed in FP64.
-//   P2P  (E-2 of Sec. 2.1) in FP32 on square-local coordinates; log via the MUFU lg2 unit.
-#include "fmm_internal.cuh"
+//        FP32, plus Re b'_0; the levels are summed in float-float.
+//   P2P  (E-2 of Sec. 2.1) in FP32 on square-local coordinates, log via the MUFU lg2 unit,
+//        sources staged in shared memory by the bulk-copy (TMA) engine; phi = far + near.
+#include "mixed_common.cuh"
 
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
 constexpr int kM2LThreads = 128;
 
-// w of a particle in its level-k square, from its offset (dx, dy) to the centre of its finest
-// square (ix, iy): w = ((i_local + 1/2) 2^-(l-k) - 1/2) + d 2^k / box.  The first part is an
-// exact dyadic number in FP32.
-__device__ __forceinline__ float2 level_w(float dx, float dy, uint32_t ix, uint32_t iy, int sh, float inv_s) {
-    const uint32_t mask = (1u << sh) - 1u;
-    const float sc = __int_as_float((127 - sh) << 23);   // 2^-sh
-    const float ox = fmaf((float)(ix & mask) + 0.5f, sc, -0.5f);
-    const float oy = fmaf((float)(iy & mask) + 0.5f, sc, -0.5f);
-    return make_float2(fmaf(dx, inv_s, ox), fmaf(dy, inv_s, oy));
-}
-
 // -------------------------------------------------------------------------------- P2M
+// One warp per 32 consecutive box-sorted particles, every level.  Per level the power sums go
+// to shared memory; lane c then sums column c down the rows, closing a run wherever the
+// square key changes (the run ends come from one ballot) with an FP64 atomic into the grid.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_p2m_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int p,
-            double box, FmmLevelPtrs g) {
+            MixedLevels lv, FmmLevelPtrs g) {
     extern __shared__ float smf[];
     __shared__ uint32_t bid[kWarpsPerBlock][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -44,14 +41,14 @@ k_p2m_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
     if (w0 >= n) return;
     const int64_t i = w0 + lane;
     const bool valid = i < n;
+    const int nvalid = (int)min((int64_t)32, n - w0);
     const float4 P = valid ? sp[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t key = valid ? skey[i] : 0u;
     const uint32_t ix = fmm_compact2(key), iy = fmm_compact2(key >> 1);
     for (int k = 2; k <= levels; ++k) {
         const int sh = levels - k;
         const uint32_t kk = key >> (2 * sh);
-        const float inv_s = (float)((double)(1 << k) / box);
-        const float2 w = level_w(P.x, P.y, ix, iy, sh, inv_s);
+        const float2 w = level_w(P.x, P.y, ix, iy, sh, lv.inv_s[k]);
         float* r = rows + lane * stride;
         float pr = P.z, pi = 0.f;
         r[0] = pr;
@@ -64,45 +61,55 @@ k_p2m_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
             r[2 * m] = pr;
             r[2 * m + 1] = pi;
         }
-        bid[warp][lane] = valid ? kk : 0xffffffffu;
+        bid[warp][lane] = kk;
+        const uint32_t nxt = __shfl_down_sync(0xffffffffu, kk, 1);
+        uint32_t ends = __ballot_sync(0xffffffffu, lane + 1 < nvalid && nxt != kk);
+        ends |= 1u << (nvalid - 1);
         __syncwarp();
         const int W = fmm_grid_width(k);
         double* A = reinterpret_cast<double*>(g.A[k]);
         for (int col = lane; col < ncol; col += 32) {
-            uint32_t cur = bid[warp][0];
             float run = 0.f;
+#pragma unroll
             for (int rr = 0; rr < 32; ++rr) {
-                const uint32_t b = bid[warp][rr];
-                if (b == 0xffffffffu) break;
-                if (b != cur) {
-                    const size_t cell = (size_t)(fmm_compact2(cur >> 1) + FMM_HALO) * W + fmm_compact2(cur) + FMM_HALO;
-                    atomicAdd(A + cell * ncol + col, (double)run);
-                    run = 0.f;
-                    cur = b;
+                if (rr < nvalid) {
+                    run += rows[rr * stride + col];
+                    if ((ends >> rr) & 1u) {
+                        const uint32_t cur = bid[warp][rr];
+                        const size_t cell =
+                            (size_t)(fmm_compact2(cur >> 1) + FMM_HALO) * W + fmm_compact2(cur) + FMM_HALO;
+                        atomicAdd(A + cell * ncol + col, fmm_f2d_bits(run));
+                        run = 0.f;
+                    }
                 }
-                run += rows[rr * stride + col];
             }
-            const size_t cell = (size_t)(fmm_compact2(cur >> 1) + FMM_HALO) * W + fmm_compact2(cur) + FMM_HALO;
-            atomicAdd(A + cell * ncol + col, (double)run);
         }
         __syncwarp();
     }
+}
+
+// -------------------------------------------------------------------------------- moment prep
+// FP64 moment grid -> FP32 grid, once per coefficient; coefficient 0 (the real total charge)
+// becomes a float-float pair.
+__global__ void k_prep_a32(const double2* __restrict__ a64, float2* __restrict__ a32, int64_t count, int p1) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const double2 v = a64[e];
+    a32[e] = (e % p1 == 0) ? fmm_d2ff_bits(v.x) : make_float2(fmm_d2ff_bits(v.x).x, fmm_d2ff_bits(v.y).x);
 }
 
 // -------------------------------------------------------------------------------- M2L (FP32 SIMT)
 struct M2LMixedArgs {
     FmmLevelPtrs g;
     const float2* T;                    // [49][P1B][P1B] FP32, zero beyond p and at [d][0][0]
-    double logw0[49];                   // log|w0| per offset (FP64 monopole term)
-    double ln_s[FMM_MAX_LEVELS + 1];
     int cta_base[FMM_MAX_LEVELS + 2];   // first CTA of each level
-    int levels, p;
+    int levels, p, kmax;                // levels 2..kmax run here
 };
 
 // One thread per target square; the CTA's 128 targets share one parity class (so one list of
 // 27 offsets) and stage each offset's operator in shared memory, read as broadcasts.
 template <int P1B>
-__global__ void __launch_bounds__(kM2LThreads) k_m2l_f32(M2LMixedArgs a) {
+__global__ void __launch_bounds__(kM2LThreads) k_m2l_f32(M2LMixedArgs a, MixedLevels lv) {
     __shared__ float2 Ts[P1B * P1B];
     const int cta = blockIdx.x;
     int k = 2;
@@ -117,11 +124,11 @@ __global__ void __launch_bounds__(kM2LThreads) k_m2l_f32(M2LMixedArgs a) {
     const int tx = 2 * (active ? u % w2 : 0) + px;
     const int ty = 2 * (active ? u / w2 : 0) + py;
     const int p1 = a.p + 1, W = fmm_grid_width(k);
-    const double2* A = reinterpret_cast<const double2*>(a.g.A[k]);
+    const float2* A = reinterpret_cast<const float2*>(a.g.A32[k]);
     float2 acc[P1B];
 #pragma unroll
     for (int l = 0; l < P1B; ++l) acc[l] = make_float2(0.f, 0.f);
-    double mono = 0.0;
+    float2 mono = make_float2(0.f, 0.f);
     for (int dy = -2 - py; dy <= 3 - py; ++dy) {
         for (int dx = -2 - px; dx <= 3 - px; ++dx) {
             if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
@@ -131,18 +138,12 @@ __global__ void __launch_bounds__(kM2LThreads) k_m2l_f32(M2LMixedArgs a) {
             for (int e = threadIdx.x; e < P1B * P1B; e += kM2LThreads) Ts[e] = Td[e];
             __syncthreads();
             // sources outside the domain read the zero halo
-            const double2* src = A + ((size_t)(ty + dy + FMM_HALO) * W + (tx + dx + FMM_HALO)) * p1;
+            const float2* src = A + ((size_t)(ty + dy + FMM_HALO) * W + (tx + dx + FMM_HALO)) * p1;
             float2 m[P1B];
 #pragma unroll
-            for (int kk = 0; kk < P1B; ++kk) {
-                if (kk < p1) {
-                    const double2 v = src[kk];
-                    m[kk] = make_float2((float)v.x, (float)v.y);
-                    if (kk == 0) mono = fma(v.x, a.logw0[d] + a.ln_s[k], mono);   // M_0 (log|w0| + ln s)
-                } else {
-                    m[kk] = make_float2(0.f, 0.f);
-                }
-            }
+            for (int kk = 0; kk < P1B; ++kk) m[kk] = (kk < p1) ? src[kk] : make_float2(0.f, 0.f);
+            mono = ff_add(mono, ff_mul(m[0], lv.logc[k][d]));   // M_0 (log|w0| + ln s), float-float
+            m[0].y = 0.f;                                        // M_0 is real; .y held its low word
 #pragma unroll
             for (int kk = 0; kk < P1B; ++kk) {
 #pragma unroll
@@ -157,77 +158,141 @@ __global__ void __launch_bounds__(kM2LThreads) k_m2l_f32(M2LMixedArgs a) {
     if (!active) return;
     const size_t t = (size_t)ty * (1u << k) + tx;
     float2* B = reinterpret_cast<float2*>(a.g.B[k]);
-    double* B0 = reinterpret_cast<double*>(a.g.B0[k]);
-    for (int l = 0; l < p1 && l < P1B; ++l) B[t * p1 + l] = acc[l];
-    B0[t] = mono + (double)acc[0].x;
+    B[t * p1] = ff_add_f(mono, acc[0].x);   // Re b'_0 as float-float
+#pragma unroll
+    for (int l = 1; l < P1B; ++l)
+        if (l < p1) B[t * p1 + l] = acc[l];
 }
 
 // -------------------------------------------------------------------------------- L2P
-__global__ void k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n,
-                            int levels, int p, double box, FmmLevelPtrs g, double* __restrict__ phi_far) {
+// One thread per particle; per level the square's p+1 coefficients are loaded together (the
+// order is padded to P1B at compile time, so all loads issue before the Horner chain).
+template <int P1B>
+__global__ void __launch_bounds__(128)
+k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int p,
+            MixedLevels lv, FmmLevelPtrs g, float2* __restrict__ phi_far) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 P = sp[i];
     const uint32_t key = skey[i];
     const uint32_t ix = fmm_compact2(key), iy = fmm_compact2(key >> 1);
     const int p1 = p + 1;
-    double far = 0.0;
+    float2 far = make_float2(0.f, 0.f);
     for (int k = 2; k <= levels; ++k) {
         const int sh = levels - k;
-        const float inv_s = (float)((double)(1 << k) / box);
-        const float2 w = level_w(P.x, P.y, ix, iy, sh, inv_s);
+        const float2 w = level_w(P.x, P.y, ix, iy, sh, lv.inv_s[k]);
         const size_t t = (size_t)(iy >> sh) * (1u << k) + (ix >> sh);
         const float2* Bt = reinterpret_cast<const float2*>(g.B[k]) + t * p1;
-        float2 u = Bt[p];
-        for (int l = p - 1; l >= 1; --l) {
-            const float2 b = Bt[l];
-            const float ur = fmaf(u.x, w.x, fmaf(-u.y, w.y, b.x));
-            const float ui = fmaf(u.x, w.y, fmaf(u.y, w.x, b.y));
+        float2 b[P1B];
+#pragma unroll
+        for (int l = 0; l < P1B; ++l) b[l] = (l < p1) ? __ldg(Bt + l) : make_float2(0.f, 0.f);
+        float2 u = b[P1B - 1];
+#pragma unroll
+        for (int l = P1B - 2; l >= 1; --l) {
+            const float ur = fmaf(u.x, w.x, fmaf(-u.y, w.y, b[l].x));
+            const float ui = fmaf(u.x, w.y, fmaf(u.y, w.x, b[l].y));
             u.x = ur;
             u.y = ui;
         }
-        const float v = fmaf(u.x, w.x, -u.y * w.y);   // Re(u w)
-        far += reinterpret_cast<const double*>(g.B0[k])[t] + (double)v;
+        const float v = fmaf(u.x, w.x, -u.y * w.y);   // Re(u w) = Re sum_{l>=1} b'_l w^l
+        far = ff_add(far, ff_add_f(b[0], v));         // b[0] = Re b'_0 as (hi, lo)
     }
     phi_far[i] = far;
 }
 
 // -------------------------------------------------------------------------------- P2P + final phi
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, int levels, double box,
-            const double* __restrict__ phi_far, double* __restrict__ phi, const unsigned int* __restrict__ status,
+// One warp per finest square.  When the square and its (up to) eight neighbours hold at most
+// kP2PCap sources, the bulk-copy (TMA) engine moves their contiguous Morton ranges into the
+// warp's shared-memory buffer (cp.async.bulk completing on an mbarrier, with a bounded wait);
+// otherwise the warp reads them from global memory.  With T targets the warp splits into
+// 32 / T' groups (T' = T rounded up to a power of two, at most 32) that take interleaved
+// sources and combine by shuffles.  Each neighbour's sum runs in FP32 and the neighbours are
+// combined in float-float, so crowded squares keep their accuracy.
+constexpr int kP2PWarps = 4;
+constexpr int kP2PCap = 512;                  // sources per warp buffer (8 KB)
+constexpr unsigned kSpinLimit = 1u << 22;     // bounded mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, P;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kP2PWarps * 32)
+k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, int levels, float s_leaf,
+            const float2* __restrict__ phi_far, double* __restrict__ phi, unsigned int* __restrict__ status,
             unsigned long long* __restrict__ counters) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t leaf = (uint32_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    __shared__ __align__(16) float4 buf[kP2PWarps][kP2PCap];
+    __shared__ __align__(8) uint64_t bar[kP2PWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t leaf = (uint32_t)blockIdx.x * kP2PWarps + warp;
     const uint32_t nleaf = 1u << (2 * levels);
     if (leaf >= nleaf) return;
-    if (*(volatile const unsigned int*)status != 0u) return;
+    if (*(volatile const unsigned int*)status != 0u) return;   // inputs failed the device checks
     const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
     const int T = (int)(t1 - t0);
     if (T == 0) return;
     const int side = 1 << levels;
-    const float s = (float)(box / (double)side);
     const int ix = (int)fmm_compact2(leaf), iy = (int)fmm_compact2(leaf >> 1);
-    uint32_t ns0[9], ns1[9];
-    float offx[9], offy[9];
-    uint64_t nsrc = 0;
-    int nn = 0;
-    for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int jx = ix + dx, jy = iy + dy;
-            if (jx < 0 || jy < 0 || jx >= side || jy >= side) continue;
-            const uint32_t nl = fmm_morton((uint32_t)jx, (uint32_t)jy);
-            ns0[nn] = leaf_start[nl];
-            ns1[nn] = leaf_start[nl + 1];
-            offx[nn] = (float)(-dx) * s;   // target-centre minus source-centre, exact
-            offy[nn] = (float)(-dy) * s;
-            nsrc += ns1[nn] - ns0[nn];
-            ++nn;
-        }
-    if (lane == 0) {
-        atomicAdd(&counters[0], (unsigned long long)T * nsrc - (unsigned long long)T);
-        atomicMax(&counters[1], (unsigned long long)T);
+    // the nine neighbour slots, fully unrolled so that they live in registers
+    uint32_t nb0[9], ncnt[9], noff[9];
+    uint32_t nsrc = 0;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const int jx = ix + (b % 3) - 1, jy = iy + (b / 3) - 1;
+        const bool in = jx >= 0 && jy >= 0 && jx < side && jy < side;
+        const uint32_t nl = in ? fmm_morton((uint32_t)jx, (uint32_t)jy) : 0u;
+        nb0[b] = in ? leaf_start[nl] : 0u;
+        ncnt[b] = in ? leaf_start[nl + 1] - nb0[b] : 0u;
+        noff[b] = nsrc;
+        nsrc += ncnt[b];
     }
+    if (lane == 0) {
+        const unsigned slot = leaf % FMM_COUNTER_SLOTS;
+        atomicAdd(&counters[slot], (unsigned long long)T * nsrc - (unsigned long long)T);
+        atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)T);
+    }
+    const bool staged = nsrc <= (uint32_t)kP2PCap;
+    const uint32_t mb = smem_u32(&bar[warp]);
+    if (staged) {
+        if (lane == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            uint64_t st64;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                         : "=l"(st64)
+                         : "r"(mb), "r"(16u * nsrc)
+                         : "memory");
+            const uint32_t dst0 = smem_u32(buf[warp]);
+#pragma unroll
+            for (int b = 0; b < 9; ++b)
+                if (ncnt[b] > 0)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            dst0 + 16u * noff[b]),
+                        "l"(sp + nb0[b]), "r"(16u * ncnt[b]), "r"(mb)
+                        : "memory");
+        }
+        __syncwarp();
+        if (!mbar_wait(mb, 0)) {
+            if (lane == 0) atomicOr(status, FMM_FLAG_TIMEOUT);
+            return;   // the copies were issued with valid sizes; nothing else waits on them
+        }
+    }
+    const float4* base = staged ? buf[warp] : sp;
     int tp = 1;
     while (tp < T && tp < 32) tp <<= 1;
     const int groups = 32 / tp;
@@ -235,27 +300,45 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
     for (int tb = 0; tb < T; tb += tp) {
         const int ti = tb + slot;
         const bool active = ti < T;
-        const uint32_t gi = t0 + (active ? ti : 0);
-        const float4 Pi = sp[gi];
+        const float4 Pi = sp[t0 + (active ? ti : 0)];
+        // at most kP2PCap / groups terms per lane go into one FP32 sum when the sources are
+        // staged; otherwise each neighbour's FP32 sum is added in float-float
+        float2 near = make_float2(0.f, 0.f);
         float acc = 0.f;
-        for (int b = 0; b < nn; ++b) {
-            const float bx = Pi.x + offx[b], by = Pi.y + offy[b];
-            for (uint32_t j = ns0[b] + grp; j < ns1[b]; j += groups) {
-                const float4 Pj = sp[j];
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const float bx = Pi.x - (float)((b % 3) - 1) * s_leaf;   // target-centre minus source-centre
+            const float by = Pi.y - (float)((b / 3) - 1) * s_leaf;
+            const float4* src = base + (staged ? noff[b] : nb0[b]);
+            for (uint32_t j = grp; j < ncnt[b]; j += groups) {
+                const float4 Pj = src[j];
                 const float ddx = bx - Pj.x, ddy = by - Pj.y;
                 const float r2 = fmaf(ddx, ddx, ddy * ddy);
-                if (j != gi && r2 > 0.f) acc = fmaf(Pj.z, __log2f(r2), acc);
+                const float lg = r2 > 0.f ? __log2f(r2) : 0.f;   // self and coincident pairs give 0
+                acc = fmaf(Pj.z, lg, acc);
+            }
+            if (!staged) {
+                near = ff_add_f(near, acc);
+                acc = 0.f;
             }
         }
-        for (int o = tp; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (active && grp == 0)
-            phi[__float_as_int(Pi.w)] = phi_far[gi] + (double)acc * 0.34657359027997264;   // ln2 / 2
+        near = ff_add_f(near, acc);
+        for (int o = tp; o < 32; o <<= 1) {
+            const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, near.x, o),
+                                             __shfl_xor_sync(0xffffffffu, near.y, o));
+            near = ff_add(near, other);
+        }
+        if (active && grp == 0) {
+            const float2 v = ff_add(phi_far[t0 + ti], ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
+            phi[__float_as_int(Pi.w)] = fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);   // ln2 / 2 as float-float above
+        }
     }
+    if (staged && lane == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
 }
 
 template <int P1B>
-void launch_m2l(const M2LMixedArgs& a, int blocks, cudaStream_t st) {
-    k_m2l_f32<P1B><<<blocks, kM2LThreads, 0, st>>>(a);
+void launch_m2l(const M2LMixedArgs& a, const MixedLevels& lv, int blocks, cudaStream_t st) {
+    k_m2l_f32<P1B><<<blocks, kM2LThreads, 0, st>>>(a, lv);
 }
 
 }  // namespace
@@ -268,10 +351,14 @@ int fmm_m2l_bucket(int p1) {
 }
 
 int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
-    if (pl->precision != FMM_MIXED_FP32) return -2;
+    if (pl->precision != FMM_MIXED_FP32 && pl->precision != FMM_MIXED_TF32 && pl->precision != FMM_MIXED_3XTF32)
+        return -2;
+    // the tensor-core M2L takes the levels whose parity sub-grid rows hold at least 128 targets
+    const bool use_tc = pl->tc != nullptr && pl->levels >= fmm_tc_kmin();
     cudaStream_t st = pl->stream;
     const int64_t n = pl->n;
-    const int L = pl->levels, p = pl->p;
+    const int L = pl->levels, p = pl->p, p1 = p + 1;
+    const MixedLevels lv = fmm_make_levels(pl);
     int launches = 0;
     cudaEventRecord(pl->ev[1], st);
     if (L >= 2) {
@@ -279,10 +366,19 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
             if (cudaMemsetAsync(pl->grids.A[k], 0, pl->a_bytes[k], st) != cudaSuccess) return -1;
         const int64_t warps = (n + 31) / 32;
         const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        const size_t shm = sizeof(float) * kWarpsPerBlock * 32 * (2 * (p + 1) + 1);
-        k_p2m_mixed<<<blocks, kWarpsPerBlock * 32, shm, st>>>(pl->sorted32, pl->sorted_key, n, L, p, pl->box,
-                                                              pl->grids);
+        const size_t shm = sizeof(float) * kWarpsPerBlock * 32 * (2 * p1 + 1);
+        if (shm > 48 * 1024 &&
+            cudaFuncSetAttribute(k_p2m_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess)
+            return -1;
+        k_p2m_mixed<<<blocks, kWarpsPerBlock * 32, shm, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids);
         ++launches;
+        for (int k = 2; k <= L; ++k) {
+            const int64_t count = (int64_t)fmm_grid_width(k) * fmm_grid_width(k) * p1;
+            k_prep_a32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(
+                reinterpret_cast<const double2*>(pl->grids.A[k]), reinterpret_cast<float2*>(pl->grids.A32[k]), count,
+                p1);
+            ++launches;
+        }
     }
     cudaEventRecord(pl->ev[2], st);
     if (L >= 2) {
@@ -291,43 +387,53 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
         a.T = pl->T32;
         a.levels = L;
         a.p = p;
-        for (int d = 0; d < 49; ++d) {
-            const int dx = d % 7 - 3, dy = d / 7 - 3;
-            a.logw0[d] = (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) ? 0.0 : 0.5 * log((double)(dx * dx + dy * dy));
-        }
-        for (int k = 0; k <= FMM_MAX_LEVELS; ++k) a.ln_s[k] = log(pl->box / (double)(1 << k));
+        a.kmax = use_tc ? fmm_tc_kmin() - 1 : L;
         int acc = 0;
         for (int k = 0; k <= FMM_MAX_LEVELS + 1; ++k) a.cta_base[k] = 0;
-        for (int k = 2; k <= L; ++k) {
+        for (int k = 2; k <= a.kmax; ++k) {
             a.cta_base[k] = acc;
             const int w2 = 1 << (k - 1);
             acc += 4 * ((w2 * w2 + kM2LThreads - 1) / kM2LThreads);
         }
-        a.cta_base[L + 1] = acc;
+        a.cta_base[a.kmax + 1] = acc;
         switch (pl->p1b) {
-            case 9: launch_m2l<9>(a, acc, st); break;
-            case 13: launch_m2l<13>(a, acc, st); break;
-            case 17: launch_m2l<17>(a, acc, st); break;
-            case 21: launch_m2l<21>(a, acc, st); break;
-            case 25: launch_m2l<25>(a, acc, st); break;
-            case 33: launch_m2l<33>(a, acc, st); break;
-            case 41: launch_m2l<41>(a, acc, st); break;
+            case 9: launch_m2l<9>(a, lv, acc, st); break;
+            case 13: launch_m2l<13>(a, lv, acc, st); break;
+            case 17: launch_m2l<17>(a, lv, acc, st); break;
+            case 21: launch_m2l<21>(a, lv, acc, st); break;
+            case 25: launch_m2l<25>(a, lv, acc, st); break;
+            case 33: launch_m2l<33>(a, lv, acc, st); break;
+            case 41: launch_m2l<41>(a, lv, acc, st); break;
             default: return -2;
         }
         ++launches;
+        if (use_tc) {
+            const int t = fmm_launch_m2l_tc(pl, lv);
+            if (t < 0) return -1;
+            launches += t;
+        }
     }
     cudaEventRecord(pl->ev[3], st);
+    float2* far = reinterpret_cast<float2*>(pl->phi_far);
     {
         const unsigned blocks = (unsigned)((n + 127) / 128);
-        k_l2p_mixed<<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, pl->box, pl->grids, pl->phi_far);
+        switch (pl->p1b) {
+#define FMM_L2P(PB)                                                                                          \
+    case PB:                                                                                                 \
+        k_l2p_mixed<PB><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids, far);  \
+        break;
+            FMM_L2P(9) FMM_L2P(13) FMM_L2P(17) FMM_L2P(21) FMM_L2P(25) FMM_L2P(33) FMM_L2P(41)
+#undef FMM_L2P
+            default: return -2;
+        }
         ++launches;
     }
     cudaEventRecord(pl->ev[4], st);
     {
         const uint32_t nleaf = 1u << (2 * L);
-        const unsigned blocks = (nleaf + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        k_p2p_mixed<<<blocks, kWarpsPerBlock * 32, 0, st>>>(pl->sorted32, pl->leaf_start, L, pl->box, pl->phi_far,
-                                                            phi, pl->d_status, pl->d_counters);
+        const unsigned blocks = (nleaf + kP2PWarps - 1) / kP2PWarps;
+        k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, st>>>(pl->sorted32, pl->leaf_start, L, lv.s_leaf, far, phi,
+                                                      pl->d_status, pl->d_counters);
         ++launches;
     }
     cudaEventRecord(pl->ev[5], st);

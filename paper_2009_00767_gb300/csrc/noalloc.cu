@@ -103,7 +103,7 @@ size_t carve(fmm_plan_s* pl, unsigned char* base) {
     }
     pl->T64 = reinterpret_cast<double2*>(take(sizeof(double2) * 49 * p1 * p1));
     pl->d_status = reinterpret_cast<unsigned int*>(take(sizeof(unsigned int)));
-    pl->d_counters = reinterpret_cast<unsigned long long*>(take(2 * sizeof(unsigned long long)));
+    pl->d_counters = reinterpret_cast<unsigned long long*>(take(2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long)));
     return off;
 }
 
@@ -153,7 +153,7 @@ extern "C" fmm_status fmm_potential_noalloc(int64_t n, int levels, int p, double
     // The array keeps the previous call's contents: clear what must start at zero.
     cudaStream_t st = pl.stream;
     if (cudaMemsetAsync(pl.d_status, 0, sizeof(unsigned int), st) != cudaSuccess ||
-        cudaMemsetAsync(pl.d_counters, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess)
+        cudaMemsetAsync(pl.d_counters, 0, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long), st) != cudaSuccess)
         return FMM_ERR_CUDA;
     const int nops = 49 * (p + 1) * (p + 1);
     k_build_ops_f64<<<(nops + 255) / 256, 256, 0, st>>>(p, pl.T64);

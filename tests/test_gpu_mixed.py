@@ -58,3 +58,41 @@ def test_mixed_full_size_uniform_1m(oracle_mod):
     err = rel_l2(phi, ref)
     print(f"mixed fp32 N=2^20 levels=8 p=20: rel L2 vs oracle {err:.3e}")
     assert err < MIXED_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [("3xtf32", MIXED_TOL), ("tf32", 1e-3)])
+@pytest.mark.parametrize("case", [
+    (1 << 16, 8, 20, "uniform", 7),     # one particle per finest square: the tensor-core level is 8
+    (150000, 8, 12, "gmm", 8),          # clustered, many empty squares, p = 12 (K = N = 32)
+    (200000, 8, 16, "annulus", 9),      # p = 16 (K = N = 48 with padding)
+])
+def test_tensor_core_m2l_matches_oracle(oracle_mod, precision, tol, case):
+    """M2L of level 8 on tcgen05 (TF32 / split 3xTF32), levels 2..7 on the CUDA cores."""
+    from gpu_util import run_fmm
+    n, lev, p, fam, seed = case
+    xy, q = getattr(inputs, fam)(n, inputs.config_seed(0, 300 + seed))
+    phi, st = run_fmm(xy, q, lev, p, precision=precision)
+    ref = oracle_mod.shiftfree(xy, q, lev, p)
+    err = rel_l2(phi, ref)
+    print(f"{precision} N={n} levels={lev} p={p} {fam}: rel L2 vs oracle {err:.3e}")
+    assert err < tol
+
+
+def test_tensor_core_full_size_uniform_1m(oracle_mod):
+    """N = 2^20 uniform, levels 8, p = 20 in 3xTF32: every element against the oracle."""
+    from gpu_util import run_fmm
+    xy, q = inputs.uniform(1 << 20, inputs.config_seed(1))
+    phi, st = run_fmm(xy, q, 8, 20, precision="3xtf32")
+    ref = oracle_mod.shiftfree(xy, q, 8, 20)
+    err = rel_l2(phi, ref)
+    print(f"3xtf32 N=2^20 levels=8 p=20: rel L2 vs oracle {err:.3e}")
+    assert err < MIXED_TOL
+
+
+def test_tensor_core_modes_below_level_8_use_the_cuda_cores(oracle_mod):
+    from gpu_util import run_fmm
+    xy, q = inputs.uniform(20000, 410)
+    a, _ = run_fmm(xy, q, 6, 14, precision="3xtf32")
+    b, _ = run_fmm(xy, q, 6, 14, precision="fp32")
+    # the same kernels run; only the order of the atomic moment sums may differ between calls
+    assert rel_l2(a, b) < 1e-9
