@@ -212,6 +212,15 @@ constexpr int kP2PWarps = 4;
 constexpr int kP2PCap = 512;                  // sources per warp buffer (8 KB)
 constexpr unsigned kSpinLimit = 1u << 22;     // bounded mbarrier wait
 
+// q-weight of one pair: log2 r^2 by the MUFU unit (flush-to-zero: r^2 of distinct particles is
+// normal); self and coincident pairs (r^2 = 0) give 0.
+__device__ __forceinline__ float p2p_lg2(float dx, float dy) {
+    const float r2 = fmaf(dx, dx, dy * dy);
+    float lg;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(r2));
+    return r2 > 0.f ? lg : 0.f;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
     return (uint32_t)__cvta_generic_to_shared(ptr);
 }
@@ -292,37 +301,63 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
             return;   // the copies were issued with valid sizes; nothing else waits on them
         }
     }
-    const float4* base = staged ? buf[warp] : sp;
+    if (staged) {
+        // move every staged source into the target square's frame: x_j + (jx - ix) s, y_j + (jy - iy) s
+        float4* sb = buf[warp];
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const float ox = (float)((b % 3) - 1) * s_leaf, oy = (float)((b / 3) - 1) * s_leaf;
+            for (uint32_t j = lane; j < ncnt[b]; j += 32) {
+                float4 v = sb[noff[b] + j];
+                v.x += ox;
+                v.y += oy;
+                sb[noff[b] + j] = v;
+            }
+        }
+        __syncwarp();
+    }
     int tp = 1;
     while (tp < T && tp < 32) tp <<= 1;
-    const int groups = 32 / tp;
-    const int slot = lane & (tp - 1), grp = lane / tp;
+    const uint32_t groups = 32 / tp;
+    const int slot = lane & (tp - 1);
+    const uint32_t grp = lane / tp;
     for (int tb = 0; tb < T; tb += tp) {
         const int ti = tb + slot;
         const bool active = ti < T;
         const float4 Pi = sp[t0 + (active ? ti : 0)];
-        // at most kP2PCap / groups terms per lane go into one FP32 sum when the sources are
-        // staged; otherwise each neighbour's FP32 sum is added in float-float
         float2 near = make_float2(0.f, 0.f);
-        float acc = 0.f;
-#pragma unroll
-        for (int b = 0; b < 9; ++b) {
-            const float bx = Pi.x - (float)((b % 3) - 1) * s_leaf;   // target-centre minus source-centre
-            const float by = Pi.y - (float)((b / 3) - 1) * s_leaf;
-            const float4* src = base + (staged ? noff[b] : nb0[b]);
-            for (uint32_t j = grp; j < ncnt[b]; j += groups) {
-                const float4 Pj = src[j];
-                const float ddx = bx - Pj.x, ddy = by - Pj.y;
-                const float r2 = fmaf(ddx, ddx, ddy * ddy);
-                const float lg = r2 > 0.f ? __log2f(r2) : 0.f;   // self and coincident pairs give 0
-                acc = fmaf(Pj.z, lg, acc);
+        if (staged) {
+            // at most kP2PCap / groups terms per lane: one FP32 sum, four sources per step
+            const float4* src = buf[warp];
+            float acc0 = 0.f, acc1 = 0.f;
+            uint32_t j = grp;
+            for (; j + 3u * groups < nsrc; j += 4u * groups) {
+                const float4 a0 = src[j], a1 = src[j + groups], a2 = src[j + 2u * groups], a3 = src[j + 3u * groups];
+                acc0 = fmaf(a0.z, p2p_lg2(Pi.x - a0.x, Pi.y - a0.y), acc0);
+                acc1 = fmaf(a1.z, p2p_lg2(Pi.x - a1.x, Pi.y - a1.y), acc1);
+                acc0 = fmaf(a2.z, p2p_lg2(Pi.x - a2.x, Pi.y - a2.y), acc0);
+                acc1 = fmaf(a3.z, p2p_lg2(Pi.x - a3.x, Pi.y - a3.y), acc1);
             }
-            if (!staged) {
+            for (; j < nsrc; j += groups) {
+                const float4 a0 = src[j];
+                acc0 = fmaf(a0.z, p2p_lg2(Pi.x - a0.x, Pi.y - a0.y), acc0);
+            }
+            near = make_float2(acc0 + acc1, 0.f);
+        } else {
+            // crowded squares: per-neighbour FP32 sums from global memory, combined in float-float
+#pragma unroll
+            for (int b = 0; b < 9; ++b) {
+                const float bx = Pi.x - (float)((b % 3) - 1) * s_leaf;   // target-centre minus source-centre
+                const float by = Pi.y - (float)((b / 3) - 1) * s_leaf;
+                const float4* src = sp + nb0[b];
+                float acc = 0.f;
+                for (uint32_t j = grp; j < ncnt[b]; j += groups) {
+                    const float4 Pj = src[j];
+                    acc = fmaf(Pj.z, p2p_lg2(bx - Pj.x, by - Pj.y), acc);
+                }
                 near = ff_add_f(near, acc);
-                acc = 0.f;
             }
         }
-        near = ff_add_f(near, acc);
         for (int o = tp; o < 32; o <<= 1) {
             const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, near.x, o),
                                              __shfl_xor_sync(0xffffffffu, near.y, o));

@@ -15,11 +15,49 @@
 namespace {
 
 constexpr int kScanThreads = 256;
+
+// a * (s.x + s.y) as an FP32 pair (FMA-exact product of the high word)
+__device__ __forceinline__ float2 scatter_mul(float a, float2 s) {
+    const float h = a * s.x;
+    const float e = fmaf(a, s.x, -h) + a * s.y;
+    const float hh = h + e;
+    return make_float2(hh, e - (hh - h));
+}
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+// Finest-square coordinate floor(fl(x 2^l / box)) clamped to [0, side - 1], the rule the oracle
+// uses, without occupying the narrow FP64 pipe in the common case: an FP32 estimate of the
+// quotient (error below 1e-3 for side <= 4096) decides whenever it is more than 2e-3 away from
+// an integer; otherwise the exact FP64 division decides.  t = x 2^l is exact.
+__device__ __forceinline__ int finest_coord(double x, double scale, float scale_over_box32, double box, int side) {
+    const float2 xf = fmm_d2ff_bits(x);   // hi word: x truncated to 24 bits
+    const float q32 = xf.x * scale_over_box32;
+    const float fl = floorf(q32);
+    const float fr = q32 - fl;
+    float f;
+    if (fr > 2e-3f && fr < 1.0f - 2e-3f) {
+        f = fl;
+    } else {
+        f = (float)floor(x * scale / box);
+    }
+    return f < 0.f ? 0 : (f > (float)(side - 1) ? side - 1 : (int)f);
+}
+
+// x in [0, box] for finite x, by integer comparison of the bit patterns (monotone for
+// non-negative doubles; -0.0 counts as 0).
+__device__ __forceinline__ bool in_box_bits(double x, long long box_bits) {
+    const long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ull) return true;
+    return b >= 0 && b <= box_bits;
+}
+
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 __global__ void k_bin(const double2* __restrict__ xy, const double* __restrict__ q, int64_t n, int levels,
-                      double box, uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
+                      double box, float scale_over_box32, uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
                       uint32_t* __restrict__ counts, unsigned int* __restrict__ status) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -28,14 +66,13 @@ __global__ void k_bin(const double2* __restrict__ xy, const double* __restrict__
     const double scale = (double)(1 << levels);
     const int side = 1 << levels;
     uint32_t key = 0;
-    if (!(isfinite(p.x) && isfinite(p.y) && isfinite(qq))) {
+    if (!(finite_bits(p.x) && finite_bits(p.y) && finite_bits(qq))) {
         atomicOr(status, FMM_FLAG_NONFINITE);
     } else {
-        if (!(p.x >= 0.0 && p.x <= box && p.y >= 0.0 && p.y <= box)) atomicOr(status, FMM_FLAG_OUT_OF_BOX);
-        double fx = floor(p.x * scale / box);
-        double fy = floor(p.y * scale / box);
-        int ix = fx < 0.0 ? 0 : (fx > (double)(side - 1) ? side - 1 : (int)fx);
-        int iy = fy < 0.0 ? 0 : (fy > (double)(side - 1) ? side - 1 : (int)fy);
+        const long long bb = __double_as_longlong(box);
+        if (!(in_box_bits(p.x, bb) && in_box_bits(p.y, bb))) atomicOr(status, FMM_FLAG_OUT_OF_BOX);
+        const int ix = finest_coord(p.x, scale, scale_over_box32, box, side);
+        const int iy = finest_coord(p.y, scale, scale_over_box32, box, side);
         key = fmm_morton((uint32_t)ix, (uint32_t)iy);
     }
     keys[i] = key;
@@ -120,7 +157,7 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t m, const ui
 
 template <bool kMixed>
 __global__ void k_scatter(const double2* __restrict__ xy, const double* __restrict__ q, int64_t n, int levels,
-                          double box, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank,
+                          float2 s_ff, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank,
                           const uint32_t* __restrict__ leaf_start, uint32_t* __restrict__ sorted_key,
                           fmm_p64* __restrict__ s64, float4* __restrict__ s32) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -131,11 +168,14 @@ __global__ void k_scatter(const double2* __restrict__ xy, const double* __restri
     double qq = q[i];
     sorted_key[pos] = key;
     if (kMixed) {
-        // coordinates relative to the finest-square centre: FP32 keeps ~1e-7 of the square side
-        const double s = box / (double)(1 << levels);
-        double cx = ((double)fmm_compact2(key) + 0.5) * s;
-        double cy = ((double)fmm_compact2(key >> 1) + 0.5) * s;
-        s32[pos] = make_float4((float)(p.x - cx), (float)(p.y - cy), (float)qq, __int_as_float((int)i));
+        // coordinates relative to the finest-square centre (ix + 1/2) s, formed in float-float
+        // (s = box / 2^l as an FP32 pair), so FP32 keeps about 1e-7 of the square side
+        const float2 cx = scatter_mul((float)fmm_compact2(key) + 0.5f, s_ff);
+        const float2 cy = scatter_mul((float)fmm_compact2(key >> 1) + 0.5f, s_ff);
+        const float2 xf = fmm_d2ff_bits(p.x), yf = fmm_d2ff_bits(p.y), qf = fmm_d2ff_bits(qq);
+        const float dx = (xf.x - cx.x) + (xf.y - cx.y);   // the high words are close: little is lost
+        const float dy = (yf.x - cy.x) + (yf.y - cy.y);
+        s32[pos] = make_float4(dx, dy, qf.x + qf.y, __int_as_float((int)i));
     } else {
         s64[pos] = fmm_p64{p.x, p.y, qq, (double)i};
     }
@@ -151,20 +191,24 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
     if (cudaMemsetAsync(pl->counts, 0, sizeof(uint32_t) * m, st) != cudaSuccess) return -1;
     const int tb = 256;
     const unsigned nblk = (unsigned)((n + tb - 1) / tb);
-    k_bin<<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, pl->box, pl->keys,
-                               pl->rank, pl->counts, pl->d_status);
+    const float scale_over_box32 = (float)((double)(1 << pl->levels) / pl->box);
+    k_bin<<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, pl->box, scale_over_box32,
+                               pl->keys, pl->rank, pl->counts, pl->d_status);
     ++launches;
     const int nb = pl->scan_blocks;
     k_scan_reduce<<<nb, kScanThreads, 0, st>>>(pl->counts, m, pl->block_sums);
     k_scan_top<<<1, kScanThreads, 0, st>>>(pl->block_sums, nb);
     k_scan_down<<<nb, kScanThreads, 0, st>>>(pl->counts, m, pl->block_sums, pl->leaf_start, (uint32_t)n);
     launches += 3;
+    const double sd = pl->box / (double)(1 << pl->levels);
+    const float s_hi = (float)sd;
+    const float2 s_ff = make_float2(s_hi, (float)(sd - (double)s_hi));
     if (pl->precision == FMM_FP64)
-        k_scatter<false><<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, pl->box,
+        k_scatter<false><<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, s_ff,
                                               pl->keys, pl->rank, pl->leaf_start, pl->sorted_key, pl->sorted64,
                                               pl->sorted32);
     else
-        k_scatter<true><<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, pl->box,
+        k_scatter<true><<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, s_ff,
                                              pl->keys, pl->rank, pl->leaf_start, pl->sorted_key, pl->sorted64,
                                              pl->sorted32);
     ++launches;

@@ -92,7 +92,9 @@ def test_tensor_core_full_size_uniform_1m(oracle_mod):
 def test_tensor_core_modes_below_level_8_use_the_cuda_cores(oracle_mod):
     from gpu_util import run_fmm
     xy, q = inputs.uniform(20000, 410)
-    a, _ = run_fmm(xy, q, 6, 14, precision="3xtf32")
-    b, _ = run_fmm(xy, q, 6, 14, precision="fp32")
-    # the same kernels run; only the order of the atomic moment sums may differ between calls
-    assert rel_l2(a, b) < 1e-9
+    a, sa = run_fmm(xy, q, 6, 14, precision="3xtf32")
+    b, sb = run_fmm(xy, q, 6, 14, precision="fp32")
+    # the same kernels run; the order of particles inside a finest square comes from atomic
+    # ranks, so FP32 sums may differ between calls at the level of FP32 rounding
+    assert sa["kernel_launches"] == sb["kernel_launches"]
+    assert rel_l2(a, b) < MIXED_TOL
