@@ -179,8 +179,11 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
         pl->a_bytes[k] = W * W * p1 * sizeof(double2);
         FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.A[k]), pl->a_bytes[k]));
         FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.B[k]), ((size_t)1 << (2 * k)) * p1 * bcplx));
-        if (precision != FMM_FP64)
+        if (precision != FMM_FP64) {
+            // the 3-cell halo of the FP32 grid stays zero for the plan's lifetime
             FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.A32[k]), W * W * p1 * sizeof(float2)));
+            if (cudaMemset(pl->grids.A32[k], 0, W * W * p1 * sizeof(float2)) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
+        }
     }
     std::vector<cd> T;
     build_operators(p, T);

@@ -26,65 +26,195 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kM2LThreads = 128;
 
 // -------------------------------------------------------------------------------- P2M
-// One warp per 32 consecutive box-sorted particles, every level.  Per level the power sums go
-// to shared memory; lane c then sums column c down the rows, closing a run wherever the
-// square key changes (the run ends come from one ballot) with an FP64 atomic into the grid.
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_p2m_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int p,
-            MixedLevels lv, FmmLevelPtrs g) {
-    extern __shared__ float smf[];
-    __shared__ uint32_t bid[kWarpsPerBlock][32];
+// Every level straight from the particles (U-bar of Sec. 2.2.1).  Squares of a level are
+// contiguous Morton ranges of the sorted particles, so the sums need no global sort of their own.
+//
+// Fine levels (at most kFineMean particles per square on average): one lane per square walks its
+// range and keeps the p+1 sums in registers; the lane owns the square, so it stores the FP32
+// moments (total charge as a float-float pair) straight into the FP32 grid, with no reduction
+// and no atomics.  Squares above kLaneMax particles are left to the whole warp afterwards.
+//
+// Coarse levels: each warp walks kCoarseChunk consecutive particles; lanes add their particles'
+// terms in registers while the square stays the same and flush (a column sum over the warp's
+// lanes in shared memory, then FP64 atomics into the level's grid) when it changes.
+constexpr int kFineMean = 64;
+constexpr int kLaneMax = 128;
+constexpr int kCoarseChunk = 256;
+
+struct P2MFineArgs {
+    int base[FMM_MAX_LEVELS + 2];   // first thread of each fine level
+    int kf, levels, p;
+};
+
+// powers q w^m, m = 1..P1B-1 added into acc (entries at m >= p1 stay untouched: the caller masks)
+template <int P1B>
+__device__ __forceinline__ void add_powers(float2 (&acc)[P1B], float q, float2 w) {
+    float pr = q, pi = 0.f;
+#pragma unroll
+    for (int m = 1; m < P1B; ++m) {
+        const float nr = fmaf(pr, w.x, -pi * w.y);
+        const float ni = fmaf(pr, w.y, pi * w.x);
+        pr = nr;
+        pi = ni;
+        acc[m].x += pr;
+        acc[m].y += pi;
+    }
+}
+
+template <int P1B>
+__global__ void __launch_bounds__(128)
+k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, const uint32_t* __restrict__ leaf_start,
+           P2MFineArgs fa, MixedLevels lv, FmmLevelPtrs g) {
+    __shared__ float red[4][32][2 * P1B + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ncol = 2 * (p + 1), stride = ncol + 1;
-    float* rows = smf + (size_t)warp * 32 * stride;
-    const int64_t w0 = ((int64_t)blockIdx.x * kWarpsPerBlock + warp) * 32;
-    if (w0 >= n) return;
-    const int64_t i = w0 + lane;
-    const bool valid = i < n;
-    const int nvalid = (int)min((int64_t)32, n - w0);
-    const float4 P = valid ? sp[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const uint32_t key = valid ? skey[i] : 0u;
-    const uint32_t ix = fmm_compact2(key), iy = fmm_compact2(key >> 1);
-    for (int k = 2; k <= levels; ++k) {
-        const int sh = levels - k;
-        const uint32_t kk = key >> (2 * sh);
-        const float2 w = level_w(P.x, P.y, ix, iy, sh, lv.inv_s[k]);
-        float* r = rows + lane * stride;
-        float pr = P.z, pi = 0.f;
-        r[0] = pr;
-        r[1] = 0.f;
-        for (int m = 1; m <= p; ++m) {
-            const float nr = fmaf(pr, w.x, -pi * w.y);
-            const float ni = fmaf(pr, w.y, pi * w.x);
-            pr = nr;
-            pi = ni;
-            r[2 * m] = pr;
-            r[2 * m + 1] = pi;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = fa.kf;
+    while (k < fa.levels && gt >= fa.base[k + 1]) ++k;
+    const bool valid = gt < fa.base[fa.levels + 1];
+    const uint32_t b = valid ? (uint32_t)(gt - fa.base[k]) : 0u;
+    const int sh = fa.levels - k;
+    const int p1 = fa.p + 1;
+    const uint32_t lo = valid ? leaf_start[(size_t)b << (2 * sh)] : 0u;
+    const uint32_t hi = valid ? leaf_start[(size_t)(b + 1) << (2 * sh)] : 0u;
+    const int W = fmm_grid_width(k);
+    const size_t cell = (size_t)(fmm_compact2(b >> 1) + FMM_HALO) * W + fmm_compact2(b) + FMM_HALO;
+    const bool large = hi - lo > (uint32_t)kLaneMax;
+    float2 acc[P1B];
+#pragma unroll
+    for (int m = 0; m < P1B; ++m) acc[m] = make_float2(0.f, 0.f);
+    float2 m0 = make_float2(0.f, 0.f);
+    if (valid && !large) {
+        for (uint32_t j = lo; j < hi; ++j) {
+            const float4 P = sp[j];
+            const uint32_t key = skey[j];
+            const float2 w = level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh, lv.inv_s[k]);
+            m0 = ff_add_f(m0, P.z);
+            add_powers<P1B>(acc, P.z, w);
         }
-        bid[warp][lane] = kk;
-        const uint32_t nxt = __shfl_down_sync(0xffffffffu, kk, 1);
-        uint32_t ends = __ballot_sync(0xffffffffu, lane + 1 < nvalid && nxt != kk);
-        ends |= 1u << (nvalid - 1);
+        float2* A = reinterpret_cast<float2*>(g.A32[k]) + cell * p1;
+        A[0] = m0;
+#pragma unroll
+        for (int m = 1; m < P1B; ++m)
+            if (m < p1) A[m] = acc[m];
+    }
+    // squares above kLaneMax particles: the whole warp, then a column sum in shared memory
+    unsigned todo = __ballot_sync(0xffffffffu, valid && large);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t lo2 = __shfl_sync(0xffffffffu, lo, src), hi2 = __shfl_sync(0xffffffffu, hi, src);
+        const int k2 = __shfl_sync(0xffffffffu, k, src);
+        const unsigned long long cell2 = __shfl_sync(0xffffffffu, (unsigned long long)cell, src);
+        const int sh2 = fa.levels - k2;
+#pragma unroll
+        for (int m = 0; m < P1B; ++m) acc[m] = make_float2(0.f, 0.f);
+        m0 = make_float2(0.f, 0.f);
+        for (uint32_t j = lo2 + lane; j < hi2; j += 32) {
+            const float4 P = sp[j];
+            const uint32_t key = skey[j];
+            const float2 w = level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh2, lv.inv_s[k2]);
+            m0 = ff_add_f(m0, P.z);
+            add_powers<P1B>(acc, P.z, w);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            m0 = ff_add(m0, make_float2(__shfl_xor_sync(0xffffffffu, m0.x, o), __shfl_xor_sync(0xffffffffu, m0.y, o)));
+        float* row = red[warp][lane];
+#pragma unroll
+        for (int m = 1; m < P1B; ++m) {
+            row[2 * m] = acc[m].x;
+            row[2 * m + 1] = acc[m].y;
+        }
         __syncwarp();
+        float2* A = reinterpret_cast<float2*>(g.A32[k2]) + cell2 * p1;
+        for (int col = 2 + lane; col < 2 * p1; col += 32) {
+            float s = 0.f;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) s += red[warp][r][col];
+            reinterpret_cast<float*>(A)[col] = s;
+        }
+        if (lane == 0) A[0] = m0;
+        __syncwarp();
+    }
+}
+
+template <int P1B>
+__global__ void __launch_bounds__(128)
+k_p2m_coarse(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int kc_max,
+             int p, MixedLevels lv, FmmLevelPtrs g) {
+    __shared__ float red[4][32][2 * P1B + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x * 4 + warp) * kCoarseChunk;
+    if (base >= n) return;
+    const int p1 = p + 1, ncol = 2 * p1;
+    float* row = red[warp][lane];
+    for (int k = 2; k <= kc_max; ++k) {
+        const int sh = levels - k;
         const int W = fmm_grid_width(k);
         double* A = reinterpret_cast<double*>(g.A[k]);
-        for (int col = lane; col < ncol; col += 32) {
-            float run = 0.f;
+        float2 acc[P1B];
 #pragma unroll
-            for (int rr = 0; rr < 32; ++rr) {
-                if (rr < nvalid) {
-                    run += rows[rr * stride + col];
-                    if ((ends >> rr) & 1u) {
-                        const uint32_t cur = bid[warp][rr];
-                        const size_t cell =
-                            (size_t)(fmm_compact2(cur >> 1) + FMM_HALO) * W + fmm_compact2(cur) + FMM_HALO;
-                        atomicAdd(A + cell * ncol + col, fmm_f2d_bits(run));
-                        run = 0.f;
+        for (int m = 0; m < P1B; ++m) acc[m] = make_float2(0.f, 0.f);
+        uint32_t cur = skey[base] >> (2 * sh);
+        auto flush = [&](uint32_t box) {
+#pragma unroll
+            for (int m = 0; m < P1B; ++m) {
+                row[2 * m] = acc[m].x;
+                row[2 * m + 1] = acc[m].y;
+                acc[m] = make_float2(0.f, 0.f);
+            }
+            __syncwarp();
+            const size_t cell = (size_t)(fmm_compact2(box >> 1) + FMM_HALO) * W + fmm_compact2(box) + FMM_HALO;
+            for (int col = lane; col < ncol; col += 32) {
+                float s = 0.f;
+#pragma unroll
+                for (int r = 0; r < 32; ++r) s += red[warp][r][col];
+                atomicAdd(A + cell * ncol + col, fmm_f2d_bits(s));
+            }
+            __syncwarp();
+        };
+        for (int r = 0; r < kCoarseChunk / 32; ++r) {
+            const int64_t j = base + 32 * r + lane;
+            const bool valid = j < n;
+            float2 c[P1B];
+            uint32_t bx = 0xffffffffu;
+            if (valid) {
+                const float4 P = sp[j];
+                const uint32_t key = skey[j];
+                bx = key >> (2 * sh);
+                const float2 w = level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh, lv.inv_s[k]);
+                c[0] = make_float2(P.z, 0.f);
+                float pr = P.z, pi = 0.f;
+#pragma unroll
+                for (int m = 1; m < P1B; ++m) {
+                    const float nr = fmaf(pr, w.x, -pi * w.y);
+                    const float ni = fmaf(pr, w.y, pi * w.x);
+                    pr = nr;
+                    pi = ni;
+                    c[m] = make_float2(pr, pi);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < P1B; ++m) c[m] = make_float2(0.f, 0.f);
+            }
+            // keys are sorted, so lanes with a square above cur are the ones not yet added; each
+            // pass adds at least one lane, so at most 32 passes close the chunk
+            for (int pass = 0; pass < 33; ++pass) {
+                if (valid && bx == cur) {
+#pragma unroll
+                    for (int m = 0; m < P1B; ++m) {
+                        acc[m].x += c[m].x;
+                        acc[m].y += c[m].y;
                     }
                 }
+                const unsigned later = __ballot_sync(0xffffffffu, valid && bx > cur);
+                if (!later) break;
+                flush(cur);
+                cur = __shfl_sync(0xffffffffu, bx, __ffs(later) - 1);
             }
+            if (!__any_sync(0xffffffffu, valid)) break;
         }
-        __syncwarp();
+        flush(cur);
     }
 }
 
@@ -397,17 +527,39 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     int launches = 0;
     cudaEventRecord(pl->ev[1], st);
     if (L >= 2) {
-        for (int k = 2; k <= L; ++k)
+        // fine levels: at most kFineMean particles per square on average
+        int kf = L;
+        while (kf > 2 && (n >> (2 * (kf - 1))) <= kFineMean) --kf;
+        const int kc_max = kf - 1;
+        for (int k = 2; k <= kc_max; ++k)
             if (cudaMemsetAsync(pl->grids.A[k], 0, pl->a_bytes[k], st) != cudaSuccess) return -1;
-        const int64_t warps = (n + 31) / 32;
-        const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-        const size_t shm = sizeof(float) * kWarpsPerBlock * 32 * (2 * p1 + 1);
-        if (shm > 48 * 1024 &&
-            cudaFuncSetAttribute(k_p2m_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess)
-            return -1;
-        k_p2m_mixed<<<blocks, kWarpsPerBlock * 32, shm, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids);
-        ++launches;
-        for (int k = 2; k <= L; ++k) {
+        P2MFineArgs fa{};
+        int acc = 0;
+        for (int k = kf; k <= L; ++k) {
+            fa.base[k] = acc;
+            acc += 1 << (2 * k);
+        }
+        fa.base[L + 1] = acc;
+        fa.kf = kf;
+        fa.levels = L;
+        fa.p = p;
+        const unsigned fblocks = (unsigned)((acc + 127) / 128);
+        const unsigned cblocks = (unsigned)((n + 4 * kCoarseChunk - 1) / (4 * kCoarseChunk));
+        switch (pl->p1b) {
+#define FMM_P2M(PB)                                                                                          \
+    case PB:                                                                                                 \
+        k_p2m_fine<PB><<<fblocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, pl->leaf_start, fa, lv,        \
+                                                pl->grids);                                                  \
+        if (kc_max >= 2)                                                                                     \
+            k_p2m_coarse<PB><<<cblocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, kc_max, p, lv,     \
+                                                      pl->grids);                                            \
+        break;
+            FMM_P2M(9) FMM_P2M(13) FMM_P2M(17) FMM_P2M(21) FMM_P2M(25) FMM_P2M(33) FMM_P2M(41)
+#undef FMM_P2M
+            default: return -2;
+        }
+        launches += kc_max >= 2 ? 2 : 1;
+        for (int k = 2; k <= kc_max; ++k) {
             const int64_t count = (int64_t)fmm_grid_width(k) * fmm_grid_width(k) * p1;
             k_prep_a32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(
                 reinterpret_cast<const double2*>(pl->grids.A[k]), reinterpret_cast<float2*>(pl->grids.A32[k]), count,
