@@ -8,12 +8,14 @@
 // outputs (N = 2H: Re b'_0..b'_p then Im b'_0..b'_p, each padded to H) and kk the inputs
 // (K = 2H per offset: Re M_0..M_p then Im M_0..M_p).  The 27 offsets of the class fall into 12
 // groups that share one source window: the source parity (qx, qy) and the source row shift sy.
-// One TMA load brings a window of 130 source cells (128 targets plus one on each side) into
-// shared memory in the canonical no-swizzle K-major layout (16-byte core-matrix rows, K-chunk
-// stride LBO = 130 x 16 B); the three column shifts of a group are then the same window read
-// from a descriptor start moved by 16 B per cell.  The operators of a group arrive by one bulk
-// copy.  A single thread issues the MMAs; the accumulator lives in tensor memory and the
-// epilogue reads it back with tcgen05.ld.
+// A window of 130 source cells (128 targets plus one on each side) is one contiguous run of
+// the K-contiguous source layout in global memory; the CTA's 128 threads copy it with 16-byte
+// cp.async into shared memory in the canonical no-swizzle K-major layout (16-byte core-matrix
+// rows, K-chunk stride LBO = 130 x 16 B), completing on the stage's mbarrier.  The three column
+// shifts of a group are then the same window read from a descriptor start moved by 16 B per
+// cell.  The operators of a group arrive by one bulk copy (cp.async.bulk).  A single thread
+// issues the MMAs; the accumulator lives in tensor memory and the epilogue reads it back with
+// tcgen05.ld.
 //
 // 3xTF32 (Ootomo & Yokota, 2022): x = x_hi + x_lo with x_hi rounded to TF32, and
 // D += A_hi B_hi + A_hi B_lo + A_lo B_hi, dropping A_lo B_lo, recovers about FP32 accuracy.
@@ -21,8 +23,6 @@
 // The monopole-log term of b'_0, sum_d M_0 (log|w0| + ln s), is not in the GEMM: the epilogue
 // sums it in float-float from the FP32 moment grid.  Every wait on an mbarrier is bounded and
 // sets a status flag when it runs out.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 
 #include <cstring>
 #include <vector>
@@ -44,7 +44,7 @@ struct TcGroup {
 };
 
 struct TcArgs {
-    CUtensorMap tmap[2][FMM_MAX_LEVELS + 1];   // [part][level]
+    const float* src[2][FMM_MAX_LEVELS + 1];   // [part][level] -> [q][w2+2][w2+2][K] (1-cell zero halo)
     const float* ops[2];                       // [part] -> [class][27 slots][KC][N][4]
     const float2* a32[FMM_MAX_LEVELS + 1];     // FP32 moment grids (3-cell halo) for the monopole term
     float2* B[FMM_MAX_LEVELS + 1];
@@ -134,7 +134,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        for (int b = 0; b < 2 * NS + 1; ++b)
+        // full[s]: one arrival per thread after its copies land, plus thread 0's expect_tx arrival
+        for (int b = 0; b < NS; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bars[b])), "r"(kThreads + 1) : "memory");
+        for (int b = NS; b < 2 * NS + 1; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[b])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -143,26 +146,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
 
-    // ---- producer + MMA issuer: one thread
-    if (threadIdx.x == 0) {
-        bool ok = true;
-        for (int g = 0; g < 12 && ok; ++g) {
-            const int s = g % NS, use = g / NS;
-            const TcGroup& G = a.groups[cls][g];
-            const uint32_t full = su32(&bars[s]), empty = su32(&bars[NS + s]);
-            if (g >= NS) ok = wait_bar(empty, (uint32_t)((use - 1) & 1));
-            if (!ok) break;
-            const uint32_t bytes = NP * (A_BYTES + (uint32_t)G.nops * OP_BYTES);
+    // ---- all threads copy the source windows; thread 0 also fetches the operators and issues MMAs
+    const int W2P = w2 + 2;
+    bool ok = true;
+    for (int g = 0; g < 12; ++g) {
+        const int s = g % NS, use = g / NS;
+        const TcGroup& G = a.groups[cls][g];
+        const uint32_t full = su32(&bars[s]), empty = su32(&bars[NS + s]);
+        if (g >= NS && !wait_bar(empty, (uint32_t)((use - 1) & 1))) ok = false;
+        const int q = G.qx + 2 * G.qy;
+        // the window: global cells (row y + sy + 1, cols u0 .. u0 + 129) of parity q, contiguous
+        const size_t cell0 = ((size_t)q * W2P + (size_t)(y + G.sy + 1)) * W2P + (size_t)u0;
+        for (int part = 0; part < NP; ++part) {
+            const uint8_t* gsrc = reinterpret_cast<const uint8_t*>(a.src[part][k] + cell0 * (4 * KC));
+            const uint32_t dst = su32(smem + s * STAGE + part * A_BYTES);
+            for (int e = threadIdx.x; e < kWin * KC; e += kThreads) {
+                const int c = e / KC, j = e - c * KC;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)(j * kWin + c) * 16u),
+                             "l"(gsrc + (size_t)e * 16)
+                             : "memory");
+            }
+        }
+        // each thread waits for its own copies, makes them visible to the tensor core's (async)
+        // proxy, then arrives
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full) : "memory");
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = NP * (uint32_t)G.nops * OP_BYTES;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(bytes) : "memory");
-            const int q = G.qx + 2 * G.qy;
             for (int part = 0; part < NP; ++part) {
-                const uint32_t dstA = su32(smem + s * STAGE + part * A_BYTES);
-                asm volatile(
-                    "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                    " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dstA),
-                    "l"(reinterpret_cast<uint64_t>(&a.tmap[part][k])), "r"(0), "r"(u0 - 1), "r"(y + G.sy), "r"(0),
-                    "r"(q), "r"(full)
-                    : "memory");
                 const uint32_t dstB = su32(smem + s * STAGE + NP * A_BYTES + part * 3 * OP_BYTES);
                 const float* srcB = a.ops[part] + ((size_t)cls * 27 + G.slot0) * (OP_BYTES / 4);
                 asm volatile(
@@ -171,15 +184,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                     "l"(srcB), "r"((uint32_t)G.nops * OP_BYTES), "r"(full)
                     : "memory");
             }
-            ok = wait_bar(full, (uint32_t)(use & 1));
-            if (!ok) {
-                wait_bar(full, (uint32_t)(use & 1));   // give copies still in flight a second bounded wait
-                break;
-            }
+            if (!wait_bar(full, (uint32_t)(use & 1))) ok = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t aBase = su32(smem + s * STAGE);
             const uint32_t bBase = su32(smem + s * STAGE + NP * A_BYTES);
-            for (int o = 0; o < G.nops; ++o) {
+            for (int o = 0; o < G.nops && ok; ++o) {
                 const uint32_t aoff = (uint32_t)(1 + G.sx[o]) * 16u;
 #pragma unroll
                 for (int ks = 0; ks < KC / 2; ++ks) {
@@ -200,13 +209,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty)
                          : "memory");
         }
+    }
+    if (threadIdx.x == 0) {
         // the final commit tracks every MMA issued above
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          su32(&bars[2 * NS]))
                      : "memory");
-        if (!ok) atomicOr(a.status, FMM_FLAG_TIMEOUT);
     }
-    __syncwarp();
+    if (!ok) atomicOr(a.status, FMM_FLAG_TIMEOUT);
     const bool done = wait_bar(su32(&bars[2 * NS]), 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
@@ -250,7 +260,7 @@ template <int KC, int NP>
 __global__ void k_prep_tc(const float2* __restrict__ a32, int k, int p1, float4* __restrict__ hi,
                           float4* __restrict__ lo) {
     constexpr int H = 2 * KC;
-    const int w2 = 1 << (k - 1);
+    const int w2 = 1 << (k - 1), W2P = w2 + 2;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= 4ll * w2 * w2) return;
     const int col = (int)(e % w2), row = (int)((e / w2) % w2), q = (int)(e / ((int64_t)w2 * w2));
@@ -264,7 +274,7 @@ __global__ void k_prep_tc(const float2* __restrict__ a32, int k, int p1, float4*
         vals[j] = m.x;                     // coefficient 0 holds M_0's high word: M_0 is real
         vals[H + j] = (j == 0) ? 0.f : m.y;
     }
-    const size_t plane = (size_t)w2 * w2;
+    const size_t cell = ((size_t)q * W2P + (size_t)(row + 1)) * W2P + (size_t)(col + 1);
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
         float h[4], l[4];
@@ -274,9 +284,8 @@ __global__ void k_prep_tc(const float2* __restrict__ a32, int k, int p1, float4*
             h[t] = tf32_rna(v);
             l[t] = v - h[t];
         }
-        const size_t off = ((size_t)q * KC + c) * plane + (size_t)row * w2 + col;
-        hi[off] = make_float4(h[0], h[1], h[2], h[3]);
-        if (NP == 2) lo[off] = make_float4(l[0], l[1], l[2], l[3]);
+        hi[cell * KC + c] = make_float4(h[0], h[1], h[2], h[3]);
+        if (NP == 2) lo[cell * KC + c] = make_float4(l[0], l[1], l[2], l[3]);
     }
 }
 
@@ -317,20 +326,6 @@ struct FmmTc {
 };
 
 int fmm_tc_kmin() { return kMinLevel; }
-
-static PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* ptr = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return nullptr;
-        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    }
-    return fn;
-}
 
 // Allocate and build the tensor-core M2L state.  Returns 0, or a negative value on failure
 // (-1 CUDA error, -2 unsupported p).
@@ -411,23 +406,15 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
             return -1;
         tc->args.ops[part] = tc->ops[part];
     }
-    // source buffers and their tensor maps, levels kMinLevel..L
-    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encoder();
-    if (!enc) return -1;
+    // source buffers (K-contiguous, 1-cell zero halo), levels kMinLevel..L
     for (int k = kMinLevel; k <= pl->levels; ++k) {
-        const uint64_t w2 = 1ull << (k - 1);
-        const size_t bytes = (size_t)4 * kc * w2 * w2 * 16;
+        const size_t w2p = ((size_t)1 << (k - 1)) + 2;
+        const size_t bytes = (size_t)4 * w2p * w2p * kc * 16;
         for (int part = 0; part < np; ++part) {
             if (cudaMalloc(&tc->src[part][k], bytes) != cudaSuccess) return -1;
             pl->workspace_bytes += bytes;
-            cuuint64_t dims[5] = {4, w2, w2, (cuuint64_t)kc, 4};
-            cuuint64_t strides[4] = {16, 16 * w2, 16 * w2 * w2, 16 * w2 * w2 * (cuuint64_t)kc};
-            cuuint32_t box[5] = {4, (cuuint32_t)kWin, 1, (cuuint32_t)kc, 1};
-            cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-            if (enc(&tc->args.tmap[part][k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, tc->src[part][k], dims, strides, box,
-                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                return -1;
+            if (cudaMemset(tc->src[part][k], 0, bytes) != cudaSuccess) return -1;
+            tc->args.src[part][k] = reinterpret_cast<const float*>(tc->src[part][k]);
         }
     }
     return 0;
