@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--batched", action="store_true",
+                    help="also time the batched form on 1024 systems (N log-uniform in [1024, 262144]) "
+                         "against a loop of single-system launches")
+    ap.add_argument("--batched-systems", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -330,6 +334,10 @@ def run_ours(args):
         p64.close()
     plan.close()
 
+    batched = None
+    if args.batched:
+        batched = run_batched(binding, torch, dev, args.batched_systems, max(3, min(args.steps, 20)), 3)
+
     cpu = None
     if rank == 0 and not args.no_cpu and ws == 1:
         cpu = cpu_baseline(w, xy, q)
@@ -347,13 +355,80 @@ def run_ours(args):
             "stage_ms": stage_avg, "roofline": roof, "roofline_stages": roof_all,
             "gpu_launches": launches, "e2e": e2e, "fp64_gpu": fp64,
             "speedup_vs_fp64_gpu": (value / fp64["value"]) if fp64 else None,
-            "cpu_baseline": cpu, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+            "cpu_baseline": cpu, "batched": batched, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                                             "reasons": clk["reasons"], "samples": clk["samples"]},
             "wall_s_timed": wall,
         }
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------- batched form
+
+def batched_workload(nsys, seed=20094767):
+    """1024 independent systems: N log-uniform in [1024, 262144], uniform or a Gaussian mixture
+    per system (the clustered recipe: 32 Gaussians, sigma log-uniform in [0.01, 0.3]),
+    q ~ U[-1, 1], depth round(log4(N / 16)) clamped to >= 2, p = 16."""
+    from paper_2009_00767_gb300 import inputs
+    u = inputs.u01(seed, 31, nsys)
+    fam = inputs.u01(seed, 32, nsys)
+    ns = np.exp(np.log(1024) + (np.log(262144) - np.log(1024)) * u).astype(np.int64)
+    levels = np.maximum(2, np.rint(np.log(ns / 16.0) / np.log(4.0))).astype(np.int32)
+    xys, qs = [], []
+    for i in range(nsys):
+        if fam[i] < 0.5:
+            xy, q = inputs.uniform(int(ns[i]), seed + 17 * i)
+        else:
+            xy, q = inputs.gmm(int(ns[i]), seed + 17 * i)
+        xys.append(xy)
+        qs.append(q)
+    return ns, levels, np.concatenate(xys), np.concatenate(qs)
+
+
+def run_batched(binding, torch, dev, nsys, steps, warmup):
+    ns, levels, xy, q = batched_workload(nsys)
+    total = int(ns.sum())
+    xy_d = torch.from_numpy(xy).to(dev)
+    q_d = torch.from_numpy(q).to(dev)
+    phi = torch.empty(total, dtype=torch.float64, device=dev)
+    b = binding.Batch(ns, levels, 16)
+    grid_mult = binding.fmm_batch_autotune(b.handle, xy_d, q_d, phi)
+    for _ in range(warmup):
+        binding.fmm_batch_potential(b.handle, xy_d, q_d, phi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        binding.fmm_batch_potential(b.handle, xy_d, q_d, phi)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / steps
+    binding.fmm_batch_sync(b.handle)
+    launches = binding.fmm_batch_launches(b.handle)
+    b.close()
+    # the same systems as a loop of single-system plans (one launch sequence per system)
+    off = np.concatenate([[0], np.cumsum(ns)])
+    plans = [binding.Plan(int(ns[i]), int(levels[i]), 16, 5.0, "fp32") for i in range(nsys)]
+    views = [(xy_d[off[i]:off[i + 1]], q_d[off[i]:off[i + 1]], phi[off[i]:off[i + 1]]) for i in range(nsys)]
+    for _ in range(max(1, warmup // 2)):
+        for pl, (x, qq, ph) in zip(plans, views):
+            binding.fmm_potential(pl.handle, x, qq, ph)
+    torch.cuda.synchronize()
+    loop_steps = max(1, steps // 4)
+    e0.record()
+    for _ in range(loop_steps):
+        for pl, (x, qq, ph) in zip(plans, views):
+            binding.fmm_potential(pl.handle, x, qq, ph)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1) / loop_steps
+    for pl in plans:
+        pl.close()
+    return {"systems": nsys, "particles": total, "ms_per_step": ms_batch, "value": total / (ms_batch * 1e-3),
+            "unit": UNIT, "loop_ms_per_step": ms_loop, "loop_value": total / (ms_loop * 1e-3),
+            "speedup_vs_loop": ms_loop / ms_batch, "graph_launches_per_step": launches, "grid_mult": grid_mult,
+            "precision": "fp32", "p": 16}
 
 
 # ---------------------------------------------------------------- CPU oracle

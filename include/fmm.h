@@ -151,6 +151,44 @@ const char* fmm_status_string(int status);
 fmm_status fmm_direct_targets(int64_t n, const double* xy, const double* q, int64_t n_targets,
                               const int64_t* targets, double* phi_t, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched form: many independent systems of uneven size, each an independent instance of
+ * the method above (its own box [0, box]^2 and quadtree depth), evaluated by one launch per
+ * stage that spans all systems, replayed as one CUDA graph.  Mixed FP32 precision only.
+ * --------------------------------------------------------------------------------------- */
+typedef struct fmm_batch_s* fmm_batch_t;
+
+/* Create a batch plan for nsys systems (1 <= nsys <= 1536; total particles < 2^31).
+ *   n[i], levels[i]  host arrays: particles (>= 1) and quadtree depth (0..12) of system i.
+ *   p, box           expansion order and box side shared by all systems.
+ *   precision        FMM_MIXED_FP32 (others return FMM_ERR_UNSUPPORTED).
+ *   stream           cudaStream_t the calls run on (NULL = default stream).
+ * Allocates every workspace, builds the operators and captures the launch sequence into a
+ * CUDA graph. */
+fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const int* levels, int p,
+                          double box, int precision, void* stream);
+
+/* phi of every system: xy [sum n][2], q [sum n], phi [sum n] are device arrays with the
+ * systems concatenated in order (system i starts at n[0] + ... + n[i-1]).  Asynchronous;
+ * allocates nothing; errors found on the device are reported by fmm_batch_sync. */
+fmm_status fmm_batch_potential(fmm_batch_t batch, const double* xy, const double* q, double* phi);
+
+/* Wait for the batch's stream; return the device-detected status of the calls since the
+ * last sync and clear it.  ms (may be NULL) receives the device time of the last call. */
+fmm_status fmm_batch_sync(fmm_batch_t batch, double* ms);
+
+/* Time the batch on the given inputs for several persistent grid sizes (blocks per SM),
+ * keep the fastest and rebuild the graph.  grid_mult_out (may be NULL) receives it.  Runs
+ * and waits for several calls on the batch's stream. */
+fmm_status fmm_batch_autotune(fmm_batch_t batch, const double* xy, const double* q, double* phi,
+                              int* grid_mult_out);
+
+/* Kernels (and memsets) the batch graph launches per call, or -1 for NULL. */
+int fmm_batch_launches(fmm_batch_t batch);
+
+/* Free the batch plan and everything it owns.  NULL is ignored. */
+void fmm_batch_destroy(fmm_batch_t batch);
+
 /* The FP64 method of fmm_potential for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a library convenience.  Some callers cannot call
  * cudaMalloc -- a loop that forbids allocation once it has started, a device whose free

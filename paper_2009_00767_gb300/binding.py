@@ -61,6 +61,12 @@ SIGNATURES = {
     "fmm_status_string": (ctypes.c_char_p, [_i32]),
     "fmm_direct_targets": (_i32, [_i64, _vp, _vp, _i64, _vp, _vp, _vp]),
     "fmm_potential_noalloc": (_i32, [_i64, _i32, _i32, _d, _vp, _vp, _vp, _vp]),
+    "fmm_batch_plan": (_i32, [ctypes.POINTER(_vp), _i32, _vp, _vp, _i32, _d, _i32, _vp]),
+    "fmm_batch_potential": (_i32, [_vp, _vp, _vp, _vp]),
+    "fmm_batch_sync": (_i32, [_vp, ctypes.POINTER(_d)]),
+    "fmm_batch_autotune": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(_i32)]),
+    "fmm_batch_launches": (_i32, [_vp]),
+    "fmm_batch_destroy": (None, [_vp]),
 }
 
 
@@ -171,6 +177,78 @@ def fmm_potential_noalloc(xy, q, phi, levels: int, p: int, box: float = 5.0, str
     """FP64 potential without a plan or any device allocation (n <= 65536, levels <= 6, p <= 20)."""
     _check(_lib.fmm_potential_noalloc(int(q.shape[0]), int(levels), int(p), float(box), _ptr(xy), _ptr(q),
                                       _ptr(phi), _stream_handle(stream)), "fmm_potential_noalloc")
+
+
+def fmm_batch_plan(n, levels, p: int, box: float = 5.0, precision="fp32", stream=None) -> int:
+    """Batch plan for len(n) independent systems (see include/fmm.h); returns the handle."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    na = np.ascontiguousarray(n, dtype=np.int64)
+    la = np.ascontiguousarray(levels, dtype=np.int32)
+    h = _vp()
+    _check(_lib.fmm_batch_plan(ctypes.byref(h), int(na.shape[0]), na.ctypes.data, la.ctypes.data, int(p), float(box),
+                               prec, _stream_handle(stream)), "fmm_batch_plan")
+    return h.value
+
+
+def fmm_batch_potential(batch: int, xy, q, phi):
+    _check(_lib.fmm_batch_potential(batch, _ptr(xy), _ptr(q), _ptr(phi)), "fmm_batch_potential")
+
+
+def fmm_batch_sync(batch: int, check: bool = True):
+    ms = _d(0.0)
+    s = _lib.fmm_batch_sync(batch, ctypes.byref(ms))
+    if check:
+        _check(s, "fmm_batch_sync")
+    return s, ms.value
+
+
+def fmm_batch_autotune(batch: int, xy, q, phi) -> int:
+    g = _i32(0)
+    _check(_lib.fmm_batch_autotune(batch, _ptr(xy), _ptr(q), _ptr(phi), ctypes.byref(g)), "fmm_batch_autotune")
+    return g.value
+
+
+def fmm_batch_launches(batch: int) -> int:
+    return int(_lib.fmm_batch_launches(batch))
+
+
+def fmm_batch_destroy(batch: int):
+    _lib.fmm_batch_destroy(batch)
+
+
+class Batch:
+    """Owner of one fmm_batch_plan handle."""
+
+    def __init__(self, n, levels, p, box=5.0, precision="fp32", stream=None):
+        self.n = np.asarray(n, dtype=np.int64)
+        self.levels = np.asarray(levels, dtype=np.int32)
+        self.handle = fmm_batch_plan(self.n, self.levels, p, box, precision, stream)
+
+    def potential(self, xy, q, phi=None, sync=True):
+        import torch
+        if phi is None:
+            phi = torch.empty(int(self.n.sum()), dtype=torch.float64, device=xy.device)
+        fmm_batch_potential(self.handle, xy, q, phi)
+        if sync:
+            fmm_batch_sync(self.handle)
+        return phi
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fmm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Plan:

@@ -16,45 +16,8 @@ namespace {
 
 constexpr int kScanThreads = 256;
 
-// a * (s.x + s.y) as an FP32 pair (FMA-exact product of the high word)
-__device__ __forceinline__ float2 scatter_mul(float a, float2 s) {
-    const float h = a * s.x;
-    const float e = fmaf(a, s.x, -h) + a * s.y;
-    const float hh = h + e;
-    return make_float2(hh, e - (hh - h));
-}
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
-
-// Finest-square coordinate floor(fl(x 2^l / box)) clamped to [0, side - 1], the rule the oracle
-// uses, without occupying the narrow FP64 pipe in the common case: an FP32 estimate of the
-// quotient (error below 1e-3 for side <= 4096) decides whenever it is more than 2e-3 away from
-// an integer; otherwise the exact FP64 division decides.  t = x 2^l is exact.
-__device__ __forceinline__ int finest_coord(double x, double scale, float scale_over_box32, double box, int side) {
-    const float2 xf = fmm_d2ff_bits(x);   // hi word: x truncated to 24 bits
-    const float q32 = xf.x * scale_over_box32;
-    const float fl = floorf(q32);
-    const float fr = q32 - fl;
-    float f;
-    if (fr > 2e-3f && fr < 1.0f - 2e-3f) {
-        f = fl;
-    } else {
-        f = (float)floor(x * scale / box);
-    }
-    return f < 0.f ? 0 : (f > (float)(side - 1) ? side - 1 : (int)f);
-}
-
-// x in [0, box] for finite x, by integer comparison of the bit patterns (monotone for
-// non-negative doubles; -0.0 counts as 0).
-__device__ __forceinline__ bool in_box_bits(double x, long long box_bits) {
-    const long long b = __double_as_longlong(x);
-    if (b == (long long)0x8000000000000000ull) return true;
-    return b >= 0 && b <= box_bits;
-}
-
-__device__ __forceinline__ bool finite_bits(double x) {
-    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
-}
 
 __global__ void k_bin(const double2* __restrict__ xy, const double* __restrict__ q, int64_t n, int levels,
                       double box, float scale_over_box32, uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
@@ -217,3 +180,12 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
 }
 
 int fmm_scan_blocks(int64_t m) { return (int)((m + kScanTile - 1) / kScanTile); }
+
+int fmm_launch_scan(const uint32_t* counts, int64_t m, uint32_t* block_sums, uint32_t* leaf_start, uint32_t n_total,
+                    cudaStream_t st) {
+    const int nb = fmm_scan_blocks(m);
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(counts, m, block_sums);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(block_sums, nb);
+    k_scan_down<<<nb, kScanThreads, 0, st>>>(counts, m, block_sums, leaf_start, n_total);
+    return cudaGetLastError() == cudaSuccess ? 3 : -1;
+}
