@@ -68,7 +68,8 @@ void free_plan(fmm_plan_s* pl) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(pl->device);
-    void* bufs[] = {pl->keys, pl->rank, pl->counts, pl->leaf_start, pl->block_sums, pl->sorted_key,
+    void* bufs[] = {pl->keys, pl->rank, pl->counts, pl->leaf_start, pl->block_sums, pl->leaf_nb, pl->leaf_bstart,
+                    pl->sorted_key,
                     pl->sorted64, pl->sorted32, pl->phi_far, pl->T64, pl->T32, pl->d_status,
                     pl->d_counters, pl->d_xy_stage, pl->d_q_stage, pl->d_phi_stage};
     for (void* b : bufs)
@@ -166,7 +167,11 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->counts, sizeof(uint32_t) * m));
     FMM_TRY(dev_alloc(pl, &pl->leaf_start, sizeof(uint32_t) * (m + 1)));
     pl->scan_blocks = fmm_scan_blocks(m);
-    FMM_TRY(dev_alloc(pl, &pl->block_sums, sizeof(uint32_t) * pl->scan_blocks));
+    FMM_TRY(dev_alloc(pl, &pl->block_sums, sizeof(uint32_t) * (pl->scan_blocks + 1)));
+    if (precision != FMM_FP64) {
+        FMM_TRY(dev_alloc(pl, &pl->leaf_nb, sizeof(uint32_t) * m));
+        FMM_TRY(dev_alloc(pl, &pl->leaf_bstart, sizeof(uint32_t) * (m + 1)));
+    }
     FMM_TRY(dev_alloc(pl, &pl->sorted_key, sizeof(uint32_t) * n));
     if (precision == FMM_FP64)
         FMM_TRY(dev_alloc(pl, &pl->sorted64, sizeof(fmm_p64) * n));

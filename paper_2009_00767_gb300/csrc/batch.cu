@@ -55,6 +55,8 @@ struct BatchArgs {
     uint32_t* rank;
     uint32_t* counts;
     uint32_t* leaf_start;
+    const uint32_t* bstart;   // near-field target blocks: exclusive scan over the concatenated squares
+    long long nl;             // concatenated finest squares
     uint32_t* sorted_key;
     float4* sorted32;
     double* a64;     // coarse moment grids (FP64, atomics)
@@ -458,7 +460,7 @@ __global__ void __launch_bounds__(kT) kb_p2p(BatchArgs a, MixedLevels lv) {
     __shared__ __align__(16) float4 buf[kT / 32][kP2PCap];
     __shared__ __align__(8) uint64_t bar[kT / 32];
     load_prefix(pre, a.wp_leaf, a.nsys);
-    const long long total = pre[a.nsys];
+    const long long total = a.bstart[a.nl];   // target blocks of up to 32 over all squares
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&bar[warp]);
     if (lane == 0) {
@@ -469,15 +471,16 @@ __global__ void __launch_bounds__(kT) kb_p2p(BatchArgs a, MixedLevels lv) {
     uint32_t phase = 0;
     const bool bad = *(volatile const unsigned int*)a.status != 0u;
     double* phi = a.call->phi;
-    for (long long gl = (long long)blockIdx.x * (kT / 32) + warp; gl < total && !bad;
-         gl += (long long)gridDim.x * (kT / 32)) {
+    for (long long w = (long long)blockIdx.x * (kT / 32) + warp; w < total && !bad;
+         w += (long long)gridDim.x * (kT / 32)) {
+        const uint32_t gl = fmm_warp_search(a.bstart, (uint32_t)a.nl, (uint32_t)w, lane);
+        const uint32_t tb = (uint32_t)w - a.bstart[gl];
         const int s = find_sys(pre, a.nsys, gl);
         const BatchSys& S = a.sys[s];
         const uint32_t leaf = (uint32_t)(gl - pre[s]);
         const uint32_t* ls = a.leaf_start + S.leaf_off;
-        const uint32_t t0 = ls[leaf], t1 = ls[leaf + 1];
-        const int T = (int)(t1 - t0);
-        if (T == 0) continue;
+        const uint32_t t0 = ls[leaf] + 32u * tb, t1 = ls[leaf + 1];
+        const int T = (int)min(32u, t1 - t0);
         const int side = 1 << S.levels;
         const float s_leaf = a.box_ff.x * __int_as_float((127 - S.levels) << 23);
         const int ix = (int)fmm_compact2(leaf), iy = (int)fmm_compact2(leaf >> 1);
@@ -529,55 +532,55 @@ __global__ void __launch_bounds__(kT) kb_p2p(BatchArgs a, MixedLevels lv) {
             __syncwarp();
         }
         int tp = 1;
-        while (tp < T && tp < 32) tp <<= 1;
+        while (tp < T) tp <<= 1;
         const uint32_t groups = 32 / tp;
         const int slot = lane & (tp - 1);
         const uint32_t grp = lane / tp;
-        for (int tb = 0; tb < T; tb += tp) {
-            const int ti = tb + slot;
-            const bool active = ti < T;
-            const float4 Pi = a.sorted32[t0 + (active ? ti : 0)];
-            float2 near = make_float2(0.f, 0.f);
-            if (staged) {
-                const float4* src = buf[warp];
-                float acc0 = 0.f, acc1 = 0.f;
-                uint32_t j = grp;
-                for (; j + 3u * groups < nsrc; j += 4u * groups) {
-                    const float4 a0 = src[j], a1 = src[j + groups], a2 = src[j + 2u * groups],
-                                 a3 = src[j + 3u * groups];
-                    acc0 = fmaf(a0.z, lg2_pair(Pi.x - a0.x, Pi.y - a0.y), acc0);
-                    acc1 = fmaf(a1.z, lg2_pair(Pi.x - a1.x, Pi.y - a1.y), acc1);
-                    acc0 = fmaf(a2.z, lg2_pair(Pi.x - a2.x, Pi.y - a2.y), acc0);
-                    acc1 = fmaf(a3.z, lg2_pair(Pi.x - a3.x, Pi.y - a3.y), acc1);
-                }
-                for (; j < nsrc; j += groups) {
-                    const float4 a0 = src[j];
-                    acc0 = fmaf(a0.z, lg2_pair(Pi.x - a0.x, Pi.y - a0.y), acc0);
-                }
-                near = make_float2(acc0 + acc1, 0.f);
-            } else {
+        const bool active = slot < T;
+        const uint32_t gi = t0 + (active ? slot : 0);
+        const float4 Pi = a.sorted32[gi];
+        float2 near = make_float2(0.f, 0.f);
+        if (staged) {
+            const float4* src = buf[warp];
+            float acc0 = 0.f, acc1 = 0.f;
+            uint32_t j = grp;
+            for (; j + 3u * groups < nsrc; j += 4u * groups) {
+                const float4 a0 = src[j], a1 = src[j + groups], a2 = src[j + 2u * groups], a3 = src[j + 3u * groups];
+                acc0 = fmaf(a0.z, lg2_pair(Pi.x - a0.x, Pi.y - a0.y), acc0);
+                acc1 = fmaf(a1.z, lg2_pair(Pi.x - a1.x, Pi.y - a1.y), acc1);
+                acc0 = fmaf(a2.z, lg2_pair(Pi.x - a2.x, Pi.y - a2.y), acc0);
+                acc1 = fmaf(a3.z, lg2_pair(Pi.x - a3.x, Pi.y - a3.y), acc1);
+            }
+            for (; j < nsrc; j += groups) {
+                const float4 a0 = src[j];
+                acc0 = fmaf(a0.z, lg2_pair(Pi.x - a0.x, Pi.y - a0.y), acc0);
+            }
+            near = make_float2(acc0 + acc1, 0.f);
+        } else {
 #pragma unroll
-                for (int b = 0; b < 9; ++b) {
-                    const float bx = Pi.x - (float)((b % 3) - 1) * s_leaf;
-                    const float by = Pi.y - (float)((b / 3) - 1) * s_leaf;
-                    const float4* src = a.sorted32 + nb0[b];
+            for (int b = 0; b < 9; ++b) {
+                const float bx = Pi.x - (float)((b % 3) - 1) * s_leaf;
+                const float by = Pi.y - (float)((b / 3) - 1) * s_leaf;
+                const float4* src = a.sorted32 + nb0[b];
+                for (uint32_t r0 = 0; r0 < ncnt[b]; r0 += kP2PCap) {
+                    const uint32_t r1 = min(ncnt[b], r0 + kP2PCap);
                     float acc = 0.f;
-                    for (uint32_t j = grp; j < ncnt[b]; j += groups) {
+                    for (uint32_t j = r0 + grp; j < r1; j += groups) {
                         const float4 Pj = src[j];
                         acc = fmaf(Pj.z, lg2_pair(bx - Pj.x, by - Pj.y), acc);
                     }
                     near = ff_add_f(near, acc);
                 }
             }
-            for (int o = tp; o < 32; o <<= 1) {
-                const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, near.x, o),
-                                                 __shfl_xor_sync(0xffffffffu, near.y, o));
-                near = ff_add(near, other);
-            }
-            if (active && grp == 0) {
-                const float2 v = ff_add(a.far[t0 + ti], ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
-                phi[S.p_off + __float_as_int(Pi.w)] = fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);
-            }
+        }
+        for (int o = tp; o < 32; o <<= 1) {
+            const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, near.x, o),
+                                             __shfl_xor_sync(0xffffffffu, near.y, o));
+            near = ff_add(near, other);
+        }
+        if (active && grp == 0) {
+            const float2 v = ff_add(a.far[gi], ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
+            phi[S.p_off + __float_as_int(Pi.w)] = fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);
         }
         __syncwarp();
     }
@@ -598,7 +601,7 @@ struct fmm_batch_s {
     long long* d_pre;                 // 5 prefix arrays, (nsys + 1) each
     BatchCall* d_call;
     BatchCall* h_call;                // pinned
-    uint32_t *keys, *rank, *counts, *leaf_start, *block_sums, *sorted_key;
+    uint32_t *keys, *rank, *counts, *leaf_start, *block_sums, *sorted_key, *leaf_nb, *bstart;
     float4* sorted32;
     double* a64;
     float2 *a32, *b32, *far;
@@ -619,6 +622,7 @@ void batch_free(fmm_batch_s* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     void* bufs[] = {b->d_sys, b->d_pre, b->d_call, b->keys, b->rank, b->counts, b->leaf_start, b->block_sums,
+                    b->leaf_nb, b->bstart,
                     b->sorted_key, b->sorted32, b->a64, b->a32, b->b32, b->far, b->T32, b->d_status};
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -668,8 +672,10 @@ int enqueue_batch_kernels(fmm_batch_s* b, const BatchArgs& a, const MixedLevels&
     }
     kb_m2l_f32<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
     kb_l2p<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
+    const int lb = fmm_launch_leaf_blocks(b->leaf_start, b->nl, b->leaf_nb, b->block_sums, b->bstart, st);
+    if (lb < 0) return -1;
     kb_p2p<<<grid, kT, pre_bytes, st>>>(a, lv);
-    launches += 3;
+    launches += 3 + lb;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
@@ -692,6 +698,8 @@ int enqueue_all(fmm_batch_s* b, cudaStream_t st) {
     a.rank = b->rank;
     a.counts = b->counts;
     a.leaf_start = b->leaf_start;
+    a.bstart = b->bstart;
+    a.nl = b->nl;
     a.sorted_key = b->sorted_key;
     a.sorted32 = b->sorted32;
     a.a64 = b->a64;
@@ -845,7 +853,8 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
     bool ok = balloc(b, &b->d_sys, sizeof(BatchSys) * nsys) && balloc(b, &b->d_pre, sizeof(long long) * pre.size()) &&
               balloc(b, &b->d_call, sizeof(BatchCall)) && balloc(b, &b->keys, 4 * nt) && balloc(b, &b->rank, 4 * nt) &&
               balloc(b, &b->counts, 4 * nl) && balloc(b, &b->leaf_start, 4 * (nl + 1)) &&
-              balloc(b, &b->block_sums, 4 * (size_t)fmm_scan_blocks(nl)) && balloc(b, &b->sorted_key, 4 * nt) &&
+              balloc(b, &b->block_sums, 4 * ((size_t)fmm_scan_blocks(nl) + 1)) && balloc(b, &b->sorted_key, 4 * nt) &&
+              balloc(b, &b->leaf_nb, 4 * nl) && balloc(b, &b->bstart, 4 * (nl + 1)) &&
               balloc(b, &b->sorted32, 16 * nt) && balloc(b, &b->a64, sizeof(double2) * coarse * p1) &&
               balloc(b, &b->a32, sizeof(float2) * b->a_cells * p1) && balloc(b, &b->b32, sizeof(float2) * bcells * p1) &&
               balloc(b, &b->far, sizeof(float2) * nt) && balloc(b, &b->d_status, sizeof(unsigned int));

@@ -89,8 +89,10 @@ struct fmm_plan_s {
     uint32_t* rank;
     uint32_t* counts;
     uint32_t* leaf_start;
-    uint32_t* block_sums;
+    uint32_t* block_sums;        // scan partials, scan_blocks + 1 entries
     int scan_blocks;
+    uint32_t* leaf_nb;           // near-field target blocks per finest square (mixed path)
+    uint32_t* leaf_bstart;       // their exclusive scan, 4^levels + 1 entries
     uint32_t* sorted_key;
     fmm_p64* sorted64;
     float4* sorted32;
@@ -187,6 +189,24 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q);
 int fmm_scan_blocks(int64_t m);
 int fmm_launch_scan(const uint32_t* counts, int64_t m, uint32_t* block_sums, uint32_t* leaf_start, uint32_t n_total,
                     cudaStream_t st);
+int fmm_launch_leaf_blocks(const uint32_t* leaf_start, int64_t m, uint32_t* nb, uint32_t* block_sums, uint32_t* bstart,
+                           cudaStream_t st);
+
+// largest i in [0, m) with pre[i] <= w, for a non-decreasing pre with pre[0] <= w: a 32-ary
+// search by the whole warp (each step probes 32 evenly spaced entries), about log32(m) loads
+static __device__ __forceinline__ uint32_t fmm_warp_search(const uint32_t* pre, uint32_t m, uint32_t w, int lane) {
+    uint32_t lo = 0, hi = m;
+    for (int it = 0; it < 8 && hi - lo > 1; ++it) {
+        const uint32_t step = (hi - lo + 31u) / 32u;
+        const uint32_t pos = lo + (uint32_t)lane * step;
+        const bool le = pos < hi && pre[pos] <= w;
+        const unsigned msk = __ballot_sync(0xffffffffu, le);
+        const int last = 31 - __clz(msk);
+        lo = lo + (uint32_t)last * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
 int fmm_launch_fp64(fmm_plan_s* pl, double* phi);
 int fmm_launch_mixed(fmm_plan_s* pl, double* phi);
 int fmm_m2l_bucket(int p1);

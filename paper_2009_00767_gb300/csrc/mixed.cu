@@ -371,19 +371,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 __global__ void __launch_bounds__(kP2PWarps * 32)
-k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, int levels, float s_leaf,
+k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
+            const uint32_t* __restrict__ bstart, uint32_t nleaf, int levels, float s_leaf,
             const float2* __restrict__ phi_far, double* __restrict__ phi, unsigned int* __restrict__ status,
             unsigned long long* __restrict__ counters) {
     __shared__ __align__(16) float4 buf[kP2PWarps][kP2PCap];
     __shared__ __align__(8) uint64_t bar[kP2PWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t leaf = (uint32_t)blockIdx.x * kP2PWarps + warp;
-    const uint32_t nleaf = 1u << (2 * levels);
-    if (leaf >= nleaf) return;
+    // one warp per block of up to 32 targets of one finest square: crowded squares spread
+    // over as many warps as they have target blocks
+    const uint32_t w = (uint32_t)blockIdx.x * kP2PWarps + warp;
+    if (w >= bstart[nleaf]) return;
     if (*(volatile const unsigned int*)status != 0u) return;   // inputs failed the device checks
+    const uint32_t leaf = fmm_warp_search(bstart, nleaf, w, lane);
+    const uint32_t tb = w - bstart[leaf];
     const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
-    const int T = (int)(t1 - t0);
-    if (T == 0) return;
+    const uint32_t b0 = t0 + 32u * tb;
+    const int T = (int)min(32u, t1 - b0);
     const int side = 1 << levels;
     const int ix = (int)fmm_compact2(leaf), iy = (int)fmm_compact2(leaf >> 1);
     // the nine neighbour slots, fully unrolled so that they live in registers
@@ -402,7 +406,7 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
     if (lane == 0) {
         const unsigned slot = leaf % FMM_COUNTER_SLOTS;
         atomicAdd(&counters[slot], (unsigned long long)T * nsrc - (unsigned long long)T);
-        atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)T);
+        atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)(t1 - t0));
     }
     const bool staged = nsrc <= (uint32_t)kP2PCap;
     const uint32_t mb = smem_u32(&bar[warp]);
@@ -410,10 +414,7 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
         if (lane == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            uint64_t st64;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                         : "=l"(st64)
-                         : "r"(mb), "r"(16u * nsrc)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(16u * nsrc)
                          : "memory");
             const uint32_t dst0 = smem_u32(buf[warp]);
 #pragma unroll
@@ -430,8 +431,6 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
             if (lane == 0) atomicOr(status, FMM_FLAG_TIMEOUT);
             return;   // the copies were issued with valid sizes; nothing else waits on them
         }
-    }
-    if (staged) {
         // move every staged source into the target square's frame: x_j + (jx - ix) s, y_j + (jy - iy) s
         float4* sb = buf[warp];
 #pragma unroll
@@ -447,56 +446,64 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
         __syncwarp();
     }
     int tp = 1;
-    while (tp < T && tp < 32) tp <<= 1;
+    while (tp < T) tp <<= 1;
     const uint32_t groups = 32 / tp;
     const int slot = lane & (tp - 1);
     const uint32_t grp = lane / tp;
-    for (int tb = 0; tb < T; tb += tp) {
-        const int ti = tb + slot;
-        const bool active = ti < T;
-        const float4 Pi = sp[t0 + (active ? ti : 0)];
-        float2 near = make_float2(0.f, 0.f);
-        if (staged) {
-            // at most kP2PCap / groups terms per lane: one FP32 sum, four sources per step
-            const float4* src = buf[warp];
-            float acc0 = 0.f, acc1 = 0.f;
-            uint32_t j = grp;
-            for (; j + 3u * groups < nsrc; j += 4u * groups) {
-                const float4 a0 = src[j], a1 = src[j + groups], a2 = src[j + 2u * groups], a3 = src[j + 3u * groups];
-                acc0 = fmaf(a0.z, p2p_lg2(Pi.x - a0.x, Pi.y - a0.y), acc0);
-                acc1 = fmaf(a1.z, p2p_lg2(Pi.x - a1.x, Pi.y - a1.y), acc1);
-                acc0 = fmaf(a2.z, p2p_lg2(Pi.x - a2.x, Pi.y - a2.y), acc0);
-                acc1 = fmaf(a3.z, p2p_lg2(Pi.x - a3.x, Pi.y - a3.y), acc1);
-            }
-            for (; j < nsrc; j += groups) {
-                const float4 a0 = src[j];
-                acc0 = fmaf(a0.z, p2p_lg2(Pi.x - a0.x, Pi.y - a0.y), acc0);
-            }
-            near = make_float2(acc0 + acc1, 0.f);
-        } else {
-            // crowded squares: per-neighbour FP32 sums from global memory, combined in float-float
+    const bool active = slot < T;
+    const uint32_t gi = b0 + (active ? slot : 0);
+    const float4 Pi = sp[gi];
+    float2 near = make_float2(0.f, 0.f);
+    if (staged) {
+        // at most kP2PCap / groups terms per lane: one FP32 sum, four sources per step
+        const float4* src = buf[warp];
+        float acc0 = 0.f, acc1 = 0.f;
+        uint32_t j = grp;
+        for (; j + 3u * groups < nsrc; j += 4u * groups) {
+            const float4 a0 = src[j], a1 = src[j + groups], a2 = src[j + 2u * groups], a3 = src[j + 3u * groups];
+            acc0 = fmaf(a0.z, p2p_lg2(Pi.x - a0.x, Pi.y - a0.y), acc0);
+            acc1 = fmaf(a1.z, p2p_lg2(Pi.x - a1.x, Pi.y - a1.y), acc1);
+            acc0 = fmaf(a2.z, p2p_lg2(Pi.x - a2.x, Pi.y - a2.y), acc0);
+            acc1 = fmaf(a3.z, p2p_lg2(Pi.x - a3.x, Pi.y - a3.y), acc1);
+        }
+        for (; j < nsrc; j += groups) {
+            const float4 a0 = src[j];
+            acc0 = fmaf(a0.z, p2p_lg2(Pi.x - a0.x, Pi.y - a0.y), acc0);
+        }
+        near = make_float2(acc0 + acc1, 0.f);
+    } else {
+        // crowded squares: FP32 sums over runs of kP2PCap sources from global memory, combined
+        // in float-float
 #pragma unroll
-            for (int b = 0; b < 9; ++b) {
-                const float bx = Pi.x - (float)((b % 3) - 1) * s_leaf;   // target-centre minus source-centre
-                const float by = Pi.y - (float)((b / 3) - 1) * s_leaf;
-                const float4* src = sp + nb0[b];
-                float acc = 0.f;
-                for (uint32_t j = grp; j < ncnt[b]; j += groups) {
-                    const float4 Pj = src[j];
-                    acc = fmaf(Pj.z, p2p_lg2(bx - Pj.x, by - Pj.y), acc);
+        for (int b = 0; b < 9; ++b) {
+            const float bx = Pi.x - (float)((b % 3) - 1) * s_leaf;   // target-centre minus source-centre
+            const float by = Pi.y - (float)((b / 3) - 1) * s_leaf;
+            const float4* src = sp + nb0[b];
+            for (uint32_t r0 = 0; r0 < ncnt[b]; r0 += kP2PCap) {
+                const uint32_t r1 = min(ncnt[b], r0 + kP2PCap);
+                float acc0 = 0.f, acc1 = 0.f;
+                uint32_t j = r0 + grp;
+                for (; j + groups < r1; j += 2u * groups) {
+                    const float4 a0 = src[j], a1 = src[j + groups];
+                    acc0 = fmaf(a0.z, p2p_lg2(bx - a0.x, by - a0.y), acc0);
+                    acc1 = fmaf(a1.z, p2p_lg2(bx - a1.x, by - a1.y), acc1);
                 }
-                near = ff_add_f(near, acc);
+                if (j < r1) {
+                    const float4 a0 = src[j];
+                    acc0 = fmaf(a0.z, p2p_lg2(bx - a0.x, by - a0.y), acc0);
+                }
+                near = ff_add_f(near, acc0 + acc1);
             }
         }
-        for (int o = tp; o < 32; o <<= 1) {
-            const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, near.x, o),
-                                             __shfl_xor_sync(0xffffffffu, near.y, o));
-            near = ff_add(near, other);
-        }
-        if (active && grp == 0) {
-            const float2 v = ff_add(phi_far[t0 + ti], ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
-            phi[__float_as_int(Pi.w)] = fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);   // ln2 / 2 as float-float above
-        }
+    }
+    for (int o = tp; o < 32; o <<= 1) {
+        const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, near.x, o),
+                                         __shfl_xor_sync(0xffffffffu, near.y, o));
+        near = ff_add(near, other);
+    }
+    if (active && grp == 0) {
+        const float2 v = ff_add(phi_far[gi], ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
+        phi[__float_as_int(Pi.w)] = fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);   // ln2 / 2 as float-float above
     }
     if (staged && lane == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
 }
@@ -618,9 +625,14 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     cudaEventRecord(pl->ev[4], st);
     {
         const uint32_t nleaf = 1u << (2 * L);
-        const unsigned blocks = (nleaf + kP2PWarps - 1) / kP2PWarps;
-        k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, st>>>(pl->sorted32, pl->leaf_start, L, lv.s_leaf, far, phi,
-                                                      pl->d_status, pl->d_counters);
+        const int r = fmm_launch_leaf_blocks(pl->leaf_start, nleaf, pl->leaf_nb, pl->block_sums, pl->leaf_bstart, st);
+        if (r < 0) return -1;
+        launches += r;
+        // upper bound of the target blocks: each square adds at most one partial block
+        const uint64_t wmax = (uint64_t)nleaf + (uint64_t)(n / 32) + 1;
+        const unsigned blocks = (unsigned)((wmax + kP2PWarps - 1) / kP2PWarps);
+        k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, st>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, nleaf, L,
+                                                      lv.s_leaf, far, phi, pl->d_status, pl->d_counters);
         ++launches;
     }
     cudaEventRecord(pl->ev[5], st);

@@ -91,7 +91,7 @@ size_t carve(fmm_plan_s* pl, unsigned char* base) {
     pl->counts = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * m));
     pl->leaf_start = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (m + 1)));
     pl->scan_blocks = fmm_scan_blocks(m);
-    pl->block_sums = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * pl->scan_blocks));
+    pl->block_sums = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (pl->scan_blocks + 1)));
     pl->sorted_key = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * n));
     pl->sorted64 = reinterpret_cast<fmm_p64*>(take(sizeof(fmm_p64) * n));
     pl->phi_far = reinterpret_cast<double*>(take(sizeof(double) * n));

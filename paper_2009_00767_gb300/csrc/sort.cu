@@ -101,6 +101,7 @@ __global__ void k_scan_top(uint32_t* __restrict__ sums, int nb) {
             if (base + j < nb) sums[base + j] = v[j] + carry;
         carry += tot;
     }
+    if (threadIdx.x == 0) sums[nb] = carry;   // the grand total, for scans whose total is not known
 }
 
 __global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t m, const uint32_t* __restrict__ sums,
@@ -115,7 +116,7 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t m, const ui
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j)
         if (base + j < m) out[base + j] = v[j] + off;
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[m] = n_total;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[m] = (n_total == 0xffffffffu) ? sums[gridDim.x] : n_total;
 }
 
 template <bool kMixed>
@@ -181,6 +182,12 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
 
 int fmm_scan_blocks(int64_t m) { return (int)((m + kScanTile - 1) / kScanTile); }
 
+// target blocks of up to 32 particles per finest square, for the near-field work split
+__global__ void k_leaf_blocks(const uint32_t* __restrict__ leaf_start, int64_t m, uint32_t* __restrict__ nb) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) nb[i] = (leaf_start[i + 1] - leaf_start[i] + 31u) / 32u;
+}
+
 int fmm_launch_scan(const uint32_t* counts, int64_t m, uint32_t* block_sums, uint32_t* leaf_start, uint32_t n_total,
                     cudaStream_t st) {
     const int nb = fmm_scan_blocks(m);
@@ -188,4 +195,11 @@ int fmm_launch_scan(const uint32_t* counts, int64_t m, uint32_t* block_sums, uin
     k_scan_top<<<1, kScanThreads, 0, st>>>(block_sums, nb);
     k_scan_down<<<nb, kScanThreads, 0, st>>>(counts, m, block_sums, leaf_start, n_total);
     return cudaGetLastError() == cudaSuccess ? 3 : -1;
+}
+
+int fmm_launch_leaf_blocks(const uint32_t* leaf_start, int64_t m, uint32_t* nb, uint32_t* block_sums, uint32_t* bstart,
+                           cudaStream_t st) {
+    k_leaf_blocks<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(leaf_start, m, nb);
+    const int r = fmm_launch_scan(nb, m, block_sums, bstart, 0xffffffffu, st);
+    return r < 0 ? -1 : r + 1;
 }

@@ -98,3 +98,16 @@ def test_tensor_core_modes_below_level_8_use_the_cuda_cores(oracle_mod):
     # ranks, so FP32 sums may differ between calls at the level of FP32 rounding
     assert sa["kernel_launches"] == sb["kernel_launches"]
     assert rel_l2(a, b) < MIXED_TOL
+
+
+def test_crowded_squares_split_over_warps(oracle_mod):
+    """Clustered charges (32 Gaussians, sigma down to 0.01) on a uniform tree: finest squares with
+    thousands of particles, whose near field is split into blocks of 32 targets over many warps."""
+    from gpu_util import run_fmm
+    xy, q = inputs.gmm(100000, inputs.config_seed(2, 7))
+    phi, st = run_fmm(xy, q, 6, 16, precision="fp32")
+    assert st["max_leaf"] > 512            # beyond the shared-memory staging: the global-memory path
+    ref = oracle_mod.shiftfree(xy, q, 6, 16)
+    err = rel_l2(phi, ref)
+    print(f"clustered N=100000 levels=6 p=16: max square {st['max_leaf']}, rel L2 vs oracle {err:.3e}")
+    assert err < MIXED_TOL
