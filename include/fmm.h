@@ -189,6 +189,55 @@ int fmm_batch_launches(fmm_batch_t batch);
 /* Free the batch plan and everything it owns.  NULL is ignored. */
 void fmm_batch_destroy(fmm_batch_t batch);
 
+/* ---------------------------------------------------------------------------------------
+ * Learned (levels, p) selector.  Features of a system: for every level k = 3..11 of the
+ * uniform quadtree over [0, box]^2, the fraction of squares whose population c falls in bin
+ * floor(log2(c + 1)) (12 bins, the last one open), then log2(N) / 22 -- 109 values.  A small
+ * MLP (IN = 111: the features, levels / 12 and p / 32 of one candidate; two hidden ReLU
+ * layers; 2 outputs) predicts log10(relative L2 error) / 8 and log(milliseconds) of the method
+ * at that candidate.  Training, inference and the statistics run in the library's kernels.
+ * --------------------------------------------------------------------------------------- */
+typedef struct fmm_selector_s* fmm_selector_t;
+
+/* Input, output and feature widths of the network (111, 2, 109); any pointer may be NULL. */
+int fmm_selector_dims(int* in, int* out, int* feat);
+
+/* A network with `hidden` units per hidden layer, He-uniform weights from a SplitMix64 seed. */
+fmm_status fmm_selector_create(fmm_selector_t* out, int hidden, uint64_t seed, void* stream);
+void fmm_selector_destroy(fmm_selector_t sel);
+int fmm_selector_num_params(fmm_selector_t sel);
+
+/* The 109 features of xy (device, [n][2]) into feat_host (host); waits for the stream. */
+fmm_status fmm_selector_features(fmm_selector_t sel, const double* xy, int64_t n, double box, float* feat_host);
+
+/* Parameters in / out as host arrays of fmm_selector_num_params floats, layout
+ * [W1 (IN x H) | b1 | W2 (H x H) | b2 | W3 (H x 2) | b3], row-major [input][output]. */
+fmm_status fmm_selector_get_params(fmm_selector_t sel, float* host);
+fmm_status fmm_selector_set_params(fmm_selector_t sel, const float* host);
+
+/* y[rows][2] = network(x[rows][IN]); host arrays; waits for the stream. */
+fmm_status fmm_selector_predict(fmm_selector_t sel, const float* x_host, int rows, float* y_host);
+
+/* Loss (1/rows) sum_r sum_j (y - t)^2 and its gradient (grad_host may be NULL); host arrays. */
+fmm_status fmm_selector_loss_grad(fmm_selector_t sel, const float* x_host, const float* t_host, int rows,
+                                  float* loss, float* grad_host);
+
+/* `epochs` full-batch Adam steps (learning rate lr); loss_out (may be NULL) gets the final
+ * loss.  The Adam state persists in the selector, so repeated calls continue training. */
+fmm_status fmm_selector_train(fmm_selector_t sel, const float* x_host, const float* t_host, int rows,
+                              int epochs, float lr, float* loss_out);
+
+/* Save / load parameters and Adam state (a versioned binary file) to resume training. */
+fmm_status fmm_selector_save(fmm_selector_t sel, const char* path);
+fmm_status fmm_selector_load(fmm_selector_t sel, const char* path);
+
+/* Choose (levels, p) for xy (device, [n][2]): candidates levels = round(log4(n/16)) - 2 .. + 2
+ * (clamped to 2..11) x p = 8, 12, .., 32; returns the cheapest predicted time among those
+ * whose predicted log10 error is at most log10(target_err) - margin_decades, else the fixed
+ * fallback (8, 20) with *used_fallback = 1. */
+fmm_status fmm_select(fmm_selector_t sel, const double* xy, int64_t n, double box, double target_err,
+                      double margin_decades, int* levels_out, int* p_out, int* used_fallback);
+
 /* The FP64 method of fmm_potential for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a library convenience.  Some callers cannot call
  * cudaMalloc -- a loop that forbids allocation once it has started, a device whose free

@@ -67,6 +67,20 @@ SIGNATURES = {
     "fmm_batch_autotune": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(_i32)]),
     "fmm_batch_launches": (_i32, [_vp]),
     "fmm_batch_destroy": (None, [_vp]),
+    "fmm_selector_dims": (_i32, [ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "fmm_selector_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.c_uint64, _vp]),
+    "fmm_selector_destroy": (None, [_vp]),
+    "fmm_selector_num_params": (_i32, [_vp]),
+    "fmm_selector_features": (_i32, [_vp, _vp, _i64, _d, _vp]),
+    "fmm_selector_get_params": (_i32, [_vp, _vp]),
+    "fmm_selector_set_params": (_i32, [_vp, _vp]),
+    "fmm_selector_predict": (_i32, [_vp, _vp, _i32, _vp]),
+    "fmm_selector_loss_grad": (_i32, [_vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_float), _vp]),
+    "fmm_selector_train": (_i32, [_vp, _vp, _vp, _i32, _i32, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
+    "fmm_selector_save": (_i32, [_vp, ctypes.c_char_p]),
+    "fmm_selector_load": (_i32, [_vp, ctypes.c_char_p]),
+    "fmm_select": (_i32, [_vp, _vp, _i64, _d, _d, _d, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                          ctypes.POINTER(_i32)]),
 }
 
 
@@ -249,6 +263,87 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Selector:
+    """Owner of one fmm_selector handle (the learned (levels, p) selector)."""
+
+    def __init__(self, hidden=64, seed=1, stream=None):
+        h = _vp()
+        _check(_lib.fmm_selector_create(ctypes.byref(h), int(hidden), int(seed), _stream_handle(stream)),
+               "fmm_selector_create")
+        self.handle = h.value
+        i, o, f = _i32(), _i32(), _i32()
+        _lib.fmm_selector_dims(ctypes.byref(i), ctypes.byref(o), ctypes.byref(f))
+        self.n_in, self.n_out, self.n_feat = i.value, o.value, f.value
+        self.hidden = int(hidden)
+        self.n_params = int(_lib.fmm_selector_num_params(self.handle))
+
+    @staticmethod
+    def _f32(a, shape):
+        return np.ascontiguousarray(a, dtype=np.float32).reshape(shape)
+
+    def features(self, xy, box=5.0) -> np.ndarray:
+        f = np.empty(self.n_feat, dtype=np.float32)
+        _check(_lib.fmm_selector_features(self.handle, _ptr(xy), int(xy.shape[0]), float(box), f.ctypes.data),
+               "fmm_selector_features")
+        return f
+
+    def params(self) -> np.ndarray:
+        w = np.empty(self.n_params, dtype=np.float32)
+        _check(_lib.fmm_selector_get_params(self.handle, w.ctypes.data), "fmm_selector_get_params")
+        return w
+
+    def set_params(self, w):
+        w = self._f32(w, (self.n_params,))
+        _check(_lib.fmm_selector_set_params(self.handle, w.ctypes.data), "fmm_selector_set_params")
+
+    def predict(self, x) -> np.ndarray:
+        x = self._f32(x, (-1, self.n_in))
+        y = np.empty((x.shape[0], self.n_out), dtype=np.float32)
+        _check(_lib.fmm_selector_predict(self.handle, x.ctypes.data, x.shape[0], y.ctypes.data), "fmm_selector_predict")
+        return y
+
+    def loss_grad(self, x, t):
+        x = self._f32(x, (-1, self.n_in))
+        t = self._f32(t, (-1, self.n_out))
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(_lib.fmm_selector_loss_grad(self.handle, x.ctypes.data, t.ctypes.data, x.shape[0], ctypes.byref(loss),
+                                           g.ctypes.data), "fmm_selector_loss_grad")
+        return float(loss.value), g
+
+    def train(self, x, t, epochs, lr=1e-3) -> float:
+        x = self._f32(x, (-1, self.n_in))
+        t = self._f32(t, (-1, self.n_out))
+        loss = ctypes.c_float(0.0)
+        _check(_lib.fmm_selector_train(self.handle, x.ctypes.data, t.ctypes.data, x.shape[0], int(epochs), float(lr),
+                                       ctypes.byref(loss)), "fmm_selector_train")
+        return float(loss.value)
+
+    def save(self, path):
+        _check(_lib.fmm_selector_save(self.handle, str(path).encode()), "fmm_selector_save")
+
+    def load(self, path):
+        _check(_lib.fmm_selector_load(self.handle, str(path).encode()), "fmm_selector_load")
+
+    def select(self, xy, target_err=1e-6, margin_decades=0.3, box=5.0):
+        lv, p, fb = _i32(), _i32(), _i32()
+        _check(_lib.fmm_select(self.handle, _ptr(xy), int(xy.shape[0]), float(box), float(target_err),
+                               float(margin_decades), ctypes.byref(lv), ctypes.byref(p), ctypes.byref(fb)),
+               "fmm_select")
+        return lv.value, p.value, bool(fb.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.fmm_selector_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

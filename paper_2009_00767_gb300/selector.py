@@ -1,0 +1,184 @@
+"""Training and evaluation of the learned (levels, p) selector.
+
+The selector (include/fmm.h, ``fmm_select``) is a small network that reads occupancy
+statistics of a particle system and predicts, for a candidate (levels, p), the relative L2
+error and the run time of the mixed-precision method; it then picks the cheapest candidate
+predicted to meet a requested accuracy, or the fixed fallback (8, 20).
+
+Its training tuples are generated by the method itself: for each synthetic system, every
+candidate of the grid is run through ``fmm_potential`` (mixed FP32), timed with CUDA events,
+and judged by the library's FP64 direct sum (``fmm_direct_targets``) on sampled targets.  The
+network is then fitted by the library's own forward / backward / Adam kernels.
+
+Workload of the tuples: N log-uniform in [2^16, 2^20]; families uniform, Gaussian mixture
+(K in [4, 64], sigma log-uniform in [0.02, 0.5], out-of-box draws redrawn) and annulus
+(r in [1, 2] about (2.5, 2.5)); q ~ U[-1, 1].
+
+    python -m paper_2009_00767_gb300.selector train --out selector.bin --systems 96
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import binding, inputs
+
+FALLBACK = (8, 20)
+P_GRID = (8, 12, 16, 20, 24, 28, 32)
+LOG10_SCALE = 8.0           # the network predicts log10(error) / 8
+ERR_FLOOR = 1e-8            # errors below this are labelled at the floor
+
+
+def candidates(n):
+    l0 = int(round(math.log(n / 16.0) / math.log(4.0)))
+    out = []
+    for lev in range(l0 - 2, l0 + 3):
+        if 2 <= lev <= 11:
+            for p in P_GRID:
+                out.append((lev, p))
+    return out
+
+
+def system(seed, n_lo=1 << 16, n_hi=1 << 20):
+    """One synthetic system of the training / evaluation family."""
+    u = inputs.u01(seed, 41, 4)
+    n = int(math.exp(math.log(n_lo) + (math.log(n_hi) - math.log(n_lo)) * u[0]))
+    fam = int(u[1] * 3)
+    if fam == 0:
+        xy, q = inputs.uniform(n, seed)
+        name = "uniform"
+    elif fam == 1:
+        k = int(4 + 60 * u[2])
+        xy, q = inputs.gmm(n, seed, k=k, sigma_lo=0.02, sigma_hi=0.5)
+        name = f"gmm{k}"
+    else:
+        xy, q = inputs.annulus(n, seed)
+        name = "annulus"
+    return name, xy, q
+
+
+def _time_plan(torch, plan, xy_d, q_d, phi, reps=3):
+    binding.fmm_potential(plan.handle, xy_d, q_d, phi)   # warm-up
+    plan.sync()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        binding.fmm_potential(plan.handle, xy_d, q_d, phi)
+        b.record()
+        plan.sync()
+        ms.append(a.elapsed_time(b))
+        if ms[-1] > 200.0:
+            break
+    return float(np.median(ms))
+
+
+def judge_targets(torch, xy_d, q_d, n, seed, s=256):
+    idx = np.unique((inputs.u01(seed, 77, s) * n).astype(np.int64))
+    idx_d = torch.from_numpy(idx).to(xy_d.device)
+    ref = torch.empty(idx.shape[0], dtype=torch.float64, device=xy_d.device)
+    binding.fmm_direct_targets(xy_d, q_d, idx_d, ref)
+    torch.cuda.synchronize()
+    return idx_d, ref
+
+
+def run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p, precision="fp32"):
+    n = int(q_d.shape[0])
+    phi = torch.empty(n, dtype=torch.float64, device=xy_d.device)
+    with binding.Plan(n, lev, p, 5.0, precision) as plan:
+        ms = _time_plan(torch, plan, xy_d, q_d, phi)
+    err = float(torch.linalg.norm(phi[idx_d] - ref) / torch.linalg.norm(ref))
+    return err, ms
+
+
+def label(err, ms):
+    return [math.log10(max(err, ERR_FLOOR)) / LOG10_SCALE, math.log(max(ms, 1e-3))]
+
+
+def generate(sel, seeds, log=print):
+    """Tuples (features ++ candidate, [log10 err / 8, log ms]) for the systems of ``seeds``."""
+    import torch
+    X, T, meta = [], [], []
+    for sd in seeds:
+        name, xy, q = system(sd)
+        xy_d = torch.from_numpy(xy).to("cuda")
+        q_d = torch.from_numpy(q).to("cuda")
+        feat = sel.features(xy_d)
+        idx_d, ref = judge_targets(torch, xy_d, q_d, q.shape[0], sd)
+        t0 = time.time()
+        for lev, p in candidates(q.shape[0]):
+            err, ms = run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p)
+            X.append(np.concatenate([feat, [lev / 12.0, p / 32.0]]))
+            T.append(label(err, ms))
+            meta.append({"seed": sd, "family": name, "n": int(q.shape[0]), "levels": lev, "p": p, "err": err, "ms": ms})
+        log(f"system {sd}: {name} N={q.shape[0]} {len(candidates(q.shape[0]))} candidates in {time.time() - t0:.1f}s")
+    return np.asarray(X, dtype=np.float32), np.asarray(T, dtype=np.float32), meta
+
+
+def best_feasible(meta_rows, target):
+    ok = [r for r in meta_rows if r["err"] <= target]
+    return min(ok, key=lambda r: r["ms"]) if ok else None
+
+
+def evaluate(sel, seeds, target=1e-6, margin=0.3):
+    """Learned pick vs the fixed fallback on held-out systems, both judged by the FP64 direct sum."""
+    import torch
+    rows = []
+    for sd in seeds:
+        name, xy, q = system(sd)
+        xy_d = torch.from_numpy(xy).to("cuda")
+        q_d = torch.from_numpy(q).to("cuda")
+        lev, p, fb = sel.select(xy_d, target, margin)
+        idx_d, ref = judge_targets(torch, xy_d, q_d, q.shape[0], sd)
+        err_l, ms_l = run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p)
+        err_f, ms_f = run_candidate(torch, xy_d, q_d, idx_d, ref, *FALLBACK)
+        rows.append({"seed": sd, "family": name, "n": int(q.shape[0]), "pick": [lev, p], "fallback_used": fb,
+                     "err_pick": err_l, "ms_pick": ms_l, "err_fallback": err_f, "ms_fallback": ms_f})
+    return rows
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    tr = sub.add_parser("train")
+    tr.add_argument("--out", required=True)
+    tr.add_argument("--systems", type=int, default=96)
+    tr.add_argument("--seed0", type=int, default=700000)
+    tr.add_argument("--epochs", type=int, default=6000)
+    tr.add_argument("--hidden", type=int, default=64)
+    tr.add_argument("--dataset", default=None, help="save the generated tuples (.npz)")
+    tr.add_argument("--eval-systems", type=int, default=24)
+    tr.add_argument("--report", default=None)
+    a = ap.parse_args(argv)
+    build_lib()
+    sel = binding.Selector(hidden=a.hidden, seed=1)
+    X, T, meta = generate(sel, range(a.seed0, a.seed0 + a.systems))
+    if a.dataset:
+        np.savez(a.dataset, X=X, T=T, meta=json.dumps(meta))
+    losses = []
+    for chunk in range(a.epochs // 500):
+        losses.append(sel.train(X, T, 500, lr=1e-3 if chunk < 8 else 3e-4))
+        print(f"epoch {(chunk + 1) * 500}: loss {losses[-1]:.5f}")
+    sel.save(a.out)
+    ev = evaluate(sel, range(a.seed0 + 10_000, a.seed0 + 10_000 + a.eval_systems))
+    rep = {"train_tuples": int(X.shape[0]), "losses": losses, "eval": ev}
+    if a.report:
+        with open(a.report, "w") as f:
+            json.dump(rep, f, indent=1)
+    met = sum(r["err_pick"] <= 1e-6 for r in ev)
+    t_l = sum(r["ms_pick"] for r in ev)
+    t_f = sum(r["ms_fallback"] for r in ev)
+    print(f"held-out: {met}/{len(ev)} picks meet 1e-6; total ms learned {t_l:.2f} vs fallback {t_f:.2f}")
+
+
+def build_lib():
+    from . import build
+    build.build()
+
+
+if __name__ == "__main__":
+    main()
