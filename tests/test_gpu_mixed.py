@@ -111,3 +111,24 @@ def test_crowded_squares_split_over_warps(oracle_mod):
     err = rel_l2(phi, ref)
     print(f"clustered N=100000 levels=6 p=16: max square {st['max_leaf']}, rel L2 vs oracle {err:.3e}")
     assert err < MIXED_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp32", "3xtf32"])
+def test_full_size_clustered_16m_sampled(oracle_mod, precision):
+    """N = 2^24 in a mixture of 32 Gaussians (sigma log-uniform in [0.01, 0.3]), levels 10,
+    p = 24: 48 sampled particles against the oracle's direct sum, one by one."""
+    import torch
+    from paper_2009_00767_gb300 import binding
+    xy, q = inputs.gmm(1 << 24, inputs.config_seed(2))
+    idx = np.unique((inputs.u01(2024, 0, 48) * (1 << 24)).astype(np.int64))
+    ref = oracle_mod.direct_targets(xy, q, idx)
+    txy = torch.from_numpy(xy).to("cuda:0")
+    tq = torch.from_numpy(q).to("cuda:0")
+    with binding.Plan(1 << 24, 10, 24, 5.0, precision) as plan:
+        phi = plan.potential(txy, tq)
+        st = plan.stats()
+    got = phi[torch.from_numpy(idx).to("cuda:0")].cpu().numpy()
+    err = rel_l2(got, ref)
+    print(f"{precision} clustered 2^24 levels=10 p=24: max square {st['max_leaf']}, ms {st['ms_total']:.2f}, "
+          f"sampled rel L2 {err:.3e}")
+    assert err < MIXED_TOL
