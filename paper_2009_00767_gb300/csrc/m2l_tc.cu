@@ -8,10 +8,12 @@
 // outputs (N = 2H: Re b'_0..b'_p then Im b'_0..b'_p, each padded to H) and kk the inputs
 // (K = 2H per offset: Re M_0..M_p then Im M_0..M_p).  The 27 offsets of the class fall into 12
 // groups that share one source window: the source parity (qx, qy) and the source row shift sy.
-// A window of 130 source cells (128 targets plus one on each side) is one contiguous run of
-// the K-contiguous source layout in global memory; the CTA's 128 threads copy it with 16-byte
-// cp.async into shared memory in the canonical no-swizzle K-major layout (16-byte core-matrix
-// rows, K-chunk stride LBO = 130 x 16 B), completing on the stage's mbarrier.  The three column
+// The source grid is stored chunk-major ([parity][K/4 chunk][row][col][4 floats], 1-cell zero
+// halo), so each K-chunk of a window of 130 source cells (128 targets plus one on each side) is
+// one contiguous run of 2080 bytes: a window is KC bulk copies (cp.async.bulk) that land in the
+// canonical no-swizzle K-major shared layout (16-byte core-matrix rows, K-chunk stride
+// LBO = 130 x 16 B) and complete on the stage's mbarrier.  Warp 0 issues the copies (running up
+// to NSW windows ahead), warp 1 issues the MMAs, all four warps run the epilogue.  The three column
 // shifts of a group are then the same window read from a descriptor start moved by 16 B per
 // cell.  The operators of a group arrive by one bulk copy (cp.async.bulk).  A single thread
 // issues the MMAs; the accumulator lives in tensor memory and the epilogue reads it back with
@@ -20,10 +22,13 @@
 // 3xTF32 (Ootomo & Yokota, 2022): x = x_hi + x_lo with x_hi rounded to TF32, and
 // D += A_hi B_hi + A_hi B_lo + A_lo B_hi, dropping A_lo B_lo, recovers about FP32 accuracy.
 //
-// The monopole-log term of b'_0, sum_d M_0 (log|w0| + ln s), is not in the GEMM: the epilogue
-// sums it in float-float from the FP32 moment grid.  Every wait on an mbarrier is bounded and
+// The monopole-log term of b'_0, sum_d M_0 (log|w0| + ln s), carries the largest part of phi; it
+// stays out of the GEMM (its (0, 0) operator entry is zero): the epilogue sums it in float-float
+// from the FP32 moment grid, in both TF32 modes; a TF32 product of a large M_0 with the log
+// would lose more than the error bound allows on clustered systems.  Every wait on an mbarrier is bounded and
 // sets a status flag when it runs out.
 
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -45,7 +50,7 @@ struct TcGroup {
 
 struct TcArgs {
     const float* src[2][FMM_MAX_LEVELS + 1];   // [part][level] -> [q][w2+2][w2+2][K] (1-cell zero halo)
-    const float* ops[2];                       // [part] -> [class][27 slots][KC][N][4]
+    const float* ops[2][FMM_MAX_LEVELS + 1];   // [part][level] -> [class][27 slots][KC][N][4]
     const float2* a32[FMM_MAX_LEVELS + 1];     // FP32 moment grids (3-cell halo) for the monopole term
     float2* B[FMM_MAX_LEVELS + 1];
     TcGroup groups[4][12];
@@ -98,32 +103,50 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int KC, int NP, int NS>
+// A CTA takes kRows tiles: the same 128 columns of kRows consecutive sub-grid rows of one
+// parity class, one TMEM accumulator each.  For each of the 12 groups the operators are loaded
+// once and serve all kRows tiles; the group's kRows source windows stream through NSW buffers.
+// Stages: ops buffers NSO (per group), window buffers NSW (per tile and group).
+constexpr int kRows = 4;
+
+template <int KC, int NP, int NSO, int NSW>
 __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ TcArgs a) {
     constexpr int N = 4 * KC, H = 2 * KC;
-    constexpr uint32_t A_BYTES = KC * kWin * 16;
-    constexpr uint32_t OP_BYTES = KC * N * 16;
-    constexpr uint32_t STAGE = NP * (A_BYTES + 3 * OP_BYTES);
-    constexpr uint32_t TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+    constexpr uint32_t A_BYTES = KC * kWin * 16;     // one window, one part
+    constexpr uint32_t OP_BYTES = KC * N * 16;       // one offset's operator, one part
+    constexpr uint32_t OPS_STAGE = NP * 3 * OP_BYTES;
+    constexpr uint32_t WIN_STAGE = NP * A_BYTES;
+    constexpr uint32_t ACC_COLS = 64;                // per tile (N <= 64)
+    constexpr uint32_t TMEM_COLS = kRows * ACC_COLS;
     constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
 
+    static_assert(NSW >= 2, "the window pipeline keeps one window in flight: it needs two window stages");
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * STAGE);   // full[NS], empty[NS], done
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * NS + 1);
+    // no swizzled layouts are used: 128-byte alignment serves the copies and the descriptors
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    uint8_t* ops_buf = smem;                                   // NSO x OPS_STAGE
+    uint8_t* win_buf = smem + NSO * OPS_STAGE;                 // NSW x WIN_STAGE
+    uint64_t* bars = reinterpret_cast<uint64_t*>(win_buf + NSW * WIN_STAGE);
+    uint64_t* ops_full = bars;                 // [NSO]
+    uint64_t* ops_empty = bars + NSO;          // [NSO]
+    uint64_t* win_full = bars + 2 * NSO;       // [NSW]
+    uint64_t* win_empty = win_full + NSW;      // [NSW]
+    uint64_t* done_bar = win_empty + NSW;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done_bar + 1);
 
-    // ---- which tile
+    // ---- which tiles
     const int cta = blockIdx.x;
     int k = kMinLevel;
     while (cta >= a.cta_base[k + 1]) ++k;
     const int w2 = 1 << (k - 1);
     const int tiles_per_row = w2 / kTile;
-    const int per_class = w2 * tiles_per_row;
+    const int bands = w2 / kRows;
+    const int per_class = bands * tiles_per_row;
     const int rel = cta - a.cta_base[k];
     const int cls = rel / per_class;
     const int rr = rel - cls * per_class;
-    const int y = rr / tiles_per_row;
-    const int u0 = (rr - y * tiles_per_row) * kTile;
+    const int y0 = (rr / tiles_per_row) * kRows;
+    const int u0 = (rr % tiles_per_row) * kTile;
     const int px = cls & 1, py = cls >> 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -134,11 +157,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        // full[s]: one arrival per thread after its copies land, plus thread 0's expect_tx arrival
-        for (int b = 0; b < NS; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bars[b])), "r"(kThreads + 1) : "memory");
-        for (int b = NS; b < 2 * NS + 1; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[b])) : "memory");
+        for (int b = 0; b < NSO; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&ops_full[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&ops_empty[b])) : "memory");
+        }
+        for (int b = 0; b < NSW; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&win_full[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&win_empty[b])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(done_bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -146,102 +173,132 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
 
-    // ---- all threads copy the source windows; thread 0 also fetches the operators and issues MMAs
     const int W2P = w2 + 2;
     bool ok = true;
-    for (int g = 0; g < 12; ++g) {
-        const int s = g % NS, use = g / NS;
-        const TcGroup& G = a.groups[cls][g];
-        const uint32_t full = su32(&bars[s]), empty = su32(&bars[NS + s]);
-        if (g >= NS && !wait_bar(empty, (uint32_t)((use - 1) & 1))) ok = false;
-        const int q = G.qx + 2 * G.qy;
-        // the window: global cells (row y + sy + 1, cols u0 .. u0 + 129) of parity q, contiguous
-        const size_t cell0 = ((size_t)q * W2P + (size_t)(y + G.sy + 1)) * W2P + (size_t)u0;
-        for (int part = 0; part < NP; ++part) {
-            const uint8_t* gsrc = reinterpret_cast<const uint8_t*>(a.src[part][k] + cell0 * (4 * KC));
-            const uint32_t dst = su32(smem + s * STAGE + part * A_BYTES);
-            for (int e = threadIdx.x; e < kWin * KC; e += kThreads) {
-                const int c = e / KC, j = e - c * KC;
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)(j * kWin + c) * 16u),
-                             "l"(gsrc + (size_t)e * 16)
+    constexpr int NWIN = 12 * kRows;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: operators once per group, then the group's kRows windows; every copy is a
+            // bulk copy completing on the stage's full barrier, so the producer runs ahead
+            for (int i = 0; i < NWIN; ++i) {
+                const int g = i / kRows, t = i % kRows;
+                const TcGroup& G = a.groups[cls][g];
+                if (t == 0) {
+                    const int so = g % NSO, uso = g / NSO;
+                    if (g >= NSO && !wait_bar(su32(&ops_empty[so]), (uint32_t)((uso - 1) & 1))) ok = false;
+                    const uint32_t bytes = NP * (uint32_t)G.nops * OP_BYTES;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&ops_full[so])),
+                                 "r"(bytes)
+                                 : "memory");
+                    for (int part = 0; part < NP; ++part) {
+                        const float* srcB = a.ops[part][k] + ((size_t)cls * 27 + G.slot0) * (OP_BYTES / 4);
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                                "r"(su32(ops_buf + so * OPS_STAGE + part * 3 * OP_BYTES)),
+                            "l"(srcB), "r"((uint32_t)G.nops * OP_BYTES), "r"(su32(&ops_full[so]))
+                            : "memory");
+                    }
+                }
+                const int sw = i % NSW, usw = i / NSW;
+                if (i >= NSW && !wait_bar(su32(&win_empty[sw]), (uint32_t)((usw - 1) & 1))) ok = false;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&win_full[sw])),
+                             "r"((uint32_t)(NP * A_BYTES))
                              : "memory");
-            }
-        }
-        // each thread waits for its own copies, makes them visible to the tensor core's (async)
-        // proxy, then arrives
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full) : "memory");
-        if (threadIdx.x == 0) {
-            const uint32_t bytes = NP * (uint32_t)G.nops * OP_BYTES;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(bytes) : "memory");
-            for (int part = 0; part < NP; ++part) {
-                const uint32_t dstB = su32(smem + s * STAGE + NP * A_BYTES + part * 3 * OP_BYTES);
-                const float* srcB = a.ops[part] + ((size_t)cls * 27 + G.slot0) * (OP_BYTES / 4);
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        dstB),
-                    "l"(srcB), "r"((uint32_t)G.nops * OP_BYTES), "r"(full)
-                    : "memory");
-            }
-            if (!wait_bar(full, (uint32_t)(use & 1))) ok = false;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t aBase = su32(smem + s * STAGE);
-            const uint32_t bBase = su32(smem + s * STAGE + NP * A_BYTES);
-            for (int o = 0; o < G.nops && ok; ++o) {
-                const uint32_t aoff = (uint32_t)(1 + G.sx[o]) * 16u;
-#pragma unroll
-                for (int ks = 0; ks < KC / 2; ++ks) {
-                    const uint32_t acc = (g | o | ks) != 0;
-                    const uint64_t ah = smem_desc(aBase + aoff + ks * 2 * (kWin * 16), kWin * 16, 128);
-                    const uint64_t bh = smem_desc(bBase + o * OP_BYTES + ks * 2 * (N * 16), N * 16, 128);
-                    mma_tf32(tmem, ah, bh, IDESC, acc);
-                    if (NP == 2) {
-                        const uint64_t al =
-                            smem_desc(aBase + A_BYTES + aoff + ks * 2 * (kWin * 16), kWin * 16, 128);
-                        const uint64_t bl = smem_desc(bBase + 3 * OP_BYTES + o * OP_BYTES + ks * 2 * (N * 16),
-                                                      N * 16, 128);
-                        mma_tf32(tmem, ah, bl, IDESC, 1u);
-                        mma_tf32(tmem, al, bh, IDESC, 1u);
+                const int q = G.qx + 2 * G.qy;
+                const int row = y0 + t + G.sy + 1;   // halo coordinates
+                for (int part = 0; part < NP; ++part) {
+                    const float* base = a.src[part][k];
+                    const uint32_t dst = su32(win_buf + sw * WIN_STAGE + part * A_BYTES);
+                    for (int j = 0; j < KC; ++j) {
+                        // chunk j of cells u0 .. u0 + 129 (halo coordinates) of this row: 2080 contiguous bytes
+                        const float* src = base + ((((size_t)q * KC + j) * W2P + row) * W2P + u0) * 4;
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+                                "r"(dst + (uint32_t)j * (kWin * 16)),
+                            "l"(src), "r"((uint32_t)(kWin * 16)), "r"(su32(&win_full[sw]))
+                            : "memory");
                     }
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty)
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            for (int i = 0; i < NWIN; ++i) {
+                const int g = i / kRows, t = i % kRows;
+                const TcGroup& G = a.groups[cls][g];
+                const int so = g % NSO, uso = g / NSO;
+                const int sw = i % NSW, usw = i / NSW;
+                if (t == 0 && !wait_bar(su32(&ops_full[so]), (uint32_t)(uso & 1))) ok = false;
+                if (!wait_bar(su32(&win_full[sw]), (uint32_t)(usw & 1))) ok = false;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t aBase = su32(win_buf + sw * WIN_STAGE);
+                const uint32_t bBase = su32(ops_buf + so * OPS_STAGE);
+                const uint32_t acc_t = tmem + (uint32_t)t * ACC_COLS;
+                for (int o = 0; o < G.nops && ok; ++o) {
+                    const uint32_t aoff = (uint32_t)(1 + G.sx[o]) * 16u;
+#pragma unroll
+                    for (int ks = 0; ks < KC / 2; ++ks) {
+                        const uint32_t acc = (g | o | ks) != 0;
+                        const uint64_t ah = smem_desc(aBase + aoff + ks * 2 * (kWin * 16), kWin * 16, 128);
+                        const uint64_t bh = smem_desc(bBase + o * OP_BYTES + ks * 2 * (N * 16), N * 16, 128);
+                        mma_tf32(acc_t, ah, bh, IDESC, acc);
+                        if (NP == 2) {
+                            const uint64_t al =
+                                smem_desc(aBase + A_BYTES + aoff + ks * 2 * (kWin * 16), kWin * 16, 128);
+                            const uint64_t bl =
+                                smem_desc(bBase + 3 * OP_BYTES + o * OP_BYTES + ks * 2 * (N * 16), N * 16, 128);
+                            mma_tf32(acc_t, ah, bl, IDESC, 1u);
+                            mma_tf32(acc_t, al, bh, IDESC, 1u);
+                        }
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 su32(&win_empty[sw]))
+                             : "memory");
+                if (t == kRows - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     su32(&ops_empty[so]))
+                                 : "memory");
+            }
+            // the final commit tracks every MMA issued above
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             su32(done_bar))
                          : "memory");
         }
-    }
-    if (threadIdx.x == 0) {
-        // the final commit tracks every MMA issued above
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         su32(&bars[2 * NS]))
-                     : "memory");
+        __syncwarp();
     }
     if (!ok) atomicOr(a.status, FMM_FLAG_TIMEOUT);
-    const bool done = wait_bar(su32(&bars[2 * NS]), 0);
+    const bool done = wait_bar(su32(done_bar), 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    // ---- epilogue: warp w reads accumulator rows (targets) 32w..32w+31
-    float v[N];
+    // ---- epilogue: warp w holds accumulator rows (targets) 32w..32w+31 of every tile
+    const int W = fmm_grid_width(k), p1 = a.p + 1;
+    const float2* A32 = a.a32[k];
+    for (int t = 0; t < kRows; ++t) {
+        float v[N];
 #pragma unroll
-    for (int c = 0; c < N; c += 16) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v + c);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (done) {
-        const int i = 32 * warp + lane;
-        const int tx = 2 * (u0 + i) + px, ty = 2 * y + py;
-        const int W = fmm_grid_width(k), p1 = a.p + 1;
-        const float2* A32 = a.a32[k];
-        float2 mono = make_float2(0.f, 0.f);
-        for (int dy = -2 - py; dy <= 3 - py; ++dy)
-            for (int dx = -2 - px; dx <= 3 - px; ++dx) {
-                if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-                const float2 m0 = A32[((size_t)(ty + dy + FMM_HALO) * W + (tx + dx + FMM_HALO)) * p1];
-                mono = ff_add(mono, ff_mul(m0, a.logc[k][(dx + 3) + 7 * (dy + 3)]));
-            }
-        float2* B = a.B[k] + ((size_t)ty * (1u << k) + tx) * p1;
-        B[0] = ff_add_f(mono, v[0]);
+        for (int c = 0; c < N; c += 16)
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * ACC_COLS + c), v + c);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (done) {
+            const int i = 32 * warp + lane;
+            const int tx = 2 * (u0 + i) + px, ty = 2 * (y0 + t) + py;
+            // the monopole-log term, summed in float-float from the FP32 moment grid
+            float2 mono = make_float2(0.f, 0.f);
+            for (int dy = -2 - py; dy <= 3 - py; ++dy)
+                for (int dx = -2 - px; dx <= 3 - px; ++dx) {
+                    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+                    const float2 m0 = A32[((size_t)(ty + dy + FMM_HALO) * W + (tx + dx + FMM_HALO)) * p1];
+                    mono = ff_add(mono, ff_mul(m0, a.logc[k][(dx + 3) + 7 * (dy + 3)]));
+                }
+            float2* B = a.B[k] + ((size_t)ty * (1u << k) + tx) * p1;
+            B[0] = ff_add_f(mono, v[0]);
 #pragma unroll
-        for (int l = 1; l < H; ++l)
-            if (l < p1) B[l] = make_float2(v[l], v[H + l]);
+            for (int l = 1; l < H; ++l)
+                if (l < p1) B[l] = make_float2(v[l], v[H + l]);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -274,7 +331,8 @@ __global__ void k_prep_tc(const float2* __restrict__ a32, int k, int p1, float4*
         vals[j] = m.x;                     // coefficient 0 holds M_0's high word: M_0 is real
         vals[H + j] = (j == 0) ? 0.f : m.y;
     }
-    const size_t cell = ((size_t)q * W2P + (size_t)(row + 1)) * W2P + (size_t)(col + 1);
+    // chunk-major source layout [q][chunk][row][col][4] (1-cell zero halo): the chunk of a run of
+    // consecutive cells of one row is one contiguous block
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
         float h[4], l[4];
@@ -284,8 +342,9 @@ __global__ void k_prep_tc(const float2* __restrict__ a32, int k, int p1, float4*
             h[t] = tf32_rna(v);
             l[t] = v - h[t];
         }
-        hi[cell * KC + c] = make_float4(h[0], h[1], h[2], h[3]);
-        if (NP == 2) lo[cell * KC + c] = make_float4(l[0], l[1], l[2], l[3]);
+        const size_t at = (((size_t)q * KC + c) * W2P + (size_t)(row + 1)) * W2P + (size_t)(col + 1);
+        hi[at] = make_float4(h[0], h[1], h[2], h[3]);
+        if (NP == 2) lo[at] = make_float4(l[0], l[1], l[2], l[3]);
     }
 }
 
@@ -300,19 +359,20 @@ float host_tf32(float x) {
     return r;
 }
 
+// shared-memory plan: (ops stages, window stages) = (2, 2), else (1, 2); 128 bytes of alignment
+// slack and 256 bytes of barriers
 template <int KC, int NP>
-size_t smem_bytes() {
-    constexpr int N = 4 * KC;
-    constexpr size_t stage = (size_t)NP * (KC * kWin * 16 + 3 * KC * N * 16);
-    const int ns = (2 * stage + 1024 + 256 <= 227 * 1024) ? 2 : 1;
-    return ns * stage + 1024 + 256;
+constexpr size_t tc_bytes(int nso, int nsw) {
+    return (size_t)nso * NP * 3 * (KC * (4 * KC) * 16) + (size_t)nsw * NP * (KC * kWin * 16) + 128 + 256;
 }
-
 template <int KC, int NP>
-int stages() {
-    constexpr int N = 4 * KC;
-    constexpr size_t stage = (size_t)NP * (KC * kWin * 16 + 3 * KC * N * 16);
-    return (2 * stage + 1024 + 256 <= 227 * 1024) ? 2 : 1;
+constexpr int tc_nso() {
+    return tc_bytes<KC, NP>(2, 2) <= 227 * 1024 ? 2 : 1;
+}
+template <int KC, int NP>
+constexpr int tc_nsw() {
+    static_assert(tc_bytes<KC, NP>(1, 2) <= 227 * 1024, "two window stages must fit");
+    return 2;
 }
 
 }  // namespace
@@ -320,7 +380,7 @@ int stages() {
 // ---------------------------------------------------------------- plan-side state
 struct FmmTc {
     int kc, np;
-    float* ops[2];
+    float* ops[2];                              // one scale-free copy per part
     float4* src[2][FMM_MAX_LEVELS + 1];
     TcArgs args;   // tensor maps and tables, filled at plan time
 };
@@ -368,45 +428,49 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
                 }
         if (slots[cls] != 27) return -1;
     }
-    // operators, real block form, [part][class][slot][KC][N][4]
+    // operators, real block form, [part][class][slot][KC][N][4]: scale-free, so one copy serves
+    // every level; the monopole-log entry (0, 0) is left out (summed in float-float by the epilogue)
     const size_t opsz = (size_t)4 * 27 * kc * N * 4;
-    std::vector<float> hostops[2];
-    for (int part = 0; part < np; ++part) hostops[part].assign(opsz, 0.f);
-    for (int cls = 0; cls < 4; ++cls)
-        for (int g = 0; g < 12; ++g) {
-            const TcGroup& G = tc->args.groups[cls][g];
-            for (int o = 0; o < G.nops; ++o) {
-                const int d = G.d[o];
-                const size_t base = ((size_t)cls * 27 + G.slot0 + o) * kc * N * 4;
-                for (int n = 0; n < N; ++n)
-                    for (int kk = 0; kk < K; ++kk) {
-                        // input kk: Re M_j (kk < H) or Im M_j; output n: Re b_l (n < H) or Im b_l
-                        const int j = kk < H ? kk : kk - H, l = n < H ? n : n - H;
-                        double val = 0.0;
-                        if (j < p1 && l < p1 && !(j == 0 && l == 0)) {
-                            const double tr = Tre[((size_t)d * p1 + j) * p1 + l];
-                            const double ti = Tim[((size_t)d * p1 + j) * p1 + l];
-                            if (n < H && kk < H) val = tr;
-                            else if (n < H) val = -ti;
-                            else if (kk < H) val = ti;
-                            else val = tr;
+    {
+        std::vector<float> hostops[2];
+        for (int part = 0; part < np; ++part) hostops[part].assign(opsz, 0.f);
+        for (int cls = 0; cls < 4; ++cls)
+            for (int g = 0; g < 12; ++g) {
+                const TcGroup& G = tc->args.groups[cls][g];
+                for (int o = 0; o < G.nops; ++o) {
+                    const int d = G.d[o];
+                    const size_t base = ((size_t)cls * 27 + G.slot0 + o) * kc * N * 4;
+                    for (int n = 0; n < N; ++n)
+                        for (int kk = 0; kk < K; ++kk) {
+                            // input kk: Re M_j (kk < H) or Im M_j; output n: Re b_l (n < H) or Im b_l
+                            const int j = kk < H ? kk : kk - H, l = n < H ? n : n - H;
+                            double val = 0.0;
+                            const bool mono = j == 0 && l == 0;   // summed in float-float instead
+                            if (j < p1 && l < p1 && !mono) {
+                                const double tr = Tre[((size_t)d * p1 + j) * p1 + l];
+                                const double ti = Tim[((size_t)d * p1 + j) * p1 + l];
+                                if (n < H && kk < H) val = tr;
+                                else if (n < H) val = -ti;
+                                else if (kk < H) val = ti;
+                                else val = tr;
+                            }
+                            const float v = (float)val;
+                            const float h = host_tf32(v);
+                            const size_t at = base + ((size_t)(kk / 4) * N + n) * 4 + (kk % 4);
+                            hostops[0][at] = h;
+                            if (np == 2) hostops[1][at] = v - h;
                         }
-                        const float v = (float)val;
-                        const float h = host_tf32(v);
-                        const size_t at = base + ((size_t)(kk / 4) * N + n) * 4 + (kk % 4);
-                        hostops[0][at] = h;
-                        if (np == 2) hostops[1][at] = v - h;
-                    }
+                }
             }
+        for (int part = 0; part < np; ++part) {
+            if (cudaMalloc(&tc->ops[part], opsz * 4) != cudaSuccess) return -1;
+            pl->workspace_bytes += opsz * 4;
+            if (cudaMemcpy(tc->ops[part], hostops[part].data(), opsz * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return -1;
+            for (int k = kMinLevel; k <= pl->levels; ++k) tc->args.ops[part][k] = tc->ops[part];
         }
-    for (int part = 0; part < np; ++part) {
-        if (cudaMalloc(&tc->ops[part], opsz * 4) != cudaSuccess) return -1;
-        pl->workspace_bytes += opsz * 4;
-        if (cudaMemcpy(tc->ops[part], hostops[part].data(), opsz * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-            return -1;
-        tc->args.ops[part] = tc->ops[part];
     }
-    // source buffers (K-contiguous, 1-cell zero halo), levels kMinLevel..L
+    // source buffers (chunk-major, 1-cell zero halo), levels kMinLevel..L
     for (int k = kMinLevel; k <= pl->levels; ++k) {
         const size_t w2p = ((size_t)1 << (k - 1)) + 2;
         const size_t bytes = (size_t)4 * w2p * w2p * kc * 16;
@@ -458,19 +522,14 @@ static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
     for (int k = kMinLevel; k <= L; ++k) {
         a.cta_base[k] = acc;
         const int w2 = 1 << (k - 1);
-        acc += 4 * w2 * (w2 / kTile);
+        acc += 4 * (w2 / kRows) * (w2 / kTile);
     }
     for (int k = L + 1; k <= FMM_MAX_LEVELS + 1; ++k) a.cta_base[k] = acc;
-    const size_t shm = smem_bytes<KC, NP>();
-    if (stages<KC, NP>() == 2) {
-        auto kern = k_m2l_tc<KC, NP, 2>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
-        kern<<<acc, kThreads, shm, st>>>(a);
-    } else {
-        auto kern = k_m2l_tc<KC, NP, 1>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
-        kern<<<acc, kThreads, shm, st>>>(a);
-    }
+    constexpr int NSO = tc_nso<KC, NP>(), NSW = tc_nsw<KC, NP>();
+    const size_t shm = tc_bytes<KC, NP>(NSO, NSW);
+    auto kern = k_m2l_tc<KC, NP, NSO, NSW>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
+    kern<<<acc, kThreads, shm, st>>>(a);
     ++launches;
     return launches;
 }
