@@ -1,23 +1,26 @@
-// m2l_tc.cu -- M2L (D-bar-1 of Sec. 2.2.1) on the 5th-generation tensor cores (tcgen05) for the
-// finest levels, in TF32 or in split 3xTF32 with FP32 accumulation in tensor memory.
+// m2l_tc.cu -- M2L (D-bar-1 of Sec. 2.2.1) on the 5th-generation tensor cores (tcgen05) for every
+// level, in TF32 or in split 3xTF32 with FP32 accumulation in tensor memory.
 //
 // For one level k and one parity class c = (px, py) of target squares, the conversion of the
 // interaction list is a real GEMM
 //     D[t][n] = sum_d sum_kk  S[t + d][kk] * Op_d[n][kk]
-// with t the targets (M = 128 consecutive targets of one row of the class's sub-grid), n the
-// outputs (N = 2H: Re b'_0..b'_p then Im b'_0..b'_p, each padded to H) and kk the inputs
-// (K = 2H per offset: Re M_0..M_p then Im M_0..M_p).  The 27 offsets of the class fall into 12
-// groups that share one source window: the source parity (qx, qy) and the source row shift sy.
-// The source grid is stored chunk-major ([parity][K/4 chunk][row][col][4 floats], 1-cell zero
-// halo), so each K-chunk of a window of 130 source cells (128 targets plus one on each side) is
-// one contiguous run of 2080 bytes: a window is KC bulk copies (cp.async.bulk) that land in the
-// canonical no-swizzle K-major shared layout (16-byte core-matrix rows, K-chunk stride
-// LBO = 130 x 16 B) and complete on the stage's mbarrier.  Warp 0 issues the copies (running up
-// to NSW windows ahead), warp 1 issues the MMAs, all four warps run the epilogue.  The three column
-// shifts of a group are then the same window read from a descriptor start moved by 16 B per
-// cell.  The operators of a group arrive by one bulk copy (cp.async.bulk).  A single thread
-// issues the MMAs; the accumulator lives in tensor memory and the epilogue reads it back with
-// tcgen05.ld.
+// with t the targets, n the outputs (N = 2H: Re b'_0..b'_p then Im b'_0..b'_p, each padded to H)
+// and kk the inputs (K = 2H per offset: Re M_0..M_p then Im M_0..M_p).  The 27 offsets of the
+// class fall into 12 groups that share one source window: the source parity (qx, qy) and the
+// source row shift sy.  The source grid of a parity is a (w2 + 2) x (w2 + 2) array with a 1-cell
+// zero halo, stored chunk-major ([parity][K/4 chunk][row][col][4 floats]); read as one flat array
+// of cells, a tile is 128 consecutive cells starting at flat position P and its window for shift
+// sy the 130 cells from P - 1 + sy (w2 + 2): each K-chunk of it is one contiguous run of 2080
+// bytes.  Rows of at least 128 targets take tiles aligned to the row; narrower sub-grids (levels
+// below 8) take consecutive runs of the flat array, and the outputs that fall on halo cells are
+// dropped.  A window is KC bulk copies (cp.async.bulk) that land in the canonical no-swizzle
+// K-major shared layout (16-byte core-matrix rows, K-chunk stride LBO = 130 x 16 B) and complete
+// on the stage's mbarrier; the three column shifts of a group are the same window read from a
+// descriptor start moved by 16 B per cell.  The operators are scale-free, so a CTA takes up to
+// eight tiles of one class from any levels and loads each group's operators (one bulk copy) once
+// for all of them.  Warp 0 issues the copies (running up to NSW windows ahead), one thread of
+// warp 1 issues the MMAs into one tensor-memory accumulator per tile, all four warps run the
+// epilogue, which reads the accumulators back with tcgen05.ld.
 //
 // 3xTF32 (Ootomo & Yokota, 2022): x = x_hi + x_lo with x_hi rounded to TF32, and
 // D += A_hi B_hi + A_hi B_lo + A_lo B_hi, dropping A_lo B_lo, recovers about FP32 accuracy.
@@ -25,8 +28,8 @@
 // The monopole-log term of b'_0, sum_d M_0 (log|w0| + ln s), carries the largest part of phi; it
 // stays out of the GEMM (its (0, 0) operator entry is zero): the epilogue sums it in float-float
 // from the FP32 moment grid, in both TF32 modes; a TF32 product of a large M_0 with the log
-// would lose more than the error bound allows on clustered systems.  Every wait on an mbarrier is bounded and
-// sets a status flag when it runs out.
+// would lose more than the error bound allows on clustered systems.  Every wait on an mbarrier
+// is bounded and sets a status flag when it runs out.
 
 #include <cmath>
 #include <cstring>
@@ -39,7 +42,9 @@ namespace {
 constexpr int kTile = 128;        // targets per tile (MMA M)
 constexpr int kWin = kTile + 2;   // source cells per window
 constexpr int kThreads = 128;
-constexpr int kMinLevel = 8;      // sub-grid rows of at least 128 targets
+constexpr int kMinLevel = 7;      // coarser levels stay on the CUDA cores (see fmm_tc_kmin)
+constexpr int kMaxRows = 8;       // tiles per CTA: 8 accumulators of 64 columns fill tensor memory
+constexpr int kSrcPad = 1024;     // cells after each source array: flat tiles past the last row read there
 constexpr unsigned kSpin = 1u << 24;
 
 struct TcGroup {
@@ -49,16 +54,36 @@ struct TcGroup {
 };
 
 struct TcArgs {
-    const float* src[2][FMM_MAX_LEVELS + 1];   // [part][level] -> [q][w2+2][w2+2][K] (1-cell zero halo)
-    const float* ops[2][FMM_MAX_LEVELS + 1];   // [part][level] -> [class][27 slots][KC][N][4]
+    const float* src[2][FMM_MAX_LEVELS + 1];   // [part][level] -> [q][KC][w2+2][w2+2][4] (1-cell zero halo)
+    const float* ops[2];                       // [part] -> [class][27 slots][KC][N][4], scale-free
     const float2* a32[FMM_MAX_LEVELS + 1];     // FP32 moment grids (3-cell halo) for the monopole term
     float2* B[FMM_MAX_LEVELS + 1];
     TcGroup groups[4][12];
     float2 logc[FMM_MAX_LEVELS + 1][49];
-    int cta_base[FMM_MAX_LEVELS + 2];
+    // the tiles of one class, finest level first: level seg_level[j] owns tiles
+    // seg_start[j] .. seg_start[j + 1] - 1; CTA b takes tiles c * rows .. of class b % 4, c = b / 4
+    int seg_start[FMM_MAX_LEVELS + 2];
+    int seg_level[FMM_MAX_LEVELS + 1];
+    int nseg, tiles, rows, tmem_cols;
     int levels, p;
     unsigned int* status;
 };
+
+// flat start (halo coordinates) of tile T of a parity sub-grid of width w2
+__host__ __device__ __forceinline__ int tile_start(int w2, int T) {
+    const int W2P = w2 + 2;
+    if (w2 >= kTile) {
+        const int per_row = w2 / kTile;
+        return (T / per_row + 1) * W2P + 1 + (T % per_row) * kTile;
+    }
+    return W2P + 1 + T * kTile;
+}
+
+__host__ __device__ __forceinline__ int tiles_of_level(int k) {
+    const int w2 = 1 << (k - 1);
+    if (w2 >= kTile) return w2 * (w2 / kTile);
+    return (w2 * (w2 + 2) - 2 + kTile - 1) / kTile;   // the flat run from (1, 1) to (w2, w2)
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -103,11 +128,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// A CTA takes kRows tiles: the same 128 columns of kRows consecutive sub-grid rows of one
-// parity class, one TMEM accumulator each.  For each of the 12 groups the operators are loaded
-// once and serve all kRows tiles; the group's kRows source windows stream through NSW buffers.
+// A CTA takes up to kMaxRows tiles of one parity class (any levels), one TMEM accumulator each.
+// For each of the 12 groups the operators are loaded once and serve all the CTA's tiles; the
+// group's source windows, one per tile, stream through NSW buffers.
 // Stages: ops buffers NSO (per group), window buffers NSW (per tile and group).
-constexpr int kRows = 4;
 
 template <int KC, int NP, int NSO, int NSW>
 __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ TcArgs a) {
@@ -117,7 +141,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     constexpr uint32_t OPS_STAGE = NP * 3 * OP_BYTES;
     constexpr uint32_t WIN_STAGE = NP * A_BYTES;
     constexpr uint32_t ACC_COLS = 64;                // per tile (N <= 64)
-    constexpr uint32_t TMEM_COLS = kRows * ACC_COLS;
     constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
 
     static_assert(NSW >= 2, "the window pipeline keeps one window in flight: it needs two window stages");
@@ -133,22 +156,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     uint64_t* win_empty = win_full + NSW;      // [NSW]
     uint64_t* done_bar = win_empty + NSW;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done_bar + 1);
+    int* tile_k = reinterpret_cast<int*>(tmem_holder + 1);   // [kMaxRows] level of each tile
+    int* tile_P = tile_k + kMaxRows;                           // [kMaxRows] flat start of each tile
 
     // ---- which tiles
-    const int cta = blockIdx.x;
-    int k = kMinLevel;
-    while (cta >= a.cta_base[k + 1]) ++k;
-    const int w2 = 1 << (k - 1);
-    const int tiles_per_row = w2 / kTile;
-    const int bands = w2 / kRows;
-    const int per_class = bands * tiles_per_row;
-    const int rel = cta - a.cta_base[k];
-    const int cls = rel / per_class;
-    const int rr = rel - cls * per_class;
-    const int y0 = (rr / tiles_per_row) * kRows;
-    const int u0 = (rr % tiles_per_row) * kTile;
+    const int cls = blockIdx.x & 3;
+    const int t0 = (blockIdx.x >> 2) * a.rows;
+    const int nrows = min(a.rows, a.tiles - t0);
     const int px = cls & 1, py = cls >> 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < nrows) {
+        const int tau = t0 + threadIdx.x;
+        int j = 0;
+        while (j + 1 < a.nseg && tau >= a.seg_start[j + 1]) ++j;
+        const int k = a.seg_level[j];
+        tile_k[threadIdx.x] = k;
+        tile_P[threadIdx.x] = tile_start(1 << (k - 1), tau - a.seg_start[j]);
+    }
+    const uint32_t TMEM_COLS = (uint32_t)a.tmem_cols;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_holder)),
@@ -173,15 +198,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
 
-    const int W2P = w2 + 2;
     bool ok = true;
-    constexpr int NWIN = 12 * kRows;
+    const int NWIN = 12 * nrows;
     if (warp == 0) {
         if (lane == 0) {
-            // producer: operators once per group, then the group's kRows windows; every copy is a
+            // producer: operators once per group, then the group's nrows windows; every copy is a
             // bulk copy completing on the stage's full barrier, so the producer runs ahead
             for (int i = 0; i < NWIN; ++i) {
-                const int g = i / kRows, t = i % kRows;
+                const int g = i / nrows, t = i % nrows;
                 const TcGroup& G = a.groups[cls][g];
                 if (t == 0) {
                     const int so = g % NSO, uso = g / NSO;
@@ -191,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                                  "r"(bytes)
                                  : "memory");
                     for (int part = 0; part < NP; ++part) {
-                        const float* srcB = a.ops[part][k] + ((size_t)cls * 27 + G.slot0) * (OP_BYTES / 4);
+                        const float* srcB = a.ops[part] + ((size_t)cls * 27 + G.slot0) * (OP_BYTES / 4);
                         asm volatile(
                             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
                                 "r"(su32(ops_buf + so * OPS_STAGE + part * 3 * OP_BYTES)),
@@ -205,13 +229,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                              "r"((uint32_t)(NP * A_BYTES))
                              : "memory");
                 const int q = G.qx + 2 * G.qy;
-                const int row = y0 + t + G.sy + 1;   // halo coordinates
+                const int k = tile_k[t];
+                const size_t W2P = ((size_t)1 << (k - 1)) + 2;
+                const size_t start = (size_t)(tile_P[t] - 1 + G.sy * (int)W2P);   // flat, >= 0
                 for (int part = 0; part < NP; ++part) {
                     const float* base = a.src[part][k];
                     const uint32_t dst = su32(win_buf + sw * WIN_STAGE + part * A_BYTES);
                     for (int j = 0; j < KC; ++j) {
-                        // chunk j of cells u0 .. u0 + 129 (halo coordinates) of this row: 2080 contiguous bytes
-                        const float* src = base + ((((size_t)q * KC + j) * W2P + row) * W2P + u0) * 4;
+                        // chunk j of the 130 cells from the window's flat start: 2080 contiguous bytes
+                        const float* src = base + (((size_t)q * KC + j) * W2P * W2P + start) * 4;
                         asm volatile(
                             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
                                 "r"(dst + (uint32_t)j * (kWin * 16)),
@@ -226,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
         if (lane == 0) {
             // MMA issuer
             for (int i = 0; i < NWIN; ++i) {
-                const int g = i / kRows, t = i % kRows;
+                const int g = i / nrows, t = i % nrows;
                 const TcGroup& G = a.groups[cls][g];
                 const int so = g % NSO, uso = g / NSO;
                 const int sw = i % NSW, usw = i / NSW;
@@ -257,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  su32(&win_empty[sw]))
                              : "memory");
-                if (t == kRows - 1)
+                if (t == nrows - 1)
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                      su32(&ops_empty[so]))
                                  : "memory");
@@ -274,17 +300,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     // ---- epilogue: warp w holds accumulator rows (targets) 32w..32w+31 of every tile
-    const int W = fmm_grid_width(k), p1 = a.p + 1;
-    const float2* A32 = a.a32[k];
-    for (int t = 0; t < kRows; ++t) {
+    const int p1 = a.p + 1;
+    for (int t = 0; t < nrows; ++t) {
         float v[N];
 #pragma unroll
         for (int c = 0; c < N; c += 16)
             tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * ACC_COLS + c), v + c);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (done) {
-            const int i = 32 * warp + lane;
-            const int tx = 2 * (u0 + i) + px, ty = 2 * (y0 + t) + py;
+        const int k = tile_k[t];
+        const int w2 = 1 << (k - 1), W2P = w2 + 2;
+        const int pos = tile_P[t] + 32 * warp + lane;
+        const int x = pos % W2P - 1, y = pos / W2P - 1;   // sub-grid cell; halo cells are dropped
+        if (done && x >= 0 && x < w2 && y < w2) {
+            const int W = fmm_grid_width(k);
+            const float2* A32 = a.a32[k];
+            const int tx = 2 * x + px, ty = 2 * y + py;
             // the monopole-log term, summed in float-float from the FP32 moment grid
             float2 mono = make_float2(0.f, 0.f);
             for (int dy = -2 - py; dy <= 3 - py; ++dy)
@@ -313,17 +343,27 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
+struct PrepArgs {
+    const float2* a32[FMM_MAX_LEVELS + 1];
+    float4* hi[FMM_MAX_LEVELS + 1];
+    float4* lo[FMM_MAX_LEVELS + 1];
+    long long base[FMM_MAX_LEVELS + 2];   // first cell (over all four parities) of each level
+    int kmin, levels, p1;
+};
+
 template <int KC, int NP>
-__global__ void k_prep_tc(const float2* __restrict__ a32, int k, int p1, float4* __restrict__ hi,
-                          float4* __restrict__ lo) {
+__global__ void k_prep_tc(const __grid_constant__ PrepArgs a) {
     constexpr int H = 2 * KC;
-    const int w2 = 1 << (k - 1), W2P = w2 + 2;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 4ll * w2 * w2) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.base[a.levels + 1]) return;
+    int k = a.kmin;
+    while (g >= a.base[k + 1]) ++k;
+    const int64_t e = g - a.base[k];
+    const int w2 = 1 << (k - 1), W2P = w2 + 2, p1 = a.p1;
     const int col = (int)(e % w2), row = (int)((e / w2) % w2), q = (int)(e / ((int64_t)w2 * w2));
     const int x = 2 * col + (q & 1), y = 2 * row + (q >> 1);
     const int W = fmm_grid_width(k);
-    const float2* src = a32 + ((size_t)(y + FMM_HALO) * W + (x + FMM_HALO)) * p1;
+    const float2* src = a.a32[k] + ((size_t)(y + FMM_HALO) * W + (x + FMM_HALO)) * p1;
     float vals[2 * H];
 #pragma unroll
     for (int j = 0; j < H; ++j) {
@@ -332,7 +372,9 @@ __global__ void k_prep_tc(const float2* __restrict__ a32, int k, int p1, float4*
         vals[H + j] = (j == 0) ? 0.f : m.y;
     }
     // chunk-major source layout [q][chunk][row][col][4] (1-cell zero halo): the chunk of a run of
-    // consecutive cells of one row is one contiguous block
+    // consecutive cells of the flat array is one contiguous block
+    float4* hi = a.hi[k];
+    float4* lo = a.lo[k];
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
         float h[4], l[4];
@@ -379,12 +421,15 @@ constexpr int tc_nsw() {
 
 // ---------------------------------------------------------------- plan-side state
 struct FmmTc {
-    int kc, np;
+    int kc, np, sms;
     float* ops[2];                              // one scale-free copy per part
     float4* src[2][FMM_MAX_LEVELS + 1];
     TcArgs args;   // tensor maps and tables, filled at plan time
 };
 
+// The tensor cores take levels kMinLevel and finer.  The coarse levels carry most of the far
+// field's amplitude, and the tensor core's FP32 accumulation (product alignment and rounding inside
+// each MMA) loses more there than FP32 FMAs; they hold few targets, so the CUDA cores take them.
 int fmm_tc_kmin() { return kMinLevel; }
 
 // Allocate and build the tensor-core M2L state.  Returns 0, or a negative value on failure
@@ -400,6 +445,10 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
     tc->kc = kc;
     tc->np = np;
     pl->tc = tc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&tc->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -1;
     const int N = 4 * kc, K = 4 * kc;
 
     // class tables: 12 groups (source parity qx, qy and row shift sy) of 1..3 offsets each
@@ -467,13 +516,13 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
             pl->workspace_bytes += opsz * 4;
             if (cudaMemcpy(tc->ops[part], hostops[part].data(), opsz * 4, cudaMemcpyHostToDevice) != cudaSuccess)
                 return -1;
-            for (int k = kMinLevel; k <= pl->levels; ++k) tc->args.ops[part][k] = tc->ops[part];
+            tc->args.ops[part] = tc->ops[part];
         }
     }
-    // source buffers (chunk-major, 1-cell zero halo), levels kMinLevel..L
+    // source buffers (chunk-major, 1-cell zero halo, kSrcPad zero cells after), levels kMinLevel..L
     for (int k = kMinLevel; k <= pl->levels; ++k) {
         const size_t w2p = ((size_t)1 << (k - 1)) + 2;
-        const size_t bytes = (size_t)4 * w2p * w2p * kc * 16;
+        const size_t bytes = ((size_t)4 * w2p * w2p * kc + kSrcPad) * 16;
         for (int part = 0; part < np; ++part) {
             if (cudaMalloc(&tc->src[part][k], bytes) != cudaSuccess) return -1;
             pl->workspace_bytes += bytes;
@@ -501,12 +550,21 @@ static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
     FmmTc* tc = pl->tc;
     cudaStream_t st = pl->stream;
     const int L = pl->levels, p1 = pl->p + 1;
-    int launches = 0;
-    for (int k = kMinLevel; k <= L; ++k) {
-        const int64_t cells = 4ll << (2 * (k - 1));
-        k_prep_tc<KC, NP><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(
-            reinterpret_cast<const float2*>(pl->grids.A32[k]), k, p1, tc->src[0][k], tc->src[1][k]);
-        ++launches;
+    {
+        PrepArgs pa{};
+        long long acc = 0;
+        for (int k = kMinLevel; k <= L; ++k) {
+            pa.a32[k] = reinterpret_cast<const float2*>(pl->grids.A32[k]);
+            pa.hi[k] = tc->src[0][k];
+            pa.lo[k] = tc->src[1][k];
+            pa.base[k] = acc;
+            acc += 4ll << (2 * (k - 1));
+        }
+        pa.base[L + 1] = acc;
+        pa.kmin = kMinLevel;
+        pa.levels = L;
+        pa.p1 = p1;
+        k_prep_tc<KC, NP><<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(pa);
     }
     TcArgs& a = tc->args;
     for (int k = 0; k <= FMM_MAX_LEVELS; ++k) {
@@ -517,24 +575,35 @@ static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
     a.levels = L;
     a.p = pl->p;
     a.status = pl->d_status;
-    int acc = 0;
-    for (int k = 0; k <= FMM_MAX_LEVELS + 1; ++k) a.cta_base[k] = 0;
-    for (int k = kMinLevel; k <= L; ++k) {
-        a.cta_base[k] = acc;
-        const int w2 = 1 << (k - 1);
-        acc += 4 * (w2 / kRows) * (w2 / kTile);
+    // the tiles of a class, finest level first; rows per CTA so that the four classes fill the
+    // SMs about once (at most kMaxRows: more tiles make more waves)
+    int tiles = 0, nseg = 0;
+    for (int k = L; k >= kMinLevel; --k) {
+        a.seg_start[nseg] = tiles;
+        a.seg_level[nseg] = k;
+        ++nseg;
+        tiles += tiles_of_level(k);
     }
-    for (int k = L + 1; k <= FMM_MAX_LEVELS + 1; ++k) a.cta_base[k] = acc;
+    a.seg_start[nseg] = tiles;
+    a.nseg = nseg;
+    a.tiles = tiles;
+    const int per_class_ctas = tc->sms / 4 > 0 ? tc->sms / 4 : 1;
+    a.rows = (tiles + per_class_ctas - 1) / per_class_ctas;
+    if (a.rows > kMaxRows) a.rows = kMaxRows;
+    if (a.rows < 1) a.rows = 1;
+    int cols = 32;
+    while (cols < a.rows * 64) cols <<= 1;
+    a.tmem_cols = cols;
+    const int items = (tiles + a.rows - 1) / a.rows;
     constexpr int NSO = tc_nso<KC, NP>(), NSW = tc_nsw<KC, NP>();
     const size_t shm = tc_bytes<KC, NP>(NSO, NSW);
     auto kern = k_m2l_tc<KC, NP, NSO, NSW>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
-    kern<<<acc, kThreads, shm, st>>>(a);
-    ++launches;
-    return launches;
+    kern<<<4 * items, kThreads, shm, st>>>(a);
+    return 2;
 }
 
-// Launch prep + tensor-core M2L for levels kMinLevel..L; returns kernels launched or -1.
+// Launch prep + tensor-core M2L for levels 2..L; returns kernels launched or -1.
 int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv) {
     const FmmTc* tc = pl->tc;
     if (!tc || pl->levels < kMinLevel) return 0;

@@ -233,8 +233,142 @@ struct M2LMixedArgs {
     FmmLevelPtrs g;
     const float2* T;                    // [49][P1B][P1B] FP32, zero beyond p and at [d][0][0]
     int cta_base[FMM_MAX_LEVELS + 2];   // first CTA of each level
-    int levels, p, kmax;                // levels 2..kmax run here
+    int levels, p, kmin, kmax;          // levels kmin..kmax run here
 };
+
+// Coarse levels (few targets, so one thread per target would leave the GPU idle and wait on
+// one long dependent chain): a CTA takes 4 x kM2LWarpTargets targets of one parity class, one
+// warp per kM2LWarpTargets targets, lanes over the outputs b'_l (l = lane, lane + 32).  The 27
+// offsets of the class run in sequence; each offset's operator is staged in shared memory (two
+// buffers), and the next offset's operator and source moments are loaded into registers while
+// the current one is applied, so the loads' latency hides behind the FMAs.  Same arithmetic as
+// the thread-per-target kernel: FP32 FMAs, the monopole-log term in float-float.
+constexpr int kM2LWarpTargets = 2;
+constexpr int kM2LWarpMaxLevel = 6;   // 4^6 targets: the finest level this kernel takes
+
+struct M2LWarpArgs {
+    FmmLevelPtrs g;
+    const float2* T;
+    int cbase[FMM_MAX_LEVELS + 2];      // first CTA of each level
+    int kw, p;                          // levels 2..kw run here
+};
+
+template <int P1B>
+__global__ void __launch_bounds__(128) k_m2l_coarse(M2LWarpArgs a, MixedLevels lv) {
+    constexpr int NT = kM2LWarpTargets, NL = (P1B + 31) / 32;
+    constexpr int TE = P1B * P1B, RT = (TE + 127) / 128;   // operator entries, per thread
+    __shared__ float2 Ts[2][TE];
+    __shared__ float2 src_s[4][NT][P1B];
+    __shared__ int dl[27];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cta = blockIdx.x;
+    int k = 2;
+    while (cta >= a.cbase[k + 1]) ++k;
+    const int w2 = 1 << (k - 1);
+    const int per_class = (w2 * w2 + 4 * NT - 1) / (4 * NT);
+    const int rel = cta - a.cbase[k];
+    const int cls = rel / per_class;
+    const int u0 = (rel - cls * per_class) * 4 * NT + warp * NT;
+    const int px = cls & 1, py = cls >> 1;
+    const int p1 = a.p + 1, W = fmm_grid_width(k);
+    const float2* A = reinterpret_cast<const float2*>(a.g.A32[k]);
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int dy = -2 - py; dy <= 3 - py; ++dy)
+            for (int dx = -2 - px; dx <= 3 - px; ++dx)
+                if (!(dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1)) dl[c++] = (dx + 3) + 7 * (dy + 3);
+    }
+    int tx[NT], ty[NT];
+    bool act[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int u = u0 + j;
+        act[j] = u < w2 * w2;
+        tx[j] = act[j] ? 2 * (u % w2) + px : px;
+        ty[j] = act[j] ? 2 * (u / w2) + py : py;
+    }
+    __syncthreads();
+    // registers holding the next offset's operator share and source moments
+    float2 tr[RT], sr[NT][NL];
+    auto fetch = [&](int i) {
+        const int d = dl[i];
+        const float2* Td = a.T + (size_t)d * TE;
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            const int e = threadIdx.x + 128 * r;
+            tr[r] = (e < TE) ? __ldg(Td + e) : make_float2(0.f, 0.f);
+        }
+        const int dx = d % 7 - 3, dy = d / 7 - 3;
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            // sources outside the domain read the zero halo
+            const float2* src = A + ((size_t)(ty[j] + dy + FMM_HALO) * W + (tx[j] + dx + FMM_HALO)) * p1;
+#pragma unroll
+            for (int i2 = 0; i2 < NL; ++i2) {
+                const int kk = lane + 32 * i2;
+                sr[j][i2] = (kk < p1) ? src[kk] : make_float2(0.f, 0.f);
+            }
+        }
+    };
+    float2 acc[NT][NL];
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+        for (int i = 0; i < NL; ++i) acc[j][i] = make_float2(0.f, 0.f);
+    float2 mono = make_float2(0.f, 0.f);   // lane j < NT: target j
+    fetch(0);
+    for (int i = 0; i < 27; ++i) {
+        const int buf = i & 1;
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            const int e = threadIdx.x + 128 * r;
+            if (e < TE) Ts[buf][e] = tr[r];
+        }
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int i2 = 0; i2 < NL; ++i2) {
+                const int kk = lane + 32 * i2;
+                if (kk < P1B) src_s[warp][j][kk] = sr[j][i2];
+            }
+        const int d = dl[i];
+        __syncthreads();   // Ts[buf] complete; the previous reader of this buffer is two offsets back
+        if (i + 1 < 27) fetch(i + 1);
+        if (lane < NT) mono = ff_add(mono, ff_mul(src_s[warp][lane][0], lv.logc[k][d]));
+#pragma unroll
+        for (int kk = 0; kk < P1B; ++kk) {
+            float2 t[NL];
+#pragma unroll
+            for (int i2 = 0; i2 < NL; ++i2) {
+                const int l = lane + 32 * i2;
+                t[i2] = (l < P1B) ? Ts[buf][kk * P1B + l] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                float2 m = src_s[warp][j][kk];
+                if (kk == 0) m.y = 0.f;   // M_0 is real; .y held its low word
+#pragma unroll
+                for (int i2 = 0; i2 < NL; ++i2) {
+                    acc[j][i2].x = fmaf(t[i2].x, m.x, fmaf(-t[i2].y, m.y, acc[j][i2].x));
+                    acc[j][i2].y = fmaf(t[i2].x, m.y, fmaf(t[i2].y, m.x, acc[j][i2].y));
+                }
+            }
+        }
+        __syncwarp();   // src_s of this warp is rewritten at the next offset
+    }
+    float2* B = reinterpret_cast<float2*>(a.g.B[k]);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const float2 mj = make_float2(__shfl_sync(0xffffffffu, mono.x, j), __shfl_sync(0xffffffffu, mono.y, j));
+        if (!act[j]) continue;
+        const size_t t = (size_t)ty[j] * (1u << k) + tx[j];
+#pragma unroll
+        for (int i2 = 0; i2 < NL; ++i2) {
+            const int l = lane + 32 * i2;
+            if (l < p1) B[t * p1 + l] = (l == 0) ? ff_add_f(mj, acc[j][i2].x) : acc[j][i2];   // Re b'_0 as float-float
+        }
+    }
+}
 
 // One thread per target square; the CTA's 128 targets share one parity class (so one list of
 // 27 offsets) and stage each offset's operator in shared memory, read as broadcasts.
@@ -242,7 +376,7 @@ template <int P1B>
 __global__ void __launch_bounds__(kM2LThreads) k_m2l_f32(M2LMixedArgs a, MixedLevels lv) {
     __shared__ float2 Ts[P1B * P1B];
     const int cta = blockIdx.x;
-    int k = 2;
+    int k = a.kmin;
     while (cta >= a.cta_base[k + 1]) ++k;
     const int w2 = 1 << (k - 1);                       // parity sub-grid width
     const int per_class = (w2 * w2 + kM2LThreads - 1) / kM2LThreads;
@@ -513,6 +647,11 @@ void launch_m2l(const M2LMixedArgs& a, const MixedLevels& lv, int blocks, cudaSt
     k_m2l_f32<P1B><<<blocks, kM2LThreads, 0, st>>>(a, lv);
 }
 
+template <int P1B>
+void launch_m2l_coarse(const M2LWarpArgs& a, const MixedLevels& lv, int blocks, cudaStream_t st) {
+    k_m2l_coarse<P1B><<<blocks, 128, 0, st>>>(a, lv);
+}
+
 }  // namespace
 
 int fmm_m2l_bucket(int p1) {
@@ -525,7 +664,7 @@ int fmm_m2l_bucket(int p1) {
 int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     if (pl->precision != FMM_MIXED_FP32 && pl->precision != FMM_MIXED_TF32 && pl->precision != FMM_MIXED_3XTF32)
         return -2;
-    // the tensor-core M2L takes the levels whose parity sub-grid rows hold at least 128 targets
+    // in the TF32 modes the tensor-core M2L takes the levels from fmm_tc_kmin() on
     const bool use_tc = pl->tc != nullptr && pl->levels >= fmm_tc_kmin();
     cudaStream_t st = pl->stream;
     const int64_t n = pl->n;
@@ -576,31 +715,59 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     }
     cudaEventRecord(pl->ev[2], st);
     if (L >= 2) {
+        // coarse levels: a CTA per 4 x kM2LWarpTargets targets of one class
+        M2LWarpArgs wa;
+        wa.g = pl->grids;
+        wa.T = pl->T32;
+        wa.p = p;
+        wa.kw = L < kM2LWarpMaxLevel ? L : kM2LWarpMaxLevel;
+        int wacc = 0;
+        for (int k = 0; k <= FMM_MAX_LEVELS + 1; ++k) wa.cbase[k] = 0;
+        for (int k = 2; k <= wa.kw; ++k) {
+            wa.cbase[k] = wacc;
+            wacc += 4 * (((1 << (2 * (k - 1))) + 4 * kM2LWarpTargets - 1) / (4 * kM2LWarpTargets));
+        }
+        wa.cbase[wa.kw + 1] = wacc;
+        switch (pl->p1b) {
+            case 9: launch_m2l_coarse<9>(wa, lv, wacc, st); break;
+            case 13: launch_m2l_coarse<13>(wa, lv, wacc, st); break;
+            case 17: launch_m2l_coarse<17>(wa, lv, wacc, st); break;
+            case 21: launch_m2l_coarse<21>(wa, lv, wacc, st); break;
+            case 25: launch_m2l_coarse<25>(wa, lv, wacc, st); break;
+            case 33: launch_m2l_coarse<33>(wa, lv, wacc, st); break;
+            case 41: launch_m2l_coarse<41>(wa, lv, wacc, st); break;
+            default: return -2;
+        }
+        ++launches;
+        // finer levels: one thread per target, or the tensor cores
         M2LMixedArgs a;
         a.g = pl->grids;
         a.T = pl->T32;
         a.levels = L;
         a.p = p;
+        a.kmin = wa.kw + 1;
         a.kmax = use_tc ? fmm_tc_kmin() - 1 : L;
         int acc = 0;
         for (int k = 0; k <= FMM_MAX_LEVELS + 1; ++k) a.cta_base[k] = 0;
-        for (int k = 2; k <= a.kmax; ++k) {
+        for (int k = a.kmin; k <= a.kmax; ++k) {
             a.cta_base[k] = acc;
             const int w2 = 1 << (k - 1);
             acc += 4 * ((w2 * w2 + kM2LThreads - 1) / kM2LThreads);
         }
         a.cta_base[a.kmax + 1] = acc;
-        switch (pl->p1b) {
-            case 9: launch_m2l<9>(a, lv, acc, st); break;
-            case 13: launch_m2l<13>(a, lv, acc, st); break;
-            case 17: launch_m2l<17>(a, lv, acc, st); break;
-            case 21: launch_m2l<21>(a, lv, acc, st); break;
-            case 25: launch_m2l<25>(a, lv, acc, st); break;
-            case 33: launch_m2l<33>(a, lv, acc, st); break;
-            case 41: launch_m2l<41>(a, lv, acc, st); break;
-            default: return -2;
+        if (acc > 0) {
+            switch (pl->p1b) {
+                case 9: launch_m2l<9>(a, lv, acc, st); break;
+                case 13: launch_m2l<13>(a, lv, acc, st); break;
+                case 17: launch_m2l<17>(a, lv, acc, st); break;
+                case 21: launch_m2l<21>(a, lv, acc, st); break;
+                case 25: launch_m2l<25>(a, lv, acc, st); break;
+                case 33: launch_m2l<33>(a, lv, acc, st); break;
+                case 41: launch_m2l<41>(a, lv, acc, st); break;
+                default: return -2;
+            }
+            ++launches;
         }
-        ++launches;
         if (use_tc) {
             const int t = fmm_launch_m2l_tc(pl, lv);
             if (t < 0) return -1;

@@ -67,7 +67,7 @@ def test_mixed_full_size_uniform_1m(oracle_mod):
     (200000, 8, 16, "annulus", 9),      # p = 16 (K = N = 48 with padding)
 ])
 def test_tensor_core_m2l_matches_oracle(oracle_mod, precision, tol, case):
-    """M2L of level 8 on tcgen05 (TF32 / split 3xTF32), levels 2..7 on the CUDA cores."""
+    """M2L of levels 7..8 on tcgen05 (TF32 / split 3xTF32), levels 2..6 on the CUDA cores."""
     from gpu_util import run_fmm
     n, lev, p, fam, seed = case
     xy, q = getattr(inputs, fam)(n, inputs.config_seed(0, 300 + seed))
@@ -89,15 +89,25 @@ def test_tensor_core_full_size_uniform_1m(oracle_mod):
     assert err < MIXED_TOL
 
 
-def test_tensor_core_modes_below_level_8_use_the_cuda_cores(oracle_mod):
+@pytest.mark.parametrize("precision,tol", [("3xtf32", MIXED_TOL), ("tf32", 1e-3)])
+@pytest.mark.parametrize("case", [
+    (3000, 2, 8, "uniform", 11),        # 2 x 2 parity sub-grids: one flat tile, mostly halo
+    (4096, 3, 5, "gmm", 12),            # p = 5 (K = N = 16)
+    (4096, 4, 16, "uniform", 13),       # the 4096-particle, levels 4, p = 16 configuration
+    (20000, 6, 14, "annulus", 14),      # 32-wide sub-grid rows: tiles span rows and halo cells
+    (60000, 7, 20, "gmm", 15),          # 64-wide rows, the largest flat-tiled level
+])
+def test_tensor_core_modes_coarse_levels(oracle_mod, precision, tol, case):
+    """Levels 2..6 on the CUDA cores (a warp per four targets); level 7 on tcgen05, whose 64-wide
+    parity sub-grid rows are read as one flat array of 128-target tiles."""
     from gpu_util import run_fmm
-    xy, q = inputs.uniform(20000, 410)
-    a, sa = run_fmm(xy, q, 6, 14, precision="3xtf32")
-    b, sb = run_fmm(xy, q, 6, 14, precision="fp32")
-    # the same kernels run; the order of particles inside a finest square comes from atomic
-    # ranks, so FP32 sums may differ between calls at the level of FP32 rounding
-    assert sa["kernel_launches"] == sb["kernel_launches"]
-    assert rel_l2(a, b) < MIXED_TOL
+    n, lev, p, fam, seed = case
+    xy, q = getattr(inputs, fam)(n, inputs.config_seed(0, 300 + seed))
+    phi, st = run_fmm(xy, q, lev, p, precision=precision)
+    ref = oracle_mod.shiftfree(xy, q, lev, p)
+    err = rel_l2(phi, ref)
+    print(f"{precision} N={n} levels={lev} p={p} {fam}: rel L2 vs oracle {err:.3e}")
+    assert err < tol
 
 
 def test_crowded_squares_split_over_warps(oracle_mod):
