@@ -41,7 +41,9 @@ UNIT = "particles/s"
 ERR_BOUND = 1e-6
 N_SMS = 152
 FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (4 sub-partitions x 32)
-MUFU_PER_SM = 16               # lg2 results per clock per SM
+MUFU_PER_SM = 32               # lg2 results per clock per SM on GB300: ncu puts the XU pipe's peak at one
+                               # warp instruction per SM cycle (6.52 M lg2 warp instructions in 160 us,
+                               # 48.4 M SM cycles, read 13.3 % of it)
 
 WORKLOADS = {
     "uniform_1m_l8_p20": dict(n=1 << 20, levels=8, p=20, family="uniform", config=1),

@@ -68,8 +68,8 @@ void free_plan(fmm_plan_s* pl) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(pl->device);
-    void* bufs[] = {pl->keys, pl->rank, pl->counts, pl->leaf_start, pl->block_sums, pl->leaf_nb, pl->leaf_bstart,
-                    pl->sorted_key,
+    void* bufs[] = {pl->keys, pl->rank, pl->counts, pl->leaf_start, pl->block_sums, pl->leaf_bstart,
+                    pl->blk_map, pl->sorted_key,
                     pl->sorted64, pl->sorted32, pl->phi_far, pl->T64, pl->T32, pl->d_status,
                     pl->d_counters, pl->d_xy_stage, pl->d_q_stage, pl->d_phi_stage};
     for (void* b : bufs)
@@ -167,10 +167,11 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->counts, sizeof(uint32_t) * m));
     FMM_TRY(dev_alloc(pl, &pl->leaf_start, sizeof(uint32_t) * (m + 1)));
     pl->scan_blocks = fmm_scan_blocks(m);
-    FMM_TRY(dev_alloc(pl, &pl->block_sums, sizeof(uint32_t) * (pl->scan_blocks + 1)));
+    // 64-bit partials in the mixed path (one scan of populations and near-field blocks)
+    FMM_TRY(dev_alloc(pl, &pl->block_sums, sizeof(unsigned long long) * (pl->scan_blocks + 1)));
     if (precision != FMM_FP64) {
-        FMM_TRY(dev_alloc(pl, &pl->leaf_nb, sizeof(uint32_t) * m));
         FMM_TRY(dev_alloc(pl, &pl->leaf_bstart, sizeof(uint32_t) * (m + 1)));
+        FMM_TRY(dev_alloc(pl, &pl->blk_map, sizeof(uint2) * ((size_t)m + (size_t)n / FMM_P2P_BLOCK + 1)));
     }
     FMM_TRY(dev_alloc(pl, &pl->sorted_key, sizeof(uint32_t) * n));
     if (precision == FMM_FP64)

@@ -672,7 +672,7 @@ int enqueue_batch_kernels(fmm_batch_s* b, const BatchArgs& a, const MixedLevels&
     }
     kb_m2l_f32<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
     kb_l2p<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
-    const int lb = fmm_launch_leaf_blocks(b->leaf_start, b->nl, b->leaf_nb, b->block_sums, b->bstart, st);
+    const int lb = fmm_launch_leaf_blocks(b->leaf_start, b->nl, 32u, b->leaf_nb, b->block_sums, b->bstart, nullptr, st);
     if (lb < 0) return -1;
     kb_p2p<<<grid, kT, pre_bytes, st>>>(a, lv);
     launches += 3 + lb;

@@ -89,10 +89,10 @@ struct fmm_plan_s {
     uint32_t* rank;
     uint32_t* counts;
     uint32_t* leaf_start;
-    uint32_t* block_sums;        // scan partials, scan_blocks + 1 entries
+    uint32_t* block_sums;        // scan partials, scan_blocks + 1 entries (64-bit in the mixed path)
     int scan_blocks;
-    uint32_t* leaf_nb;           // near-field target blocks per finest square (mixed path)
-    uint32_t* leaf_bstart;       // their exclusive scan, 4^levels + 1 entries
+    uint32_t* leaf_bstart;       // near-field target blocks: exclusive scan over the squares, 4^levels + 1
+    uint2* blk_map;              // near-field block -> (square, block inside it), mixed path
     uint32_t* sorted_key;
     fmm_p64* sorted64;
     float4* sorted32;
@@ -189,8 +189,12 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q);
 int fmm_scan_blocks(int64_t m);
 int fmm_launch_scan(const uint32_t* counts, int64_t m, uint32_t* block_sums, uint32_t* leaf_start, uint32_t n_total,
                     cudaStream_t st);
-int fmm_launch_leaf_blocks(const uint32_t* leaf_start, int64_t m, uint32_t* nb, uint32_t* block_sums, uint32_t* bstart,
-                           cudaStream_t st);
+// Near-field target blocks: nb[i] = ceil(population of square i / block), bstart = their exclusive
+// scan (m + 1 entries), and, if map is not null, map[b] = (square, index of b inside it).
+int fmm_launch_leaf_blocks(const uint32_t* leaf_start, int64_t m, uint32_t block, uint32_t* nb, uint32_t* block_sums,
+                           uint32_t* bstart, uint2* map, cudaStream_t st);
+// targets per near-field block of the mixed path (the batched form uses 32)
+#define FMM_P2P_BLOCK 24
 
 // largest i in [0, m) with pre[i] <= w, for a non-decreasing pre with pre[0] <= w: a 32-ary
 // search by the whole warp (each step probes 32 evenly spaced entries), about log32(m) loads

@@ -13,23 +13,23 @@
 // sy the 130 cells from P - 1 + sy (w2 + 2): each K-chunk of it is one contiguous run of 2080
 // bytes.  Rows of at least 128 targets take tiles aligned to the row; narrower sub-grids (levels
 // below 8) take consecutive runs of the flat array, and the outputs that fall on halo cells are
-// dropped.  A window is KC bulk copies (cp.async.bulk) that land in the canonical no-swizzle
-// K-major shared layout (16-byte core-matrix rows, K-chunk stride LBO = 130 x 16 B) and complete
-// on the stage's mbarrier; the three column shifts of a group are the same window read from a
+// dropped.  A window is KC bulk copies (cp.async.bulk) per part, issued by the producer warp's
+// lanes in parallel, that land in the canonical no-swizzle K-major shared layout (16-byte
+// core-matrix rows, K-chunk stride LBO = 130 x 16 B) and complete on the stage's mbarrier; the three column shifts of a group are the same window read from a
 // descriptor start moved by 16 B per cell.  The operators are scale-free, so a CTA takes up to
 // eight tiles of one class from any levels and loads each group's operators (one bulk copy) once
 // for all of them.  Warp 0 issues the copies (running up to NSW windows ahead), one thread of
 // warp 1 issues the MMAs into one tensor-memory accumulator per tile, all four warps run the
-// epilogue, which reads the accumulators back with tcgen05.ld.
+// epilogue, which reads the accumulators back with tcgen05.ld and stores them.
 //
 // 3xTF32 (Ootomo & Yokota, 2022): x = x_hi + x_lo with x_hi rounded to TF32, and
 // D += A_hi B_hi + A_hi B_lo + A_lo B_hi, dropping A_lo B_lo, recovers about FP32 accuracy.
 //
 // The monopole-log term of b'_0, sum_d M_0 (log|w0| + ln s), carries the largest part of phi; it
-// stays out of the GEMM (its (0, 0) operator entry is zero): the epilogue sums it in float-float
-// from the FP32 moment grid, in both TF32 modes; a TF32 product of a large M_0 with the log
-// would lose more than the error bound allows on clustered systems.  Every wait on an mbarrier
-// is bounded and sets a status flag when it runs out.
+// stays out of the GEMM (its (0, 0) operator entry is zero): k_m2l_mono sums it in float-float
+// from the FP32 moment grid after the GEMM, in both TF32 modes; a TF32 product of a large M_0
+// with the log would lose more than the error bound allows on clustered systems.  Every wait on
+// an mbarrier is bounded and sets a status flag when it runs out.
 
 #include <cmath>
 #include <cstring>
@@ -56,10 +56,8 @@ struct TcGroup {
 struct TcArgs {
     const float* src[2][FMM_MAX_LEVELS + 1];   // [part][level] -> [q][KC][w2+2][w2+2][4] (1-cell zero halo)
     const float* ops[2];                       // [part] -> [class][27 slots][KC][N][4], scale-free
-    const float2* a32[FMM_MAX_LEVELS + 1];     // FP32 moment grids (3-cell halo) for the monopole term
     float2* B[FMM_MAX_LEVELS + 1];
     TcGroup groups[4][12];
-    float2 logc[FMM_MAX_LEVELS + 1][49];
     // the tiles of one class, finest level first: level seg_level[j] owns tiles
     // seg_start[j] .. seg_start[j + 1] - 1; CTA b takes tiles c * rows .. of class b % 4, c = b / 4
     int seg_start[FMM_MAX_LEVELS + 2];
@@ -201,50 +199,57 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     bool ok = true;
     const int NWIN = 12 * nrows;
     if (warp == 0) {
-        if (lane == 0) {
-            // producer: operators once per group, then the group's nrows windows; every copy is a
-            // bulk copy completing on the stage's full barrier, so the producer runs ahead
-            for (int i = 0; i < NWIN; ++i) {
-                const int g = i / nrows, t = i % nrows;
-                const TcGroup& G = a.groups[cls][g];
-                if (t == 0) {
-                    const int so = g % NSO, uso = g / NSO;
+        // producer warp: lane 0 waits for a free stage and posts its byte count, then the lanes
+        // issue the stage's bulk copies in parallel (an operator part, or one K chunk of one part
+        // of the window each); every copy completes on the stage's full barrier, so the producer
+        // runs ahead of the MMAs
+        for (int i = 0; i < NWIN; ++i) {
+            const int g = i / nrows, t = i % nrows;
+            const TcGroup& G = a.groups[cls][g];
+            if (t == 0) {
+                const int so = g % NSO, uso = g / NSO;
+                const uint32_t bytes = (uint32_t)G.nops * OP_BYTES;
+                if (lane == 0) {
                     if (g >= NSO && !wait_bar(su32(&ops_empty[so]), (uint32_t)((uso - 1) & 1))) ok = false;
-                    const uint32_t bytes = NP * (uint32_t)G.nops * OP_BYTES;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&ops_full[so])),
-                                 "r"(bytes)
+                                 "r"(NP * bytes)
                                  : "memory");
-                    for (int part = 0; part < NP; ++part) {
-                        const float* srcB = a.ops[part] + ((size_t)cls * 27 + G.slot0) * (OP_BYTES / 4);
-                        asm volatile(
-                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-                                "r"(su32(ops_buf + so * OPS_STAGE + part * 3 * OP_BYTES)),
-                            "l"(srcB), "r"((uint32_t)G.nops * OP_BYTES), "r"(su32(&ops_full[so]))
-                            : "memory");
-                    }
                 }
-                const int sw = i % NSW, usw = i / NSW;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+                if (lane < NP) {
+                    const float* srcB = a.ops[lane] + ((size_t)cls * 27 + G.slot0) * (OP_BYTES / 4);
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            su32(ops_buf + so * OPS_STAGE + lane * 3 * OP_BYTES)),
+                        "l"(srcB), "r"(bytes), "r"(su32(&ops_full[so]))
+                        : "memory");
+                }
+            }
+            const int sw = i % NSW, usw = i / NSW;
+            if (lane == 0) {
                 if (i >= NSW && !wait_bar(su32(&win_empty[sw]), (uint32_t)((usw - 1) & 1))) ok = false;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&win_full[sw])),
                              "r"((uint32_t)(NP * A_BYTES))
                              : "memory");
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            if (lane < NP * KC) {
+                // chunk j of part `part` of the 130 cells from the window's flat start: 2080
+                // contiguous bytes (past a chunk's end it reads the next chunk or the zero pad,
+                // which only feed dropped outputs)
+                const int part = lane / KC, j = lane % KC;
                 const int q = G.qx + 2 * G.qy;
                 const int k = tile_k[t];
                 const size_t W2P = ((size_t)1 << (k - 1)) + 2;
                 const size_t start = (size_t)(tile_P[t] - 1 + G.sy * (int)W2P);   // flat, >= 0
-                for (int part = 0; part < NP; ++part) {
-                    const float* base = a.src[part][k];
-                    const uint32_t dst = su32(win_buf + sw * WIN_STAGE + part * A_BYTES);
-                    for (int j = 0; j < KC; ++j) {
-                        // chunk j of the 130 cells from the window's flat start: 2080 contiguous bytes
-                        const float* src = base + (((size_t)q * KC + j) * W2P * W2P + start) * 4;
-                        asm volatile(
-                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-                                "r"(dst + (uint32_t)j * (kWin * 16)),
-                            "l"(src), "r"((uint32_t)(kWin * 16)), "r"(su32(&win_full[sw]))
-                            : "memory");
-                    }
-                }
+                const float* src = a.src[part][k] + (((size_t)q * KC + j) * W2P * W2P + start) * 4;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        su32(win_buf + sw * WIN_STAGE + part * A_BYTES + j * (kWin * 16))),
+                    "l"(src), "r"((uint32_t)(kWin * 16)), "r"(su32(&win_full[sw]))
+                    : "memory");
             }
         }
         __syncwarp();
@@ -312,19 +317,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
         const int pos = tile_P[t] + 32 * warp + lane;
         const int x = pos % W2P - 1, y = pos / W2P - 1;   // sub-grid cell; halo cells are dropped
         if (done && x >= 0 && x < w2 && y < w2) {
-            const int W = fmm_grid_width(k);
-            const float2* A32 = a.a32[k];
             const int tx = 2 * x + px, ty = 2 * y + py;
-            // the monopole-log term, summed in float-float from the FP32 moment grid
-            float2 mono = make_float2(0.f, 0.f);
-            for (int dy = -2 - py; dy <= 3 - py; ++dy)
-                for (int dx = -2 - px; dx <= 3 - px; ++dx) {
-                    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-                    const float2 m0 = A32[((size_t)(ty + dy + FMM_HALO) * W + (tx + dx + FMM_HALO)) * p1];
-                    mono = ff_add(mono, ff_mul(m0, a.logc[k][(dx + 3) + 7 * (dy + 3)]));
-                }
+            // Re b'_0 without the monopole-log term, which k_m2l_mono adds in float-float
             float2* B = a.B[k] + ((size_t)ty * (1u << k) + tx) * p1;
-            B[0] = ff_add_f(mono, v[0]);
+            B[0] = make_float2(v[0], 0.f);
 #pragma unroll
             for (int l = 1; l < H; ++l)
                 if (l < p1) B[l] = make_float2(v[l], v[H + l]);
@@ -390,6 +386,62 @@ __global__ void k_prep_tc(const __grid_constant__ PrepArgs a) {
     }
 }
 
+// The monopole-log term of b'_0 for the tensor-core levels, sum_d M_0[t + d] (log|w0_d| + ln s_k)
+// over the target's interaction list, summed in float-float (in the order dy, then dx) and added to
+// the GEMM's Re b'_0: one thread per target, the 27 loads of a target issued together.
+struct MonoArgs {
+    const float2* a32[FMM_MAX_LEVELS + 1];
+    float2* B[FMM_MAX_LEVELS + 1];
+    float2 logc[FMM_MAX_LEVELS + 1][49];
+    long long base[FMM_MAX_LEVELS + 2];   // first target of each level
+    int kmin, levels, p1;
+};
+
+// the 27 list offsets of targets of parity (PX, PY), loads first, then the float-float sum
+template <int PX, int PY>
+__device__ __forceinline__ float2 mono_sum(const float2* __restrict__ A32, const float2 (&logc)[49], size_t c0, int W,
+                                           int p1) {
+    float2 m0[49];
+#pragma unroll
+    for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+        for (int dx = -3; dx <= 3; ++dx) {
+            const bool adj = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
+            const bool in = dx >= -2 - PX && dx <= 3 - PX && dy >= -2 - PY && dy <= 3 - PY;
+            if (in && !adj) m0[(dy + 3) * 7 + dx + 3] = A32[(c0 + (ptrdiff_t)dy * W + dx) * p1];
+        }
+    float2 mono = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+        for (int dx = -3; dx <= 3; ++dx) {
+            const bool adj = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
+            const bool in = dx >= -2 - PX && dx <= 3 - PX && dy >= -2 - PY && dy <= 3 - PY;
+            if (in && !adj) mono = ff_add(mono, ff_mul(m0[(dy + 3) * 7 + dx + 3], logc[(dx + 3) + 7 * (dy + 3)]));
+        }
+    return mono;
+}
+
+__global__ void k_m2l_mono(const __grid_constant__ MonoArgs a) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.base[a.levels + 1]) return;
+    int k = a.kmin;
+    while (g >= a.base[k + 1]) ++k;
+    const int64_t t = g - a.base[k];
+    const int side = 1 << k, W = fmm_grid_width(k), p1 = a.p1;
+    const int tx = (int)(t % side), ty = (int)(t / side);
+    const size_t c0 = (size_t)(ty + FMM_HALO) * W + (tx + FMM_HALO);
+    float2 mono;
+    switch ((tx & 1) + 2 * (ty & 1)) {
+        case 0: mono = mono_sum<0, 0>(a.a32[k], a.logc[k], c0, W, p1); break;
+        case 1: mono = mono_sum<1, 0>(a.a32[k], a.logc[k], c0, W, p1); break;
+        case 2: mono = mono_sum<0, 1>(a.a32[k], a.logc[k], c0, W, p1); break;
+        default: mono = mono_sum<1, 1>(a.a32[k], a.logc[k], c0, W, p1); break;
+    }
+    float2* B = a.B[k] + (size_t)t * p1;
+    B[0] = ff_add_f(mono, B[0].x);   // Re b'_0 as float-float
+}
+
 // host-side round to nearest TF32 (ties away), the rounding cvt.rna.tf32.f32 does on the device
 float host_tf32(float x) {
     uint32_t u;
@@ -424,7 +476,7 @@ struct FmmTc {
     int kc, np, sms;
     float* ops[2];                              // one scale-free copy per part
     float4* src[2][FMM_MAX_LEVELS + 1];
-    TcArgs args;   // tensor maps and tables, filled at plan time
+    TcArgs args;   // tables, filled at plan time
 };
 
 // The tensor cores take levels kMinLevel and finer.  The coarse levels carry most of the far
@@ -478,7 +530,7 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
         if (slots[cls] != 27) return -1;
     }
     // operators, real block form, [part][class][slot][KC][N][4]: scale-free, so one copy serves
-    // every level; the monopole-log entry (0, 0) is left out (summed in float-float by the epilogue)
+    // every level; the monopole-log entry (0, 0) is left out (summed in float-float by k_m2l_mono)
     const size_t opsz = (size_t)4 * 27 * kc * N * 4;
     {
         std::vector<float> hostops[2];
@@ -567,11 +619,7 @@ static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
         k_prep_tc<KC, NP><<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(pa);
     }
     TcArgs& a = tc->args;
-    for (int k = 0; k <= FMM_MAX_LEVELS; ++k) {
-        a.a32[k] = reinterpret_cast<const float2*>(pl->grids.A32[k]);
-        a.B[k] = reinterpret_cast<float2*>(pl->grids.B[k]);
-    }
-    memcpy(a.logc, lv.logc, sizeof(a.logc));
+    for (int k = 0; k <= FMM_MAX_LEVELS; ++k) a.B[k] = reinterpret_cast<float2*>(pl->grids.B[k]);
     a.levels = L;
     a.p = pl->p;
     a.status = pl->d_status;
@@ -600,7 +648,23 @@ static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
     auto kern = k_m2l_tc<KC, NP, NSO, NSW>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
     kern<<<4 * items, kThreads, shm, st>>>(a);
-    return 2;
+    {
+        MonoArgs ma{};
+        long long acc = 0;
+        for (int k = kMinLevel; k <= L; ++k) {
+            ma.a32[k] = reinterpret_cast<const float2*>(pl->grids.A32[k]);
+            ma.B[k] = reinterpret_cast<float2*>(pl->grids.B[k]);
+            ma.base[k] = acc;
+            acc += 1ll << (2 * k);
+        }
+        ma.base[L + 1] = acc;
+        memcpy(ma.logc, lv.logc, sizeof(ma.logc));
+        ma.kmin = kMinLevel;
+        ma.levels = L;
+        ma.p1 = p1;
+        k_m2l_mono<<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(ma);
+    }
+    return 3;
 }
 
 // Launch prep + tensor-core M2L for levels 2..L; returns kernels launched or -1.

@@ -17,34 +17,31 @@
 //   L2P  (D-bar-2 by linearity) per particle and level: Re sum_{l>=1} b'_l w^l by Horner in
 //        FP32, plus Re b'_0; the levels are summed in float-float.
 //   P2P  (E-2 of Sec. 2.1) in FP32 on square-local coordinates, log via the MUFU lg2 unit,
-//        sources staged in shared memory by the bulk-copy (TMA) engine; phi = far + near.
+//        lanes over sources and one register partial per target; phi = far + near.
 #include "mixed_common.cuh"
 
 namespace {
 
-constexpr int kWarpsPerBlock = 4;
 constexpr int kM2LThreads = 128;
 
 // -------------------------------------------------------------------------------- P2M
 // Every level straight from the particles (U-bar of Sec. 2.2.1).  Squares of a level are
 // contiguous Morton ranges of the sorted particles, so the sums need no global sort of their own.
 //
-// Fine levels (at most kFineMean particles per square on average): one lane per square walks its
-// range and keeps the p+1 sums in registers; the lane owns the square, so it stores the FP32
-// moments (total charge as a float-float pair) straight into the FP32 grid, with no reduction
-// and no atomics.  Squares above kLaneMax particles are left to the whole warp afterwards.
+// Fine levels (the finest three, l - 2 .. l): one lane per finest square, 32 consecutive squares
+// per warp in Morton order, so that each group of 4^(l - k) consecutive lanes is one level-k
+// square.  For each level the lane sums its own particles' terms in registers (its square fixes
+// the particles' offsets inside every coarser square, so no key is read), then the group's
+// partial sums are combined by a shuffle reduce-scatter that leaves each lane of the group with
+// a share of the coefficients to store: no atomics, coalesced stores.  Squares above kLaneMax
+// particles are summed by the whole warp and added by the owning group before the store.
 //
-// Coarse levels: each warp walks kCoarseChunk consecutive particles; lanes add their particles'
-// terms in registers while the square stays the same and flush (a column sum over the warp's
-// lanes in shared memory, then FP64 atomics into the level's grid) when it changes.
-constexpr int kFineMean = 64;
+// Coarse levels (2 .. l - 3): each warp walks kCoarseChunk consecutive particles; lanes add their
+// particles' terms in registers while the square stays the same and flush (a column sum over the
+// warp's lanes in shared memory, then FP64 atomics into the level's grid) when it changes.
+constexpr int kFineLevels = 3;
 constexpr int kLaneMax = 128;
 constexpr int kCoarseChunk = 256;
-
-struct P2MFineArgs {
-    int base[FMM_MAX_LEVELS + 2];   // first thread of each fine level
-    int kf, levels, p;
-};
 
 // powers q w^m, m = 1..P1B-1 added into acc (entries at m >= p1 stay untouched: the caller masks)
 template <int P1B>
@@ -61,80 +58,189 @@ __device__ __forceinline__ void add_powers(float2 (&acc)[P1B], float q, float2 w
     }
 }
 
-template <int P1B>
-__global__ void __launch_bounds__(128)
-k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, const uint32_t* __restrict__ leaf_start,
-           P2MFineArgs fa, MixedLevels lv, FmmLevelPtrs g) {
-    __shared__ float red[4][32][2 * P1B + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    int k = fa.kf;
-    while (k < fa.levels && gt >= fa.base[k + 1]) ++k;
-    const bool valid = gt < fa.base[fa.levels + 1];
-    const uint32_t b = valid ? (uint32_t)(gt - fa.base[k]) : 0u;
-    const int sh = fa.levels - k;
-    const int p1 = fa.p + 1;
-    const uint32_t lo = valid ? leaf_start[(size_t)b << (2 * sh)] : 0u;
-    const uint32_t hi = valid ? leaf_start[(size_t)(b + 1) << (2 * sh)] : 0u;
-    const int W = fmm_grid_width(k);
-    const size_t cell = (size_t)(fmm_compact2(b >> 1) + FMM_HALO) * W + fmm_compact2(b) + FMM_HALO;
-    const bool large = hi - lo > (uint32_t)kLaneMax;
-    float2 acc[P1B];
+// Sum over each aligned group of G lanes of v[0 .. VP), scattered: afterwards the lane of rank r
+// in its group holds entries [r VP / G, (r + 1) VP / G) of the group's sum in v[0 .. VP / G).
+// At the step with mask m a lane keeps the half of its live blocks whose bit m matches its own
+// rank bit and sends the other half to its partner.
+template <int G, int VP>
+__device__ __forceinline__ void group_reduce_scatter(float (&v)[VP], int lane) {
+    constexpr int B = VP / G;
 #pragma unroll
-    for (int m = 0; m < P1B; ++m) acc[m] = make_float2(0.f, 0.f);
-    float2 m0 = make_float2(0.f, 0.f);
-    if (valid && !large) {
-        for (uint32_t j = lo; j < hi; ++j) {
-            const float4 P = sp[j];
-            const uint32_t key = skey[j];
-            const float2 w = level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh, lv.inv_s[k]);
-            m0 = ff_add_f(m0, P.z);
-            add_powers<P1B>(acc, P.z, w);
+    for (int m = G / 2; m >= 1; m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < m * B; ++i) {
+            const float send = up ? v[i] : v[i + m * B];
+            const float keep = up ? v[i + m * B] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
         }
-        float2* A = reinterpret_cast<float2*>(g.A32[k]) + cell * p1;
-        A[0] = m0;
-#pragma unroll
-        for (int m = 1; m < P1B; ++m)
-            if (m < p1) A[m] = acc[m];
     }
-    // squares above kLaneMax particles: the whole warp, then a column sum in shared memory
+}
+
+// the three power chains of the fused fine levels, with packed FP32x2 accumulation
+template <int P1B>
+__device__ __forceinline__ void add_powers3(float2 (&a0)[P1B], float2 (&a1)[P1B], float2 (&a2)[P1B], float q,
+                                            float2 w0, float2 w1, float2 w2) {
+    float r0 = q, i0 = 0.f, r1 = q, i1 = 0.f, r2 = q, i2 = 0.f;
+#pragma unroll
+    for (int m = 1; m < P1B; ++m) {
+        const float n0 = fmaf(r0, w0.x, -i0 * w0.y), j0 = fmaf(r0, w0.y, i0 * w0.x);
+        const float n1 = fmaf(r1, w1.x, -i1 * w1.y), j1 = fmaf(r1, w1.y, i1 * w1.x);
+        const float n2 = fmaf(r2, w2.x, -i2 * w2.y), j2 = fmaf(r2, w2.y, i2 * w2.x);
+        r0 = n0, i0 = j0, r1 = n1, i1 = j1, r2 = n2, i2 = j2;
+        a0[m] = __fadd2_rn(a0[m], make_float2(r0, i0));
+        a1[m] = __fadd2_rn(a1[m], make_float2(r1, i1));
+        a2[m] = __fadd2_rn(a2[m], make_float2(r2, i2));
+    }
+}
+
+// Level k = l - log4(G) of the lane's finest square sq (particles [lo, hi), offset (ox, oy) of
+// its centre in units of the level-k square): the group's sums of the lane partials acc and m0,
+// the crowded squares of the warp added, stored by the group's lanes.
+template <int P1B, int G>
+__device__ __forceinline__ void p2m_fine_finish(const float2 (&acc)[P1B], float2 m0, const float4* __restrict__ sp,
+                                                uint32_t sq, uint32_t lo, uint32_t hi, bool valid, int levels, int p1,
+                                                float inv_s, float ox, float oy, float* red, int lane,
+                                                FmmLevelPtrs g) {
+    constexpr int V = 2 * (P1B - 1);              // Re, Im of coefficients 1 .. P1B - 1
+    constexpr int VP = (V + G - 1) / G * G;
+    constexpr int B = VP / G;
+    constexpr int SH = G == 1 ? 0 : (G == 4 ? 1 : 2);
+    const int k = levels - SH;
+    const bool large = hi - lo > (uint32_t)kLaneMax;
+    float v[VP];
+#pragma unroll
+    for (int i = 0; i < VP; ++i) v[i] = i < V ? ((i & 1) ? acc[1 + i / 2].y : acc[1 + i / 2].x) : 0.f;
+    group_reduce_scatter<G, VP>(v, lane);
+#pragma unroll
+    for (int m = 1; m < G; m <<= 1)
+        m0 = ff_add(m0, make_float2(__shfl_xor_sync(0xffffffffu, m0.x, m), __shfl_xor_sync(0xffffffffu, m0.y, m)));
+    // crowded squares: the whole warp sums the particles, the owning group adds its share
     unsigned todo = __ballot_sync(0xffffffffu, valid && large);
     while (todo) {
         const int src = __ffs(todo) - 1;
         todo &= todo - 1;
         const uint32_t lo2 = __shfl_sync(0xffffffffu, lo, src), hi2 = __shfl_sync(0xffffffffu, hi, src);
-        const int k2 = __shfl_sync(0xffffffffu, k, src);
-        const unsigned long long cell2 = __shfl_sync(0xffffffffu, (unsigned long long)cell, src);
-        const int sh2 = fa.levels - k2;
+        const float ox2 = __shfl_sync(0xffffffffu, ox, src), oy2 = __shfl_sync(0xffffffffu, oy, src);
+        float2 a2[P1B];
 #pragma unroll
-        for (int m = 0; m < P1B; ++m) acc[m] = make_float2(0.f, 0.f);
-        m0 = make_float2(0.f, 0.f);
+        for (int m = 0; m < P1B; ++m) a2[m] = make_float2(0.f, 0.f);
+        float2 mm = make_float2(0.f, 0.f);
         for (uint32_t j = lo2 + lane; j < hi2; j += 32) {
             const float4 P = sp[j];
-            const uint32_t key = skey[j];
-            const float2 w = level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh2, lv.inv_s[k2]);
-            m0 = ff_add_f(m0, P.z);
-            add_powers<P1B>(acc, P.z, w);
+            mm = ff_add_f(mm, P.z);
+            add_powers<P1B>(a2, P.z, make_float2(fmaf(P.x, inv_s, ox2), fmaf(P.y, inv_s, oy2)));
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            m0 = ff_add(m0, make_float2(__shfl_xor_sync(0xffffffffu, m0.x, o), __shfl_xor_sync(0xffffffffu, m0.y, o)));
-        float* row = red[warp][lane];
+        for (int o = 16; o > 0; o >>= 1) {
+            mm = ff_add(mm, make_float2(__shfl_xor_sync(0xffffffffu, mm.x, o), __shfl_xor_sync(0xffffffffu, mm.y, o)));
 #pragma unroll
-        for (int m = 1; m < P1B; ++m) {
-            row[2 * m] = acc[m].x;
-            row[2 * m + 1] = acc[m].y;
+            for (int m = 1; m < P1B; ++m) {
+                a2[m].x += __shfl_xor_sync(0xffffffffu, a2[m].x, o);
+                a2[m].y += __shfl_xor_sync(0xffffffffu, a2[m].y, o);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int m = 1; m < P1B; ++m) {
+                red[2 * (m - 1)] = a2[m].x;
+                red[2 * (m - 1) + 1] = a2[m].y;
+            }
         }
         __syncwarp();
-        float2* A = reinterpret_cast<float2*>(g.A32[k2]) + cell2 * p1;
-        for (int col = 2 + lane; col < 2 * p1; col += 32) {
-            float s = 0.f;
+        if ((lane & ~(G - 1)) == (src & ~(G - 1))) {
+            const int r = lane & (G - 1);
 #pragma unroll
-            for (int r = 0; r < 32; ++r) s += red[warp][r][col];
-            reinterpret_cast<float*>(A)[col] = s;
+            for (int i = 0; i < B; ++i)
+                if (r * B + i < V) v[i] += red[r * B + i];
+            m0 = ff_add(m0, mm);
         }
-        if (lane == 0) A[0] = m0;
         __syncwarp();
+    }
+    if (!valid) return;
+    const uint32_t b = sq >> (2 * SH);
+    const int W = fmm_grid_width(k);
+    const size_t cell = (size_t)(fmm_compact2(b >> 1) + FMM_HALO) * W + fmm_compact2(b) + FMM_HALO;
+    float* A = reinterpret_cast<float*>(reinterpret_cast<float2*>(g.A32[k]) + cell * p1);
+    const int r = lane & (G - 1);
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        const int e = r * B + i;
+        if (e < 2 * (p1 - 1)) A[2 + e] = v[i];
+    }
+    if (r == 0) {
+        A[0] = m0.x;   // total charge as a float-float pair
+        A[1] = m0.y;
+    }
+}
+
+// offset of the finest square's centre in units of its ancestor SH levels up: exact dyadic
+__device__ __forceinline__ float fine_offset(uint32_t i, int sh) {
+    const uint32_t mask = (1u << sh) - 1u;
+    return fmaf((float)(i & mask) + 0.5f, __int_as_float((127 - sh) << 23), -0.5f);
+}
+
+// levels max(2, l - 2) .. l, one lane per finest square.  Orders up to 24 walk the particles
+// once, with the three levels' power chains interleaved; higher orders take one pass per level.
+template <int P1B>
+__global__ void __launch_bounds__(128)
+k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, int levels, int p, MixedLevels lv,
+           FmmLevelPtrs g) {
+    __shared__ float red[4][2 * P1B];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t sq = blockIdx.x * 128u + threadIdx.x;
+    const bool valid = sq < (1u << (2 * levels));
+    const uint32_t lo = valid ? leaf_start[sq] : 0u, hi = valid ? leaf_start[sq + 1] : 0u;
+    const bool large = hi - lo > (uint32_t)kLaneMax;
+    const int p1 = p + 1;
+    const uint32_t ix = fmm_compact2(sq), iy = fmm_compact2(sq >> 1);
+    const float ox1 = fine_offset(ix, 1), oy1 = fine_offset(iy, 1);
+    const float ox2 = fine_offset(ix, 2), oy2 = fine_offset(iy, 2);
+    const float s0 = lv.inv_s[levels], s1 = lv.inv_s[levels - 1], s2 = lv.inv_s[levels >= 2 ? levels - 2 : 0];
+    float2 m0 = make_float2(0.f, 0.f);
+    if constexpr (P1B <= 25) {
+        float2 a0[P1B], a1[P1B], a2[P1B];
+#pragma unroll
+        for (int m = 0; m < P1B; ++m) a0[m] = a1[m] = a2[m] = make_float2(0.f, 0.f);
+        if (valid && !large && lo < hi) {
+            float4 nx = sp[lo];
+            for (uint32_t j = lo; j < hi; ++j) {
+                const float4 P = nx;
+                if (j + 1 < hi) nx = sp[j + 1];
+                m0 = ff_add_f(m0, P.z);
+                add_powers3<P1B>(a0, a1, a2, P.z, make_float2(P.x * s0, P.y * s0),
+                                 make_float2(fmaf(P.x, s1, ox1), fmaf(P.y, s1, oy1)),
+                                 make_float2(fmaf(P.x, s2, ox2), fmaf(P.y, s2, oy2)));
+            }
+        }
+        p2m_fine_finish<P1B, 1>(a0, m0, sp, sq, lo, hi, valid, levels, p1, s0, 0.f, 0.f, red[warp], lane, g);
+        if (levels - 1 >= 2)
+            p2m_fine_finish<P1B, 4>(a1, m0, sp, sq, lo, hi, valid, levels, p1, s1, ox1, oy1, red[warp], lane, g);
+        if (levels - 2 >= 2)
+            p2m_fine_finish<P1B, 16>(a2, m0, sp, sq, lo, hi, valid, levels, p1, s2, ox2, oy2, red[warp], lane, g);
+    } else {
+        if (valid && !large)
+            for (uint32_t j = lo; j < hi; ++j) m0 = ff_add_f(m0, sp[j].z);
+        float2 a[P1B];
+#pragma unroll
+        for (int sh = 0; sh < 3; ++sh) {
+            if (levels - sh < 2) break;
+            const float sc = sh == 0 ? s0 : (sh == 1 ? s1 : s2);
+            const float ox = sh == 0 ? 0.f : (sh == 1 ? ox1 : ox2), oy = sh == 0 ? 0.f : (sh == 1 ? oy1 : oy2);
+#pragma unroll
+            for (int m = 0; m < P1B; ++m) a[m] = make_float2(0.f, 0.f);
+            if (valid && !large)
+                for (uint32_t j = lo; j < hi; ++j) {
+                    const float4 P = sp[j];
+                    add_powers<P1B>(a, P.z, make_float2(fmaf(P.x, sc, ox), fmaf(P.y, sc, oy)));
+                }
+            if (sh == 0)
+                p2m_fine_finish<P1B, 1>(a, m0, sp, sq, lo, hi, valid, levels, p1, sc, ox, oy, red[warp], lane, g);
+            else if (sh == 1)
+                p2m_fine_finish<P1B, 4>(a, m0, sp, sq, lo, hi, valid, levels, p1, sc, ox, oy, red[warp], lane, g);
+            else
+                p2m_fine_finish<P1B, 16>(a, m0, sp, sq, lo, hi, valid, levels, p1, sc, ox, oy, red[warp], lane, g);
+        }
     }
 }
 
@@ -465,181 +571,230 @@ k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
 }
 
 // -------------------------------------------------------------------------------- P2P + final phi
-// One warp per finest square.  When the square and its (up to) eight neighbours hold at most
-// kP2PCap sources, the bulk-copy (TMA) engine moves their contiguous Morton ranges into the
-// warp's shared-memory buffer (cp.async.bulk completing on an mbarrier, with a bounded wait);
-// otherwise the warp reads them from global memory.  With T targets the warp splits into
-// 32 / T' groups (T' = T rounded up to a power of two, at most 32) that take interleaved
-// sources and combine by shuffles.  Each neighbour's sum runs in FP32 and the neighbours are
-// combined in float-float, so crowded squares keep their accuracy.
+// Near field (E-2 of Sec. 2.1): every particle of a finest square against the particles of that
+// square and its (up to) eight neighbours, in FP32 on square-local coordinates.
+//
+// One warp per block of up to FMM_P2P_BLOCK targets of one finest square (a block -> square map
+// spares the warp a search); crowded squares spread over as many warps as they have blocks.
+// The lanes walk the sources 32 at a time (the own square's
+// first, then the neighbours'), each lane holding one source moved into the target square's
+// frame, and keep one FP32 partial sum per target in registers; the targets' coordinates are
+// shared-memory broadcasts, two targets per load.  The arithmetic of two targets runs in packed
+// FP32x2 instructions, so a pair costs one lg2 on the MUFU unit and two to three FP32 slots.
+// Coincidence (r^2 = 0: the target itself, duplicate points) only arises within the own square,
+// whose chunks test r^2 > 0; a neighbour's pair adds 2^-100 to r^2 instead, which keeps the
+// logarithm finite should two particles of adjacent squares round to the same FP32 point and
+// changes no other pair.  After each run of kP2PRun chunks the partials of each target are
+// combined across the warp by a shuffle reduce-scatter (lane t ends with target t's sum) and
+// added in float-float, so crowded squares keep their accuracy.
 constexpr int kP2PWarps = 4;
-constexpr int kP2PCap = 512;                  // sources per warp buffer (8 KB)
-constexpr unsigned kSpinLimit = 1u << 22;     // bounded mbarrier wait
+constexpr int kP2PRun = 16;   // chunks of 32 sources summed in FP32 before the float-float add
 
-// q-weight of one pair: log2 r^2 by the MUFU unit (flush-to-zero: r^2 of distinct particles is
-// normal); self and coincident pairs (r^2 = 0) give 0.
-__device__ __forceinline__ float p2p_lg2(float dx, float dy) {
-    const float r2 = fmaf(dx, dx, dy * dy);
-    float lg;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(r2));
-    return r2 > 0.f ? lg : 0.f;
+__device__ __forceinline__ float mufu_lg2(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* ptr) {
-    return (uint32_t)__cvta_generic_to_shared(ptr);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (unsigned it = 0; it < kSpinLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred P;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, P;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
+// Sum of v[l & (W - 1)] over the warp's lanes, returned in lane l (v[t] = p[t / 2].x or .y for
+// t < 2 NP, 0 beyond).  The low log2(W) lane bits scatter (at the step with mask m a lane keeps
+// the half of its live entries whose bit m matches its own and sends the other half to its
+// partner), the remaining bits add by butterfly.
+template <int W, int NP>
+__device__ __forceinline__ float warp_reduce_scatter(const float2 (&p)[NP], int lane) {
+    float v[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) v[i] = i < 2 * NP ? ((i & 1) ? p[i >> 1].y : p[i >> 1].x) : 0.f;
+#pragma unroll
+    for (int m = W / 2; m >= 1; m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < m; ++i) {
+            const float send = up ? v[i] : v[i + m];
+            const float keep = up ? v[i + m] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
     }
-    return false;
+    float s = v[0];
+#pragma unroll
+    for (int m = W; m < 32; m <<= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    return s;
 }
 
-__global__ void __launch_bounds__(kP2PWarps * 32)
+// one chunk: the lane's source (sx, sy, q) against the NP target pairs of the block (the
+// coordinates of targets past the block's end are zero and their sums are dropped)
+template <bool kOwn, int NP>
+__device__ __forceinline__ void p2p_chunk(float2 (&part)[NP], const float4* __restrict__ tg, float4 src) {
+    const float2 nsx = make_float2(-src.x, -src.x), nsy = make_float2(-src.y, -src.y);
+    const float2 q2 = make_float2(src.z, src.z);
+    const float2 tiny = make_float2(0x1p-100f, 0x1p-100f);
+#pragma unroll
+    for (int tp = 0; tp < NP; ++tp) {
+        const float4 t = tg[tp];   // {x of target 2tp, x of 2tp + 1, y of 2tp, y of 2tp + 1}
+        const float2 dx = __fadd2_rn(make_float2(t.x, t.y), nsx);
+        const float2 dy = __fadd2_rn(make_float2(t.z, t.w), nsy);
+        float2 r2, lg;
+        if (kOwn) {
+            r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+            lg = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
+            lg.x = r2.x > 0.f ? lg.x : 0.f;
+            lg.y = r2.y > 0.f ? lg.y : 0.f;
+        } else {
+            r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, tiny));
+            lg = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
+        }
+        part[tp] = __ffma2_rn(q2, lg, part[tp]);
+    }
+}
+
+// The block's sources: the own square's particles [t0, t0 + n_own) in nch_own chunks, then the
+// eight neighbours' in slot order (seg: sorted index minus slot and the frame shift per
+// neighbour, thr: first slot of neighbours 1..7).
+struct P2PSources {
+    const float4* sp;
+    const int4* seg;
+    uint32_t thr[7];
+    uint32_t t0, n_own, nch_own, n_nb;
+
+    // source of chunk c for this lane, in the target square's frame; slots past a part's end
+    // carry q = 0
+    __device__ __forceinline__ float4 load(uint32_t c, int lane) const {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < nch_own) {
+            const uint32_t s = 32u * c + (uint32_t)lane;
+            if (s < n_own) v = sp[t0 + s];
+        } else {
+            const uint32_t s = 32u * (c - nch_own) + (uint32_t)lane;
+            if (s < n_nb) {
+                int b = 0;
+#pragma unroll
+                for (int i = 0; i < 7; ++i) b += s >= thr[i] ? 1 : 0;
+                const int4 g = seg[b];
+                v = sp[s + (uint32_t)g.x];
+                v.x += __int_as_float(g.y);
+                v.y += __int_as_float(g.z);
+            }
+        }
+        return v;
+    }
+};
+
+// the near-field sum (log2 r^2 units, float-float) of target `lane` of a block of at most 2 NP
+// targets
+template <int NP>
+__device__ __forceinline__ float2 p2p_block(const P2PSources& S, const float4* __restrict__ tg, int lane) {
+    constexpr int W = NP <= 2 ? 4 : (NP <= 4 ? 8 : (NP <= 8 ? 16 : 32));
+    const uint32_t nch = S.nch_own + (S.n_nb + 31u) / 32u;
+    float2 near = make_float2(0.f, 0.f);
+    for (uint32_t r0 = 0; r0 < nch; r0 += kP2PRun) {
+        const uint32_t r1 = min(nch, r0 + (uint32_t)kP2PRun);
+        float2 part[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) part[i] = make_float2(0.f, 0.f);
+        float4 cur = S.load(r0, lane);
+        for (uint32_t c = r0; c < r1; ++c) {
+            const float4 nxt = (c + 1 < r1) ? S.load(c + 1, lane) : cur;
+            if (c < S.nch_own)
+                p2p_chunk<true, NP>(part, tg, cur);
+            else
+                p2p_chunk<false, NP>(part, tg, cur);
+            cur = nxt;
+        }
+        near = ff_add_f(near, warp_reduce_scatter<W, NP>(part, lane));
+    }
+    return near;
+}
+
+__global__ void __launch_bounds__(kP2PWarps * 32, 6)
 k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
-            const uint32_t* __restrict__ bstart, uint32_t nleaf, int levels, float s_leaf,
-            const float2* __restrict__ phi_far, double* __restrict__ phi, unsigned int* __restrict__ status,
-            unsigned long long* __restrict__ counters) {
-    __shared__ __align__(16) float4 buf[kP2PWarps][kP2PCap];
-    __shared__ __align__(8) uint64_t bar[kP2PWarps];
+            const uint32_t* __restrict__ bstart, const uint2* __restrict__ bmap, uint32_t nleaf, int levels,
+            float s_leaf, const float2* __restrict__ phi_far, double* __restrict__ phi,
+            unsigned int* __restrict__ status, unsigned long long* __restrict__ counters) {
+    __shared__ __align__(16) float4 tgt[kP2PWarps][16];   // zero past the block's targets
+    __shared__ __align__(16) int4 seg[kP2PWarps][8];   // neighbours in slot order: {index - slot, ox, oy, -}
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // one warp per block of up to 32 targets of one finest square: crowded squares spread
-    // over as many warps as they have target blocks
     const uint32_t w = (uint32_t)blockIdx.x * kP2PWarps + warp;
     if (w >= bstart[nleaf]) return;
     if (*(volatile const unsigned int*)status != 0u) return;   // inputs failed the device checks
-    const uint32_t leaf = fmm_warp_search(bstart, nleaf, w, lane);
-    const uint32_t tb = w - bstart[leaf];
+    const uint2 lt = bmap[w];   // (square, block inside it)
+    const uint32_t leaf = lt.x;
     const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
-    const uint32_t b0 = t0 + 32u * tb;
-    const int T = (int)min(32u, t1 - b0);
+    const uint32_t b0 = t0 + (uint32_t)FMM_P2P_BLOCK * lt.y;
+    const int T = (int)min((uint32_t)FMM_P2P_BLOCK, t1 - b0);
+    // the final write's inputs, loaded early: the target's input index and its far field
+    int idx = 0;
+    float2 far = make_float2(0.f, 0.f);
+    if (lane < T) {
+        idx = __float_as_int(sp[b0 + lane].w);
+        far = phi_far[b0 + lane];
+    }
+    const uint32_t n_own = t1 - t0;
     const int side = 1 << levels;
     const int ix = (int)fmm_compact2(leaf), iy = (int)fmm_compact2(leaf >> 1);
-    // the nine neighbour slots, fully unrolled so that they live in registers
-    uint32_t nb0[9], ncnt[9], noff[9];
-    uint32_t nsrc = 0;
-#pragma unroll
-    for (int b = 0; b < 9; ++b) {
-        const int jx = ix + (b % 3) - 1, jy = iy + (b / 3) - 1;
-        const bool in = jx >= 0 && jy >= 0 && jx < side && jy < side;
-        const uint32_t nl = in ? fmm_morton((uint32_t)jx, (uint32_t)jy) : 0u;
-        nb0[b] = in ? leaf_start[nl] : 0u;
-        ncnt[b] = in ? leaf_start[nl + 1] - nb0[b] : 0u;
-        noff[b] = nsrc;
-        nsrc += ncnt[b];
+    // lane b < 9, b != 4, looks up neighbour b = (dx + 1) + 3 (dy + 1); the eight neighbours'
+    // sources take consecutive slots of the neighbour chunks
+    uint32_t first = 0, cnt = 0;
+    if (lane < 9 && lane != 4) {
+        const int jx = ix + lane % 3 - 1, jy = iy + lane / 3 - 1;
+        if (jx >= 0 && jy >= 0 && jx < side && jy < side) {
+            const uint32_t nl = fmm_morton((uint32_t)jx, (uint32_t)jy);
+            first = leaf_start[nl];
+            cnt = leaf_start[nl + 1] - first;
+        }
     }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t n_nb = __shfl_sync(0xffffffffu, incl, 8);
+    if (lane < 9 && lane != 4)
+        seg[warp][lane - (lane > 4)] = make_int4((int)(first - excl), __float_as_int((float)(lane % 3 - 1) * s_leaf),
+                                                 __float_as_int((float)(lane / 3 - 1) * s_leaf), 0);
+    P2PSources S;
+    S.sp = sp;
+    S.seg = seg[warp];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) S.thr[i - 1] = __shfl_sync(0xffffffffu, excl, i + (i >= 4));
+    S.t0 = t0;
+    S.n_own = n_own;
+    S.nch_own = (n_own + 31u) / 32u;
+    S.n_nb = n_nb;
     if (lane == 0) {
         const unsigned slot = leaf % FMM_COUNTER_SLOTS;
-        atomicAdd(&counters[slot], (unsigned long long)T * nsrc - (unsigned long long)T);
-        atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)(t1 - t0));
+        atomicAdd(&counters[slot], (unsigned long long)T * (n_own + n_nb) - (unsigned long long)T);
+        atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)n_own);
     }
-    const bool staged = nsrc <= (uint32_t)kP2PCap;
-    const uint32_t mb = smem_u32(&bar[warp]);
-    if (staged) {
-        if (lane == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(16u * nsrc)
-                         : "memory");
-            const uint32_t dst0 = smem_u32(buf[warp]);
-#pragma unroll
-            for (int b = 0; b < 9; ++b)
-                if (ncnt[b] > 0)
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            dst0 + 16u * noff[b]),
-                        "l"(sp + nb0[b]), "r"(16u * ncnt[b]), "r"(mb)
-                        : "memory");
+    {
+        float x = 0.f, y = 0.f;
+        if (lane < T) {
+            const float4 P = sp[b0 + lane];
+            x = P.x;
+            y = P.y;
         }
-        __syncwarp();
-        if (!mbar_wait(mb, 0)) {
-            if (lane == 0) atomicOr(status, FMM_FLAG_TIMEOUT);
-            return;   // the copies were issued with valid sizes; nothing else waits on them
-        }
-        // move every staged source into the target square's frame: x_j + (jx - ix) s, y_j + (jy - iy) s
-        float4* sb = buf[warp];
-#pragma unroll
-        for (int b = 0; b < 9; ++b) {
-            const float ox = (float)((b % 3) - 1) * s_leaf, oy = (float)((b / 3) - 1) * s_leaf;
-            for (uint32_t j = lane; j < ncnt[b]; j += 32) {
-                float4 v = sb[noff[b] + j];
-                v.x += ox;
-                v.y += oy;
-                sb[noff[b] + j] = v;
-            }
-        }
-        __syncwarp();
+        float* t = reinterpret_cast<float*>(&tgt[warp][lane >> 1]);
+        t[lane & 1] = x;
+        t[2 + (lane & 1)] = y;
     }
-    int tp = 1;
-    while (tp < T) tp <<= 1;
-    const uint32_t groups = 32 / tp;
-    const int slot = lane & (tp - 1);
-    const uint32_t grp = lane / tp;
-    const bool active = slot < T;
-    const uint32_t gi = b0 + (active ? slot : 0);
-    const float4 Pi = sp[gi];
-    float2 near = make_float2(0.f, 0.f);
-    if (staged) {
-        // at most kP2PCap / groups terms per lane: one FP32 sum, four sources per step
-        const float4* src = buf[warp];
-        float acc0 = 0.f, acc1 = 0.f;
-        uint32_t j = grp;
-        for (; j + 3u * groups < nsrc; j += 4u * groups) {
-            const float4 a0 = src[j], a1 = src[j + groups], a2 = src[j + 2u * groups], a3 = src[j + 3u * groups];
-            acc0 = fmaf(a0.z, p2p_lg2(Pi.x - a0.x, Pi.y - a0.y), acc0);
-            acc1 = fmaf(a1.z, p2p_lg2(Pi.x - a1.x, Pi.y - a1.y), acc1);
-            acc0 = fmaf(a2.z, p2p_lg2(Pi.x - a2.x, Pi.y - a2.y), acc0);
-            acc1 = fmaf(a3.z, p2p_lg2(Pi.x - a3.x, Pi.y - a3.y), acc1);
-        }
-        for (; j < nsrc; j += groups) {
-            const float4 a0 = src[j];
-            acc0 = fmaf(a0.z, p2p_lg2(Pi.x - a0.x, Pi.y - a0.y), acc0);
-        }
-        near = make_float2(acc0 + acc1, 0.f);
-    } else {
-        // crowded squares: FP32 sums over runs of kP2PCap sources from global memory, combined
-        // in float-float
-#pragma unroll
-        for (int b = 0; b < 9; ++b) {
-            const float bx = Pi.x - (float)((b % 3) - 1) * s_leaf;   // target-centre minus source-centre
-            const float by = Pi.y - (float)((b / 3) - 1) * s_leaf;
-            const float4* src = sp + nb0[b];
-            for (uint32_t r0 = 0; r0 < ncnt[b]; r0 += kP2PCap) {
-                const uint32_t r1 = min(ncnt[b], r0 + kP2PCap);
-                float acc0 = 0.f, acc1 = 0.f;
-                uint32_t j = r0 + grp;
-                for (; j + groups < r1; j += 2u * groups) {
-                    const float4 a0 = src[j], a1 = src[j + groups];
-                    acc0 = fmaf(a0.z, p2p_lg2(bx - a0.x, by - a0.y), acc0);
-                    acc1 = fmaf(a1.z, p2p_lg2(bx - a1.x, by - a1.y), acc1);
-                }
-                if (j < r1) {
-                    const float4 a0 = src[j];
-                    acc0 = fmaf(a0.z, p2p_lg2(bx - a0.x, by - a0.y), acc0);
-                }
-                near = ff_add_f(near, acc0 + acc1);
-            }
-        }
+    __syncwarp();
+    // the block's target pairs, rounded up to an even count, fix the unrolled width
+    float2 near;
+    static_assert(FMM_P2P_BLOCK <= 24, "the unrolled widths below cover blocks of up to 24 targets");
+    switch ((T + 3) >> 2) {
+        case 1: near = p2p_block<2>(S, tgt[warp], lane); break;
+        case 2: near = p2p_block<4>(S, tgt[warp], lane); break;
+        case 3: near = p2p_block<6>(S, tgt[warp], lane); break;
+        case 4: near = p2p_block<8>(S, tgt[warp], lane); break;
+        case 5: near = p2p_block<10>(S, tgt[warp], lane); break;
+        default: near = p2p_block<12>(S, tgt[warp], lane); break;
     }
-    for (int o = tp; o < 32; o <<= 1) {
-        const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, near.x, o),
-                                         __shfl_xor_sync(0xffffffffu, near.y, o));
-        near = ff_add(near, other);
+    if (lane < T) {
+        // near field x ln2 / 2 (as a float-float pair) turns sum q log2 r^2 into sum q ln r
+        const float2 v = ff_add(far, ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
+        phi[idx] = fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);
     }
-    if (active && grp == 0) {
-        const float2 v = ff_add(phi_far[gi], ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
-        phi[__float_as_int(Pi.w)] = fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);   // ln2 / 2 as float-float above
-    }
-    if (staged && lane == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
 }
 
 template <int P1B>
@@ -673,29 +828,17 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     int launches = 0;
     cudaEventRecord(pl->ev[1], st);
     if (L >= 2) {
-        // fine levels: at most kFineMean particles per square on average
-        int kf = L;
-        while (kf > 2 && (n >> (2 * (kf - 1))) <= kFineMean) --kf;
+        // fine levels: the finest kFineLevels; coarser ones by the particle-parallel kernel
+        const int kf = L - (kFineLevels - 1) > 2 ? L - (kFineLevels - 1) : 2;
         const int kc_max = kf - 1;
         for (int k = 2; k <= kc_max; ++k)
             if (cudaMemsetAsync(pl->grids.A[k], 0, pl->a_bytes[k], st) != cudaSuccess) return -1;
-        P2MFineArgs fa{};
-        int acc = 0;
-        for (int k = kf; k <= L; ++k) {
-            fa.base[k] = acc;
-            acc += 1 << (2 * k);
-        }
-        fa.base[L + 1] = acc;
-        fa.kf = kf;
-        fa.levels = L;
-        fa.p = p;
-        const unsigned fblocks = (unsigned)((acc + 127) / 128);
+        const unsigned fblocks = (unsigned)(((1ull << (2 * L)) + 127) / 128);
         const unsigned cblocks = (unsigned)((n + 4 * kCoarseChunk - 1) / (4 * kCoarseChunk));
         switch (pl->p1b) {
 #define FMM_P2M(PB)                                                                                          \
     case PB:                                                                                                 \
-        k_p2m_fine<PB><<<fblocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, pl->leaf_start, fa, lv,        \
-                                                pl->grids);                                                  \
+        k_p2m_fine<PB><<<fblocks, 128, 0, st>>>(pl->sorted32, pl->leaf_start, L, p, lv, pl->grids);           \
         if (kc_max >= 2)                                                                                     \
             k_p2m_coarse<PB><<<cblocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, kc_max, p, lv,     \
                                                       pl->grids);                                            \
@@ -792,14 +935,12 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     cudaEventRecord(pl->ev[4], st);
     {
         const uint32_t nleaf = 1u << (2 * L);
-        const int r = fmm_launch_leaf_blocks(pl->leaf_start, nleaf, pl->leaf_nb, pl->block_sums, pl->leaf_bstart, st);
-        if (r < 0) return -1;
-        launches += r;
+        // the near-field blocks (leaf_bstart, blk_map) came with the sort's scan
         // upper bound of the target blocks: each square adds at most one partial block
-        const uint64_t wmax = (uint64_t)nleaf + (uint64_t)(n / 32) + 1;
+        const uint64_t wmax = (uint64_t)nleaf + (uint64_t)(n / FMM_P2P_BLOCK) + 1;
         const unsigned blocks = (unsigned)((wmax + kP2PWarps - 1) / kP2PWarps);
-        k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, st>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, nleaf, L,
-                                                      lv.s_leaf, far, phi, pl->d_status, pl->d_counters);
+        k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, st>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, pl->blk_map,
+                                                      nleaf, L, lv.s_leaf, far, phi, pl->d_status, pl->d_counters);
         ++launches;
     }
     cudaEventRecord(pl->ev[5], st);

@@ -43,35 +43,36 @@ __global__ void k_bin(const double2* __restrict__ xy, const double* __restrict__
 }
 
 // block-wide exclusive scan of kScanItems values per thread; returns the block total
-__device__ uint32_t block_exclusive_scan(uint32_t (&v)[kScanItems], uint32_t* warp_tot) {
-    uint32_t s = 0;
+template <typename T>
+__device__ T block_exclusive_scan(T (&v)[kScanItems], T* warp_tot) {
+    T s = 0;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) { uint32_t t = v[j]; v[j] = s; s += t; }
+    for (int j = 0; j < kScanItems; ++j) { T t = v[j]; v[j] = s; s += t; }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t inc = s;
+    T inc = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
     if (lane == 31) warp_tot[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = lane < (kScanThreads / 32) ? warp_tot[lane] : 0u;
-        uint32_t wi = w;
+        T w = lane < (kScanThreads / 32) ? warp_tot[lane] : T(0);
+        T wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            T y = __shfl_up_sync(0xffffffffu, wi, o);
             if (lane >= o) wi += y;
         }
         if (lane < (kScanThreads / 32)) warp_tot[lane] = wi - w;   // exclusive warp offsets
         if (lane == (kScanThreads / 32) - 1) warp_tot[kScanThreads / 32] = wi;
     }
     __syncthreads();
-    uint32_t base = warp_tot[warp] + inc - s;
+    T base = warp_tot[warp] + inc - s;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) v[j] += base;
-    uint32_t total = warp_tot[kScanThreads / 32];
+    T total = warp_tot[kScanThreads / 32];
     __syncthreads();
     return total;
 }
@@ -119,6 +120,70 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t m, const ui
     if (blockIdx.x == 0 && threadIdx.x == 0) out[m] = (n_total == 0xffffffffu) ? sums[gridDim.x] : n_total;
 }
 
+// Mixed path: one scan of (population, near-field blocks) pairs packed in 64 bits (the low word
+// never carries: n < 2^32) gives leaf_start and the block starts at once; the down-sweep also
+// writes the block -> (square, block inside it) map.
+__device__ __forceinline__ unsigned long long pop_blocks(uint32_t c) {
+    return (unsigned long long)c | ((unsigned long long)((c + FMM_P2P_BLOCK - 1u) / FMM_P2P_BLOCK) << 32);
+}
+
+__global__ void k_scan2_reduce(const uint32_t* __restrict__ in, int64_t m, unsigned long long* __restrict__ sums) {
+    __shared__ unsigned long long wt[kScanThreads / 32 + 1];
+    unsigned long long v[kScanItems];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) v[j] = (base + j < m) ? pop_blocks(in[base + j]) : 0ull;
+    unsigned long long tot = block_exclusive_scan(v, wt);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan2_top(unsigned long long* __restrict__ sums, int nb) {
+    __shared__ unsigned long long wt[kScanThreads / 32 + 1];
+    unsigned long long carry = 0;
+    for (int t0 = 0; t0 < nb; t0 += kScanTile) {
+        unsigned long long v[kScanItems];
+        int base = t0 + threadIdx.x * kScanItems;
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j) v[j] = (base + j < nb) ? sums[base + j] : 0ull;
+        unsigned long long tot = block_exclusive_scan(v, wt);
+#pragma unroll
+        for (int j = 0; j < kScanItems; ++j)
+            if (base + j < nb) sums[base + j] = v[j] + carry;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void k_scan2_down(const uint32_t* __restrict__ in, int64_t m, const unsigned long long* __restrict__ sums,
+                             uint32_t* __restrict__ leaf_start, uint32_t* __restrict__ bstart,
+                             uint2* __restrict__ map) {
+    __shared__ unsigned long long wt[kScanThreads / 32 + 1];
+    unsigned long long v[kScanItems];
+    uint32_t nbk[kScanItems];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = (base + j < m) ? pop_blocks(in[base + j]) : 0ull;
+        nbk[j] = (uint32_t)(v[j] >> 32);
+    }
+    block_exclusive_scan(v, wt);
+    const unsigned long long off = sums[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+        if (base + j < m) {
+            const unsigned long long e = v[j] + off;
+            const uint32_t b0 = (uint32_t)(e >> 32);
+            leaf_start[base + j] = (uint32_t)e;
+            bstart[base + j] = b0;
+            for (uint32_t b = 0; b < nbk[j]; ++b) map[b0 + b] = make_uint2((uint32_t)(base + j), b);
+        }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long tot = sums[gridDim.x];
+        leaf_start[m] = (uint32_t)tot;
+        bstart[m] = (uint32_t)(tot >> 32);
+    }
+}
+
 template <bool kMixed>
 __global__ void k_scatter(const double2* __restrict__ xy, const double* __restrict__ q, int64_t n, int levels,
                           float2 s_ff, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank,
@@ -160,9 +225,18 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
                                pl->keys, pl->rank, pl->counts, pl->d_status);
     ++launches;
     const int nb = pl->scan_blocks;
-    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(pl->counts, m, pl->block_sums);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(pl->block_sums, nb);
-    k_scan_down<<<nb, kScanThreads, 0, st>>>(pl->counts, m, pl->block_sums, pl->leaf_start, (uint32_t)n);
+    if (pl->precision == FMM_FP64) {
+        k_scan_reduce<<<nb, kScanThreads, 0, st>>>(pl->counts, m, pl->block_sums);
+        k_scan_top<<<1, kScanThreads, 0, st>>>(pl->block_sums, nb);
+        k_scan_down<<<nb, kScanThreads, 0, st>>>(pl->counts, m, pl->block_sums, pl->leaf_start, (uint32_t)n);
+    } else {
+        // the near-field blocks come with the same scan (block_sums holds 64-bit partials here)
+        unsigned long long* sums = reinterpret_cast<unsigned long long*>(pl->block_sums);
+        k_scan2_reduce<<<nb, kScanThreads, 0, st>>>(pl->counts, m, sums);
+        k_scan2_top<<<1, kScanThreads, 0, st>>>(sums, nb);
+        k_scan2_down<<<nb, kScanThreads, 0, st>>>(pl->counts, m, sums, pl->leaf_start, pl->leaf_bstart,
+                                                  pl->blk_map);
+    }
     launches += 3;
     const double sd = pl->box / (double)(1 << pl->levels);
     const float s_hi = (float)sd;
@@ -182,10 +256,19 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
 
 int fmm_scan_blocks(int64_t m) { return (int)((m + kScanTile - 1) / kScanTile); }
 
-// target blocks of up to 32 particles per finest square, for the near-field work split
-__global__ void k_leaf_blocks(const uint32_t* __restrict__ leaf_start, int64_t m, uint32_t* __restrict__ nb) {
+// target blocks of up to `block` particles per finest square, for the near-field work split
+__global__ void k_leaf_blocks(const uint32_t* __restrict__ leaf_start, int64_t m, uint32_t block,
+                              uint32_t* __restrict__ nb) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) nb[i] = (leaf_start[i + 1] - leaf_start[i] + 31u) / 32u;
+    if (i < m) nb[i] = (leaf_start[i + 1] - leaf_start[i] + block - 1u) / block;
+}
+
+// block -> (square, block index inside the square), one thread per square
+__global__ void k_block_map(const uint32_t* __restrict__ bstart, int64_t m, uint2* __restrict__ map) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t b0 = bstart[i], b1 = bstart[i + 1];
+    for (uint32_t b = b0; b < b1; ++b) map[b] = make_uint2((uint32_t)i, b - b0);
 }
 
 int fmm_launch_scan(const uint32_t* counts, int64_t m, uint32_t* block_sums, uint32_t* leaf_start, uint32_t n_total,
@@ -197,9 +280,13 @@ int fmm_launch_scan(const uint32_t* counts, int64_t m, uint32_t* block_sums, uin
     return cudaGetLastError() == cudaSuccess ? 3 : -1;
 }
 
-int fmm_launch_leaf_blocks(const uint32_t* leaf_start, int64_t m, uint32_t* nb, uint32_t* block_sums, uint32_t* bstart,
-                           cudaStream_t st) {
-    k_leaf_blocks<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(leaf_start, m, nb);
+int fmm_launch_leaf_blocks(const uint32_t* leaf_start, int64_t m, uint32_t block, uint32_t* nb, uint32_t* block_sums,
+                           uint32_t* bstart, uint2* map, cudaStream_t st) {
+    const unsigned g = (unsigned)((m + 255) / 256);
+    k_leaf_blocks<<<g, 256, 0, st>>>(leaf_start, m, block, nb);
     const int r = fmm_launch_scan(nb, m, block_sums, bstart, 0xffffffffu, st);
-    return r < 0 ? -1 : r + 1;
+    if (r < 0) return -1;
+    if (map == nullptr) return r + 1;
+    k_block_map<<<g, 256, 0, st>>>(bstart, m, map);
+    return cudaGetLastError() == cudaSuccess ? r + 2 : -1;
 }
