@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uniform_1m_l8_p20", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default="3xtf32",
+                    help="fp32 (CUDA-core M2L), 3xtf32 / tf32 or bf16x3 / bf16 (tensor-core M2L from level 7), fp64")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=20)
@@ -85,10 +86,10 @@ def make_inputs(w, rank=0):
 
 # ---------------------------------------------------------------- algorithmic work per launch
 
-def m2l_pairs(levels):
-    """(target, source) square pairs of the interaction lists of levels 2..levels inside the box."""
+def m2l_pairs(levels, kmin=2):
+    """(target, source) square pairs of the interaction lists of levels kmin..levels inside the box."""
     total = 0
-    for k in range(2, levels + 1):
+    for k in range(kmin, levels + 1):
         side = 1 << k
         t = np.arange(side)
         cnt = np.zeros(side, dtype=np.int64)   # per-axis counts are not separable; count per offset
@@ -108,20 +109,43 @@ def m2l_pairs(levels):
     return total
 
 
+TC_KMIN = 7   # the tensor-core M2L takes levels 7 and finer
+
+
 def roofline_for(stage, stats, ms, w, peaks, sm_clock_mhz, precision, traffic):
     p1 = w["p"] + 1
     n = w["n"]
+    if stage == "m2l_tc":
+        # the tensor-core kernel alone: algorithmic flops of its levels (split products not counted)
+        # against the tensor peak of the operand type
+        flops = m2l_pairs(w["levels"], TC_KMIN) * 8 * p1 * p1
+        bf = precision.startswith("bf16")
+        peak = peaks.get("bf16_tflops", 1939.8) / (1.0 if bf else 2.0)
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": traffic,
+                "peak_basis": "measured bf16 dense (MEASURED_PEAKS.json)" + ("" if bf else " x 1/2 for TF32"),
+                "work_per_launch": f"{flops:.4g} flop = IL pairs of levels {TC_KMIN}..{w['levels']} x 8 (p+1)^2"}
+    if stage == "p2p_kernel":
+        pairs = stats["p2p_pairs"]
+        peak = N_SMS * MUFU_PER_SM * sm_clock_mhz * 1e6 / 1e12   # Tlg2/s
+        ach = pairs / (ms * 1e-3) / 1e12
+        return {"kernel": "k_p2p_mixed", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tlg2/s",
+                "frac": ach / peak, "traffic": traffic,
+                "peak_basis": f"MUFU lg2: {N_SMS} SMs x {MUFU_PER_SM}/clk x {sm_clock_mhz:.0f} MHz",
+                "work_per_launch": f"{pairs} ordered pairs, one lg2 each"}
     if stage == "m2l":
         flops = m2l_pairs(w["levels"]) * 8 * p1 * p1
-        if precision in ("tf32", "3xtf32"):
-            # the stage runs levels >= 8 on the tensor cores and the coarser ones on the CUDA cores;
-            # algorithmic flops of all levels over the stage time, against the TF32 tensor peak
-            # (measured dense bf16 x the nominal TF32/BF16 ratio of 1/2)
-            peak = peaks.get("bf16_tflops", 1939.8) / 2.0
+        if precision in ("tf32", "3xtf32", "bf16", "bf16x3"):
+            # the stage runs levels >= 7 on the tensor cores and the coarser ones on the CUDA cores;
+            # algorithmic flops of all levels over the stage time, against the tensor peak of the
+            # operand type (measured dense bf16; x the nominal TF32/BF16 ratio of 1/2 for TF32)
+            bf = precision.startswith("bf16")
+            peak = peaks.get("bf16_tflops", 1939.8) / (1.0 if bf else 2.0)
             ach = flops / (ms * 1e-3) / 1e12
             return {"kernel": "m2l", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": traffic,
-                    "peak_basis": "measured bf16 dense (MEASURED_PEAKS.json) x 1/2 for TF32",
+                    "peak_basis": "measured bf16 dense (MEASURED_PEAKS.json)" + ("" if bf else " x 1/2 for TF32"),
                     "work_per_launch": f"{flops:.4g} flop = IL pairs x 8 (p+1)^2 (split products not counted)"}
         if precision in ("fp32", "fp64"):
             lanes = FP32_LANES_PER_SM if precision == "fp32" else None
@@ -226,7 +250,7 @@ def time_plan(binding, torch, w, precision, xy_d, q_d, steps, warmup, flush, str
         binding.fmm_potential(plan.handle, xy_d, q_d, phi)
         plan.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    stage_ms = {k: [] for k in ("sort", "p2m", "m2l", "l2p", "p2p")}
+    stage_ms = {k: [] for k in ("sort", "p2m", "m2l", "l2p", "p2p", "m2l_tc", "p2p_kernel")}
     launches = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -298,14 +322,17 @@ def run_ours(args):
     got = phi[idx_d]
     err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
 
-    # per-stage device times and the dominant kernel's roofline
-    stage_avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
-    dom = max(stage_avg, key=stage_avg.get)
-    sm_clk = clk["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    roof = roofline_for(dom, last, stage_avg[dom], w, peaks, peaks.get("sm_max_mhz", 2070.0), args.precision,
-                        load_traffic(dom))
-    roof_all = {k: roofline_for(k, last, stage_avg[k], w, peaks, peaks.get("sm_max_mhz", 2070.0), args.precision,
-                                load_traffic(k)) for k in stage_avg}
+    # per-stage device times, the two kernels the library times alone, and the dominant one's
+    # roofline (a single kernel where one is timed alone, else the stage)
+    stage_avg = {k: float(np.mean(stage_ms[k])) for k in ("sort", "p2m", "m2l", "l2p", "p2p")}
+    kern_avg = {k: float(np.mean(stage_ms[k])) for k in ("m2l_tc", "p2p_kernel")}
+    cands = {k: stage_avg[k] for k in ("sort", "p2m", "l2p")}
+    cands.update({"m2l_tc": kern_avg["m2l_tc"]} if kern_avg["m2l_tc"] > 0 else {"m2l": stage_avg["m2l"]})
+    cands.update({"p2p_kernel": kern_avg["p2p_kernel"]} if kern_avg["p2p_kernel"] > 0 else {"p2p": stage_avg["p2p"]})
+    dom = max(cands, key=cands.get)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    roof = roofline_for(dom, last, cands[dom], w, peaks, sm_max, args.precision, load_traffic(dom))
+    roof_all = {k: roofline_for(k, last, v, w, peaks, sm_max, args.precision, load_traffic(k)) for k, v in cands.items()}
 
     # end to end through the host-buffer entry point: H2D of xy, q and D2H of phi every step
     xy_h = torch.from_numpy(xy).pin_memory()
@@ -354,7 +381,7 @@ def run_ours(args):
                        "precision": args.precision, "parallelism": f"replicas x{ws}",
                        "l2": "256 MB buffer written between timed steps (outside the events)"},
             "rel_l2_err": err, "meets_error_bound": err <= ERR_BOUND,
-            "stage_ms": stage_avg, "roofline": roof, "roofline_stages": roof_all,
+            "stage_ms": stage_avg, "kernel_ms": kern_avg, "roofline": roof, "roofline_stages": roof_all,
             "gpu_launches": launches, "e2e": e2e, "fp64_gpu": fp64,
             "speedup_vs_fp64_gpu": (value / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu, "batched": batched, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],

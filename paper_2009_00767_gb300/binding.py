@@ -44,7 +44,8 @@ class fmm_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_sort", ctypes.c_double), ("ms_p2m", ctypes.c_double),
                 ("ms_m2l", ctypes.c_double), ("ms_l2p", ctypes.c_double), ("ms_p2p", ctypes.c_double),
                 ("p2p_pairs", ctypes.c_int64), ("max_leaf", ctypes.c_int64), ("kernel_launches", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_uint64)]
+                ("workspace_bytes", ctypes.c_uint64), ("ms_m2l_tc", ctypes.c_double),
+                ("ms_p2p_kernel", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

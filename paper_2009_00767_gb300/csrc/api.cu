@@ -82,7 +82,7 @@ void free_plan(fmm_plan_s* pl) {
     fmm_tc_destroy(pl);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     if (pl->h_counters) cudaFreeHost(pl->h_counters);
-    for (int e = 0; e < 6; ++e)
+    for (int e = 0; e < 10; ++e)
         if (pl->ev[e]) cudaEventDestroy(pl->ev[e]);
     cudaSetDevice(prev);
     delete pl;
@@ -101,10 +101,25 @@ struct DeviceGuard {
     }
 };
 
+// the mixed path's accumulators (square populations, coarse FP64 moment grids) back to zero
+fmm_status reset_accumulators(fmm_plan_s* pl, cudaStream_t st) {
+    const size_t m = (size_t)1 << (2 * pl->levels);
+    if (cudaMemsetAsync(pl->counts, 0, sizeof(uint32_t) * m, st) != cudaSuccess) return FMM_ERR_CUDA;
+    for (int k = 2; k <= pl->levels; ++k)
+        if (cudaMemsetAsync(pl->grids.A[k], 0, pl->a_bytes[k], st) != cudaSuccess) return FMM_ERR_CUDA;
+    pl->clean = 1;
+    return FMM_OK;
+}
+
 fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* phi) {
     cudaStream_t st = pl->stream;
     if (cudaMemsetAsync(pl->d_counters, 0, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long), st) != cudaSuccess)
         return FMM_ERR_CUDA;
+    if (pl->precision != FMM_FP64) {
+        if (!pl->clean && reset_accumulators(pl, st) != FMM_OK) return FMM_ERR_CUDA;
+        pl->clean = 0;   // until the whole call is enqueued
+    }
+    pl->ev_kernels = 0;
     cudaEventRecord(pl->ev[0], st);
     int launches = fmm_launch_sort(pl, xy, q);
     if (launches < 0) return FMM_ERR_CUDA;
@@ -113,6 +128,7 @@ fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* ph
     if (more < 0) return FMM_ERR_CUDA;
     pl->launches = launches + more;
     pl->events_recorded = 1;
+    if (pl->precision != FMM_FP64) pl->clean = 1;
     return FMM_OK;
 }
 
@@ -196,8 +212,8 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->T64, sizeof(double2) * T.size()));
     if (cudaMemcpy(pl->T64, T.data(), sizeof(double2) * T.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         FMM_TRY(FMM_ERR_CUDA);
-    if (precision == FMM_MIXED_BF16 || precision == FMM_MIXED_BF16X3) FMM_TRY(FMM_ERR_UNSUPPORTED);
-    if (precision == FMM_MIXED_TF32 || precision == FMM_MIXED_3XTF32) {
+    if (precision == FMM_MIXED_TF32 || precision == FMM_MIXED_3XTF32 || precision == FMM_MIXED_BF16 ||
+        precision == FMM_MIXED_BF16X3) {
         std::vector<double> tre(T.size()), tim(T.size());
         for (size_t i = 0; i < T.size(); ++i) {
             tre[i] = T[i].real();
@@ -234,7 +250,7 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->d_xy_stage, sizeof(double) * 2 * n));
     FMM_TRY(dev_alloc(pl, &pl->d_q_stage, sizeof(double) * n));
     FMM_TRY(dev_alloc(pl, &pl->d_phi_stage, sizeof(double) * n));
-    for (int e = 0; e < 6; ++e)
+    for (int e = 0; e < 10; ++e)
         if (cudaEventCreate(&pl->ev[e]) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
 #undef FMM_TRY
     pl->last.n = n;
@@ -296,6 +312,12 @@ fmm_status fmm_sync(fmm_plan_t plan) {
         plan->last.ms_l2p = ms[3];
         plan->last.ms_p2p = ms[4];
         plan->last.ms_total = tot;
+        float kt = 0.f;
+        plan->last.ms_m2l_tc = (plan->ev_kernels & 1) && cudaEventElapsedTime(&kt, plan->ev[6], plan->ev[7]) ==
+                                                              cudaSuccess ? kt : 0.0;
+        plan->last.ms_p2p_kernel = (plan->ev_kernels & 2) && cudaEventElapsedTime(&kt, plan->ev[8], plan->ev[9]) ==
+                                                                  cudaSuccess ? kt : 0.0;
+        plan->ev_kernels = 0;
         unsigned long long pairs = 0, mx = 0;
         for (int c = 0; c < FMM_COUNTER_SLOTS; ++c) {
             pairs += plan->h_counters[c];

@@ -93,6 +93,8 @@ struct fmm_plan_s {
     int scan_blocks;
     uint32_t* leaf_bstart;       // near-field target blocks: exclusive scan over the squares, 4^levels + 1
     uint2* blk_map;              // near-field block -> (square, block inside it), mixed path
+    int clean;                   // mixed path: counts and the coarse FP64 moment grids are zero (each
+                                 // call's kernels leave them so; a call that failed to enqueue does not)
     uint32_t* sorted_key;
     fmm_p64* sorted64;
     float4* sorted32;
@@ -115,7 +117,8 @@ struct fmm_plan_s {
     double* d_q_stage;
     double* d_phi_stage;
 
-    cudaEvent_t ev[6];
+    cudaEvent_t ev[10];   // stage boundaries [0..5]; the tensor-core M2L kernel [6, 7]; the P2P kernel [8, 9]
+    int ev_kernels;       // bit 0: [6, 7] recorded this call, bit 1: [8, 9]
     int events_recorded;
     int launches;
     fmm_stats last;

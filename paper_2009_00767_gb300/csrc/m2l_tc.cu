@@ -31,6 +31,8 @@
 // with the log would lose more than the error bound allows on clustered systems.  Every wait on
 // an mbarrier is bounded and sets a status flag when it runs out.
 
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -53,9 +55,13 @@ struct TcGroup {
     int d[3];
 };
 
+constexpr int kMaxParts = 3;     // split parts of an operand: TF32 x2 (hi, lo), BF16 x3 (hi, mid, lo)
+
 struct TcArgs {
-    const float* src[2][FMM_MAX_LEVELS + 1];   // [part][level] -> [q][KC][w2+2][w2+2][4] (1-cell zero halo)
-    const float* ops[2];                       // [part] -> [class][27 slots][KC][N][4], scale-free
+    // [part][level] -> [q][KC][w2+2][w2+2][16 bytes] (1-cell zero halo); a 16-byte K chunk holds 4
+    // TF32 or 8 BF16 values
+    const uint8_t* src[kMaxParts][FMM_MAX_LEVELS + 1];
+    const uint8_t* ops[kMaxParts];             // [part] -> [class][27 slots][KC][N][16 bytes], scale-free
     float2* B[FMM_MAX_LEVELS + 1];
     TcGroup groups[4][12];
     // the tiles of one class, finest level first: level seg_level[j] owns tiles
@@ -106,14 +112,30 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-        : "memory");
+// one MMA, D (+)= A B^T: kind::f16 with BF16 operands, or kind::tf32
+template <bool BF>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    if constexpr (BF)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
 }
+
+// The split products kept, as (A part, B part), in order: TF32 x2 drops lo lo; BF16 x3 keeps every
+// term down to 2^-16 of the product (hi hi, hi mid, mid hi, hi lo, lo hi, mid mid).
+__device__ constexpr int kProdA[6] = {0, 0, 1, 0, 2, 1};
+__device__ constexpr int kProdB[6] = {0, 1, 0, 2, 0, 1};
+__host__ __device__ constexpr int num_products(int np) { return np == 1 ? 1 : (np == 2 ? 3 : 6); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
@@ -131,15 +153,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 // group's source windows, one per tile, stream through NSW buffers.
 // Stages: ops buffers NSO (per group), window buffers NSW (per tile and group).
 
-template <int KC, int NP, int NSO, int NSW>
+// H: coefficients per real half, padded to a multiple of 8 (N = K per offset = 2H); BF: BF16
+// operands (else TF32); NP: split parts per operand.
+template <int H, bool BF, int NP, int NSO, int NSW>
 __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ TcArgs a) {
-    constexpr int N = 4 * KC, H = 2 * KC;
+    constexpr int N = 2 * H;
+    constexpr int KC = BF ? H / 4 : H / 2;           // 16-byte K chunks per offset
     constexpr uint32_t A_BYTES = KC * kWin * 16;     // one window, one part
     constexpr uint32_t OP_BYTES = KC * N * 16;       // one offset's operator, one part
     constexpr uint32_t OPS_STAGE = NP * 3 * OP_BYTES;
     constexpr uint32_t WIN_STAGE = NP * A_BYTES;
     constexpr uint32_t ACC_COLS = 64;                // per tile (N <= 64)
-    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+    constexpr uint32_t FMT = BF ? 1u : 2u;           // operand format: BF16 (kind::f16) or TF32
+    constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
+    constexpr int NPROD = num_products(NP);
+    static_assert(KC % 2 == 0 && NP * KC <= 32, "an MMA takes two K chunks; one producer lane per chunk");
 
     static_assert(NSW >= 2, "the window pipeline keeps one window in flight: it needs two window stages");
     extern __shared__ uint8_t smem_raw[];
@@ -218,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) break;
                 if (lane < NP) {
-                    const float* srcB = a.ops[lane] + ((size_t)cls * 27 + G.slot0) * (OP_BYTES / 4);
+                    const uint8_t* srcB = a.ops[lane] + ((size_t)cls * 27 + G.slot0) * OP_BYTES;
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                             su32(ops_buf + so * OPS_STAGE + lane * 3 * OP_BYTES)),
@@ -244,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                 const int k = tile_k[t];
                 const size_t W2P = ((size_t)1 << (k - 1)) + 2;
                 const size_t start = (size_t)(tile_P[t] - 1 + G.sy * (int)W2P);   // flat, >= 0
-                const float* src = a.src[part][k] + (((size_t)q * KC + j) * W2P * W2P + start) * 4;
+                const uint8_t* src = a.src[part][k] + (((size_t)q * KC + j) * W2P * W2P + start) * 16;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         su32(win_buf + sw * WIN_STAGE + part * A_BYTES + j * (kWin * 16))),
@@ -271,17 +299,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                     const uint32_t aoff = (uint32_t)(1 + G.sx[o]) * 16u;
 #pragma unroll
                     for (int ks = 0; ks < KC / 2; ++ks) {
-                        const uint32_t acc = (g | o | ks) != 0;
-                        const uint64_t ah = smem_desc(aBase + aoff + ks * 2 * (kWin * 16), kWin * 16, 128);
-                        const uint64_t bh = smem_desc(bBase + o * OP_BYTES + ks * 2 * (N * 16), N * 16, 128);
-                        mma_tf32(acc_t, ah, bh, IDESC, acc);
-                        if (NP == 2) {
-                            const uint64_t al =
-                                smem_desc(aBase + A_BYTES + aoff + ks * 2 * (kWin * 16), kWin * 16, 128);
-                            const uint64_t bl =
-                                smem_desc(bBase + 3 * OP_BYTES + o * OP_BYTES + ks * 2 * (N * 16), N * 16, 128);
-                            mma_tf32(acc_t, ah, bl, IDESC, 1u);
-                            mma_tf32(acc_t, al, bh, IDESC, 1u);
+#pragma unroll
+                        for (int pr = 0; pr < NPROD; ++pr) {
+                            const uint32_t acc = (g | o | ks | pr) != 0;
+                            const uint64_t ad = smem_desc(aBase + kProdA[pr] * A_BYTES + aoff + ks * 2 * (kWin * 16),
+                                                          kWin * 16, 128);
+                            const uint64_t bd = smem_desc(
+                                bBase + (kProdB[pr] * 3 + o) * OP_BYTES + ks * 2 * (N * 16), N * 16, 128);
+                            mma_issue<BF>(acc_t, ad, bd, IDESC, acc);
                         }
                     }
                 }
@@ -331,25 +356,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
-// FP32 moment grid (3-cell halo) -> the GEMM's source layout, one thread per cell of a parity
-// sub-grid: out[part][q][KC][w2][w2][4] with the K index Re M_0..M_p, pad, Im M_0..M_p, pad.
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
 
+__device__ __forceinline__ uint32_t bf16_rn_bits(float x) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
 struct PrepArgs {
     const float2* a32[FMM_MAX_LEVELS + 1];
-    float4* hi[FMM_MAX_LEVELS + 1];
-    float4* lo[FMM_MAX_LEVELS + 1];
+    uint4* out[kMaxParts][FMM_MAX_LEVELS + 1];
     long long base[FMM_MAX_LEVELS + 2];   // first cell (over all four parities) of each level
     int kmin, levels, p1;
 };
 
-template <int KC, int NP>
+// FP32 moment grid (3-cell halo) -> the GEMM's source layout, one thread per cell of a parity
+// sub-grid: out[part][q][KC][w2][w2][16 bytes] with the K index Re M_0..M_p, pad, Im M_0..M_p,
+// pad, each value split into NP parts: TF32 x2 hi = rna(x), lo = x - hi; BF16 x3 hi = rn(x),
+// mid = rn(x - hi), lo = rn(x - hi - mid) (each difference exact in FP32).
+template <int H, bool BF, int NP>
 __global__ void k_prep_tc(const __grid_constant__ PrepArgs a) {
-    constexpr int H = 2 * KC;
+    constexpr int KC = BF ? H / 4 : H / 2, PER = BF ? 8 : 4;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= a.base[a.levels + 1]) return;
     int k = a.kmin;
@@ -367,22 +397,32 @@ __global__ void k_prep_tc(const __grid_constant__ PrepArgs a) {
         vals[j] = m.x;                     // coefficient 0 holds M_0's high word: M_0 is real
         vals[H + j] = (j == 0) ? 0.f : m.y;
     }
-    // chunk-major source layout [q][chunk][row][col][4] (1-cell zero halo): the chunk of a run of
+    // chunk-major source layout [q][chunk][row][col] (1-cell zero halo): the chunk of a run of
     // consecutive cells of the flat array is one contiguous block
-    float4* hi = a.hi[k];
-    float4* lo = a.lo[k];
+    const size_t cell = (size_t)(row + 1) * W2P + (size_t)(col + 1);
 #pragma unroll
     for (int c = 0; c < KC; ++c) {
-        float h[4], l[4];
+        uint32_t w[NP][4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const float v = vals[4 * c + t];
-            h[t] = tf32_rna(v);
-            l[t] = v - h[t];
+        for (int t = 0; t < PER; ++t) {
+            float r = vals[PER * c + t];
+#pragma unroll
+            for (int part = 0; part < NP; ++part) {
+                if constexpr (BF) {
+                    const uint32_t b = bf16_rn_bits(r);
+                    r -= __uint_as_float(b << 16);
+                    if (t & 1) w[part][t >> 1] |= b << 16;
+                    else w[part][t >> 1] = b;
+                } else {
+                    const float h = (part + 1 < NP || NP == 1) ? tf32_rna(r) : r;   // x2: lo stays FP32
+                    r -= h;
+                    w[part][t] = __float_as_uint(h);
+                }
+            }
         }
-        const size_t at = (((size_t)q * KC + c) * W2P + (size_t)(row + 1)) * W2P + (size_t)(col + 1);
-        hi[at] = make_float4(h[0], h[1], h[2], h[3]);
-        if (NP == 2) lo[at] = make_float4(l[0], l[1], l[2], l[3]);
+        const size_t at = ((size_t)q * KC + c) * (size_t)W2P * W2P + cell;
+#pragma unroll
+        for (int part = 0; part < NP; ++part) a.out[part][k][at] = make_uint4(w[part][0], w[part][1], w[part][2], w[part][3]);
     }
 }
 
@@ -453,29 +493,46 @@ float host_tf32(float x) {
     return r;
 }
 
-// shared-memory plan: (ops stages, window stages) = (2, 2), else (1, 2); 128 bytes of alignment
-// slack and 256 bytes of barriers
-template <int KC, int NP>
+// host-side round to nearest even BF16 (finite inputs), returned as its 16 bits
+uint16_t host_bf16_bits(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf16_bits_to_float(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+// shared-memory plan: two operator stages and as many window stages (2 to 4) as fit, else one
+// operator stage and two window stages; 128 bytes of alignment slack and 256 bytes of barriers
+template <int H, bool BF, int NP>
 constexpr size_t tc_bytes(int nso, int nsw) {
-    return (size_t)nso * NP * 3 * (KC * (4 * KC) * 16) + (size_t)nsw * NP * (KC * kWin * 16) + 128 + 256;
+    constexpr int KC = BF ? H / 4 : H / 2;
+    return (size_t)nso * NP * 3 * (KC * (2 * H) * 16) + (size_t)nsw * NP * (KC * kWin * 16) + 128 + 256;
 }
-template <int KC, int NP>
+template <int H, bool BF, int NP>
 constexpr int tc_nso() {
-    return tc_bytes<KC, NP>(2, 2) <= 227 * 1024 ? 2 : 1;
+    return tc_bytes<H, BF, NP>(2, 2) <= 227 * 1024 ? 2 : 1;
 }
-template <int KC, int NP>
+template <int H, bool BF, int NP>
 constexpr int tc_nsw() {
-    static_assert(tc_bytes<KC, NP>(1, 2) <= 227 * 1024, "two window stages must fit");
-    return 2;
+    static_assert(tc_bytes<H, BF, NP>(1, 2) <= 227 * 1024, "two window stages must fit");
+    constexpr int nso = tc_nso<H, BF, NP>();
+    return tc_bytes<H, BF, NP>(nso, 4) <= 227 * 1024 ? 4 : (tc_bytes<H, BF, NP>(nso, 3) <= 227 * 1024 ? 3 : 2);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- plan-side state
 struct FmmTc {
-    int kc, np, sms;
-    float* ops[2];                              // one scale-free copy per part
-    float4* src[2][FMM_MAX_LEVELS + 1];
+    int h, kc, np, sms;
+    bool bf;                                    // BF16 operands (else TF32)
+    uint8_t* ops[kMaxParts];                    // one scale-free copy per part
+    uint8_t* src[kMaxParts][FMM_MAX_LEVELS + 1];
     TcArgs args;   // tables, filled at plan time
 };
 
@@ -484,24 +541,28 @@ struct FmmTc {
 // each MMA) loses more there than FP32 FMAs; they hold few targets, so the CUDA cores take them.
 int fmm_tc_kmin() { return kMinLevel; }
 
-// Allocate and build the tensor-core M2L state.  Returns 0, or a negative value on failure
-// (-1 CUDA error, -2 unsupported p).
+// Allocate and build the tensor-core M2L state for the plan's precision (TF32, 3xTF32, BF16 or
+// BF16x3).  Returns 0, or a negative value on failure (-1 CUDA error, -2 unsupported p).
 int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vector<double>& Tim) {
     const int p1 = pl->p + 1;
     const int H = ((p1 + 7) / 8) * 8;
-    const int kc = H / 2;
-    if (kc != 4 && kc != 8 && kc != 12 && kc != 16) return -2;
-    const int np = pl->precision == FMM_MIXED_3XTF32 ? 2 : 1;
+    if (H != 8 && H != 16 && H != 24 && H != 32) return -2;
+    const bool bf = pl->precision == FMM_MIXED_BF16 || pl->precision == FMM_MIXED_BF16X3;
+    const int kc = bf ? H / 4 : H / 2;
+    const int per = bf ? 8 : 4, elem = bf ? 2 : 4;
+    const int np = pl->precision == FMM_MIXED_3XTF32 ? 2 : (pl->precision == FMM_MIXED_BF16X3 ? 3 : 1);
     FmmTc* tc = new FmmTc();
     memset(tc, 0, sizeof(FmmTc));
+    tc->h = H;
     tc->kc = kc;
     tc->np = np;
+    tc->bf = bf;
     pl->tc = tc;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&tc->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return -1;
-    const int N = 4 * kc, K = 4 * kc;
+    const int N = 2 * H, K = 2 * H;
 
     // class tables: 12 groups (source parity qx, qy and row shift sy) of 1..3 offsets each
     int slots[4] = {0, 0, 0, 0};
@@ -529,18 +590,20 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
                 }
         if (slots[cls] != 27) return -1;
     }
-    // operators, real block form, [part][class][slot][KC][N][4]: scale-free, so one copy serves
-    // every level; the monopole-log entry (0, 0) is left out (summed in float-float by k_m2l_mono)
-    const size_t opsz = (size_t)4 * 27 * kc * N * 4;
+    // operators, real block form, [part][class][slot][KC][N][16 bytes]: scale-free, so one copy
+    // serves every level; the monopole-log entry (0, 0) is left out (summed in float-float by
+    // k_m2l_mono).  Each value is split into np parts as the sources are (TF32 x2: hi, FP32 lo;
+    // BF16 x3: hi, mid, lo, the differences taken in FP64).
+    const size_t opsz = (size_t)4 * 27 * kc * N * 16;   // bytes per part
     {
-        std::vector<float> hostops[2];
-        for (int part = 0; part < np; ++part) hostops[part].assign(opsz, 0.f);
+        std::vector<uint8_t> hostops[kMaxParts];
+        for (int part = 0; part < np; ++part) hostops[part].assign(opsz, 0);
         for (int cls = 0; cls < 4; ++cls)
             for (int g = 0; g < 12; ++g) {
                 const TcGroup& G = tc->args.groups[cls][g];
                 for (int o = 0; o < G.nops; ++o) {
                     const int d = G.d[o];
-                    const size_t base = ((size_t)cls * 27 + G.slot0 + o) * kc * N * 4;
+                    const size_t base = ((size_t)cls * 27 + G.slot0 + o) * kc * N * 16;
                     for (int n = 0; n < N; ++n)
                         for (int kk = 0; kk < K; ++kk) {
                             // input kk: Re M_j (kk < H) or Im M_j; output n: Re b_l (n < H) or Im b_l
@@ -555,18 +618,27 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
                                 else if (kk < H) val = ti;
                                 else val = tr;
                             }
-                            const float v = (float)val;
-                            const float h = host_tf32(v);
-                            const size_t at = base + ((size_t)(kk / 4) * N + n) * 4 + (kk % 4);
-                            hostops[0][at] = h;
-                            if (np == 2) hostops[1][at] = v - h;
+                            const size_t at = base + ((size_t)(kk / per) * N + n) * 16 + (size_t)(kk % per) * elem;
+                            if (bf) {
+                                double r = val;
+                                for (int part = 0; part < np; ++part) {
+                                    const uint16_t b = host_bf16_bits((float)r);
+                                    r -= (double)bf16_bits_to_float(b);
+                                    memcpy(&hostops[part][at], &b, 2);
+                                }
+                            } else {
+                                const float v = (float)val;
+                                const float h = host_tf32(v);
+                                const float parts[2] = {h, v - h};
+                                for (int part = 0; part < np; ++part) memcpy(&hostops[part][at], &parts[part], 4);
+                            }
                         }
                 }
             }
         for (int part = 0; part < np; ++part) {
-            if (cudaMalloc(&tc->ops[part], opsz * 4) != cudaSuccess) return -1;
-            pl->workspace_bytes += opsz * 4;
-            if (cudaMemcpy(tc->ops[part], hostops[part].data(), opsz * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            if (cudaMalloc(&tc->ops[part], opsz) != cudaSuccess) return -1;
+            pl->workspace_bytes += opsz;
+            if (cudaMemcpy(tc->ops[part], hostops[part].data(), opsz, cudaMemcpyHostToDevice) != cudaSuccess)
                 return -1;
             tc->args.ops[part] = tc->ops[part];
         }
@@ -579,7 +651,7 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
             if (cudaMalloc(&tc->src[part][k], bytes) != cudaSuccess) return -1;
             pl->workspace_bytes += bytes;
             if (cudaMemset(tc->src[part][k], 0, bytes) != cudaSuccess) return -1;
-            tc->args.src[part][k] = reinterpret_cast<const float*>(tc->src[part][k]);
+            tc->args.src[part][k] = tc->src[part][k];
         }
     }
     return 0;
@@ -588,7 +660,7 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
 void fmm_tc_destroy(fmm_plan_s* pl) {
     FmmTc* tc = pl->tc;
     if (!tc) return;
-    for (int part = 0; part < 2; ++part) {
+    for (int part = 0; part < kMaxParts; ++part) {
         if (tc->ops[part]) cudaFree(tc->ops[part]);
         for (int k = 0; k <= FMM_MAX_LEVELS; ++k)
             if (tc->src[part][k]) cudaFree(tc->src[part][k]);
@@ -597,8 +669,8 @@ void fmm_tc_destroy(fmm_plan_s* pl) {
     pl->tc = nullptr;
 }
 
-template <int KC, int NP>
-static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
+template <int H, bool BF, int NP>
+static int launch_tc(fmm_plan_s* pl, const MixedLevels& lv) {
     FmmTc* tc = pl->tc;
     cudaStream_t st = pl->stream;
     const int L = pl->levels, p1 = pl->p + 1;
@@ -607,8 +679,7 @@ static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
         long long acc = 0;
         for (int k = kMinLevel; k <= L; ++k) {
             pa.a32[k] = reinterpret_cast<const float2*>(pl->grids.A32[k]);
-            pa.hi[k] = tc->src[0][k];
-            pa.lo[k] = tc->src[1][k];
+            for (int part = 0; part < NP; ++part) pa.out[part][k] = reinterpret_cast<uint4*>(tc->src[part][k]);
             pa.base[k] = acc;
             acc += 4ll << (2 * (k - 1));
         }
@@ -616,7 +687,7 @@ static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
         pa.kmin = kMinLevel;
         pa.levels = L;
         pa.p1 = p1;
-        k_prep_tc<KC, NP><<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(pa);
+        k_prep_tc<H, BF, NP><<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(pa);
     }
     TcArgs& a = tc->args;
     for (int k = 0; k <= FMM_MAX_LEVELS; ++k) a.B[k] = reinterpret_cast<float2*>(pl->grids.B[k]);
@@ -643,11 +714,14 @@ static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
     while (cols < a.rows * 64) cols <<= 1;
     a.tmem_cols = cols;
     const int items = (tiles + a.rows - 1) / a.rows;
-    constexpr int NSO = tc_nso<KC, NP>(), NSW = tc_nsw<KC, NP>();
-    const size_t shm = tc_bytes<KC, NP>(NSO, NSW);
-    auto kern = k_m2l_tc<KC, NP, NSO, NSW>;
+    constexpr int NSO = tc_nso<H, BF, NP>(), NSW = tc_nsw<H, BF, NP>();
+    const size_t shm = tc_bytes<H, BF, NP>(NSO, NSW);
+    auto kern = k_m2l_tc<H, BF, NP, NSO, NSW>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
+    cudaEventRecord(pl->ev[6], st);
     kern<<<4 * items, kThreads, shm, st>>>(a);
+    cudaEventRecord(pl->ev[7], st);
+    pl->ev_kernels |= 1;
     {
         MonoArgs ma{};
         long long acc = 0;
@@ -671,12 +745,16 @@ static int launch_tc_kc(fmm_plan_s* pl, const MixedLevels& lv) {
 int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv) {
     const FmmTc* tc = pl->tc;
     if (!tc || pl->levels < kMinLevel) return 0;
-    const bool x3 = tc->np == 2;
-    switch (tc->kc) {
-        case 4: return x3 ? launch_tc_kc<4, 2>(pl, lv) : launch_tc_kc<4, 1>(pl, lv);
-        case 8: return x3 ? launch_tc_kc<8, 2>(pl, lv) : launch_tc_kc<8, 1>(pl, lv);
-        case 12: return x3 ? launch_tc_kc<12, 2>(pl, lv) : launch_tc_kc<12, 1>(pl, lv);
-        case 16: return x3 ? launch_tc_kc<16, 2>(pl, lv) : launch_tc_kc<16, 1>(pl, lv);
+#define FMM_TC_CASES(H)                                                                                     \
+    case H:                                                                                                 \
+        if (tc->bf) return tc->np == 3 ? launch_tc<H, true, 3>(pl, lv) : launch_tc<H, true, 1>(pl, lv);    \
+        return tc->np == 2 ? launch_tc<H, false, 2>(pl, lv) : launch_tc<H, false, 1>(pl, lv);
+    switch (tc->h) {
+        FMM_TC_CASES(8)
+        FMM_TC_CASES(16)
+        FMM_TC_CASES(24)
+        FMM_TC_CASES(32)
         default: return -1;
     }
+#undef FMM_TC_CASES
 }

@@ -325,13 +325,25 @@ k_p2m_coarse(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, i
 }
 
 // -------------------------------------------------------------------------------- moment prep
-// FP64 moment grid -> FP32 grid, once per coefficient; coefficient 0 (the real total charge)
-// becomes a float-float pair.
-__global__ void k_prep_a32(const double2* __restrict__ a64, float2* __restrict__ a32, int64_t count, int p1) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= count) return;
-    const double2 v = a64[e];
-    a32[e] = (e % p1 == 0) ? fmm_d2ff_bits(v.x) : make_float2(fmm_d2ff_bits(v.x).x, fmm_d2ff_bits(v.y).x);
+// FP64 moment grids of the coarse levels -> FP32 grids, one thread per coefficient over all the
+// levels; coefficient 0 (the real total charge) becomes a float-float pair.  The FP64 accumulator
+// goes back to zero for the next call.
+struct PrepA32Args {
+    double2* a64[FMM_MAX_LEVELS + 1];
+    float2* a32[FMM_MAX_LEVELS + 1];
+    int64_t base[FMM_MAX_LEVELS + 2];   // first coefficient of each level 2..kmax
+    int kmax, p1;
+};
+
+__global__ void k_prep_a32(const __grid_constant__ PrepA32Args a) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.base[a.kmax + 1]) return;
+    int k = 2;
+    while (g >= a.base[k + 1]) ++k;
+    const int64_t e = g - a.base[k];
+    const double2 v = a.a64[k][e];
+    a.a64[k][e] = make_double2(0.0, 0.0);
+    a.a32[k][e] = (e % a.p1 == 0) ? fmm_d2ff_bits(v.x) : make_float2(fmm_d2ff_bits(v.x).x, fmm_d2ff_bits(v.y).x);
 }
 
 // -------------------------------------------------------------------------------- M2L (FP32 SIMT)
@@ -817,9 +829,10 @@ int fmm_m2l_bucket(int p1) {
 }
 
 int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
-    if (pl->precision != FMM_MIXED_FP32 && pl->precision != FMM_MIXED_TF32 && pl->precision != FMM_MIXED_3XTF32)
+    if (pl->precision != FMM_MIXED_FP32 && pl->precision != FMM_MIXED_TF32 && pl->precision != FMM_MIXED_3XTF32 &&
+        pl->precision != FMM_MIXED_BF16 && pl->precision != FMM_MIXED_BF16X3)
         return -2;
-    // in the TF32 modes the tensor-core M2L takes the levels from fmm_tc_kmin() on
+    // in the tensor-core modes the tensor-core M2L takes the levels from fmm_tc_kmin() on
     const bool use_tc = pl->tc != nullptr && pl->levels >= fmm_tc_kmin();
     cudaStream_t st = pl->stream;
     const int64_t n = pl->n;
@@ -830,9 +843,7 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     if (L >= 2) {
         // fine levels: the finest kFineLevels; coarser ones by the particle-parallel kernel
         const int kf = L - (kFineLevels - 1) > 2 ? L - (kFineLevels - 1) : 2;
-        const int kc_max = kf - 1;
-        for (int k = 2; k <= kc_max; ++k)
-            if (cudaMemsetAsync(pl->grids.A[k], 0, pl->a_bytes[k], st) != cudaSuccess) return -1;
+        const int kc_max = kf - 1;   // the coarse FP64 grids are zero here (k_prep_a32 re-zeroes them)
         const unsigned fblocks = (unsigned)(((1ull << (2 * L)) + 127) / 128);
         const unsigned cblocks = (unsigned)((n + 4 * kCoarseChunk - 1) / (4 * kCoarseChunk));
         switch (pl->p1b) {
@@ -848,11 +859,19 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
             default: return -2;
         }
         launches += kc_max >= 2 ? 2 : 1;
-        for (int k = 2; k <= kc_max; ++k) {
-            const int64_t count = (int64_t)fmm_grid_width(k) * fmm_grid_width(k) * p1;
-            k_prep_a32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(
-                reinterpret_cast<const double2*>(pl->grids.A[k]), reinterpret_cast<float2*>(pl->grids.A32[k]), count,
-                p1);
+        if (kc_max >= 2) {
+            PrepA32Args pa{};
+            int64_t acc = 0;
+            for (int k = 2; k <= kc_max; ++k) {
+                pa.a64[k] = reinterpret_cast<double2*>(pl->grids.A[k]);
+                pa.a32[k] = reinterpret_cast<float2*>(pl->grids.A32[k]);
+                pa.base[k] = acc;
+                acc += (int64_t)fmm_grid_width(k) * fmm_grid_width(k) * p1;
+            }
+            pa.base[kc_max + 1] = acc;
+            pa.kmax = kc_max;
+            pa.p1 = p1;
+            k_prep_a32<<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(pa);
             ++launches;
         }
     }
@@ -939,8 +958,11 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
         // upper bound of the target blocks: each square adds at most one partial block
         const uint64_t wmax = (uint64_t)nleaf + (uint64_t)(n / FMM_P2P_BLOCK) + 1;
         const unsigned blocks = (unsigned)((wmax + kP2PWarps - 1) / kP2PWarps);
+        cudaEventRecord(pl->ev[8], st);
         k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, st>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, pl->blk_map,
                                                       nleaf, L, lv.s_leaf, far, phi, pl->d_status, pl->d_counters);
+        cudaEventRecord(pl->ev[9], st);
+        pl->ev_kernels |= 2;
         ++launches;
     }
     cudaEventRecord(pl->ev[5], st);

@@ -122,7 +122,7 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, int64_t m, const ui
 
 // Mixed path: one scan of (population, near-field blocks) pairs packed in 64 bits (the low word
 // never carries: n < 2^32) gives leaf_start and the block starts at once; the down-sweep also
-// writes the block -> (square, block inside it) map.
+// writes the block -> (square, block inside it) map and zeroes the populations it has read.
 __device__ __forceinline__ unsigned long long pop_blocks(uint32_t c) {
     return (unsigned long long)c | ((unsigned long long)((c + FMM_P2P_BLOCK - 1u) / FMM_P2P_BLOCK) << 32);
 }
@@ -154,7 +154,7 @@ __global__ void k_scan2_top(unsigned long long* __restrict__ sums, int nb) {
     if (threadIdx.x == 0) sums[nb] = carry;
 }
 
-__global__ void k_scan2_down(const uint32_t* __restrict__ in, int64_t m, const unsigned long long* __restrict__ sums,
+__global__ void k_scan2_down(uint32_t* __restrict__ in, int64_t m, const unsigned long long* __restrict__ sums,
                              uint32_t* __restrict__ leaf_start, uint32_t* __restrict__ bstart,
                              uint2* __restrict__ map) {
     __shared__ unsigned long long wt[kScanThreads / 32 + 1];
@@ -165,6 +165,7 @@ __global__ void k_scan2_down(const uint32_t* __restrict__ in, int64_t m, const u
     for (int j = 0; j < kScanItems; ++j) {
         v[j] = (base + j < m) ? pop_blocks(in[base + j]) : 0ull;
         nbk[j] = (uint32_t)(v[j] >> 32);
+        if (base + j < m) in[base + j] = 0u;   // the populations start the next call at zero
     }
     block_exclusive_scan(v, wt);
     const unsigned long long off = sums[blockIdx.x];
@@ -217,7 +218,9 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
     const int64_t m = (int64_t)1 << (2 * pl->levels);
     cudaStream_t st = pl->stream;
     int launches = 0;
-    if (cudaMemsetAsync(pl->counts, 0, sizeof(uint32_t) * m, st) != cudaSuccess) return -1;
+    // the mixed path's scan returns counts to zero for the next call
+    if (pl->precision == FMM_FP64 && cudaMemsetAsync(pl->counts, 0, sizeof(uint32_t) * m, st) != cudaSuccess)
+        return -1;
     const int tb = 256;
     const unsigned nblk = (unsigned)((n + tb - 1) / tb);
     const float scale_over_box32 = (float)((double)(1 << pl->levels) / pl->box);

@@ -60,14 +60,16 @@ def test_mixed_full_size_uniform_1m(oracle_mod):
     assert err < MIXED_TOL
 
 
-@pytest.mark.parametrize("precision,tol", [("3xtf32", MIXED_TOL), ("tf32", 1e-3)])
+@pytest.mark.parametrize("precision,tol", [("3xtf32", MIXED_TOL), ("tf32", 1e-3), ("bf16x3", MIXED_TOL),
+                                           ("bf16", 1e-2)])
 @pytest.mark.parametrize("case", [
     (1 << 16, 8, 20, "uniform", 7),     # one particle per finest square: the tensor-core level is 8
     (150000, 8, 12, "gmm", 8),          # clustered, many empty squares, p = 12 (K = N = 32)
     (200000, 8, 16, "annulus", 9),      # p = 16 (K = N = 48 with padding)
 ])
 def test_tensor_core_m2l_matches_oracle(oracle_mod, precision, tol, case):
-    """M2L of levels 7..8 on tcgen05 (TF32 / split 3xTF32), levels 2..6 on the CUDA cores."""
+    """M2L of levels 7..8 on tcgen05 (TF32 / split 3xTF32, BF16 / split BF16x3), levels 2..6 on the
+    CUDA cores."""
     from gpu_util import run_fmm
     n, lev, p, fam, seed = case
     xy, q = getattr(inputs, fam)(n, inputs.config_seed(0, 300 + seed))
@@ -78,18 +80,20 @@ def test_tensor_core_m2l_matches_oracle(oracle_mod, precision, tol, case):
     assert err < tol
 
 
-def test_tensor_core_full_size_uniform_1m(oracle_mod):
-    """N = 2^20 uniform, levels 8, p = 20 in 3xTF32: every element against the oracle."""
+@pytest.mark.parametrize("precision", ["3xtf32", "bf16x3"])
+def test_tensor_core_full_size_uniform_1m(oracle_mod, precision):
+    """N = 2^20 uniform, levels 8, p = 20 in 3xTF32 and BF16x3: every element against the oracle."""
     from gpu_util import run_fmm
     xy, q = inputs.uniform(1 << 20, inputs.config_seed(1))
-    phi, st = run_fmm(xy, q, 8, 20, precision="3xtf32")
+    phi, st = run_fmm(xy, q, 8, 20, precision=precision)
     ref = oracle_mod.shiftfree(xy, q, 8, 20)
     err = rel_l2(phi, ref)
-    print(f"3xtf32 N=2^20 levels=8 p=20: rel L2 vs oracle {err:.3e}")
+    print(f"{precision} N=2^20 levels=8 p=20: rel L2 vs oracle {err:.3e}")
     assert err < MIXED_TOL
 
 
-@pytest.mark.parametrize("precision,tol", [("3xtf32", MIXED_TOL), ("tf32", 1e-3)])
+@pytest.mark.parametrize("precision,tol", [("3xtf32", MIXED_TOL), ("tf32", 1e-3), ("bf16x3", MIXED_TOL),
+                                           ("bf16", 1e-2)])
 @pytest.mark.parametrize("case", [
     (3000, 2, 8, "uniform", 11),        # 2 x 2 parity sub-grids: one flat tile, mostly halo
     (4096, 3, 5, "gmm", 12),            # p = 5 (K = N = 16)
@@ -123,7 +127,7 @@ def test_crowded_squares_split_over_warps(oracle_mod):
     assert err < MIXED_TOL
 
 
-@pytest.mark.parametrize("precision", ["fp32", "3xtf32"])
+@pytest.mark.parametrize("precision", ["fp32", "3xtf32", "bf16x3"])
 def test_full_size_clustered_16m_sampled(oracle_mod, precision):
     """N = 2^24 in a mixture of 32 Gaussians (sigma log-uniform in [0.01, 0.3]), levels 10,
     p = 24: 48 sampled particles against the oracle's direct sum, one by one."""
