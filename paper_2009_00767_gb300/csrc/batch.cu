@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "mixed_common.cuh"
+#include "p2p_block.cuh"
 
 namespace {
 
@@ -22,8 +23,6 @@ constexpr int kT = 128;   // threads per block of every batched kernel
 constexpr int kCoarseChunk = 256;
 constexpr int kLaneMax = 128;
 constexpr int kFineMean = 64;
-constexpr int kP2PCap = 512;
-constexpr unsigned kSpin = 1u << 22;
 
 struct BatchSys {
     long long p_off;                       // first particle of the system (input and sorted order)
@@ -56,6 +55,7 @@ struct BatchArgs {
     uint32_t* counts;
     uint32_t* leaf_start;
     const uint32_t* bstart;   // near-field target blocks: exclusive scan over the concatenated squares
+    const uint2* bmap;        // near-field block -> (concatenated square, block inside it)
     long long nl;             // concatenated finest squares
     uint32_t* sorted_key;
     float4* sorted32;
@@ -430,161 +430,41 @@ __global__ void __launch_bounds__(kT) kb_l2p(BatchArgs a, MixedLevels lv) {
     }
 }
 
-// -------------------------------------------------------------------------------- P2P + phi
-__device__ __forceinline__ float lg2_pair(float dx, float dy) {
-    const float r2 = fmaf(dx, dx, dy * dy);
-    float lg;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(r2));
-    return r2 > 0.f ? lg : 0.f;
-}
-
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-    for (unsigned it = 0; it < kSpin; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred P;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, P;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// one warp per finest square of any system (see mixed.cu); the warp's mbarrier phase flips
-// with every staged square it handles
+// One warp per near-field block of any system (blocks of up to FMM_P2P_BLOCK targets, the block
+// map giving the square), grid-stride; the block's near field is p2p_near (p2p_block.cuh), as in
+// the single-system path.
 __global__ void __launch_bounds__(kT) kb_p2p(BatchArgs a, MixedLevels lv) {
     extern __shared__ long long pre[];
-    __shared__ __align__(16) float4 buf[kT / 32][kP2PCap];
-    __shared__ __align__(8) uint64_t bar[kT / 32];
+    __shared__ __align__(16) float4 tgt[kT / 32][16];
+    __shared__ __align__(16) int4 seg[kT / 32][8];
     load_prefix(pre, a.wp_leaf, a.nsys);
-    const long long total = a.bstart[a.nl];   // target blocks of up to 32 over all squares
+    const long long total = a.bstart[a.nl];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&bar[warp]);
-    if (lane == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    uint32_t phase = 0;
     const bool bad = *(volatile const unsigned int*)a.status != 0u;
     double* phi = a.call->phi;
     for (long long w = (long long)blockIdx.x * (kT / 32) + warp; w < total && !bad;
          w += (long long)gridDim.x * (kT / 32)) {
-        const uint32_t gl = fmm_warp_search(a.bstart, (uint32_t)a.nl, (uint32_t)w, lane);
-        const uint32_t tb = (uint32_t)w - a.bstart[gl];
-        const int s = find_sys(pre, a.nsys, gl);
+        const uint2 lt = a.bmap[w];
+        const int s = find_sys(pre, a.nsys, (long long)lt.x);
         const BatchSys& S = a.sys[s];
-        const uint32_t leaf = (uint32_t)(gl - pre[s]);
+        const uint32_t leaf = (uint32_t)((long long)lt.x - pre[s]);
         const uint32_t* ls = a.leaf_start + S.leaf_off;
-        const uint32_t t0 = ls[leaf] + 32u * tb, t1 = ls[leaf + 1];
-        const int T = (int)min(32u, t1 - t0);
-        const int side = 1 << S.levels;
+        const uint32_t t0 = ls[leaf], t1 = ls[leaf + 1];
+        const uint32_t b0 = t0 + (uint32_t)FMM_P2P_BLOCK * lt.y;
+        const int T = (int)min((uint32_t)FMM_P2P_BLOCK, t1 - b0);
+        int idx = 0;
+        float2 far = make_float2(0.f, 0.f);
+        if (lane < T) {
+            idx = __float_as_int(a.sorted32[b0 + lane].w);
+            far = a.far[b0 + lane];
+        }
         const float s_leaf = a.box_ff.x * __int_as_float((127 - S.levels) << 23);
-        const int ix = (int)fmm_compact2(leaf), iy = (int)fmm_compact2(leaf >> 1);
-        uint32_t nb0[9], ncnt[9], noff[9];
-        uint32_t nsrc = 0;
-#pragma unroll
-        for (int b = 0; b < 9; ++b) {
-            const int jx = ix + (b % 3) - 1, jy = iy + (b / 3) - 1;
-            const bool in = jx >= 0 && jy >= 0 && jx < side && jy < side;
-            const uint32_t nl = in ? fmm_morton((uint32_t)jx, (uint32_t)jy) : 0u;
-            nb0[b] = in ? ls[nl] : 0u;
-            ncnt[b] = in ? ls[nl + 1] - nb0[b] : 0u;
-            noff[b] = nsrc;
-            nsrc += ncnt[b];
-        }
-        const bool staged = nsrc <= (uint32_t)kP2PCap;
-        if (staged) {
-            __syncwarp();
-            if (lane == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(16u * nsrc)
-                             : "memory");
-                const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(buf[warp]);
-#pragma unroll
-                for (int b = 0; b < 9; ++b)
-                    if (ncnt[b] > 0)
-                        asm volatile(
-                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-                                "r"(dst0 + 16u * noff[b]),
-                            "l"(a.sorted32 + nb0[b]), "r"(16u * ncnt[b]), "r"(mb)
-                            : "memory");
-            }
-            if (!bar_wait(mb, phase)) {
-                if (lane == 0) atomicOr(a.status, FMM_FLAG_TIMEOUT);
-                break;
-            }
-            phase ^= 1u;
-            float4* sb = buf[warp];
-#pragma unroll
-            for (int b = 0; b < 9; ++b) {
-                const float ox = (float)((b % 3) - 1) * s_leaf, oy = (float)((b / 3) - 1) * s_leaf;
-                for (uint32_t j = lane; j < ncnt[b]; j += 32) {
-                    float4 v = sb[noff[b] + j];
-                    v.x += ox;
-                    v.y += oy;
-                    sb[noff[b] + j] = v;
-                }
-            }
-            __syncwarp();
-        }
-        int tp = 1;
-        while (tp < T) tp <<= 1;
-        const uint32_t groups = 32 / tp;
-        const int slot = lane & (tp - 1);
-        const uint32_t grp = lane / tp;
-        const bool active = slot < T;
-        const uint32_t gi = t0 + (active ? slot : 0);
-        const float4 Pi = a.sorted32[gi];
-        float2 near = make_float2(0.f, 0.f);
-        if (staged) {
-            const float4* src = buf[warp];
-            float acc0 = 0.f, acc1 = 0.f;
-            uint32_t j = grp;
-            for (; j + 3u * groups < nsrc; j += 4u * groups) {
-                const float4 a0 = src[j], a1 = src[j + groups], a2 = src[j + 2u * groups], a3 = src[j + 3u * groups];
-                acc0 = fmaf(a0.z, lg2_pair(Pi.x - a0.x, Pi.y - a0.y), acc0);
-                acc1 = fmaf(a1.z, lg2_pair(Pi.x - a1.x, Pi.y - a1.y), acc1);
-                acc0 = fmaf(a2.z, lg2_pair(Pi.x - a2.x, Pi.y - a2.y), acc0);
-                acc1 = fmaf(a3.z, lg2_pair(Pi.x - a3.x, Pi.y - a3.y), acc1);
-            }
-            for (; j < nsrc; j += groups) {
-                const float4 a0 = src[j];
-                acc0 = fmaf(a0.z, lg2_pair(Pi.x - a0.x, Pi.y - a0.y), acc0);
-            }
-            near = make_float2(acc0 + acc1, 0.f);
-        } else {
-#pragma unroll
-            for (int b = 0; b < 9; ++b) {
-                const float bx = Pi.x - (float)((b % 3) - 1) * s_leaf;
-                const float by = Pi.y - (float)((b / 3) - 1) * s_leaf;
-                const float4* src = a.sorted32 + nb0[b];
-                for (uint32_t r0 = 0; r0 < ncnt[b]; r0 += kP2PCap) {
-                    const uint32_t r1 = min(ncnt[b], r0 + kP2PCap);
-                    float acc = 0.f;
-                    for (uint32_t j = r0 + grp; j < r1; j += groups) {
-                        const float4 Pj = src[j];
-                        acc = fmaf(Pj.z, lg2_pair(bx - Pj.x, by - Pj.y), acc);
-                    }
-                    near = ff_add_f(near, acc);
-                }
-            }
-        }
-        for (int o = tp; o < 32; o <<= 1) {
-            const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, near.x, o),
-                                             __shfl_xor_sync(0xffffffffu, near.y, o));
-            near = ff_add(near, other);
-        }
-        if (active && grp == 0) {
-            const float2 v = ff_add(a.far[gi], ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
-            phi[S.p_off + __float_as_int(Pi.w)] = fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);
-        }
-        __syncwarp();
+        uint32_t nsrc;
+        const float2 near =
+            p2p_near(a.sorted32, ls, leaf, t0, t1, b0, T, S.levels, s_leaf, tgt[warp], seg[warp], lane, &nsrc);
+        if (lane < T) phi[S.p_off + idx] = p2p_phi(far, near);
+        __syncwarp();   // tgt and seg are rewritten by the next block
     }
-    if (lane == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mb) : "memory");
 }
 
 }  // namespace
@@ -602,6 +482,7 @@ struct fmm_batch_s {
     BatchCall* d_call;
     BatchCall* h_call;                // pinned
     uint32_t *keys, *rank, *counts, *leaf_start, *block_sums, *sorted_key, *leaf_nb, *bstart;
+    uint2* bmap;
     float4* sorted32;
     double* a64;
     float2 *a32, *b32, *far;
@@ -622,7 +503,7 @@ void batch_free(fmm_batch_s* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     void* bufs[] = {b->d_sys, b->d_pre, b->d_call, b->keys, b->rank, b->counts, b->leaf_start, b->block_sums,
-                    b->leaf_nb, b->bstart,
+                    b->leaf_nb, b->bstart, b->bmap,
                     b->sorted_key, b->sorted32, b->a64, b->a32, b->b32, b->far, b->T32, b->d_status};
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -672,7 +553,8 @@ int enqueue_batch_kernels(fmm_batch_s* b, const BatchArgs& a, const MixedLevels&
     }
     kb_m2l_f32<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
     kb_l2p<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
-    const int lb = fmm_launch_leaf_blocks(b->leaf_start, b->nl, 32u, b->leaf_nb, b->block_sums, b->bstart, nullptr, st);
+    const int lb = fmm_launch_leaf_blocks(b->leaf_start, b->nl, (uint32_t)FMM_P2P_BLOCK, b->leaf_nb, b->block_sums,
+                                          b->bstart, b->bmap, st);
     if (lb < 0) return -1;
     kb_p2p<<<grid, kT, pre_bytes, st>>>(a, lv);
     launches += 3 + lb;
@@ -699,6 +581,7 @@ int enqueue_all(fmm_batch_s* b, cudaStream_t st) {
     a.counts = b->counts;
     a.leaf_start = b->leaf_start;
     a.bstart = b->bstart;
+    a.bmap = b->bmap;
     a.nl = b->nl;
     a.sorted_key = b->sorted_key;
     a.sorted32 = b->sorted32;
@@ -855,6 +738,7 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
               balloc(b, &b->counts, 4 * nl) && balloc(b, &b->leaf_start, 4 * (nl + 1)) &&
               balloc(b, &b->block_sums, 4 * ((size_t)fmm_scan_blocks(nl) + 1)) && balloc(b, &b->sorted_key, 4 * nt) &&
               balloc(b, &b->leaf_nb, 4 * nl) && balloc(b, &b->bstart, 4 * (nl + 1)) &&
+              balloc(b, &b->bmap, sizeof(uint2) * ((size_t)nl + (size_t)nt / FMM_P2P_BLOCK + 1)) &&
               balloc(b, &b->sorted32, 16 * nt) && balloc(b, &b->a64, sizeof(double2) * coarse * p1) &&
               balloc(b, &b->a32, sizeof(float2) * b->a_cells * p1) && balloc(b, &b->b32, sizeof(float2) * bcells * p1) &&
               balloc(b, &b->far, sizeof(float2) * nt) && balloc(b, &b->d_status, sizeof(unsigned int));

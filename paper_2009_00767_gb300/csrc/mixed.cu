@@ -19,6 +19,7 @@
 //   P2P  (E-2 of Sec. 2.1) in FP32 on square-local coordinates, log via the MUFU lg2 unit,
 //        lanes over sources and one register partial per target; phi = far + near.
 #include "mixed_common.cuh"
+#include "p2p_block.cuh"
 
 namespace {
 
@@ -74,23 +75,6 @@ __device__ __forceinline__ void group_reduce_scatter(float (&v)[VP], int lane) {
             const float keep = up ? v[i + m * B] : v[i];
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
         }
-    }
-}
-
-// the three power chains of the fused fine levels, with packed FP32x2 accumulation
-template <int P1B>
-__device__ __forceinline__ void add_powers3(float2 (&a0)[P1B], float2 (&a1)[P1B], float2 (&a2)[P1B], float q,
-                                            float2 w0, float2 w1, float2 w2) {
-    float r0 = q, i0 = 0.f, r1 = q, i1 = 0.f, r2 = q, i2 = 0.f;
-#pragma unroll
-    for (int m = 1; m < P1B; ++m) {
-        const float n0 = fmaf(r0, w0.x, -i0 * w0.y), j0 = fmaf(r0, w0.y, i0 * w0.x);
-        const float n1 = fmaf(r1, w1.x, -i1 * w1.y), j1 = fmaf(r1, w1.y, i1 * w1.x);
-        const float n2 = fmaf(r2, w2.x, -i2 * w2.y), j2 = fmaf(r2, w2.y, i2 * w2.x);
-        r0 = n0, i0 = j0, r1 = n1, i1 = j1, r2 = n2, i2 = j2;
-        a0[m] = __fadd2_rn(a0[m], make_float2(r0, i0));
-        a1[m] = __fadd2_rn(a1[m], make_float2(r1, i1));
-        a2[m] = __fadd2_rn(a2[m], make_float2(r2, i2));
     }
 }
 
@@ -180,10 +164,29 @@ __device__ __forceinline__ float fine_offset(uint32_t i, int sh) {
     return fmaf((float)(i & mask) + 0.5f, __int_as_float((127 - sh) << 23), -0.5f);
 }
 
-// levels max(2, l - 2) .. l, one lane per finest square.  Orders up to 24 walk the particles
-// once, with the three levels' power chains interleaved; higher orders take one pass per level.
+// two particles' power chains in packed FP32x2 (lane a, lane b of each register pair): ar[m]
+// accumulates (Re of a, Re of b), ai[m] (Im of a, Im of b)
 template <int P1B>
-__global__ void __launch_bounds__(128)
+__device__ __forceinline__ void add_powers_pair(float2 (&ar)[P1B], float2 (&ai)[P1B], float2 q2, float2 wx,
+                                                float2 wy) {
+    const float2 nwy = make_float2(-wy.x, -wy.y);
+    float2 pr = q2, pi = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 1; m < P1B; ++m) {
+        const float2 nr = __ffma2_rn(pr, wx, __fmul2_rn(pi, nwy));
+        const float2 ni = __ffma2_rn(pr, wy, __fmul2_rn(pi, wx));
+        pr = nr;
+        pi = ni;
+        ar[m] = __fadd2_rn(ar[m], pr);
+        ai[m] = __fadd2_rn(ai[m], pi);
+    }
+}
+
+// levels max(2, l - 2) .. l, one lane per finest square.  Per level the lane walks its particles
+// two at a time, the pair's power chains in packed FP32x2 arithmetic (the particles stay in L1
+// between the levels' passes); the total charge is summed once, in float-float.
+template <int P1B>
+__global__ void __launch_bounds__(128, P1B <= 25 ? 4 : 1)
 k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, int levels, int p, MixedLevels lv,
            FmmLevelPtrs g) {
     __shared__ float red[4][2 * P1B];
@@ -191,56 +194,41 @@ k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_star
     const uint32_t sq = blockIdx.x * 128u + threadIdx.x;
     const bool valid = sq < (1u << (2 * levels));
     const uint32_t lo = valid ? leaf_start[sq] : 0u, hi = valid ? leaf_start[sq + 1] : 0u;
-    const bool large = hi - lo > (uint32_t)kLaneMax;
+    const bool walk = valid && hi - lo <= (uint32_t)kLaneMax;   // crowded squares: the whole warp
     const int p1 = p + 1;
     const uint32_t ix = fmm_compact2(sq), iy = fmm_compact2(sq >> 1);
-    const float ox1 = fine_offset(ix, 1), oy1 = fine_offset(iy, 1);
-    const float ox2 = fine_offset(ix, 2), oy2 = fine_offset(iy, 2);
-    const float s0 = lv.inv_s[levels], s1 = lv.inv_s[levels - 1], s2 = lv.inv_s[levels >= 2 ? levels - 2 : 0];
     float2 m0 = make_float2(0.f, 0.f);
-    if constexpr (P1B <= 25) {
-        float2 a0[P1B], a1[P1B], a2[P1B];
+    if (walk)
+        for (uint32_t j = lo; j < hi; ++j) m0 = ff_add_f(m0, sp[j].z);
+#pragma unroll 1
+    for (int sh = 0; sh < kFineLevels; ++sh) {
+        if (levels - sh < 2) break;
+        const float s = lv.inv_s[levels - sh];
+        const float ox = sh == 0 ? 0.f : fine_offset(ix, sh), oy = sh == 0 ? 0.f : fine_offset(iy, sh);
+        const float2 s2 = make_float2(s, s), ox2 = make_float2(ox, ox), oy2 = make_float2(oy, oy);
+        float2 ar[P1B], ai[P1B];
 #pragma unroll
-        for (int m = 0; m < P1B; ++m) a0[m] = a1[m] = a2[m] = make_float2(0.f, 0.f);
-        if (valid && !large && lo < hi) {
-            float4 nx = sp[lo];
-            for (uint32_t j = lo; j < hi; ++j) {
-                const float4 P = nx;
-                if (j + 1 < hi) nx = sp[j + 1];
-                m0 = ff_add_f(m0, P.z);
-                add_powers3<P1B>(a0, a1, a2, P.z, make_float2(P.x * s0, P.y * s0),
-                                 make_float2(fmaf(P.x, s1, ox1), fmaf(P.y, s1, oy1)),
-                                 make_float2(fmaf(P.x, s2, ox2), fmaf(P.y, s2, oy2)));
+        for (int m = 0; m < P1B; ++m) ar[m] = ai[m] = make_float2(0.f, 0.f);
+        if (walk && lo < hi) {
+            // pairs (j, j + 1); an odd count ends with a zero-charge partner
+            float4 na = sp[lo], nb = lo + 1 < hi ? sp[lo + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (uint32_t j = lo; j < hi; j += 2) {
+                const float4 a = na, b = nb;
+                if (j + 2 < hi) na = sp[j + 2];
+                nb = j + 3 < hi ? sp[j + 3] : make_float4(0.f, 0.f, 0.f, 0.f);
+                add_powers_pair<P1B>(ar, ai, make_float2(a.z, b.z), __ffma2_rn(make_float2(a.x, b.x), s2, ox2),
+                                     __ffma2_rn(make_float2(a.y, b.y), s2, oy2));
             }
         }
-        p2m_fine_finish<P1B, 1>(a0, m0, sp, sq, lo, hi, valid, levels, p1, s0, 0.f, 0.f, red[warp], lane, g);
-        if (levels - 1 >= 2)
-            p2m_fine_finish<P1B, 4>(a1, m0, sp, sq, lo, hi, valid, levels, p1, s1, ox1, oy1, red[warp], lane, g);
-        if (levels - 2 >= 2)
-            p2m_fine_finish<P1B, 16>(a2, m0, sp, sq, lo, hi, valid, levels, p1, s2, ox2, oy2, red[warp], lane, g);
-    } else {
-        if (valid && !large)
-            for (uint32_t j = lo; j < hi; ++j) m0 = ff_add_f(m0, sp[j].z);
-        float2 a[P1B];
+        float2 acc[P1B];
 #pragma unroll
-        for (int sh = 0; sh < 3; ++sh) {
-            if (levels - sh < 2) break;
-            const float sc = sh == 0 ? s0 : (sh == 1 ? s1 : s2);
-            const float ox = sh == 0 ? 0.f : (sh == 1 ? ox1 : ox2), oy = sh == 0 ? 0.f : (sh == 1 ? oy1 : oy2);
-#pragma unroll
-            for (int m = 0; m < P1B; ++m) a[m] = make_float2(0.f, 0.f);
-            if (valid && !large)
-                for (uint32_t j = lo; j < hi; ++j) {
-                    const float4 P = sp[j];
-                    add_powers<P1B>(a, P.z, make_float2(fmaf(P.x, sc, ox), fmaf(P.y, sc, oy)));
-                }
-            if (sh == 0)
-                p2m_fine_finish<P1B, 1>(a, m0, sp, sq, lo, hi, valid, levels, p1, sc, ox, oy, red[warp], lane, g);
-            else if (sh == 1)
-                p2m_fine_finish<P1B, 4>(a, m0, sp, sq, lo, hi, valid, levels, p1, sc, ox, oy, red[warp], lane, g);
-            else
-                p2m_fine_finish<P1B, 16>(a, m0, sp, sq, lo, hi, valid, levels, p1, sc, ox, oy, red[warp], lane, g);
-        }
+        for (int m = 0; m < P1B; ++m) acc[m] = make_float2(ar[m].x + ar[m].y, ai[m].x + ai[m].y);
+        if (sh == 0)
+            p2m_fine_finish<P1B, 1>(acc, m0, sp, sq, lo, hi, valid, levels, p1, s, ox, oy, red[warp], lane, g);
+        else if (sh == 1)
+            p2m_fine_finish<P1B, 4>(acc, m0, sp, sq, lo, hi, valid, levels, p1, s, ox, oy, red[warp], lane, g);
+        else
+            p2m_fine_finish<P1B, 16>(acc, m0, sp, sq, lo, hi, valid, levels, p1, s, ox, oy, red[warp], lane, g);
     }
 }
 
@@ -583,139 +571,10 @@ k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
 }
 
 // -------------------------------------------------------------------------------- P2P + final phi
-// Near field (E-2 of Sec. 2.1): every particle of a finest square against the particles of that
-// square and its (up to) eight neighbours, in FP32 on square-local coordinates.
-//
-// One warp per block of up to FMM_P2P_BLOCK targets of one finest square (a block -> square map
-// spares the warp a search); crowded squares spread over as many warps as they have blocks.
-// The lanes walk the sources 32 at a time (the own square's
-// first, then the neighbours'), each lane holding one source moved into the target square's
-// frame, and keep one FP32 partial sum per target in registers; the targets' coordinates are
-// shared-memory broadcasts, two targets per load.  The arithmetic of two targets runs in packed
-// FP32x2 instructions, so a pair costs one lg2 on the MUFU unit and two to three FP32 slots.
-// Coincidence (r^2 = 0: the target itself, duplicate points) only arises within the own square,
-// whose chunks test r^2 > 0; a neighbour's pair adds 2^-100 to r^2 instead, which keeps the
-// logarithm finite should two particles of adjacent squares round to the same FP32 point and
-// changes no other pair.  After each run of kP2PRun chunks the partials of each target are
-// combined across the warp by a shuffle reduce-scatter (lane t ends with target t's sum) and
-// added in float-float, so crowded squares keep their accuracy.
+// One warp per block of up to FMM_P2P_BLOCK targets of one finest square (the block -> square map
+// spares the warp a search); crowded squares spread over as many warps as they have blocks.  The
+// block's near field is p2p_near (p2p_block.cuh).
 constexpr int kP2PWarps = 4;
-constexpr int kP2PRun = 16;   // chunks of 32 sources summed in FP32 before the float-float add
-
-__device__ __forceinline__ float mufu_lg2(float x) {
-    float r;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// Sum of v[l & (W - 1)] over the warp's lanes, returned in lane l (v[t] = p[t / 2].x or .y for
-// t < 2 NP, 0 beyond).  The low log2(W) lane bits scatter (at the step with mask m a lane keeps
-// the half of its live entries whose bit m matches its own and sends the other half to its
-// partner), the remaining bits add by butterfly.
-template <int W, int NP>
-__device__ __forceinline__ float warp_reduce_scatter(const float2 (&p)[NP], int lane) {
-    float v[W];
-#pragma unroll
-    for (int i = 0; i < W; ++i) v[i] = i < 2 * NP ? ((i & 1) ? p[i >> 1].y : p[i >> 1].x) : 0.f;
-#pragma unroll
-    for (int m = W / 2; m >= 1; m >>= 1) {
-        const bool up = (lane & m) != 0;
-#pragma unroll
-        for (int i = 0; i < m; ++i) {
-            const float send = up ? v[i] : v[i + m];
-            const float keep = up ? v[i + m] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-        }
-    }
-    float s = v[0];
-#pragma unroll
-    for (int m = W; m < 32; m <<= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-    return s;
-}
-
-// one chunk: the lane's source (sx, sy, q) against the NP target pairs of the block (the
-// coordinates of targets past the block's end are zero and their sums are dropped)
-template <bool kOwn, int NP>
-__device__ __forceinline__ void p2p_chunk(float2 (&part)[NP], const float4* __restrict__ tg, float4 src) {
-    const float2 nsx = make_float2(-src.x, -src.x), nsy = make_float2(-src.y, -src.y);
-    const float2 q2 = make_float2(src.z, src.z);
-    const float2 tiny = make_float2(0x1p-100f, 0x1p-100f);
-#pragma unroll
-    for (int tp = 0; tp < NP; ++tp) {
-        const float4 t = tg[tp];   // {x of target 2tp, x of 2tp + 1, y of 2tp, y of 2tp + 1}
-        const float2 dx = __fadd2_rn(make_float2(t.x, t.y), nsx);
-        const float2 dy = __fadd2_rn(make_float2(t.z, t.w), nsy);
-        float2 r2, lg;
-        if (kOwn) {
-            r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-            lg = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
-            lg.x = r2.x > 0.f ? lg.x : 0.f;
-            lg.y = r2.y > 0.f ? lg.y : 0.f;
-        } else {
-            r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, tiny));
-            lg = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
-        }
-        part[tp] = __ffma2_rn(q2, lg, part[tp]);
-    }
-}
-
-// The block's sources: the own square's particles [t0, t0 + n_own) in nch_own chunks, then the
-// eight neighbours' in slot order (seg: sorted index minus slot and the frame shift per
-// neighbour, thr: first slot of neighbours 1..7).
-struct P2PSources {
-    const float4* sp;
-    const int4* seg;
-    uint32_t thr[7];
-    uint32_t t0, n_own, nch_own, n_nb;
-
-    // source of chunk c for this lane, in the target square's frame; slots past a part's end
-    // carry q = 0
-    __device__ __forceinline__ float4 load(uint32_t c, int lane) const {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c < nch_own) {
-            const uint32_t s = 32u * c + (uint32_t)lane;
-            if (s < n_own) v = sp[t0 + s];
-        } else {
-            const uint32_t s = 32u * (c - nch_own) + (uint32_t)lane;
-            if (s < n_nb) {
-                int b = 0;
-#pragma unroll
-                for (int i = 0; i < 7; ++i) b += s >= thr[i] ? 1 : 0;
-                const int4 g = seg[b];
-                v = sp[s + (uint32_t)g.x];
-                v.x += __int_as_float(g.y);
-                v.y += __int_as_float(g.z);
-            }
-        }
-        return v;
-    }
-};
-
-// the near-field sum (log2 r^2 units, float-float) of target `lane` of a block of at most 2 NP
-// targets
-template <int NP>
-__device__ __forceinline__ float2 p2p_block(const P2PSources& S, const float4* __restrict__ tg, int lane) {
-    constexpr int W = NP <= 2 ? 4 : (NP <= 4 ? 8 : (NP <= 8 ? 16 : 32));
-    const uint32_t nch = S.nch_own + (S.n_nb + 31u) / 32u;
-    float2 near = make_float2(0.f, 0.f);
-    for (uint32_t r0 = 0; r0 < nch; r0 += kP2PRun) {
-        const uint32_t r1 = min(nch, r0 + (uint32_t)kP2PRun);
-        float2 part[NP];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) part[i] = make_float2(0.f, 0.f);
-        float4 cur = S.load(r0, lane);
-        for (uint32_t c = r0; c < r1; ++c) {
-            const float4 nxt = (c + 1 < r1) ? S.load(c + 1, lane) : cur;
-            if (c < S.nch_own)
-                p2p_chunk<true, NP>(part, tg, cur);
-            else
-                p2p_chunk<false, NP>(part, tg, cur);
-            cur = nxt;
-        }
-        near = ff_add_f(near, warp_reduce_scatter<W, NP>(part, lane));
-    }
-    return near;
-}
 
 __global__ void __launch_bounds__(kP2PWarps * 32, 6)
 k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
@@ -723,7 +582,8 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
             float s_leaf, const float2* __restrict__ phi_far, double* __restrict__ phi,
             unsigned int* __restrict__ status, unsigned long long* __restrict__ counters) {
     __shared__ __align__(16) float4 tgt[kP2PWarps][16];   // zero past the block's targets
-    __shared__ __align__(16) int4 seg[kP2PWarps][8];   // neighbours in slot order: {index - slot, ox, oy, -}
+    __shared__ __align__(16) int4 seg[kP2PWarps][8];      // neighbours in slot order: {index - slot, ox, oy, -}
+    static_assert(FMM_P2P_BLOCK <= 24, "p2p_near takes blocks of up to 24 targets");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t w = (uint32_t)blockIdx.x * kP2PWarps + warp;
     if (w >= bstart[nleaf]) return;
@@ -740,73 +600,14 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
         idx = __float_as_int(sp[b0 + lane].w);
         far = phi_far[b0 + lane];
     }
-    const uint32_t n_own = t1 - t0;
-    const int side = 1 << levels;
-    const int ix = (int)fmm_compact2(leaf), iy = (int)fmm_compact2(leaf >> 1);
-    // lane b < 9, b != 4, looks up neighbour b = (dx + 1) + 3 (dy + 1); the eight neighbours'
-    // sources take consecutive slots of the neighbour chunks
-    uint32_t first = 0, cnt = 0;
-    if (lane < 9 && lane != 4) {
-        const int jx = ix + lane % 3 - 1, jy = iy + lane / 3 - 1;
-        if (jx >= 0 && jy >= 0 && jx < side && jy < side) {
-            const uint32_t nl = fmm_morton((uint32_t)jx, (uint32_t)jy);
-            first = leaf_start[nl];
-            cnt = leaf_start[nl + 1] - first;
-        }
-    }
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const uint32_t excl = incl - cnt;
-    const uint32_t n_nb = __shfl_sync(0xffffffffu, incl, 8);
-    if (lane < 9 && lane != 4)
-        seg[warp][lane - (lane > 4)] = make_int4((int)(first - excl), __float_as_int((float)(lane % 3 - 1) * s_leaf),
-                                                 __float_as_int((float)(lane / 3 - 1) * s_leaf), 0);
-    P2PSources S;
-    S.sp = sp;
-    S.seg = seg[warp];
-#pragma unroll
-    for (int i = 1; i < 8; ++i) S.thr[i - 1] = __shfl_sync(0xffffffffu, excl, i + (i >= 4));
-    S.t0 = t0;
-    S.n_own = n_own;
-    S.nch_own = (n_own + 31u) / 32u;
-    S.n_nb = n_nb;
+    uint32_t nsrc;
+    const float2 near = p2p_near(sp, leaf_start, leaf, t0, t1, b0, T, levels, s_leaf, tgt[warp], seg[warp], lane, &nsrc);
     if (lane == 0) {
         const unsigned slot = leaf % FMM_COUNTER_SLOTS;
-        atomicAdd(&counters[slot], (unsigned long long)T * (n_own + n_nb) - (unsigned long long)T);
-        atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)n_own);
+        atomicAdd(&counters[slot], (unsigned long long)T * nsrc - (unsigned long long)T);
+        atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)(t1 - t0));
     }
-    {
-        float x = 0.f, y = 0.f;
-        if (lane < T) {
-            const float4 P = sp[b0 + lane];
-            x = P.x;
-            y = P.y;
-        }
-        float* t = reinterpret_cast<float*>(&tgt[warp][lane >> 1]);
-        t[lane & 1] = x;
-        t[2 + (lane & 1)] = y;
-    }
-    __syncwarp();
-    // the block's target pairs, rounded up to an even count, fix the unrolled width
-    float2 near;
-    static_assert(FMM_P2P_BLOCK <= 24, "the unrolled widths below cover blocks of up to 24 targets");
-    switch ((T + 3) >> 2) {
-        case 1: near = p2p_block<2>(S, tgt[warp], lane); break;
-        case 2: near = p2p_block<4>(S, tgt[warp], lane); break;
-        case 3: near = p2p_block<6>(S, tgt[warp], lane); break;
-        case 4: near = p2p_block<8>(S, tgt[warp], lane); break;
-        case 5: near = p2p_block<10>(S, tgt[warp], lane); break;
-        default: near = p2p_block<12>(S, tgt[warp], lane); break;
-    }
-    if (lane < T) {
-        // near field x ln2 / 2 (as a float-float pair) turns sum q log2 r^2 into sum q ln r
-        const float2 v = ff_add(far, ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
-        phi[idx] = fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);
-    }
+    if (lane < T) phi[idx] = p2p_phi(far, near);
 }
 
 template <int P1B>

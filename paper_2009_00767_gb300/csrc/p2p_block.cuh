@@ -1,0 +1,211 @@
+// p2p_block.cuh -- the near field (E-2 of Sec. 2.1) of one block of targets, shared by the
+// single-system kernel (mixed.cu) and the batched one (batch.cu).
+#pragma once
+
+#include "mixed_common.cuh"
+
+namespace {
+
+// Near field (E-2 of Sec. 2.1): every particle of a finest square against the particles of that
+// square and its (up to) eight neighbours, in FP32 on square-local coordinates.
+//
+// One warp takes a block of up to 24 targets of one finest square.  The lanes walk the sources 32
+// at a time (the own square's first, then the neighbours'), each lane holding one source moved into the target square's
+// frame, and keep one FP32 partial sum per target in registers; the targets' coordinates are
+// shared-memory broadcasts, two targets per load.  The arithmetic of two targets runs in packed
+// FP32x2 instructions, so a pair costs one lg2 on the MUFU unit and two to three FP32 slots.
+// Coincidence (r^2 = 0: the target itself, duplicate points) only arises within the own square,
+// whose chunks test r^2 > 0; a neighbour's pair adds 2^-100 to r^2 instead, which keeps the
+// logarithm finite should two particles of adjacent squares round to the same FP32 point and
+// changes no other pair.  After each run of kP2PRun chunks the partials of each target are
+// combined across the warp by a shuffle reduce-scatter (lane t ends with target t's sum) and
+// added in float-float, so crowded squares keep their accuracy.
+constexpr int kP2PRun = 16;   // chunks of 32 sources summed in FP32 before the float-float add
+
+__device__ __forceinline__ float mufu_lg2(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Sum of v[l & (W - 1)] over the warp's lanes, returned in lane l (v[t] = p[t / 2].x or .y for
+// t < 2 NP, 0 beyond).  The low log2(W) lane bits scatter (at the step with mask m a lane keeps
+// the half of its live entries whose bit m matches its own and sends the other half to its
+// partner), the remaining bits add by butterfly.
+template <int W, int NP>
+__device__ __forceinline__ float warp_reduce_scatter(const float2 (&p)[NP], int lane) {
+    float v[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) v[i] = i < 2 * NP ? ((i & 1) ? p[i >> 1].y : p[i >> 1].x) : 0.f;
+#pragma unroll
+    for (int m = W / 2; m >= 1; m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < m; ++i) {
+            const float send = up ? v[i] : v[i + m];
+            const float keep = up ? v[i + m] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    float s = v[0];
+#pragma unroll
+    for (int m = W; m < 32; m <<= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    return s;
+}
+
+// one chunk: the lane's source (sx, sy, q) against the NP target pairs of the block (the
+// coordinates of targets past the block's end are zero and their sums are dropped)
+template <bool kOwn, int NP>
+__device__ __forceinline__ void p2p_chunk(float2 (&part)[NP], const float4* __restrict__ tg, float4 src) {
+    const float2 nsx = make_float2(-src.x, -src.x), nsy = make_float2(-src.y, -src.y);
+    const float2 q2 = make_float2(src.z, src.z);
+    const float2 tiny = make_float2(0x1p-100f, 0x1p-100f);
+#pragma unroll
+    for (int tp = 0; tp < NP; ++tp) {
+        const float4 t = tg[tp];   // {x of target 2tp, x of 2tp + 1, y of 2tp, y of 2tp + 1}
+        const float2 dx = __fadd2_rn(make_float2(t.x, t.y), nsx);
+        const float2 dy = __fadd2_rn(make_float2(t.z, t.w), nsy);
+        float2 r2, lg;
+        if (kOwn) {
+            r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+            lg = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
+            lg.x = r2.x > 0.f ? lg.x : 0.f;
+            lg.y = r2.y > 0.f ? lg.y : 0.f;
+        } else {
+            r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, tiny));
+            lg = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
+        }
+        part[tp] = __ffma2_rn(q2, lg, part[tp]);
+    }
+}
+
+// The block's sources: the own square's particles [t0, t0 + n_own) in nch_own chunks, then the
+// eight neighbours' in slot order (seg: sorted index minus slot and the frame shift per
+// neighbour, thr: first slot of neighbours 1..7).
+struct P2PSources {
+    const float4* sp;
+    const int4* seg;
+    uint32_t thr[7];
+    uint32_t t0, n_own, nch_own, n_nb;
+
+    // source of chunk c for this lane, in the target square's frame; slots past a part's end
+    // carry q = 0
+    __device__ __forceinline__ float4 load(uint32_t c, int lane) const {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < nch_own) {
+            const uint32_t s = 32u * c + (uint32_t)lane;
+            if (s < n_own) v = sp[t0 + s];
+        } else {
+            const uint32_t s = 32u * (c - nch_own) + (uint32_t)lane;
+            if (s < n_nb) {
+                int b = 0;
+#pragma unroll
+                for (int i = 0; i < 7; ++i) b += s >= thr[i] ? 1 : 0;
+                const int4 g = seg[b];
+                v = sp[s + (uint32_t)g.x];
+                v.x += __int_as_float(g.y);
+                v.y += __int_as_float(g.z);
+            }
+        }
+        return v;
+    }
+};
+
+// the near-field sum (log2 r^2 units, float-float) of target `lane` of a block of at most 2 NP
+// targets
+template <int NP>
+__device__ __forceinline__ float2 p2p_block(const P2PSources& S, const float4* __restrict__ tg, int lane) {
+    constexpr int W = NP <= 2 ? 4 : (NP <= 4 ? 8 : (NP <= 8 ? 16 : 32));
+    const uint32_t nch = S.nch_own + (S.n_nb + 31u) / 32u;
+    float2 near = make_float2(0.f, 0.f);
+    for (uint32_t r0 = 0; r0 < nch; r0 += kP2PRun) {
+        const uint32_t r1 = min(nch, r0 + (uint32_t)kP2PRun);
+        float2 part[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) part[i] = make_float2(0.f, 0.f);
+        float4 cur = S.load(r0, lane);
+        for (uint32_t c = r0; c < r1; ++c) {
+            const float4 nxt = (c + 1 < r1) ? S.load(c + 1, lane) : cur;
+            if (c < S.nch_own)
+                p2p_chunk<true, NP>(part, tg, cur);
+            else
+                p2p_chunk<false, NP>(part, tg, cur);
+            cur = nxt;
+        }
+        near = ff_add_f(near, warp_reduce_scatter<W, NP>(part, lane));
+    }
+    return near;
+}
+
+// The near field of the targets [b0, b0 + T) (T <= 24) of finest square `leaf` (particles
+// [t0, t1)) of a quadtree of depth `levels` whose CSR over the sorted array is `ls`; s_leaf is the
+// square's side.  Returns target `lane`'s sum in log2 r^2 units as a float-float pair and the
+// block's source count in *nsrc.  tgt (16 float4) and seg (8 int4) are the warp's shared memory.
+__device__ __forceinline__ float2 p2p_near(const float4* __restrict__ sp, const uint32_t* __restrict__ ls,
+                                           uint32_t leaf, uint32_t t0, uint32_t t1, uint32_t b0, int T, int levels,
+                                           float s_leaf, float4* tgt, int4* seg, int lane, uint32_t* nsrc) {
+    const uint32_t n_own = t1 - t0;
+    const int side = 1 << levels;
+    const int ix = (int)fmm_compact2(leaf), iy = (int)fmm_compact2(leaf >> 1);
+    // lane b < 9, b != 4, looks up neighbour b = (dx + 1) + 3 (dy + 1); the eight neighbours'
+    // sources take consecutive slots of the neighbour chunks
+    uint32_t first = 0, cnt = 0;
+    if (lane < 9 && lane != 4) {
+        const int jx = ix + lane % 3 - 1, jy = iy + lane / 3 - 1;
+        if (jx >= 0 && jy >= 0 && jx < side && jy < side) {
+            const uint32_t nl = fmm_morton((uint32_t)jx, (uint32_t)jy);
+            first = ls[nl];
+            cnt = ls[nl + 1] - first;
+        }
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t n_nb = __shfl_sync(0xffffffffu, incl, 8);
+    if (lane < 9 && lane != 4)
+        seg[lane - (lane > 4)] = make_int4((int)(first - excl), __float_as_int((float)(lane % 3 - 1) * s_leaf),
+                                           __float_as_int((float)(lane / 3 - 1) * s_leaf), 0);
+    P2PSources S;
+    S.sp = sp;
+    S.seg = seg;
+#pragma unroll
+    for (int i = 1; i < 8; ++i) S.thr[i - 1] = __shfl_sync(0xffffffffu, excl, i + (i >= 4));
+    S.t0 = t0;
+    S.n_own = n_own;
+    S.nch_own = (n_own + 31u) / 32u;
+    S.n_nb = n_nb;
+    *nsrc = n_own + n_nb;
+    {
+        float x = 0.f, y = 0.f;
+        if (lane < T) {
+            const float4 P = sp[b0 + lane];
+            x = P.x;
+            y = P.y;
+        }
+        float* t = reinterpret_cast<float*>(&tgt[lane >> 1]);
+        t[lane & 1] = x;
+        t[2 + (lane & 1)] = y;
+    }
+    __syncwarp();
+    // the block's target pairs, rounded up to an even count, fix the unrolled width
+    switch ((T + 3) >> 2) {
+        case 1: return p2p_block<2>(S, tgt, lane);
+        case 2: return p2p_block<4>(S, tgt, lane);
+        case 3: return p2p_block<6>(S, tgt, lane);
+        case 4: return p2p_block<8>(S, tgt, lane);
+        case 5: return p2p_block<10>(S, tgt, lane);
+        default: return p2p_block<12>(S, tgt, lane);
+    }
+}
+
+// phi = far + near x ln2 / 2 (the float-float factor turns sum q log2 r^2 into sum q ln r)
+__device__ __forceinline__ double p2p_phi(float2 far, float2 near) {
+    const float2 v = ff_add(far, ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));
+    return fmm_f2d_bits(v.x) + fmm_f2d_bits(v.y);
+}
+
+}  // namespace
