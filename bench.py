@@ -109,7 +109,7 @@ def m2l_pairs(levels, kmin=2):
     return total
 
 
-TC_KMIN = 7   # the tensor-core M2L takes levels 7 and finer
+TC_KMIN = 6   # the tensor-core M2L takes levels 6 and finer
 
 
 def roofline_for(stage, stats, ms, w, peaks, sm_clock_mhz, precision, traffic):

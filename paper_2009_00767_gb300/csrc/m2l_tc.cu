@@ -44,7 +44,7 @@ namespace {
 constexpr int kTile = 128;        // targets per tile (MMA M)
 constexpr int kWin = kTile + 2;   // source cells per window
 constexpr int kThreads = 128;
-constexpr int kMinLevel = 7;      // coarser levels stay on the CUDA cores (see fmm_tc_kmin)
+constexpr int kMinLevel = 6;      // coarser levels stay on the CUDA cores (see fmm_tc_kmin)
 constexpr int kMaxRows = 8;       // tiles per CTA: 8 accumulators of 64 columns fill tensor memory
 constexpr int kSrcPad = 1024;     // cells after each source array: flat tiles past the last row read there
 constexpr unsigned kSpin = 1u << 24;
@@ -292,21 +292,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                 if (t == 0 && !wait_bar(su32(&ops_full[so]), (uint32_t)(uso & 1))) ok = false;
                 if (!wait_bar(su32(&win_full[sw]), (uint32_t)(usw & 1))) ok = false;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t aBase = su32(win_buf + sw * WIN_STAGE);
-                const uint32_t bBase = su32(ops_buf + so * OPS_STAGE);
+                // descriptors: the window's and the group's base descriptors once, then constant
+                // offsets in 16-byte units on the start-address field (shared addresses stay below
+                // 2^18 bytes, so the 14-bit field never carries), keeping the one issuing thread's
+                // work per MMA to a few instructions
+                const uint64_t aDesc = smem_desc(su32(win_buf + sw * WIN_STAGE), kWin * 16, 128);
+                const uint64_t bDesc = smem_desc(su32(ops_buf + so * OPS_STAGE), N * 16, 128);
                 const uint32_t acc_t = tmem + (uint32_t)t * ACC_COLS;
-                for (int o = 0; o < G.nops && ok; ++o) {
-                    const uint32_t aoff = (uint32_t)(1 + G.sx[o]) * 16u;
+                const int nops = G.nops;
+                for (int o = 0; o < nops && ok; ++o) {
+                    const uint64_t ad0 = aDesc + (uint64_t)(1 + G.sx[o]);   // column shift: one 16-byte cell
+                    const uint64_t bd0 = bDesc + (uint64_t)(o * (OP_BYTES / 16));
+                    const uint32_t acc0 = (g | o) != 0;
 #pragma unroll
                     for (int ks = 0; ks < KC / 2; ++ks) {
 #pragma unroll
                         for (int pr = 0; pr < NPROD; ++pr) {
-                            const uint32_t acc = (g | o | ks | pr) != 0;
-                            const uint64_t ad = smem_desc(aBase + kProdA[pr] * A_BYTES + aoff + ks * 2 * (kWin * 16),
-                                                          kWin * 16, 128);
-                            const uint64_t bd = smem_desc(
-                                bBase + (kProdB[pr] * 3 + o) * OP_BYTES + ks * 2 * (N * 16), N * 16, 128);
-                            mma_issue<BF>(acc_t, ad, bd, IDESC, acc);
+                            const uint64_t ad = ad0 + (uint64_t)((kProdA[pr] * A_BYTES + ks * 2 * (kWin * 16)) / 16);
+                            const uint64_t bd =
+                                bd0 + (uint64_t)((kProdB[pr] * 3 * OP_BYTES + ks * 2 * (N * 16)) / 16);
+                            mma_issue<BF>(acc_t, ad, bd, IDESC, (ks | pr) != 0 ? 1u : acc0);
                         }
                     }
                 }

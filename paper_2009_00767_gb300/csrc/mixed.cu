@@ -350,7 +350,7 @@ struct M2LMixedArgs {
 // the current one is applied, so the loads' latency hides behind the FMAs.  Same arithmetic as
 // the thread-per-target kernel: FP32 FMAs, the monopole-log term in float-float.
 constexpr int kM2LWarpTargets = 2;
-constexpr int kM2LWarpMaxLevel = 6;   // 4^6 targets: the finest level this kernel takes
+constexpr int kM2LWarpMaxLevel = 5;   // 4^5 targets: the finest level this kernel takes
 
 struct M2LWarpArgs {
     FmmLevelPtrs g;
@@ -573,7 +573,8 @@ k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
 // -------------------------------------------------------------------------------- P2P + final phi
 // One warp per block of up to FMM_P2P_BLOCK targets of one finest square (the block -> square map
 // spares the warp a search); crowded squares spread over as many warps as they have blocks.  The
-// block's near field is p2p_near (p2p_block.cuh).
+// block's near field is p2p_near (p2p_block.cuh).  (A persistent variant that ran each block's
+// lookups one block ahead measured no faster: the time goes to the blocks' own work.)
 constexpr int kP2PWarps = 4;
 
 __global__ void __launch_bounds__(kP2PWarps * 32, 6)
@@ -586,9 +587,11 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
     static_assert(FMM_P2P_BLOCK <= 24, "p2p_near takes blocks of up to 24 targets");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t w = (uint32_t)blockIdx.x * kP2PWarps + warp;
+    // the map has an entry for every warp of the grid (its size is the grid's bound), so it is
+    // read together with the bound and the status word
+    const uint2 lt = bmap[w];   // (square, block inside it)
     if (w >= bstart[nleaf]) return;
     if (*(volatile const unsigned int*)status != 0u) return;   // inputs failed the device checks
-    const uint2 lt = bmap[w];   // (square, block inside it)
     const uint32_t leaf = lt.x;
     const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
     const uint32_t b0 = t0 + (uint32_t)FMM_P2P_BLOCK * lt.y;

@@ -123,6 +123,8 @@ __device__ __forceinline__ float2 p2p_block(const P2PSources& S, const float4* _
         float2 part[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) part[i] = make_float2(0.f, 0.f);
+        // the next chunk's loads are in flight while one is summed (a deeper ring, unrolled, made
+        // the kernel's code outgrow the instruction cache)
         float4 cur = S.load(r0, lane);
         for (uint32_t c = r0; c < r1; ++c) {
             const float4 nxt = (c + 1 < r1) ? S.load(c + 1, lane) : cur;
@@ -137,27 +139,32 @@ __device__ __forceinline__ float2 p2p_block(const P2PSources& S, const float4* _
     return near;
 }
 
-// The near field of the targets [b0, b0 + T) (T <= 24) of finest square `leaf` (particles
-// [t0, t1)) of a quadtree of depth `levels` whose CSR over the sorted array is `ls`; s_leaf is the
-// square's side.  Returns target `lane`'s sum in log2 r^2 units as a float-float pair and the
-// block's source count in *nsrc.  tgt (16 float4) and seg (8 int4) are the warp's shared memory.
-__device__ __forceinline__ float2 p2p_near(const float4* __restrict__ sp, const uint32_t* __restrict__ ls,
-                                           uint32_t leaf, uint32_t t0, uint32_t t1, uint32_t b0, int T, int levels,
-                                           float s_leaf, float4* tgt, int4* seg, int lane, uint32_t* nsrc) {
-    const uint32_t n_own = t1 - t0;
-    const int side = 1 << levels;
-    const int ix = (int)fmm_compact2(leaf), iy = (int)fmm_compact2(leaf >> 1);
-    // lane b < 9, b != 4, looks up neighbour b = (dx + 1) + 3 (dy + 1); the eight neighbours'
-    // sources take consecutive slots of the neighbour chunks
+// Neighbour b = (dx + 1) + 3 (dy + 1) of finest square `leaf` (lane b < 9, b != 4; other lanes
+// and squares outside the domain give an empty range): its first sorted particle and count.
+__device__ __forceinline__ uint2 p2p_neighbour(const uint32_t* __restrict__ ls, uint32_t leaf, int levels, int lane) {
     uint32_t first = 0, cnt = 0;
     if (lane < 9 && lane != 4) {
-        const int jx = ix + lane % 3 - 1, jy = iy + lane / 3 - 1;
+        const int side = 1 << levels;
+        const int jx = (int)fmm_compact2(leaf) + lane % 3 - 1, jy = (int)fmm_compact2(leaf >> 1) + lane / 3 - 1;
         if (jx >= 0 && jy >= 0 && jx < side && jy < side) {
             const uint32_t nl = fmm_morton((uint32_t)jx, (uint32_t)jy);
             first = ls[nl];
             cnt = ls[nl + 1] - first;
         }
     }
+    return make_uint2(first, cnt);
+}
+
+// The near field of the targets [b0, b0 + T) (T <= 24) of a finest square with particles
+// [t0, t1), whose neighbours' ranges nb came from p2p_neighbour; s_leaf is the square's side.
+// Returns target `lane`'s sum in log2 r^2 units as a float-float pair and the block's source
+// count in *nsrc.  tgt (16 float4) and seg (8 int4) are the warp's shared memory.
+__device__ __forceinline__ float2 p2p_near_nb(const float4* __restrict__ sp, uint32_t t0, uint32_t t1, uint32_t b0,
+                                              int T, uint2 nb, float s_leaf, float4* tgt, int4* seg, int lane,
+                                              uint32_t* nsrc) {
+    const uint32_t n_own = t1 - t0;
+    // the eight neighbours' sources take consecutive slots of the neighbour chunks
+    const uint32_t first = nb.x, cnt = nb.y;
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 16; o <<= 1) {
@@ -200,6 +207,14 @@ __device__ __forceinline__ float2 p2p_near(const float4* __restrict__ sp, const 
         case 5: return p2p_block<10>(S, tgt, lane);
         default: return p2p_block<12>(S, tgt, lane);
     }
+}
+
+// p2p_near_nb with the neighbours looked up first (square `leaf` of a quadtree of depth `levels`
+// whose CSR over the sorted array is ls)
+__device__ __forceinline__ float2 p2p_near(const float4* __restrict__ sp, const uint32_t* __restrict__ ls,
+                                           uint32_t leaf, uint32_t t0, uint32_t t1, uint32_t b0, int T, int levels,
+                                           float s_leaf, float4* tgt, int4* seg, int lane, uint32_t* nsrc) {
+    return p2p_near_nb(sp, t0, t1, b0, T, p2p_neighbour(ls, leaf, levels, lane), s_leaf, tgt, seg, lane, nsrc);
 }
 
 // phi = far + near x ln2 / 2 (the float-float factor turns sum q log2 r^2 into sum q ln r)
