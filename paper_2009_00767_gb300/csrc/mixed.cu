@@ -29,13 +29,13 @@ constexpr int kM2LThreads = 128;
 // Every level straight from the particles (U-bar of Sec. 2.2.1).  Squares of a level are
 // contiguous Morton ranges of the sorted particles, so the sums need no global sort of their own.
 //
-// Fine levels (the finest three, l - 2 .. l): one lane per finest square, 32 consecutive squares
-// per warp in Morton order, so that each group of 4^(l - k) consecutive lanes is one level-k
-// square.  For each level the lane sums its own particles' terms in registers (its square fixes
-// the particles' offsets inside every coarser square, so no key is read), then the group's
-// partial sums are combined by a shuffle reduce-scatter that leaves each lane of the group with
-// a share of the coefficients to store: no atomics, coalesced stores.  Squares above kLaneMax
-// particles are summed by the whole warp and added by the owning group before the store.
+// Fine levels (the finest three, l - 2 .. l): two lanes per finest square, 16 consecutive squares
+// per warp in Morton order, so that each group of 2 * 4^(l - k) consecutive lanes is one level-k
+// square.  For each level a lane sums its half of the square's particles in registers (the
+// square fixes the particles' offsets inside every coarser square, so no key is read), then the
+// group's partial sums are combined by a shuffle reduce-scatter that leaves each lane of the
+// group with a share of the coefficients to store: no atomics, coalesced stores.  Squares above
+// kLaneMax particles are summed by the whole warp and added by the owning group before the store.
 //
 // Coarse levels (2 .. l - 3): each warp walks kCoarseChunk consecutive particles; lanes add their
 // particles' terms in registers while the square stays the same and flush (a column sum over the
@@ -81,15 +81,14 @@ __device__ __forceinline__ void group_reduce_scatter(float (&v)[VP], int lane) {
 // Level k = l - log4(G) of the lane's finest square sq (particles [lo, hi), offset (ox, oy) of
 // its centre in units of the level-k square): the group's sums of the lane partials acc and m0,
 // the crowded squares of the warp added, stored by the group's lanes.
-template <int P1B, int G>
+template <int P1B, int G, int SH>
 __device__ __forceinline__ void p2m_fine_finish(const float2 (&acc)[P1B], float2 m0, const float4* __restrict__ sp,
-                                                uint32_t sq, uint32_t lo, uint32_t hi, bool valid, int levels, int p1,
-                                                float inv_s, float ox, float oy, float* red, int lane,
-                                                FmmLevelPtrs g) {
+                                                uint32_t sq, uint32_t lo, uint32_t hi, bool valid, bool owner,
+                                                int levels, int p1, float inv_s, float ox, float oy, float* red,
+                                                int lane, FmmLevelPtrs g) {
     constexpr int V = 2 * (P1B - 1);              // Re, Im of coefficients 1 .. P1B - 1
     constexpr int VP = (V + G - 1) / G * G;
     constexpr int B = VP / G;
-    constexpr int SH = G == 1 ? 0 : (G == 4 ? 1 : 2);
     const int k = levels - SH;
     const bool large = hi - lo > (uint32_t)kLaneMax;
     float v[VP];
@@ -100,7 +99,7 @@ __device__ __forceinline__ void p2m_fine_finish(const float2 (&acc)[P1B], float2
     for (int m = 1; m < G; m <<= 1)
         m0 = ff_add(m0, make_float2(__shfl_xor_sync(0xffffffffu, m0.x, m), __shfl_xor_sync(0xffffffffu, m0.y, m)));
     // crowded squares: the whole warp sums the particles, the owning group adds its share
-    unsigned todo = __ballot_sync(0xffffffffu, valid && large);
+    unsigned todo = __ballot_sync(0xffffffffu, valid && large && owner);
     while (todo) {
         const int src = __ffs(todo) - 1;
         todo &= todo - 1;
@@ -182,24 +181,29 @@ __device__ __forceinline__ void add_powers_pair(float2 (&ar)[P1B], float2 (&ai)[
     }
 }
 
-// levels max(2, l - 2) .. l, one lane per finest square.  Per level the lane walks its particles
-// two at a time, the pair's power chains in packed FP32x2 arithmetic (the particles stay in L1
-// between the levels' passes); the total charge is summed once, in float-float.
+// levels max(2, l - 2) .. l, two lanes per finest square, each taking half of its particles.  Per
+// level a lane walks its half two particles at a time, the pair's power chains in packed FP32x2
+// arithmetic (the particles stay in L1 between the levels' passes); the total charge is summed
+// once, in float-float.  The two halves join in the group reductions (2, 8 and 32 lanes).
 template <int P1B>
 __global__ void __launch_bounds__(128, P1B <= 25 ? 4 : 1)
 k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, int levels, int p, MixedLevels lv,
            FmmLevelPtrs g) {
     __shared__ float red[4][2 * P1B];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t sq = blockIdx.x * 128u + threadIdx.x;
+    const uint32_t t = blockIdx.x * 128u + threadIdx.x;
+    const uint32_t sq = t >> 1;
+    const bool owner = (t & 1u) == 0u;
     const bool valid = sq < (1u << (2 * levels));
     const uint32_t lo = valid ? leaf_start[sq] : 0u, hi = valid ? leaf_start[sq + 1] : 0u;
     const bool walk = valid && hi - lo <= (uint32_t)kLaneMax;   // crowded squares: the whole warp
+    const uint32_t mid = lo + ((hi - lo + 1u) >> 1);
+    const uint32_t a0 = owner ? lo : mid, a1 = owner ? mid : hi;   // this lane's half
     const int p1 = p + 1;
     const uint32_t ix = fmm_compact2(sq), iy = fmm_compact2(sq >> 1);
     float2 m0 = make_float2(0.f, 0.f);
     if (walk)
-        for (uint32_t j = lo; j < hi; ++j) m0 = ff_add_f(m0, sp[j].z);
+        for (uint32_t j = a0; j < a1; ++j) m0 = ff_add_f(m0, sp[j].z);
 #pragma unroll 1
     for (int sh = 0; sh < kFineLevels; ++sh) {
         if (levels - sh < 2) break;
@@ -209,13 +213,13 @@ k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_star
         float2 ar[P1B], ai[P1B];
 #pragma unroll
         for (int m = 0; m < P1B; ++m) ar[m] = ai[m] = make_float2(0.f, 0.f);
-        if (walk && lo < hi) {
+        if (walk && a0 < a1) {
             // pairs (j, j + 1); an odd count ends with a zero-charge partner
-            float4 na = sp[lo], nb = lo + 1 < hi ? sp[lo + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-            for (uint32_t j = lo; j < hi; j += 2) {
+            float4 na = sp[a0], nb = a0 + 1 < a1 ? sp[a0 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (uint32_t j = a0; j < a1; j += 2) {
                 const float4 a = na, b = nb;
-                if (j + 2 < hi) na = sp[j + 2];
-                nb = j + 3 < hi ? sp[j + 3] : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j + 2 < a1) na = sp[j + 2];
+                nb = j + 3 < a1 ? sp[j + 3] : make_float4(0.f, 0.f, 0.f, 0.f);
                 add_powers_pair<P1B>(ar, ai, make_float2(a.z, b.z), __ffma2_rn(make_float2(a.x, b.x), s2, ox2),
                                      __ffma2_rn(make_float2(a.y, b.y), s2, oy2));
             }
@@ -224,11 +228,14 @@ k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_star
 #pragma unroll
         for (int m = 0; m < P1B; ++m) acc[m] = make_float2(ar[m].x + ar[m].y, ai[m].x + ai[m].y);
         if (sh == 0)
-            p2m_fine_finish<P1B, 1>(acc, m0, sp, sq, lo, hi, valid, levels, p1, s, ox, oy, red[warp], lane, g);
+            p2m_fine_finish<P1B, 2, 0>(acc, m0, sp, sq, lo, hi, valid, owner, levels, p1, s, ox, oy, red[warp], lane,
+                                       g);
         else if (sh == 1)
-            p2m_fine_finish<P1B, 4>(acc, m0, sp, sq, lo, hi, valid, levels, p1, s, ox, oy, red[warp], lane, g);
+            p2m_fine_finish<P1B, 8, 1>(acc, m0, sp, sq, lo, hi, valid, owner, levels, p1, s, ox, oy, red[warp], lane,
+                                       g);
         else
-            p2m_fine_finish<P1B, 16>(acc, m0, sp, sq, lo, hi, valid, levels, p1, s, ox, oy, red[warp], lane, g);
+            p2m_fine_finish<P1B, 32, 2>(acc, m0, sp, sq, lo, hi, valid, owner, levels, p1, s, ox, oy, red[warp],
+                                        lane, g);
     }
 }
 
@@ -267,46 +274,71 @@ k_p2m_coarse(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, i
             }
             __syncwarp();
         };
-        for (int r = 0; r < kCoarseChunk / 32; ++r) {
-            const int64_t j = base + 32 * r + lane;
-            const bool valid = j < n;
-            float2 c[P1B];
-            uint32_t bx = 0xffffffffu;
-            if (valid) {
-                const float4 P = sp[j];
-                const uint32_t key = skey[j];
-                bx = key >> (2 * sh);
-                const float2 w = level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh, lv.inv_s[k]);
-                c[0] = make_float2(P.z, 0.f);
-                float pr = P.z, pi = 0.f;
+        // rounds of 64 particles, lane + 32 s (s = 0, 1) of each: when every particle of the
+        // round lies in the current square the pair's power chains run in packed FP32x2; a round
+        // that crosses a square boundary takes its two 32-particle halves in order, adding while
+        // the square is unchanged and flushing when it changes
+        for (int r = 0; r < kCoarseChunk / 64; ++r) {
+            const int64_t j0 = base + 64 * r + lane, j1 = j0 + 32;
+            const bool v0 = j0 < n, v1 = j1 < n;
+            const float4 P0 = v0 ? sp[j0] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 P1 = v1 ? sp[j1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const uint32_t key0 = v0 ? skey[j0] : 0u, key1 = v1 ? skey[j1] : 0u;
+            const uint32_t bx0 = v0 ? key0 >> (2 * sh) : 0xffffffffu, bx1 = v1 ? key1 >> (2 * sh) : 0xffffffffu;
+            if (__all_sync(0xffffffffu, (!v0 || bx0 == cur) && (!v1 || bx1 == cur))) {
+                const float2 w0 = level_w(P0.x, P0.y, fmm_compact2(key0), fmm_compact2(key0 >> 1), sh, lv.inv_s[k]);
+                const float2 w1 = level_w(P1.x, P1.y, fmm_compact2(key1), fmm_compact2(key1 >> 1), sh, lv.inv_s[k]);
+                const float2 wx = make_float2(w0.x, w1.x), wy = make_float2(w0.y, w1.y);
+                const float2 nwy = make_float2(-w0.y, -w1.y);
+                float2 pr = make_float2(P0.z, P1.z), pi = make_float2(0.f, 0.f);   // q = 0 past the end
+                acc[0].x += pr.x + pr.y;
 #pragma unroll
                 for (int m = 1; m < P1B; ++m) {
-                    const float nr = fmaf(pr, w.x, -pi * w.y);
-                    const float ni = fmaf(pr, w.y, pi * w.x);
+                    const float2 nr = __ffma2_rn(pr, wx, __fmul2_rn(pi, nwy));
+                    const float2 ni = __ffma2_rn(pr, wy, __fmul2_rn(pi, wx));
                     pr = nr;
                     pi = ni;
-                    c[m] = make_float2(pr, pi);
+                    acc[m].x += pr.x + pr.y;
+                    acc[m].y += pi.x + pi.y;
                 }
             } else {
+#pragma unroll 1
+                for (int half = 0; half < 2; ++half) {
+                    const bool valid = half ? v1 : v0;
+                    const float4 P = half ? P1 : P0;
+                    const uint32_t key = half ? key1 : key0, bx = half ? bx1 : bx0;
+                    float2 c[P1B];
+                    {
+                        const float2 w = level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh, lv.inv_s[k]);
+                        c[0] = make_float2(P.z, 0.f);
+                        float pr = P.z, pi = 0.f;   // q = 0 past the end
 #pragma unroll
-                for (int m = 0; m < P1B; ++m) c[m] = make_float2(0.f, 0.f);
-            }
-            // keys are sorted, so lanes with a square above cur are the ones not yet added; each
-            // pass adds at least one lane, so at most 32 passes close the chunk
-            for (int pass = 0; pass < 33; ++pass) {
-                if (valid && bx == cur) {
+                        for (int m = 1; m < P1B; ++m) {
+                            const float nr = fmaf(pr, w.x, -pi * w.y);
+                            const float ni = fmaf(pr, w.y, pi * w.x);
+                            pr = nr;
+                            pi = ni;
+                            c[m] = make_float2(pr, pi);
+                        }
+                    }
+                    // keys are sorted, so lanes with a square above cur are the ones not yet
+                    // added; each pass adds at least one lane, so at most 32 passes close the half
+                    for (int pass = 0; pass < 33; ++pass) {
+                        if (valid && bx == cur) {
 #pragma unroll
-                    for (int m = 0; m < P1B; ++m) {
-                        acc[m].x += c[m].x;
-                        acc[m].y += c[m].y;
+                            for (int m = 0; m < P1B; ++m) {
+                                acc[m].x += c[m].x;
+                                acc[m].y += c[m].y;
+                            }
+                        }
+                        const unsigned later = __ballot_sync(0xffffffffu, valid && bx > cur);
+                        if (!later) break;
+                        flush(cur);
+                        cur = __shfl_sync(0xffffffffu, bx, __ffs(later) - 1);
                     }
                 }
-                const unsigned later = __ballot_sync(0xffffffffu, valid && bx > cur);
-                if (!later) break;
-                flush(cur);
-                cur = __shfl_sync(0xffffffffu, bx, __ffs(later) - 1);
             }
-            if (!__any_sync(0xffffffffu, valid)) break;
+            if (!__any_sync(0xffffffffu, v1)) break;
         }
         flush(cur);
     }
@@ -536,8 +568,9 @@ __global__ void __launch_bounds__(kM2LThreads) k_m2l_f32(M2LMixedArgs a, MixedLe
 
 // -------------------------------------------------------------------------------- L2P
 // One thread per particle; per level the square's p+1 coefficients are loaded together (the
-// order is padded to P1B at compile time, so all loads issue before the Horner chain).
-template <int P1B>
+// order is padded to P1B at compile time, so all loads issue before the Horner chain; kExact:
+// p + 1 == P1B, so no load needs a guard).
+template <int P1B, bool kExact>
 __global__ void __launch_bounds__(128)
 k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int p,
             MixedLevels lv, FmmLevelPtrs g, float2* __restrict__ phi_far) {
@@ -555,7 +588,7 @@ k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
         const float2* Bt = reinterpret_cast<const float2*>(g.B[k]) + t * p1;
         float2 b[P1B];
 #pragma unroll
-        for (int l = 0; l < P1B; ++l) b[l] = (l < p1) ? __ldg(Bt + l) : make_float2(0.f, 0.f);
+        for (int l = 0; l < P1B; ++l) b[l] = (kExact || l < p1) ? __ldg(Bt + l) : make_float2(0.f, 0.f);
         float2 u = b[P1B - 1];
 #pragma unroll
         for (int l = P1B - 2; l >= 1; --l) {
@@ -648,7 +681,7 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
         // fine levels: the finest kFineLevels; coarser ones by the particle-parallel kernel
         const int kf = L - (kFineLevels - 1) > 2 ? L - (kFineLevels - 1) : 2;
         const int kc_max = kf - 1;   // the coarse FP64 grids are zero here (k_prep_a32 re-zeroes them)
-        const unsigned fblocks = (unsigned)(((1ull << (2 * L)) + 127) / 128);
+        const unsigned fblocks = (unsigned)(((2ull << (2 * L)) + 127) / 128);   // two lanes per finest square
         const unsigned cblocks = (unsigned)((n + 4 * kCoarseChunk - 1) / (4 * kCoarseChunk));
         switch (pl->p1b) {
 #define FMM_P2M(PB)                                                                                          \
@@ -747,7 +780,11 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
         switch (pl->p1b) {
 #define FMM_L2P(PB)                                                                                          \
     case PB:                                                                                                 \
-        k_l2p_mixed<PB><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids, far);  \
+        if (p1 == PB)                                                                                        \
+            k_l2p_mixed<PB, true><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids, far); \
+        else                                                                                                 \
+            k_l2p_mixed<PB, false><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids,   \
+                                                           far);                                             \
         break;
             FMM_L2P(9) FMM_L2P(13) FMM_L2P(17) FMM_L2P(21) FMM_L2P(25) FMM_L2P(33) FMM_L2P(41)
 #undef FMM_L2P

@@ -154,6 +154,26 @@ __global__ void k_scan2_top(unsigned long long* __restrict__ sums, int nb) {
     if (threadIdx.x == 0) sums[nb] = carry;
 }
 
+// sum over the CTA's threads (every thread gets it)
+__device__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long* wt) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) wt[warp] = x;
+    __syncthreads();
+    unsigned long long t = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) t += wt[w];
+    __syncthreads();
+    return t;
+}
+
+// few scan blocks (at most kLocalTopMax): each CTA of the down-sweep sums the partials before it
+// itself, which spares the separate top-level pass
+constexpr int kLocalTopMax = 1024;
+
+template <bool kLocalTop>
 __global__ void k_scan2_down(uint32_t* __restrict__ in, int64_t m, const unsigned long long* __restrict__ sums,
                              uint32_t* __restrict__ leaf_start, uint32_t* __restrict__ bstart,
                              uint2* __restrict__ map) {
@@ -168,7 +188,14 @@ __global__ void k_scan2_down(uint32_t* __restrict__ in, int64_t m, const unsigne
         if (base + j < m) in[base + j] = 0u;   // the populations start the next call at zero
     }
     block_exclusive_scan(v, wt);
-    const unsigned long long off = sums[blockIdx.x];
+    unsigned long long off;
+    if (kLocalTop) {
+        unsigned long long part = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanThreads) part += sums[b];
+        off = block_sum_u64(part, wt);
+    } else {
+        off = sums[blockIdx.x];
+    }
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j)
         if (base + j < m) {
@@ -178,10 +205,18 @@ __global__ void k_scan2_down(uint32_t* __restrict__ in, int64_t m, const unsigne
             bstart[base + j] = b0;
             for (uint32_t b = 0; b < nbk[j]; ++b) map[b0 + b] = make_uint2((uint32_t)(base + j), b);
         }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const unsigned long long tot = sums[gridDim.x];
-        leaf_start[m] = (uint32_t)tot;
-        bstart[m] = (uint32_t)(tot >> 32);
+    if (blockIdx.x == gridDim.x - 1) {
+        unsigned long long tot;
+        if (kLocalTop) {
+            // this CTA's offset plus its own partial
+            tot = off + sums[blockIdx.x];
+        } else {
+            tot = sums[gridDim.x];
+        }
+        if (threadIdx.x == 0) {
+            leaf_start[m] = (uint32_t)tot;
+            bstart[m] = (uint32_t)(tot >> 32);
+        }
     }
 }
 
@@ -236,9 +271,15 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
         // the near-field blocks come with the same scan (block_sums holds 64-bit partials here)
         unsigned long long* sums = reinterpret_cast<unsigned long long*>(pl->block_sums);
         k_scan2_reduce<<<nb, kScanThreads, 0, st>>>(pl->counts, m, sums);
-        k_scan2_top<<<1, kScanThreads, 0, st>>>(sums, nb);
-        k_scan2_down<<<nb, kScanThreads, 0, st>>>(pl->counts, m, sums, pl->leaf_start, pl->leaf_bstart,
-                                                  pl->blk_map);
+        if (nb <= kLocalTopMax) {
+            k_scan2_down<true><<<nb, kScanThreads, 0, st>>>(pl->counts, m, sums, pl->leaf_start, pl->leaf_bstart,
+                                                            pl->blk_map);
+            launches -= 1;
+        } else {
+            k_scan2_top<<<1, kScanThreads, 0, st>>>(sums, nb);
+            k_scan2_down<false><<<nb, kScanThreads, 0, st>>>(pl->counts, m, sums, pl->leaf_start, pl->leaf_bstart,
+                                                             pl->blk_map);
+        }
     }
     launches += 3;
     const double sd = pl->box / (double)(1 << pl->levels);
