@@ -61,7 +61,9 @@ struct TcArgs {
     // [part][level] -> [q][KC][w2+2][w2+2][16 bytes] (1-cell zero halo); a 16-byte K chunk holds 4
     // TF32 or 8 BF16 values
     const uint8_t* src[kMaxParts][FMM_MAX_LEVELS + 1];
-    const uint8_t* ops[kMaxParts];             // [part] -> [class][27 slots][KC][N][16 bytes], scale-free
+    // [class][27 slots][KC][NP * N rows][16 bytes], scale-free: within a K chunk the operator's parts
+    // are stacked along N (rows part * N + n), so one MMA can take several parts at once
+    const uint8_t* ops;
     float2* B[FMM_MAX_LEVELS + 1];
     TcGroup groups[4][12];
     // the tiles of one class, finest level first: level seg_level[j] owns tiles
@@ -131,11 +133,22 @@ __device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t ad, uint64_t b
             : "memory");
 }
 
-// The split products kept, as (A part, B part), in order: TF32 x2 drops lo lo; BF16 x3 keeps every
-// term down to 2^-16 of the product (hi hi, hi mid, mid hi, hi lo, lo hi, mid mid).
-__device__ constexpr int kProdA[6] = {0, 0, 1, 0, 2, 1};
-__device__ constexpr int kProdB[6] = {0, 1, 0, 2, 0, 1};
-__host__ __device__ constexpr int num_products(int np) { return np == 1 ? 1 : (np == 2 ? 3 : 6); }
+// The split products kept: TF32 x2 drops lo lo; BF16 x3 keeps every term down to 2^-16 of the
+// product (hi hi, hi mid, mid hi, hi lo, lo hi, mid mid).  Products that share an A part go in one
+// MMA over stacked B parts, whose columns land side by side in the accumulator (column block j
+// holds the products with B part (first part + j)); the epilogue adds the blocks.  As (A part,
+// first B part, B parts) in issue order, the widest first (it initialises every column block):
+//   TF32 x2: (hi, hi, 2) = hi hi | hi lo, then (lo, hi, 1) = lo hi;
+//   BF16 x3: (hi, hi, 2), (mid, hi, 2), (hi, lo, 1), (lo, hi, 1).
+__device__ constexpr int kMmaA[4] = {0, 1, 0, 2};
+__device__ constexpr int kMmaB[4] = {0, 0, 2, 0};
+__host__ __device__ constexpr int num_mmas(int np) { return np == 1 ? 1 : (np == 2 ? 2 : 4); }
+__host__ __device__ constexpr int mma_width(int np, int mm) {
+    return np == 1 ? 1 : (np == 2 ? (mm == 0 ? 2 : 1) : (mm < 2 ? 2 : 1));
+}
+__host__ __device__ constexpr int stack_width(int np) { return np == 1 ? 1 : 2; }   // column blocks
+// accumulator columns per tile: the stacked width rounded up to a multiple of 32
+__host__ __device__ constexpr int acc_cols(int n, int np) { return (stack_width(np) * n + 31) / 32 * 32; }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
@@ -160,13 +173,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     constexpr int N = 2 * H;
     constexpr int KC = BF ? H / 4 : H / 2;           // 16-byte K chunks per offset
     constexpr uint32_t A_BYTES = KC * kWin * 16;     // one window, one part
-    constexpr uint32_t OP_BYTES = KC * N * 16;       // one offset's operator, one part
-    constexpr uint32_t OPS_STAGE = NP * 3 * OP_BYTES;
+    constexpr uint32_t ROWS = NP * N;                // stacked operator rows per K chunk
+    constexpr uint32_t OP_BYTES = KC * ROWS * 16;    // one offset's operator, all parts
+    constexpr uint32_t OPS_STAGE = 3 * OP_BYTES;
     constexpr uint32_t WIN_STAGE = NP * A_BYTES;
-    constexpr uint32_t ACC_COLS = 64;                // per tile (N <= 64)
+    constexpr uint32_t ACC_COLS = acc_cols(N, NP);   // per tile
     constexpr uint32_t FMT = BF ? 1u : 2u;           // operand format: BF16 (kind::f16) or TF32
-    constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(N >> 3) << 17) | ((128u >> 4) << 24);
-    constexpr int NPROD = num_products(NP);
+    constexpr uint32_t IDESC_BASE = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 4) << 24);
+    constexpr int NMMA = num_mmas(NP);
+    static_assert(stack_width(NP) * N <= 256 && N % 16 == 0, "MMA N of 16..256 in steps of 16");
     static_assert(KC % 2 == 0 && NP * KC <= 32, "an MMA takes two K chunks; one producer lane per chunk");
 
     static_assert(NSW >= 2, "the window pipeline keeps one window in flight: it needs two window stages");
@@ -240,16 +255,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                 if (lane == 0) {
                     if (g >= NSO && !wait_bar(su32(&ops_empty[so]), (uint32_t)((uso - 1) & 1))) ok = false;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&ops_full[so])),
-                                 "r"(NP * bytes)
+                                 "r"(bytes)
                                  : "memory");
                 }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) break;
-                if (lane < NP) {
-                    const uint8_t* srcB = a.ops[lane] + ((size_t)cls * 27 + G.slot0) * OP_BYTES;
+                if (lane == 0) {
+                    // the group's offsets are consecutive slots: one copy
+                    const uint8_t* srcB = a.ops + ((size_t)cls * 27 + G.slot0) * OP_BYTES;
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            su32(ops_buf + so * OPS_STAGE + lane * 3 * OP_BYTES)),
+                            su32(ops_buf + so * OPS_STAGE)),
                         "l"(srcB), "r"(bytes), "r"(su32(&ops_full[so]))
                         : "memory");
                 }
@@ -297,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                 // 2^18 bytes, so the 14-bit field never carries), keeping the one issuing thread's
                 // work per MMA to a few instructions
                 const uint64_t aDesc = smem_desc(su32(win_buf + sw * WIN_STAGE), kWin * 16, 128);
-                const uint64_t bDesc = smem_desc(su32(ops_buf + so * OPS_STAGE), N * 16, 128);
+                const uint64_t bDesc = smem_desc(su32(ops_buf + so * OPS_STAGE), ROWS * 16, 128);
                 const uint32_t acc_t = tmem + (uint32_t)t * ACC_COLS;
                 const int nops = G.nops;
                 for (int o = 0; o < nops && ok; ++o) {
@@ -307,11 +323,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
 #pragma unroll
                     for (int ks = 0; ks < KC / 2; ++ks) {
 #pragma unroll
-                        for (int pr = 0; pr < NPROD; ++pr) {
-                            const uint64_t ad = ad0 + (uint64_t)((kProdA[pr] * A_BYTES + ks * 2 * (kWin * 16)) / 16);
+                        for (int mm = 0; mm < NMMA; ++mm) {
+                            const uint64_t ad = ad0 + (uint64_t)((kMmaA[mm] * A_BYTES + ks * 2 * (kWin * 16)) / 16);
                             const uint64_t bd =
-                                bd0 + (uint64_t)((kProdB[pr] * 3 * OP_BYTES + ks * 2 * (N * 16)) / 16);
-                            mma_issue<BF>(acc_t, ad, bd, IDESC, (ks | pr) != 0 ? 1u : acc0);
+                                bd0 + (uint64_t)((kMmaB[mm] * N * 16 + ks * 2 * (ROWS * 16)) / 16);
+                            const uint32_t width = (uint32_t)mma_width(NP, mm);
+                            mma_issue<BF>(acc_t, ad, bd, IDESC_BASE | ((width * N) >> 3) << 17,
+                                          (ks | mm) != 0 ? 1u : acc0);
                         }
                     }
                 }
@@ -337,11 +355,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     // ---- epilogue: warp w holds accumulator rows (targets) 32w..32w+31 of every tile
     const int p1 = a.p + 1;
     for (int t = 0; t < nrows; ++t) {
-        float v[N];
+        constexpr int SW = stack_width(NP);
+        float v[SW * N];
 #pragma unroll
-        for (int c = 0; c < N; c += 16)
+        for (int c = 0; c < SW * N; c += 16)
             tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * ACC_COLS + c), v + c);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (SW == 2) {
+#pragma unroll
+            for (int c = 0; c < N; ++c) v[c] += v[N + c];   // the column blocks of the stacked products
+        }
         const int k = tile_k[t];
         const int w2 = 1 << (k - 1), W2P = w2 + 2;
         const int pos = tile_P[t] + 32 * warp + lane;
@@ -536,7 +559,7 @@ constexpr int tc_nsw() {
 struct FmmTc {
     int h, kc, np, sms;
     bool bf;                                    // BF16 operands (else TF32)
-    uint8_t* ops[kMaxParts];                    // one scale-free copy per part
+    uint8_t* ops;                               // one scale-free copy, the parts stacked
     uint8_t* src[kMaxParts][FMM_MAX_LEVELS + 1];
     TcArgs args;   // tables, filled at plan time
 };
@@ -599,16 +622,15 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
     // serves every level; the monopole-log entry (0, 0) is left out (summed in float-float by
     // k_m2l_mono).  Each value is split into np parts as the sources are (TF32 x2: hi, FP32 lo;
     // BF16 x3: hi, mid, lo, the differences taken in FP64).
-    const size_t opsz = (size_t)4 * 27 * kc * N * 16;   // bytes per part
+    const size_t opsz = (size_t)4 * 27 * kc * np * N * 16;   // bytes, all parts
     {
-        std::vector<uint8_t> hostops[kMaxParts];
-        for (int part = 0; part < np; ++part) hostops[part].assign(opsz, 0);
+        std::vector<uint8_t> hostops(opsz, 0);
         for (int cls = 0; cls < 4; ++cls)
             for (int g = 0; g < 12; ++g) {
                 const TcGroup& G = tc->args.groups[cls][g];
                 for (int o = 0; o < G.nops; ++o) {
                     const int d = G.d[o];
-                    const size_t base = ((size_t)cls * 27 + G.slot0 + o) * kc * N * 16;
+                    const size_t base = ((size_t)cls * 27 + G.slot0 + o) * kc * np * N * 16;
                     for (int n = 0; n < N; ++n)
                         for (int kk = 0; kk < K; ++kk) {
                             // input kk: Re M_j (kk < H) or Im M_j; output n: Re b_l (n < H) or Im b_l
@@ -623,30 +645,30 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
                                 else if (kk < H) val = ti;
                                 else val = tr;
                             }
-                            const size_t at = base + ((size_t)(kk / per) * N + n) * 16 + (size_t)(kk % per) * elem;
+                            // row part * N + n of K chunk kk / per
+                            const size_t at0 = base + (size_t)(kk / per) * np * N * 16 + (size_t)n * 16 +
+                                               (size_t)(kk % per) * elem;
                             if (bf) {
                                 double r = val;
                                 for (int part = 0; part < np; ++part) {
                                     const uint16_t b = host_bf16_bits((float)r);
                                     r -= (double)bf16_bits_to_float(b);
-                                    memcpy(&hostops[part][at], &b, 2);
+                                    memcpy(&hostops[at0 + (size_t)part * N * 16], &b, 2);
                                 }
                             } else {
                                 const float v = (float)val;
                                 const float h = host_tf32(v);
                                 const float parts[2] = {h, v - h};
-                                for (int part = 0; part < np; ++part) memcpy(&hostops[part][at], &parts[part], 4);
+                                for (int part = 0; part < np; ++part)
+                                    memcpy(&hostops[at0 + (size_t)part * N * 16], &parts[part], 4);
                             }
                         }
                 }
             }
-        for (int part = 0; part < np; ++part) {
-            if (cudaMalloc(&tc->ops[part], opsz) != cudaSuccess) return -1;
-            pl->workspace_bytes += opsz;
-            if (cudaMemcpy(tc->ops[part], hostops[part].data(), opsz, cudaMemcpyHostToDevice) != cudaSuccess)
-                return -1;
-            tc->args.ops[part] = tc->ops[part];
-        }
+        if (cudaMalloc(&tc->ops, opsz) != cudaSuccess) return -1;
+        pl->workspace_bytes += opsz;
+        if (cudaMemcpy(tc->ops, hostops.data(), opsz, cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+        tc->args.ops = tc->ops;
     }
     // source buffers (chunk-major, 1-cell zero halo, kSrcPad zero cells after), levels kMinLevel..L
     for (int k = kMinLevel; k <= pl->levels; ++k) {
@@ -665,8 +687,8 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
 void fmm_tc_destroy(fmm_plan_s* pl) {
     FmmTc* tc = pl->tc;
     if (!tc) return;
+    if (tc->ops) cudaFree(tc->ops);
     for (int part = 0; part < kMaxParts; ++part) {
-        if (tc->ops[part]) cudaFree(tc->ops[part]);
         for (int k = 0; k <= FMM_MAX_LEVELS; ++k)
             if (tc->src[part][k]) cudaFree(tc->src[part][k]);
     }
@@ -712,11 +734,13 @@ static int launch_tc(fmm_plan_s* pl, const MixedLevels& lv) {
     a.nseg = nseg;
     a.tiles = tiles;
     const int per_class_ctas = tc->sms / 4 > 0 ? tc->sms / 4 : 1;
+    constexpr int ACC = acc_cols(2 * H, NP);
+    const int max_rows = 512 / ACC < kMaxRows ? 512 / ACC : kMaxRows;   // accumulators fit tensor memory
     a.rows = (tiles + per_class_ctas - 1) / per_class_ctas;
-    if (a.rows > kMaxRows) a.rows = kMaxRows;
+    if (a.rows > max_rows) a.rows = max_rows;
     if (a.rows < 1) a.rows = 1;
     int cols = 32;
-    while (cols < a.rows * 64) cols <<= 1;
+    while (cols < a.rows * ACC) cols <<= 1;
     a.tmem_cols = cols;
     const int items = (tiles + a.rows - 1) / a.rows;
     constexpr int NSO = tc_nso<H, BF, NP>(), NSW = tc_nsw<H, BF, NP>();
