@@ -84,6 +84,9 @@ void free_plan(fmm_plan_s* pl) {
     if (pl->h_counters) cudaFreeHost(pl->h_counters);
     for (int e = 0; e < 10; ++e)
         if (pl->ev[e]) cudaEventDestroy(pl->ev[e]);
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+    if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+    if (pl->stream2) cudaStreamDestroy(pl->stream2);
     cudaSetDevice(prev);
     delete pl;
 }
@@ -252,6 +255,13 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->d_phi_stage, sizeof(double) * n));
     for (int e = 0; e < 10; ++e)
         if (cudaEventCreate(&pl->ev[e]) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
+    if (precision != FMM_FP64) {
+        // the mixed path's near field runs on a second stream of the plan's own
+        if (cudaStreamCreateWithFlags(&pl->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess)
+            FMM_TRY(FMM_ERR_CUDA);
+    }
 #undef FMM_TRY
     pl->last.n = n;
     pl->last.levels = levels;
@@ -310,13 +320,15 @@ fmm_status fmm_sync(fmm_plan_t plan) {
         plan->last.ms_p2m = ms[1];
         plan->last.ms_m2l = ms[2];
         plan->last.ms_l2p = ms[3];
-        plan->last.ms_p2p = ms[4];
+        plan->last.ms_p2p = ms[4];   // FP64 path: the P2P stage; the mixed path's is set below
         plan->last.ms_total = tot;
         float kt = 0.f;
         plan->last.ms_m2l_tc = (plan->ev_kernels & 1) && cudaEventElapsedTime(&kt, plan->ev[6], plan->ev[7]) ==
                                                               cudaSuccess ? kt : 0.0;
         plan->last.ms_p2p_kernel = (plan->ev_kernels & 2) && cudaEventElapsedTime(&kt, plan->ev[8], plan->ev[9]) ==
                                                                   cudaSuccess ? kt : 0.0;
+        // the mixed path's P2P runs beside P2M and M2L on the second stream: its stage is its kernel
+        if (plan->ev_kernels & 2) plan->last.ms_p2p = plan->last.ms_p2p_kernel;
         plan->ev_kernels = 0;
         unsigned long long pairs = 0, mx = 0;
         for (int c = 0; c < FMM_COUNTER_SLOTS; ++c) {

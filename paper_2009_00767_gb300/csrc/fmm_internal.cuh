@@ -11,8 +11,9 @@
 //                            zero halo, row-major, p+1 complex coefficients per square
 //   B[k]                     local coefficients of level k, (2^k)^2 row-major, p+1 complex each
 //   A32[k]                   (mixed) FP32 copy of A[k]; slot 0 holds M_0 as a float-float pair
-//   (mixed) B[k] slot 0 holds Re b'_0 as a float-float pair; phi_far holds float-float pairs
-//   phi_far[n]               far field summed over levels, FP64, box-sorted order
+//   (mixed) B[k] slot 0 holds Re b'_0 as a float-float pair
+//   phi_far[n]               FP64 path: far field summed over levels, box-sorted order; mixed
+//                            path: the near field as float-float pairs (log2 r^2 units)
 //   T64                      49 x (p+1) x (p+1) complex FP64 M2L operators, layout [d][k][l],
 //                            d = (dx + 3) + 7 (dy + 3), zero for the 9 adjacent offsets
 // Because keys are Morton-ordered, the particles of every square of every level are one
@@ -101,7 +102,7 @@ struct fmm_plan_s {
 
     FmmLevelPtrs grids;
     size_t a_bytes[FMM_MAX_LEVELS + 1];
-    double* phi_far;
+    double* phi_far;                  // FP64 path: far field; mixed path: near field (float2 per particle)
 
     double2* T64;       // FP64 operators [49][p+1][p+1]
     float2* T32;        // FP32 operators [49][p1b][p1b], zero-padded, [d][0][0] = 0 (mixed SIMT M2L)
@@ -117,6 +118,8 @@ struct fmm_plan_s {
     double* d_q_stage;
     double* d_phi_stage;
 
+    cudaStream_t stream2;          // mixed path: the near field runs here, beside P2M and M2L
+    cudaEvent_t ev_fork, ev_join;  // untimed: stream -> stream2 after the sort, back before L2P
     cudaEvent_t ev[10];   // stage boundaries [0..5]; the tensor-core M2L kernel [6, 7]; the P2P kernel [8, 9]
     int ev_kernels;       // bit 0: [6, 7] recorded this call, bit 1: [8, 9]
     int events_recorded;

@@ -566,14 +566,17 @@ __global__ void __launch_bounds__(kM2LThreads) k_m2l_f32(M2LMixedArgs a, MixedLe
         if (l < p1) B[t * p1 + l] = acc[l];
 }
 
-// -------------------------------------------------------------------------------- L2P
+// -------------------------------------------------------------------------------- L2P + final phi
 // One thread per particle; per level the square's p+1 coefficients are loaded together (the
 // order is padded to P1B at compile time, so all loads issue before the Horner chain; kExact:
-// p + 1 == P1B, so no load needs a guard).
+// p + 1 == P1B, so no load needs a guard).  The levels are summed in float-float, the particle's
+// near field (from the P2P kernel, which runs concurrently with P2P and M2L on a second stream)
+// is added, and phi is written in input order unless the inputs failed the device checks.
 template <int P1B, bool kExact>
 __global__ void __launch_bounds__(128)
 k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int p,
-            MixedLevels lv, FmmLevelPtrs g, float2* __restrict__ phi_far) {
+            MixedLevels lv, FmmLevelPtrs g, const float2* __restrict__ near, const unsigned int* __restrict__ status,
+            double* __restrict__ phi) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 P = sp[i];
@@ -600,21 +603,24 @@ k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
         const float v = fmaf(u.x, w.x, -u.y * w.y);   // Re(u w) = Re sum_{l>=1} b'_l w^l
         far = ff_add(far, ff_add_f(b[0], v));         // b[0] = Re b'_0 as (hi, lo)
     }
-    phi_far[i] = far;
+    if (*(volatile const unsigned int*)status != 0u) return;   // inputs failed the device checks
+    phi[__float_as_int(P.w)] = p2p_phi(far, near[i]);
 }
 
-// -------------------------------------------------------------------------------- P2P + final phi
+// -------------------------------------------------------------------------------- P2P
 // One warp per block of up to FMM_P2P_BLOCK targets of one finest square (the block -> square map
 // spares the warp a search); crowded squares spread over as many warps as they have blocks.  The
-// block's near field is p2p_near (p2p_block.cuh).  (A persistent variant that ran each block's
-// lookups one block ahead measured no faster: the time goes to the blocks' own work.)
+// block's near field is p2p_near (p2p_block.cuh); it is stored per sorted particle (log2 r^2 units,
+// float-float) for L2P to finish phi.  The kernel needs only the sort's output, so it runs on a
+// second stream beside P2M and M2L.  (A persistent variant that ran each block's lookups one block
+// ahead measured no faster: the time goes to the blocks' own work.)
 constexpr int kP2PWarps = 4;
 
 __global__ void __launch_bounds__(kP2PWarps * 32, 6)
 k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
             const uint32_t* __restrict__ bstart, const uint2* __restrict__ bmap, uint32_t nleaf, int levels,
-            float s_leaf, const float2* __restrict__ phi_far, double* __restrict__ phi,
-            unsigned int* __restrict__ status, unsigned long long* __restrict__ counters) {
+            float s_leaf, float2* __restrict__ near_out, unsigned int* __restrict__ status,
+            unsigned long long* __restrict__ counters) {
     __shared__ __align__(16) float4 tgt[kP2PWarps][16];   // zero past the block's targets
     __shared__ __align__(16) int4 seg[kP2PWarps][8];      // neighbours in slot order: {index - slot, ox, oy, -}
     static_assert(FMM_P2P_BLOCK <= 24, "p2p_near takes blocks of up to 24 targets");
@@ -629,13 +635,6 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
     const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
     const uint32_t b0 = t0 + (uint32_t)FMM_P2P_BLOCK * lt.y;
     const int T = (int)min((uint32_t)FMM_P2P_BLOCK, t1 - b0);
-    // the final write's inputs, loaded early: the target's input index and its far field
-    int idx = 0;
-    float2 far = make_float2(0.f, 0.f);
-    if (lane < T) {
-        idx = __float_as_int(sp[b0 + lane].w);
-        far = phi_far[b0 + lane];
-    }
     uint32_t nsrc;
     const float2 near = p2p_near(sp, leaf_start, leaf, t0, t1, b0, T, levels, s_leaf, tgt[warp], seg[warp], lane, &nsrc);
     if (lane == 0) {
@@ -643,8 +642,35 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
         atomicAdd(&counters[slot], (unsigned long long)T * nsrc - (unsigned long long)T);
         atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)(t1 - t0));
     }
-    if (lane < T) phi[idx] = p2p_phi(far, near);
+    if (lane < T) near_out[b0 + lane] = near;
 }
+
+}  // namespace
+
+// The near field on the plan's second stream: forked from the plan's stream at this point of its
+// work (any point after the sort will do), joined back before L2P.
+int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv) {
+    cudaStream_t st = pl->stream, s2 = pl->stream2;
+    if (cudaEventRecord(pl->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(s2, pl->ev_fork, 0) != cudaSuccess)
+        return -1;
+    const int L = pl->levels;
+    const int64_t n = pl->n;
+    const uint32_t nleaf = 1u << (2 * L);
+    // the near-field blocks (leaf_bstart, blk_map) came with the sort's scan; upper bound of the
+    // blocks: each square adds at most one partial block
+    const uint64_t wmax = (uint64_t)nleaf + (uint64_t)(n / FMM_P2P_BLOCK) + 1;
+    const unsigned blocks = (unsigned)((wmax + kP2PWarps - 1) / kP2PWarps);
+    cudaEventRecord(pl->ev[8], s2);
+    k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, s2>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, pl->blk_map, nleaf,
+                                                  L, lv.s_leaf, reinterpret_cast<float2*>(pl->phi_far), pl->d_status,
+                                                  pl->d_counters);
+    cudaEventRecord(pl->ev[9], s2);
+    pl->ev_kernels |= 2;
+    if (cudaEventRecord(pl->ev_join, s2) != cudaSuccess) return -1;
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+namespace {
 
 template <int P1B>
 void launch_m2l(const M2LMixedArgs& a, const MixedLevels& lv, int blocks, cudaStream_t st) {
@@ -676,6 +702,7 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     const int L = pl->levels, p = pl->p, p1 = p + 1;
     const MixedLevels lv = fmm_make_levels(pl);
     int launches = 0;
+    const float2* near = reinterpret_cast<const float2*>(pl->phi_far);   // near field per sorted particle
     cudaEventRecord(pl->ev[1], st);
     if (L >= 2) {
         // fine levels: the finest kFineLevels; coarser ones by the particle-parallel kernel
@@ -683,10 +710,14 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
         const int kc_max = kf - 1;   // the coarse FP64 grids are zero here (k_prep_a32 re-zeroes them)
         const unsigned fblocks = (unsigned)(((2ull << (2 * L)) + 127) / 128);   // two lanes per finest square
         const unsigned cblocks = (unsigned)((n + 4 * kCoarseChunk - 1) / (4 * kCoarseChunk));
+        // the near field forks after the fine P2M kernel: it then runs beside the coarse P2M and the
+        // M2L's smaller kernels (forked at the sort it slowed the register-heavy fine P2M; forked at
+        // the tensor-core kernel it slowed that kernel's single MMA-issuing thread)
         switch (pl->p1b) {
 #define FMM_P2M(PB)                                                                                          \
     case PB:                                                                                                 \
         k_p2m_fine<PB><<<fblocks, 128, 0, st>>>(pl->sorted32, pl->leaf_start, L, p, lv, pl->grids);           \
+        if (fmm_launch_p2p_concurrent(pl, lv) < 0) return -1;                                                \
         if (kc_max >= 2)                                                                                     \
             k_p2m_coarse<PB><<<cblocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, kc_max, p, lv,     \
                                                       pl->grids);                                            \
@@ -695,7 +726,7 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
 #undef FMM_P2M
             default: return -2;
         }
-        launches += kc_max >= 2 ? 2 : 1;
+        launches += kc_max >= 2 ? 3 : 2;   // with the near-field kernel
         if (kc_max >= 2) {
             PrepA32Args pa{};
             int64_t acc = 0;
@@ -773,18 +804,24 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
             launches += t;
         }
     }
+    if (L < 2) {   // no far field: the near field alone
+        const int r = fmm_launch_p2p_concurrent(pl, lv);
+        if (r < 0) return -1;
+        launches += r;
+    }
     cudaEventRecord(pl->ev[3], st);
-    float2* far = reinterpret_cast<float2*>(pl->phi_far);
+    if (cudaStreamWaitEvent(st, pl->ev_join, 0) != cudaSuccess) return -1;   // the near field is done
     {
         const unsigned blocks = (unsigned)((n + 127) / 128);
         switch (pl->p1b) {
 #define FMM_L2P(PB)                                                                                          \
     case PB:                                                                                                 \
         if (p1 == PB)                                                                                        \
-            k_l2p_mixed<PB, true><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids, far); \
+            k_l2p_mixed<PB, true><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids,    \
+                                                          near, pl->d_status, phi);                          \
         else                                                                                                 \
             k_l2p_mixed<PB, false><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids,   \
-                                                           far);                                             \
+                                                           near, pl->d_status, phi);                         \
         break;
             FMM_L2P(9) FMM_L2P(13) FMM_L2P(17) FMM_L2P(21) FMM_L2P(25) FMM_L2P(33) FMM_L2P(41)
 #undef FMM_L2P
@@ -793,19 +830,6 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
         ++launches;
     }
     cudaEventRecord(pl->ev[4], st);
-    {
-        const uint32_t nleaf = 1u << (2 * L);
-        // the near-field blocks (leaf_bstart, blk_map) came with the sort's scan
-        // upper bound of the target blocks: each square adds at most one partial block
-        const uint64_t wmax = (uint64_t)nleaf + (uint64_t)(n / FMM_P2P_BLOCK) + 1;
-        const unsigned blocks = (unsigned)((wmax + kP2PWarps - 1) / kP2PWarps);
-        cudaEventRecord(pl->ev[8], st);
-        k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, st>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, pl->blk_map,
-                                                      nleaf, L, lv.s_leaf, far, phi, pl->d_status, pl->d_counters);
-        cudaEventRecord(pl->ev[9], st);
-        pl->ev_kernels |= 2;
-        ++launches;
-    }
     cudaEventRecord(pl->ev[5], st);
     if (cudaGetLastError() != cudaSuccess) return -1;
     return launches;

@@ -77,4 +77,6 @@ inline MixedLevels fmm_make_levels(const fmm_plan_s* pl) {
 int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vector<double>& Tim);
 void fmm_tc_destroy(fmm_plan_s* pl);
 int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv);
+// the near field on the plan's second stream (mixed.cu); kernels launched, or -1
+int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv);
 int fmm_tc_kmin();
