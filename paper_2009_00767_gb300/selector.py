@@ -6,7 +6,8 @@ error and the run time of the mixed-precision method; it then picks the cheapest
 predicted to meet a requested accuracy, or the fixed fallback (8, 20).
 
 Its training tuples are generated by the method itself: for each synthetic system, every
-candidate of the grid is run through ``fmm_potential`` (mixed FP32), timed with CUDA events,
+candidate of the grid is run through ``fmm_potential`` (in the precision given, by default the
+mixed FP32 form, which takes every p of fmm_select's grid), timed with CUDA events,
 and judged by the library's FP64 direct sum (``fmm_direct_targets``) on sampled targets.  The
 network is then fitted by the library's own forward / backward / Adam kernels.
 
@@ -29,17 +30,21 @@ from . import binding, inputs
 
 FALLBACK = (8, 20)
 P_GRID = (8, 12, 16, 20, 24, 28, 32)
+DEFAULT_PRECISION = "fp32"
+TENSOR_CORE = ("tf32", "3xtf32", "bf16", "bf16x3")   # these take p + 1 <= 32 coefficients
 LOG10_SCALE = 8.0           # the network predicts log10(error) / 8
 ERR_FLOOR = 1e-8            # errors below this are labelled at the floor
 
 
-def candidates(n):
+def candidates(n, precision=DEFAULT_PRECISION):
     l0 = int(round(math.log(n / 16.0) / math.log(4.0)))
+    pmax = 31 if precision in TENSOR_CORE else 40
     out = []
     for lev in range(l0 - 2, l0 + 3):
         if 2 <= lev <= 11:
             for p in P_GRID:
-                out.append((lev, p))
+                if p <= pmax:
+                    out.append((lev, p))
     return out
 
 
@@ -86,7 +91,7 @@ def judge_targets(torch, xy_d, q_d, n, seed, s=256):
     return idx_d, ref
 
 
-def run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p, precision="fp32"):
+def run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p, precision=DEFAULT_PRECISION):
     n = int(q_d.shape[0])
     phi = torch.empty(n, dtype=torch.float64, device=xy_d.device)
     with binding.Plan(n, lev, p, 5.0, precision) as plan:
@@ -99,7 +104,7 @@ def label(err, ms):
     return [math.log10(max(err, ERR_FLOOR)) / LOG10_SCALE, math.log(max(ms, 1e-3))]
 
 
-def generate(sel, seeds, log=print):
+def generate(sel, seeds, log=print, precision=DEFAULT_PRECISION):
     """Tuples (features ++ candidate, [log10 err / 8, log ms]) for the systems of ``seeds``."""
     import torch
     X, T, meta = [], [], []
@@ -110,12 +115,13 @@ def generate(sel, seeds, log=print):
         feat = sel.features(xy_d)
         idx_d, ref = judge_targets(torch, xy_d, q_d, q.shape[0], sd)
         t0 = time.time()
-        for lev, p in candidates(q.shape[0]):
-            err, ms = run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p)
+        for lev, p in candidates(q.shape[0], precision):
+            err, ms = run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p, precision)
             X.append(np.concatenate([feat, [lev / 12.0, p / 32.0]]))
             T.append(label(err, ms))
             meta.append({"seed": sd, "family": name, "n": int(q.shape[0]), "levels": lev, "p": p, "err": err, "ms": ms})
-        log(f"system {sd}: {name} N={q.shape[0]} {len(candidates(q.shape[0]))} candidates in {time.time() - t0:.1f}s")
+        log(f"system {sd}: {name} N={q.shape[0]} {len(candidates(q.shape[0], precision))} candidates in "
+            f"{time.time() - t0:.1f}s")
     return np.asarray(X, dtype=np.float32), np.asarray(T, dtype=np.float32), meta
 
 
@@ -124,7 +130,7 @@ def best_feasible(meta_rows, target):
     return min(ok, key=lambda r: r["ms"]) if ok else None
 
 
-def evaluate(sel, seeds, target=1e-6, margin=0.3):
+def evaluate(sel, seeds, target=1e-6, margin=0.3, precision=DEFAULT_PRECISION):
     """Learned pick vs the fixed fallback on held-out systems, both judged by the FP64 direct sum."""
     import torch
     rows = []
@@ -134,8 +140,8 @@ def evaluate(sel, seeds, target=1e-6, margin=0.3):
         q_d = torch.from_numpy(q).to("cuda")
         lev, p, fb = sel.select(xy_d, target, margin)
         idx_d, ref = judge_targets(torch, xy_d, q_d, q.shape[0], sd)
-        err_l, ms_l = run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p)
-        err_f, ms_f = run_candidate(torch, xy_d, q_d, idx_d, ref, *FALLBACK)
+        err_l, ms_l = run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p, precision)
+        err_f, ms_f = run_candidate(torch, xy_d, q_d, idx_d, ref, *FALLBACK, precision)
         rows.append({"seed": sd, "family": name, "n": int(q.shape[0]), "pick": [lev, p], "fallback_used": fb,
                      "err_pick": err_l, "ms_pick": ms_l, "err_fallback": err_f, "ms_fallback": ms_f})
     return rows
@@ -153,10 +159,11 @@ def main(argv=None):
     tr.add_argument("--dataset", default=None, help="save the generated tuples (.npz)")
     tr.add_argument("--eval-systems", type=int, default=24)
     tr.add_argument("--report", default=None)
+    tr.add_argument("--precision", default=DEFAULT_PRECISION)
     a = ap.parse_args(argv)
     build_lib()
     sel = binding.Selector(hidden=a.hidden, seed=1)
-    X, T, meta = generate(sel, range(a.seed0, a.seed0 + a.systems))
+    X, T, meta = generate(sel, range(a.seed0, a.seed0 + a.systems), precision=a.precision)
     if a.dataset:
         np.savez(a.dataset, X=X, T=T, meta=json.dumps(meta))
     losses = []
@@ -164,8 +171,8 @@ def main(argv=None):
         losses.append(sel.train(X, T, 500, lr=1e-3 if chunk < 8 else 3e-4))
         print(f"epoch {(chunk + 1) * 500}: loss {losses[-1]:.5f}")
     sel.save(a.out)
-    ev = evaluate(sel, range(a.seed0 + 10_000, a.seed0 + 10_000 + a.eval_systems))
-    rep = {"train_tuples": int(X.shape[0]), "losses": losses, "eval": ev}
+    ev = evaluate(sel, range(a.seed0 + 10_000, a.seed0 + 10_000 + a.eval_systems), precision=a.precision)
+    rep = {"train_tuples": int(X.shape[0]), "precision": a.precision, "losses": losses, "eval": ev}
     if a.report:
         with open(a.report, "w") as f:
             json.dump(rep, f, indent=1)
