@@ -26,9 +26,10 @@
 // D += A_hi B_hi + A_hi B_lo + A_lo B_hi, dropping A_lo B_lo, recovers about FP32 accuracy.
 //
 // The monopole-log term of b'_0, sum_d M_0 (log|w0| + ln s), carries the largest part of phi; it
-// stays out of the GEMM (its (0, 0) operator entry is zero): k_m2l_mono sums it in float-float
-// from the FP32 moment grid after the GEMM, in both TF32 modes; a TF32 product of a large M_0
-// with the log would lose more than the error bound allows on clustered systems.  Every wait on
+// stays out of the GEMM (its (0, 0) operator entry is zero): k_prep_tc sums it in float-float
+// from the FP32 moment grid before the GEMM, in every mode, and the epilogue adds the GEMM's part
+// to it; a TF32 or BF16 product of a large M_0 with the log would lose more than the error bound
+// allows on clustered systems.  Every wait on
 // an mbarrier is bounded and sets a status flag when it runs out.
 
 #include <cuda_bf16.h>
@@ -349,12 +350,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
         __syncwarp();
     }
     if (!ok) atomicOr(a.status, FMM_FLAG_TIMEOUT);
+    // warp w holds accumulator rows (targets) 32w..32w+31 of every tile: each thread's targets,
+    // and the monopole-log part of their Re b'_0 that k_prep_tc left in B, loaded while the MMAs
+    // run (kept in registers: the tile loops are unrolled over kMaxRows)
+    const int p1 = a.p + 1;
+    float2* bt[kMaxRows];
+    float2 b0[kMaxRows];
+#pragma unroll
+    for (int t = 0; t < kMaxRows; ++t) {
+        bt[t] = nullptr;
+        b0[t] = make_float2(0.f, 0.f);
+        if (t < nrows) {
+            const int k = tile_k[t];
+            const int w2 = 1 << (k - 1), W2P = w2 + 2;
+            const int pos = tile_P[t] + 32 * warp + lane;
+            const int x = pos % W2P - 1, y = pos / W2P - 1;   // sub-grid cell; halo cells are dropped
+            if (x >= 0 && x < w2 && y < w2) {
+                bt[t] = a.B[k] + ((size_t)(2 * y + py) * (1u << k) + (2 * x + px)) * p1;
+                b0[t] = bt[t][0];
+            }
+        }
+    }
     const bool done = wait_bar(su32(done_bar), 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    // ---- epilogue: warp w holds accumulator rows (targets) 32w..32w+31 of every tile
-    const int p1 = a.p + 1;
-    for (int t = 0; t < nrows; ++t) {
+    // ---- epilogue
+#pragma unroll
+    for (int t = 0; t < kMaxRows; ++t) {
+        if (t >= nrows) break;
         constexpr int SW = stack_width(NP);
         float v[SW * N];
 #pragma unroll
@@ -365,15 +388,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
 #pragma unroll
             for (int c = 0; c < N; ++c) v[c] += v[N + c];   // the column blocks of the stacked products
         }
-        const int k = tile_k[t];
-        const int w2 = 1 << (k - 1), W2P = w2 + 2;
-        const int pos = tile_P[t] + 32 * warp + lane;
-        const int x = pos % W2P - 1, y = pos / W2P - 1;   // sub-grid cell; halo cells are dropped
-        if (done && x >= 0 && x < w2 && y < w2) {
-            const int tx = 2 * x + px, ty = 2 * y + py;
-            // Re b'_0 without the monopole-log term, which k_m2l_mono adds in float-float
-            float2* B = a.B[k] + ((size_t)ty * (1u << k) + tx) * p1;
-            B[0] = make_float2(v[0], 0.f);
+        if (done && bt[t] != nullptr) {
+            // Re b'_0: the GEMM's part added to the monopole-log term
+            float2* B = bt[t];
+            B[0] = ff_add_f(b0[t], v[0]);
 #pragma unroll
             for (int l = 1; l < H; ++l)
                 if (l < p1) B[l] = make_float2(v[l], v[H + l]);
@@ -394,9 +412,36 @@ __device__ __forceinline__ uint32_t bf16_rn_bits(float x) {
     return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
+// the 27 list offsets of targets of parity (PX, PY), loads first, then the float-float sum
+template <int PX, int PY>
+__device__ __forceinline__ float2 mono_sum(const float2* __restrict__ A32, const float2 (&logc)[49], size_t c0, int W,
+                                           int p1) {
+    float2 m0[49];
+#pragma unroll
+    for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+        for (int dx = -3; dx <= 3; ++dx) {
+            const bool adj = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
+            const bool in = dx >= -2 - PX && dx <= 3 - PX && dy >= -2 - PY && dy <= 3 - PY;
+            if (in && !adj) m0[(dy + 3) * 7 + dx + 3] = A32[(c0 + (ptrdiff_t)dy * W + dx) * p1];
+        }
+    float2 mono = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+        for (int dx = -3; dx <= 3; ++dx) {
+            const bool adj = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
+            const bool in = dx >= -2 - PX && dx <= 3 - PX && dy >= -2 - PY && dy <= 3 - PY;
+            if (in && !adj) mono = ff_add(mono, ff_mul(m0[(dy + 3) * 7 + dx + 3], logc[(dx + 3) + 7 * (dy + 3)]));
+        }
+    return mono;
+}
+
 struct PrepArgs {
     const float2* a32[FMM_MAX_LEVELS + 1];
     uint4* out[kMaxParts][FMM_MAX_LEVELS + 1];
+    float2* B[FMM_MAX_LEVELS + 1];
+    float2 logc[FMM_MAX_LEVELS + 1][49];
     long long base[FMM_MAX_LEVELS + 2];   // first cell (over all four parities) of each level
     int kmin, levels, p1;
 };
@@ -405,6 +450,11 @@ struct PrepArgs {
 // sub-grid: out[part][q][KC][w2][w2][16 bytes] with the K index Re M_0..M_p, pad, Im M_0..M_p,
 // pad, each value split into NP parts: TF32 x2 hi = rna(x), lo = x - hi; BF16 x3 hi = rn(x),
 // mid = rn(x - hi), lo = rn(x - hi - mid) (each difference exact in FP32).
+// The same thread, as the target square of that cell, also writes the monopole-log term of b'_0,
+// sum_d M_0[t + d] (log|w0_d| + ln s_k) over its interaction list, summed in float-float (in the
+// order dy, then dx, the 27 loads issued together) into B's slot 0, where the tensor-core kernel's
+// epilogue adds the GEMM's part: it stays out of the GEMM (its operator entry (0, 0) is zero), as
+// a TF32 or BF16 product of a large M_0 with the log would lose more than the error bound allows.
 template <int H, bool BF, int NP>
 __global__ void k_prep_tc(const __grid_constant__ PrepArgs a) {
     constexpr int KC = BF ? H / 4 : H / 2, PER = BF ? 8 : 4;
@@ -452,62 +502,15 @@ __global__ void k_prep_tc(const __grid_constant__ PrepArgs a) {
 #pragma unroll
         for (int part = 0; part < NP; ++part) a.out[part][k][at] = make_uint4(w[part][0], w[part][1], w[part][2], w[part][3]);
     }
-}
-
-// The monopole-log term of b'_0 for the tensor-core levels, sum_d M_0[t + d] (log|w0_d| + ln s_k)
-// over the target's interaction list, summed in float-float (in the order dy, then dx) and added to
-// the GEMM's Re b'_0: one thread per target, the 27 loads of a target issued together.
-struct MonoArgs {
-    const float2* a32[FMM_MAX_LEVELS + 1];
-    float2* B[FMM_MAX_LEVELS + 1];
-    float2 logc[FMM_MAX_LEVELS + 1][49];
-    long long base[FMM_MAX_LEVELS + 2];   // first target of each level
-    int kmin, levels, p1;
-};
-
-// the 27 list offsets of targets of parity (PX, PY), loads first, then the float-float sum
-template <int PX, int PY>
-__device__ __forceinline__ float2 mono_sum(const float2* __restrict__ A32, const float2 (&logc)[49], size_t c0, int W,
-                                           int p1) {
-    float2 m0[49];
-#pragma unroll
-    for (int dy = -3; dy <= 3; ++dy)
-#pragma unroll
-        for (int dx = -3; dx <= 3; ++dx) {
-            const bool adj = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
-            const bool in = dx >= -2 - PX && dx <= 3 - PX && dy >= -2 - PY && dy <= 3 - PY;
-            if (in && !adj) m0[(dy + 3) * 7 + dx + 3] = A32[(c0 + (ptrdiff_t)dy * W + dx) * p1];
-        }
-    float2 mono = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int dy = -3; dy <= 3; ++dy)
-#pragma unroll
-        for (int dx = -3; dx <= 3; ++dx) {
-            const bool adj = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1;
-            const bool in = dx >= -2 - PX && dx <= 3 - PX && dy >= -2 - PY && dy <= 3 - PY;
-            if (in && !adj) mono = ff_add(mono, ff_mul(m0[(dy + 3) * 7 + dx + 3], logc[(dx + 3) + 7 * (dy + 3)]));
-        }
-    return mono;
-}
-
-__global__ void k_m2l_mono(const __grid_constant__ MonoArgs a) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.base[a.levels + 1]) return;
-    int k = a.kmin;
-    while (g >= a.base[k + 1]) ++k;
-    const int64_t t = g - a.base[k];
-    const int side = 1 << k, W = fmm_grid_width(k), p1 = a.p1;
-    const int tx = (int)(t % side), ty = (int)(t / side);
-    const size_t c0 = (size_t)(ty + FMM_HALO) * W + (tx + FMM_HALO);
+    const size_t c0 = (size_t)(y + FMM_HALO) * W + (x + FMM_HALO);
     float2 mono;
-    switch ((tx & 1) + 2 * (ty & 1)) {
+    switch (q) {
         case 0: mono = mono_sum<0, 0>(a.a32[k], a.logc[k], c0, W, p1); break;
         case 1: mono = mono_sum<1, 0>(a.a32[k], a.logc[k], c0, W, p1); break;
         case 2: mono = mono_sum<0, 1>(a.a32[k], a.logc[k], c0, W, p1); break;
         default: mono = mono_sum<1, 1>(a.a32[k], a.logc[k], c0, W, p1); break;
     }
-    float2* B = a.B[k] + (size_t)t * p1;
-    B[0] = ff_add_f(mono, B[0].x);   // Re b'_0 as float-float
+    a.B[k][((size_t)y * (1u << k) + x) * p1] = mono;   // Re b'_0 as float-float, the GEMM's part to come
 }
 
 // host-side round to nearest TF32 (ties away), the rounding cvt.rna.tf32.f32 does on the device
@@ -620,7 +623,7 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
     }
     // operators, real block form, [part][class][slot][KC][N][16 bytes]: scale-free, so one copy
     // serves every level; the monopole-log entry (0, 0) is left out (summed in float-float by
-    // k_m2l_mono).  Each value is split into np parts as the sources are (TF32 x2: hi, FP32 lo;
+    // k_prep_tc).  Each value is split into np parts as the sources are (TF32 x2: hi, FP32 lo;
     // BF16 x3: hi, mid, lo, the differences taken in FP64).
     const size_t opsz = (size_t)4 * 27 * kc * np * N * 16;   // bytes, all parts
     {
@@ -707,6 +710,7 @@ static int launch_tc(fmm_plan_s* pl, const MixedLevels& lv) {
         for (int k = kMinLevel; k <= L; ++k) {
             pa.a32[k] = reinterpret_cast<const float2*>(pl->grids.A32[k]);
             for (int part = 0; part < NP; ++part) pa.out[part][k] = reinterpret_cast<uint4*>(tc->src[part][k]);
+            pa.B[k] = reinterpret_cast<float2*>(pl->grids.B[k]);
             pa.base[k] = acc;
             acc += 4ll << (2 * (k - 1));
         }
@@ -714,6 +718,7 @@ static int launch_tc(fmm_plan_s* pl, const MixedLevels& lv) {
         pa.kmin = kMinLevel;
         pa.levels = L;
         pa.p1 = p1;
+        memcpy(pa.logc, lv.logc, sizeof(pa.logc));
         k_prep_tc<H, BF, NP><<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(pa);
     }
     TcArgs& a = tc->args;
@@ -751,23 +756,7 @@ static int launch_tc(fmm_plan_s* pl, const MixedLevels& lv) {
     kern<<<4 * items, kThreads, shm, st>>>(a);
     cudaEventRecord(pl->ev[7], st);
     pl->ev_kernels |= 1;
-    {
-        MonoArgs ma{};
-        long long acc = 0;
-        for (int k = kMinLevel; k <= L; ++k) {
-            ma.a32[k] = reinterpret_cast<const float2*>(pl->grids.A32[k]);
-            ma.B[k] = reinterpret_cast<float2*>(pl->grids.B[k]);
-            ma.base[k] = acc;
-            acc += 1ll << (2 * k);
-        }
-        ma.base[L + 1] = acc;
-        memcpy(ma.logc, lv.logc, sizeof(ma.logc));
-        ma.kmin = kMinLevel;
-        ma.levels = L;
-        ma.p1 = p1;
-        k_m2l_mono<<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(ma);
-    }
-    return 3;
+    return 2;
 }
 
 // Launch prep + tensor-core M2L for levels 2..L; returns kernels launched or -1.
