@@ -115,23 +115,37 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// one MMA, D (+)= A B^T: kind::f16 with BF16 operands, or kind::tf32
+// One MMA, D (+)= A B^T (kind::f16 with BF16 operands, or kind::tf32), issued by the lane that
+// elect.sync picks in a converged warp: the whole warp runs the issuing loop, so its descriptors
+// stay warp-uniform values, and the leader (the lowest lane, the same one every time) issues.
 template <bool BF>
 __device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
     if constexpr (BF)
         asm volatile(
-            "{\n\t.reg .pred p;\n\t"
+            "{\n\t.reg .pred p, e;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
             "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
             : "memory");
     else
         asm volatile(
-            "{\n\t.reg .pred p;\n\t"
+            "{\n\t.reg .pred p, e;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
             "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
             : "memory");
+}
+
+// tcgen05.commit by the elected lane (the one that issued the MMAs): the barrier's arrival
+// tracks the completion of every MMA that lane has issued so far
+__device__ __forceinline__ void commit_elect(uint32_t bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(bar)
+        : "memory");
 }
 
 // The split products kept: TF32 x2 drops lo lo; BF16 x3 keeps every term down to 2^-16 of the
@@ -242,35 +256,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
 
     bool ok = true;
     const int NWIN = 12 * nrows;
-    if (warp == 0) {
-        // producer warp: lane 0 waits for a free stage and posts its byte count, then the lanes
-        // issue the stage's bulk copies in parallel (an operator part, or one K chunk of one part
-        // of the window each); every copy completes on the stage's full barrier, so the producer
-        // runs ahead of the MMAs
+    if (warp == 2) {
+        // operator producer: each group's operators (its offsets are consecutive slots) as soon
+        // as the stage's previous group has been consumed; lane 0 posts the byte count, then the
+        // lanes copy 16-byte-aligned slices in parallel
+        for (int g = 0; g < 12; ++g) {
+            const TcGroup& G = a.groups[cls][g];
+            const int so = g % NSO, uso = g / NSO;
+            const uint32_t bytes = (uint32_t)G.nops * OP_BYTES;
+            if (lane == 0) {
+                if (g >= NSO && !wait_bar(su32(&ops_empty[so]), (uint32_t)((uso - 1) & 1))) ok = false;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&ops_full[so])),
+                             "r"(bytes)
+                             : "memory");
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            const uint32_t units = bytes / 16u, per = (units + 31u) / 32u;
+            const uint32_t u0 = min(units, (uint32_t)lane * per), u1 = min(units, u0 + per);
+            if (u1 > u0) {
+                const uint8_t* srcB = a.ops + ((size_t)cls * 27 + G.slot0) * OP_BYTES + (size_t)u0 * 16u;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        su32(ops_buf + so * OPS_STAGE + u0 * 16u)),
+                    "l"(srcB), "r"((u1 - u0) * 16u), "r"(su32(&ops_full[so]))
+                    : "memory");
+            }
+        }
+        __syncwarp();
+    } else if (warp == 0) {
+        // window producer: lane 0 waits for a free stage and posts its byte count, then the lanes
+        // issue the window's bulk copies in parallel (one K chunk of one part each); every copy
+        // completes on the stage's full barrier, so the producer runs ahead of the MMAs
         for (int i = 0; i < NWIN; ++i) {
             const int g = i / nrows, t = i % nrows;
             const TcGroup& G = a.groups[cls][g];
-            if (t == 0) {
-                const int so = g % NSO, uso = g / NSO;
-                const uint32_t bytes = (uint32_t)G.nops * OP_BYTES;
-                if (lane == 0) {
-                    if (g >= NSO && !wait_bar(su32(&ops_empty[so]), (uint32_t)((uso - 1) & 1))) ok = false;
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&ops_full[so])),
-                                 "r"(bytes)
-                                 : "memory");
-                }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) break;
-                if (lane == 0) {
-                    // the group's offsets are consecutive slots: one copy
-                    const uint8_t* srcB = a.ops + ((size_t)cls * 27 + G.slot0) * OP_BYTES;
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            su32(ops_buf + so * OPS_STAGE)),
-                        "l"(srcB), "r"(bytes), "r"(su32(&ops_full[so]))
-                        : "memory");
-                }
-            }
             const int sw = i % NSW, usw = i / NSW;
             if (lane == 0) {
                 if (i >= NSW && !wait_bar(su32(&win_empty[sw]), (uint32_t)((usw - 1) & 1))) ok = false;
@@ -299,54 +319,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
         }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0) {
-            // MMA issuer
-            for (int i = 0; i < NWIN; ++i) {
-                const int g = i / nrows, t = i % nrows;
-                const TcGroup& G = a.groups[cls][g];
-                const int so = g % NSO, uso = g / NSO;
-                const int sw = i % NSW, usw = i / NSW;
-                if (t == 0 && !wait_bar(su32(&ops_full[so]), (uint32_t)(uso & 1))) ok = false;
-                if (!wait_bar(su32(&win_full[sw]), (uint32_t)(usw & 1))) ok = false;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                // descriptors: the window's and the group's base descriptors once, then constant
-                // offsets in 16-byte units on the start-address field (shared addresses stay below
-                // 2^18 bytes, so the 14-bit field never carries), keeping the one issuing thread's
-                // work per MMA to a few instructions
-                const uint64_t aDesc = smem_desc(su32(win_buf + sw * WIN_STAGE), kWin * 16, 128);
-                const uint64_t bDesc = smem_desc(su32(ops_buf + so * OPS_STAGE), ROWS * 16, 128);
-                const uint32_t acc_t = tmem + (uint32_t)t * ACC_COLS;
-                const int nops = G.nops;
-                for (int o = 0; o < nops && ok; ++o) {
-                    const uint64_t ad0 = aDesc + (uint64_t)(1 + G.sx[o]);   // column shift: one 16-byte cell
-                    const uint64_t bd0 = bDesc + (uint64_t)(o * (OP_BYTES / 16));
-                    const uint32_t acc0 = (g | o) != 0;
+        // MMA issuer: the whole warp runs the loop (waits, descriptors) in step, one elected lane
+        // issues the MMAs and commits
+        for (int i = 0; i < NWIN; ++i) {
+            const int g = i / nrows, t = i % nrows;
+            const TcGroup& G = a.groups[cls][g];
+            const int so = g % NSO, uso = g / NSO;
+            const int sw = i % NSW, usw = i / NSW;
+            if (t == 0 && !wait_bar(su32(&ops_full[so]), (uint32_t)(uso & 1))) ok = false;
+            if (!wait_bar(su32(&win_full[sw]), (uint32_t)(usw & 1))) ok = false;
+            ok = __all_sync(0xffffffffu, ok);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // descriptors: the window's and the group's base descriptors once, then constant
+            // offsets in 16-byte units on the start-address field (shared addresses stay below
+            // 2^18 bytes, so the 14-bit field never carries)
+            const uint64_t aDesc = smem_desc(su32(win_buf + sw * WIN_STAGE), kWin * 16, 128);
+            const uint64_t bDesc = smem_desc(su32(ops_buf + so * OPS_STAGE), ROWS * 16, 128);
+            const uint32_t acc_t = tmem + (uint32_t)t * ACC_COLS;
+            const int nops = G.nops;
+            for (int o = 0; o < nops && ok; ++o) {
+                const uint64_t ad0 = aDesc + (uint64_t)(1 + G.sx[o]);   // column shift: one 16-byte cell
+                const uint64_t bd0 = bDesc + (uint64_t)(o * (OP_BYTES / 16));
+                const uint32_t acc0 = (g | o) != 0;
 #pragma unroll
-                    for (int ks = 0; ks < KC / 2; ++ks) {
+                for (int ks = 0; ks < KC / 2; ++ks) {
 #pragma unroll
-                        for (int mm = 0; mm < NMMA; ++mm) {
-                            const uint64_t ad = ad0 + (uint64_t)((kMmaA[mm] * A_BYTES + ks * 2 * (kWin * 16)) / 16);
-                            const uint64_t bd =
-                                bd0 + (uint64_t)((kMmaB[mm] * N * 16 + ks * 2 * (ROWS * 16)) / 16);
-                            const uint32_t width = (uint32_t)mma_width(NP, mm);
-                            mma_issue<BF>(acc_t, ad, bd, IDESC_BASE | ((width * N) >> 3) << 17,
-                                          (ks | mm) != 0 ? 1u : acc0);
-                        }
+                    for (int mm = 0; mm < NMMA; ++mm) {
+                        const uint64_t ad = ad0 + (uint64_t)((kMmaA[mm] * A_BYTES + ks * 2 * (kWin * 16)) / 16);
+                        const uint64_t bd = bd0 + (uint64_t)((kMmaB[mm] * N * 16 + ks * 2 * (ROWS * 16)) / 16);
+                        const uint32_t width = (uint32_t)mma_width(NP, mm);
+                        mma_issue<BF>(acc_t, ad, bd, IDESC_BASE | ((width * N) >> 3) << 17,
+                                      (ks | mm) != 0 ? 1u : acc0);
                     }
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 su32(&win_empty[sw]))
-                             : "memory");
-                if (t == nrows - 1)
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     su32(&ops_empty[so]))
-                                 : "memory");
             }
-            // the final commit tracks every MMA issued above
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             su32(done_bar))
-                         : "memory");
+            commit_elect(su32(&win_empty[sw]));
+            if (t == nrows - 1) commit_elect(su32(&ops_empty[so]));
         }
+        // the final commit tracks every MMA issued above
+        commit_elect(su32(done_bar));
         __syncwarp();
     }
     if (!ok) atomicOr(a.status, FMM_FLAG_TIMEOUT);
