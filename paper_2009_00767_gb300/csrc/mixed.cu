@@ -572,6 +572,31 @@ __global__ void __launch_bounds__(kM2LThreads) k_m2l_f32(M2LMixedArgs a, MixedLe
 // p + 1 == P1B, so no load needs a guard).  The levels are summed in float-float, the particle's
 // near field (from the P2P kernel, which runs concurrently with P2P and M2L on a second stream)
 // is added, and phi is written in input order unless the inputs failed the device checks.
+// u z + c for complex u, z, c (FP32)
+__device__ __forceinline__ float2 cfma(float2 u, float2 z, float2 c) {
+    return make_float2(fmaf(u.x, z.x, fmaf(-u.y, z.y, c.x)), fmaf(u.x, z.y, fmaf(u.y, z.x, c.y)));
+}
+
+// Re sum_{l=1}^{P1B-1} b_l w^l, the even and odd powers as two Horner chains in z = w^2
+template <int P1B>
+__device__ __forceinline__ float l2p_split_horner(const float2 (&b)[P1B], float2 w) {
+    static_assert(P1B >= 2, "at least b_0 and b_1");
+    constexpr int LO = (P1B - 1) % 2 == 1 ? P1B - 1 : P1B - 2;   // highest odd index
+    constexpr int LE = (P1B - 1) % 2 == 0 ? P1B - 1 : P1B - 2;   // highest even index
+    const float2 z = make_float2(fmaf(w.x, w.x, -w.y * w.y), 2.f * w.x * w.y);
+    float2 o = b[LO];
+#pragma unroll
+    for (int l = LO - 2; l >= 1; l -= 2) o = cfma(o, z, b[l]);
+    float v = fmaf(o.x, w.x, -o.y * w.y);   // Re(w O)
+    if constexpr (LE >= 2) {
+        float2 e = b[LE];
+#pragma unroll
+        for (int l = LE - 2; l >= 2; l -= 2) e = cfma(e, z, b[l]);
+        v += fmaf(e.x, z.x, -e.y * z.y);   // Re(z E)
+    }
+    return v;
+}
+
 template <int P1B, bool kExact>
 __global__ void __launch_bounds__(128)
 k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int p,
@@ -592,15 +617,9 @@ k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
         float2 b[P1B];
 #pragma unroll
         for (int l = 0; l < P1B; ++l) b[l] = (kExact || l < p1) ? __ldg(Bt + l) : make_float2(0.f, 0.f);
-        float2 u = b[P1B - 1];
-#pragma unroll
-        for (int l = P1B - 2; l >= 1; --l) {
-            const float ur = fmaf(u.x, w.x, fmaf(-u.y, w.y, b[l].x));
-            const float ui = fmaf(u.x, w.y, fmaf(u.y, w.x, b[l].y));
-            u.x = ur;
-            u.y = ui;
-        }
-        const float v = fmaf(u.x, w.x, -u.y * w.y);   // Re(u w) = Re sum_{l>=1} b'_l w^l
+        // Re sum_{l>=1} b'_l w^l = Re(z E(z) + w O(z)) with z = w^2, E(z) = sum_{m>=1} b'_{2m} z^(m-1),
+        // O(z) = sum_{m>=0} b'_{2m+1} z^m: two independent Horner chains of half the length
+        const float v = l2p_split_horner<P1B>(b, w);
         far = ff_add(far, ff_add_f(b[0], v));         // b[0] = Re b'_0 as (hi, lo)
     }
     if (*(volatile const unsigned int*)status != 0u) return;   // inputs failed the device checks
