@@ -12,7 +12,7 @@ meets the 1e-6 error bound); the plain FP64 GPU path is timed beside it.
 Timing: W warm-up steps, then exactly K steps timed with CUDA events on the
 plan's stream; between steps a 256 MB buffer is written to flush the 129 MB
 L2 (outside the events).  The accuracy gate compares phi at 4096 sampled
-targets with the FP64 direct sum (the library's FP64 judge kernel, itself
+targets with the FP64 direct sum (the library's FP64 direct-sum kernel, itself
 tested against the CPU oracle).
 
 --impl reference times the FP64 CPU oracle (the method's plain statement,
@@ -322,7 +322,7 @@ def run_ours(args):
         ms_step = float(t.item())
     value = ws * w["n"] / (ms_step * 1e-3)
 
-    # accuracy gate: FP64 direct sum at 4096 sampled targets (GPU judge)
+    # accuracy gate: FP64 direct sum at 4096 sampled targets (on the GPU)
     from paper_2009_00767_gb300 import inputs as inp
     S = min(4096, w["n"])
     idx = np.unique((inp.u01(4242, 0, S) * w["n"]).astype(np.int64))

@@ -146,7 +146,7 @@ void fmm_plan_destroy(fmm_plan_t plan);
 /* Static English text for a status code; never NULL. */
 const char* fmm_status_string(int status);
 
-/* FP64 direct sum at selected targets (the judge of every accuracy figure):
+/* FP64 direct sum at selected targets (the reference of every accuracy figure):
  *   phi_t[t] = sum_{j != targets[t], r > 0} q_j log|z_targets[t] - z_j|.
  *   xy, q      device, the n particles as in fmm_potential.
  *   targets    device, const int64_t[n_targets], each in [0, n).

@@ -217,7 +217,7 @@ k_p2p_f64(const fmm_p64* __restrict__ sp, const uint32_t* __restrict__ leaf_star
     }
 }
 
-// -------------------------------------------------------------------------------- direct judge
+// -------------------------------------------------------------------------------- FP64 direct sum
 __global__ void k_direct_f64(int64_t n, const double2* __restrict__ xy, const double* __restrict__ q,
                              const int64_t* __restrict__ targets, double* __restrict__ out) {
     __shared__ double red[32];

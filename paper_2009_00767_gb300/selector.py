@@ -8,7 +8,7 @@ predicted to meet a requested accuracy, or the fixed fallback (8, 20).
 Its training tuples are generated by the method itself: for each synthetic system, every
 candidate of the grid is run through ``fmm_potential`` (in the precision given, by default the
 mixed FP32 form, which takes every p of fmm_select's grid), timed with CUDA events,
-and judged by the library's FP64 direct sum (``fmm_direct_targets``) on sampled targets.  The
+and measured against the library's FP64 direct sum (``fmm_direct_targets``) on sampled targets.  The
 network is then fitted by the library's own forward / backward / Adam kernels.
 
 Workload of the tuples: N log-uniform in [2^16, 2^20]; families uniform, Gaussian mixture
@@ -82,7 +82,7 @@ def _time_plan(torch, plan, xy_d, q_d, phi, reps=3):
     return float(np.median(ms))
 
 
-def judge_targets(torch, xy_d, q_d, n, seed, s=256):
+def reference_targets(torch, xy_d, q_d, n, seed, s=256):
     idx = np.unique((inputs.u01(seed, 77, s) * n).astype(np.int64))
     idx_d = torch.from_numpy(idx).to(xy_d.device)
     ref = torch.empty(idx.shape[0], dtype=torch.float64, device=xy_d.device)
@@ -113,7 +113,7 @@ def generate(sel, seeds, log=print, precision=DEFAULT_PRECISION):
         xy_d = torch.from_numpy(xy).to("cuda")
         q_d = torch.from_numpy(q).to("cuda")
         feat = sel.features(xy_d)
-        idx_d, ref = judge_targets(torch, xy_d, q_d, q.shape[0], sd)
+        idx_d, ref = reference_targets(torch, xy_d, q_d, q.shape[0], sd)
         t0 = time.time()
         for lev, p in candidates(q.shape[0], precision):
             err, ms = run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p, precision)
@@ -131,7 +131,7 @@ def best_feasible(meta_rows, target):
 
 
 def evaluate(sel, seeds, target=1e-6, margin=0.3, precision=DEFAULT_PRECISION):
-    """Learned pick vs the fixed fallback on held-out systems, both judged by the FP64 direct sum."""
+    """Learned pick vs the fixed fallback on held-out systems, both measured against the FP64 direct sum."""
     import torch
     rows = []
     for sd in seeds:
@@ -139,7 +139,7 @@ def evaluate(sel, seeds, target=1e-6, margin=0.3, precision=DEFAULT_PRECISION):
         xy_d = torch.from_numpy(xy).to("cuda")
         q_d = torch.from_numpy(q).to("cuda")
         lev, p, fb = sel.select(xy_d, target, margin)
-        idx_d, ref = judge_targets(torch, xy_d, q_d, q.shape[0], sd)
+        idx_d, ref = reference_targets(torch, xy_d, q_d, q.shape[0], sd)
         err_l, ms_l = run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p, precision)
         err_f, ms_f = run_candidate(torch, xy_d, q_d, idx_d, ref, *FALLBACK, precision)
         rows.append({"seed": sd, "family": name, "n": int(q.shape[0]), "pick": [lev, p], "fallback_used": fb,

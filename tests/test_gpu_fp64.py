@@ -104,7 +104,7 @@ def test_host_entry_point(oracle_mod):
     assert rel_l2(phi, oracle_mod.shiftfree(xy, q, 4, 12)) < TOL
 
 
-def test_direct_judge_matches_oracle(oracle_mod):
+def test_direct_sum_matches_oracle(oracle_mod):
     import torch
     from gpu_util import to_dev
     from paper_2009_00767_gb300 import binding

@@ -69,7 +69,7 @@ def test_training_fits_and_resumes_from_a_checkpoint(tmp_path):
 
 @pytest.mark.skipif(not os.path.exists(MODEL), reason="no trained selector model in the package")
 def test_trained_selector_beats_the_fixed_fallback():
-    """Held-out systems: the learned pick meets 1e-6 (judged by the FP64 direct sum) and costs
+    """Held-out systems: the learned pick meets 1e-6 (measured against the FP64 direct sum) and costs
     less in total than the fixed (levels, p) = (8, 20)."""
     from paper_2009_00767_gb300 import binding, selector
     s = binding.Selector(hidden=64, seed=1)
