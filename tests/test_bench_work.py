@@ -1,0 +1,49 @@
+"""The algorithmic work bench.py divides by (CPU only): the interaction-list pair count behind the
+M2L flops against the oracle's own interaction lists, and the roofline fractions it reports."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+@pytest.mark.parametrize("levels,kmin", [(2, 2), (3, 2), (4, 2), (5, 2), (5, 4)])
+def test_m2l_pairs_match_the_oracle_interaction_lists(oracle_mod, levels, kmin):
+    import bench
+    brute = 0
+    for k in range(kmin, levels + 1):
+        side = 1 << k
+        for by in range(side):
+            for bx in range(side):
+                brute += len(oracle_mod.interaction_list(bx, by, k))
+    assert bench.m2l_pairs(levels, kmin) == brute
+
+
+def test_interior_square_has_27_sources(oracle_mod):
+    # the paper's 6 x 6 parent-neighbour block minus the 3 x 3 adjacent squares
+    assert len(oracle_mod.interaction_list(5, 6, 4)) == 27
+
+
+def test_roofline_fractions():
+    import bench
+    w = dict(n=1 << 20, levels=8, p=20)
+    peaks = {"bf16_tflops": 1886.0, "hbm_gbs": 6788.3}
+    stats = {"p2p_pairs": 150_218_432}
+    r = bench.roofline_for("p2p_kernel", stats, 0.1, w, peaks, 2070.0, "bf16x3", None)
+    assert r["bound"] == "alu" and r["unit"] == "Tlg2/s"
+    assert r["peak"] == pytest.approx(152 * 32 * 2070e6 / 1e12)
+    assert r["achieved"] == pytest.approx(150_218_432 / 1e-4 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    t = bench.roofline_for("m2l_tc", stats, 0.08, w, peaks, 2070.0, "bf16x3", 123)
+    assert t["bound"] == "tensor" and t["peak"] == 1886.0 and t["traffic"] == 123
+    assert t["achieved"] == pytest.approx(bench.m2l_pairs(8, bench.TC_KMIN) * 8 * 21 * 21 / 8e-5 / 1e12)
+    t32 = bench.roofline_for("m2l_tc", stats, 0.08, w, peaks, 2070.0, "3xtf32", None)
+    assert t32["peak"] == pytest.approx(943.0)   # TF32 at half the BF16 rate
+    f = bench.roofline_for("l2p", stats, 0.05, w, peaks, 2070.0, "bf16x3", None)
+    assert f["bound"] == "alu" and f["unit"] == "TFLOP/s"
+    assert f["achieved"] == pytest.approx(8 * 20 * (1 << 20) * 7 / 5e-5 / 1e12)
+    s = bench.roofline_for("sort", stats, 0.05, w, peaks, 2070.0, "bf16x3", None)
+    assert s["bound"] == "hbm" and s["peak"] == 6788.3
