@@ -42,9 +42,8 @@ UNIT = "particles/s"
 ERR_BOUND = 1e-6
 N_SMS = 152
 FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM (4 sub-partitions x 32)
-MUFU_PER_SM = 32               # lg2 results per clock per SM on GB300: ncu puts the XU pipe's peak at one
-                               # warp instruction per SM cycle (6.52 M lg2 warp instructions in 160 us,
-                               # 48.4 M SM cycles, read 13.3 % of it)
+MUFU_PER_SM = 16               # lg2 results per clock per SM: measured by the library's probe
+                               # (fmm_probe_peak: 5.01e12 lg2/s on 152 SMs at 2.06 GHz)
 
 WORKLOADS = {
     "uniform_1m_l8_p20": dict(n=1 << 20, levels=8, p=20, family="uniform", config=1),
@@ -361,6 +360,14 @@ def run_ours(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     roof = roofline_for(dom, last, cands[dom], w, peaks, sm_max, args.precision, load_traffic(dom))
     roof_all = {k: roofline_for(k, last, v, w, peaks, sm_max, args.precision, load_traffic(k)) for k, v in cands.items()}
+    # the arithmetic units measured by the library's own probes (a few ms, after the timed region),
+    # beside the peaks derived from unit counts and the maximum clock
+    probe = {"fp32_tflops": binding.fmm_probe_peak(binding.FMM_PROBE_FP32_FMA) / 1e12,
+             "mufu_tlg2_per_s": binding.fmm_probe_peak(binding.FMM_PROBE_MUFU_LG2) / 1e12,
+             "fp64_tflops": binding.fmm_probe_peak(binding.FMM_PROBE_FP64_FMA) / 1e12}
+    for r in [roof] + list(roof_all.values()):
+        if r and r.get("bound") == "alu":
+            r["peak_probe"] = probe["mufu_tlg2_per_s"] if r["unit"] == "Tlg2/s" else probe["fp32_tflops"]
 
     # end to end through the host-buffer entry point: H2D of xy, q and D2H of phi every step
     xy_h = torch.from_numpy(xy).pin_memory()
@@ -410,7 +417,7 @@ def run_ours(args):
                        "l2": "256 MB buffer written between timed steps (outside the events)"},
             "rel_l2_err": err, "meets_error_bound": err <= ERR_BOUND,
             "stage_ms": stage_avg, "kernel_ms": kern_avg, "roofline": roof, "roofline_stages": roof_all,
-            "gpu_launches": launches, "e2e": e2e, "fp64_gpu": fp64,
+            "gpu_launches": launches, "e2e": e2e, "fp64_gpu": fp64, "alu_peaks_probe": probe,
             "speedup_vs_fp64_gpu": (value / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu, "batched": batched, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                                             "reasons": clk["reasons"], "samples": clk["samples"]},

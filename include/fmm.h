@@ -157,6 +157,20 @@ const char* fmm_status_string(int status);
 fmm_status fmm_direct_targets(int64_t n, const double* xy, const double* q, int64_t n_targets,
                               const int64_t* targets, double* phi_t, void* stream);
 
+/* Throughput probes for the roofline denominators of the arithmetic-bound stages.  They have no
+ * counterpart in the paper; they measure the units its near field (Sec. 2.1, E-2: one logarithm
+ * per pair) and its FP32 expansion sums run on.
+ *   unit       FMM_PROBE_FP32_FMA: FP32 flop/s (an FMA counts 2);
+ *              FMM_PROBE_MUFU_LG2: lg2.approx results/s;
+ *              FMM_PROBE_FP64_FMA: FP64 flop/s.
+ *   ops_per_s  host, written with the best rate of three timed launches (0 on failure).
+ *   stream     cudaStream_t (NULL = default stream), on the current device.
+ * Runs four launches of a few milliseconds each and blocks until they finish; allocates 4 bytes of
+ * device memory for the call.  FMM_ERR_INVALID_ARG for an unknown unit or a null ops_per_s,
+ * FMM_ERR_OOM or FMM_ERR_CUDA when a CUDA call fails. */
+enum { FMM_PROBE_FP32_FMA = 0, FMM_PROBE_MUFU_LG2 = 1, FMM_PROBE_FP64_FMA = 2 };
+fmm_status fmm_probe_peak(int unit, double* ops_per_s, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * Batched form: many independent systems of uneven size, each an independent instance of
  * the method above (its own box [0, box]^2 and quadtree depth), evaluated by one launch per

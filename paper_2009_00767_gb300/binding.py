@@ -61,6 +61,7 @@ SIGNATURES = {
     "fmm_plan_destroy": (None, [_vp]),
     "fmm_status_string": (ctypes.c_char_p, [_i32]),
     "fmm_direct_targets": (_i32, [_i64, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "fmm_probe_peak": (_i32, [_i32, ctypes.POINTER(_d), _vp]),
     "fmm_potential_noalloc": (_i32, [_i64, _i32, _i32, _d, _vp, _vp, _vp, _vp]),
     "fmm_batch_plan": (_i32, [ctypes.POINTER(_vp), _i32, _vp, _vp, _i32, _d, _i32, _vp]),
     "fmm_batch_potential": (_i32, [_vp, _vp, _vp, _vp]),
@@ -186,6 +187,16 @@ def fmm_direct_targets(xy, q, targets, phi_t, stream=None):
     nt = int(targets.shape[0])
     _check(_lib.fmm_direct_targets(n, _ptr(xy), _ptr(q), nt, _ptr(targets), _ptr(phi_t), _stream_handle(stream)),
            "fmm_direct_targets")
+
+
+FMM_PROBE_FP32_FMA, FMM_PROBE_MUFU_LG2, FMM_PROBE_FP64_FMA = 0, 1, 2
+
+
+def fmm_probe_peak(unit: int, stream=None) -> float:
+    """Measured throughput of one arithmetic unit (FP32 flop/s, lg2/s or FP64 flop/s)."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.fmm_probe_peak(int(unit), ctypes.byref(out), _stream_handle(stream)), "fmm_probe_peak")
+    return float(out.value)
 
 
 def fmm_potential_noalloc(xy, q, phi, levels: int, p: int, box: float = 5.0, stream=None):

@@ -58,6 +58,10 @@ def test_status_strings_and_host_side_argument_checks(lib):
     assert L.fmm_plan(ctypes.byref(h), 10, 3, 8, -1.0, 0, None) == b.FMM_ERR_INVALID_ARG
     assert L.fmm_plan(ctypes.byref(h), 10, 3, 8, float("nan"), 0, None) == b.FMM_ERR_INVALID_ARG
     assert L.fmm_plan(ctypes.byref(h), 10, 3, 8, 5.0, 99, None) == b.FMM_ERR_INVALID_ARG
+    d = ctypes.c_double(1.0)
+    assert L.fmm_probe_peak(7, ctypes.byref(d), None) == b.FMM_ERR_INVALID_ARG
+    assert L.fmm_probe_peak(-1, ctypes.byref(d), None) == b.FMM_ERR_INVALID_ARG
+    assert L.fmm_probe_peak(0, None, None) == b.FMM_ERR_INVALID_ARG
     assert L.fmm_plan(None, 10, 3, 8, 5.0, 0, None) == b.FMM_ERR_INVALID_ARG
     assert L.fmm_potential(None, None, None, None) == b.FMM_ERR_INVALID_ARG
     assert L.fmm_sync(None) == b.FMM_ERR_INVALID_ARG

@@ -34,7 +34,7 @@ def test_roofline_fractions():
     stats = {"p2p_pairs": 150_218_432}
     r = bench.roofline_for("p2p_kernel", stats, 0.1, w, peaks, 2070.0, "bf16x3", None)
     assert r["bound"] == "alu" and r["unit"] == "Tlg2/s"
-    assert r["peak"] == pytest.approx(152 * 32 * 2070e6 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 16 * 2070e6 / 1e12)
     assert r["achieved"] == pytest.approx(150_218_432 / 1e-4 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     t = bench.roofline_for("m2l_tc", stats, 0.08, w, peaks, 2070.0, "bf16x3", 123)
