@@ -47,3 +47,14 @@ def test_roofline_fractions():
     assert f["achieved"] == pytest.approx(8 * 20 * (1 << 20) * 7 / 5e-5 / 1e12)
     s = bench.roofline_for("sort", stats, 0.05, w, peaks, 2070.0, "bf16x3", None)
     assert s["bound"] == "hbm" and s["peak"] == 6788.3
+
+
+def test_cpu_baseline_all_cores_and_one_thread(oracle_mod):
+    import bench
+    w = bench.WORKLOADS["uniform_4k_l4_p16"]
+    xy, q = bench.make_inputs(w)
+    threads = oracle_mod.get_threads()
+    r = bench.cpu_baseline(w, xy, q)
+    assert r["kind"] == "oracle" and r["cores"] == threads and r["value"] > 0
+    assert r["one_thread"]["cores"] == 1 and r["one_thread"]["value"] > 0
+    assert oracle_mod.get_threads() == threads   # the thread count is restored
