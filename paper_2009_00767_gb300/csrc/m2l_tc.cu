@@ -1,5 +1,6 @@
-// m2l_tc.cu -- M2L (D-bar-1 of Sec. 2.2.1) on the 5th-generation tensor cores (tcgen05) for every
-// level, in TF32 or in split 3xTF32 with FP32 accumulation in tensor memory.
+// m2l_tc.cu -- M2L (D-bar-1 of Sec. 2.2.1) on the 5th-generation tensor cores (tcgen05) for the
+// levels from 6 down, in TF32 or BF16, unsplit or split (3xTF32, BF16x3), with FP32 accumulation
+// in tensor memory.
 //
 // For one level k and one parity class c = (px, py) of target squares, the conversion of the
 // interaction list is a real GEMM
@@ -8,29 +9,33 @@
 // and kk the inputs (K = 2H per offset: Re M_0..M_p then Im M_0..M_p).  The 27 offsets of the
 // class fall into 12 groups that share one source window: the source parity (qx, qy) and the
 // source row shift sy.  The source grid of a parity is a (w2 + 2) x (w2 + 2) array with a 1-cell
-// zero halo, stored chunk-major ([parity][K/4 chunk][row][col][4 floats]); read as one flat array
+// zero halo, stored chunk-major ([parity][K chunk][row][col][16 bytes]); read as one flat array
 // of cells, a tile is 128 consecutive cells starting at flat position P and its window for shift
 // sy the 130 cells from P - 1 + sy (w2 + 2): each K-chunk of it is one contiguous run of 2080
 // bytes.  Rows of at least 128 targets take tiles aligned to the row; narrower sub-grids (levels
 // below 8) take consecutive runs of the flat array, and the outputs that fall on halo cells are
-// dropped.  A window is KC bulk copies (cp.async.bulk) per part, issued by the producer warp's
-// lanes in parallel, that land in the canonical no-swizzle K-major shared layout (16-byte
-// core-matrix rows, K-chunk stride LBO = 130 x 16 B) and complete on the stage's mbarrier; the three column shifts of a group are the same window read from a
-// descriptor start moved by 16 B per cell.  The operators are scale-free, so a CTA takes up to
-// eight tiles of one class from any levels and loads each group's operators (one bulk copy) once
-// for all of them.  Warp 0 issues the copies (running up to NSW windows ahead), one thread of
-// warp 1 issues the MMAs into one tensor-memory accumulator per tile, all four warps run the
-// epilogue, which reads the accumulators back with tcgen05.ld and stores them.
+// dropped.
 //
-// 3xTF32 (Ootomo & Yokota, 2022): x = x_hi + x_lo with x_hi rounded to TF32, and
-// D += A_hi B_hi + A_hi B_lo + A_lo B_hi, dropping A_lo B_lo, recovers about FP32 accuracy.
+// A CTA takes up to eight tiles of one class from any levels (the operators are scale-free) and
+// one tensor-memory accumulator per tile.  Warp 0 streams the windows (one 2080-byte bulk copy per
+// K chunk and part, issued by its lanes in parallel, up to NSW windows ahead) into the canonical
+// no-swizzle K-major shared layout (16-byte core-matrix rows, K-chunk stride LBO = 130 x 16 B);
+// warp 2 loads each group's operators, once for all the CTA's tiles; warp 1, converged, runs the
+// issuing loop and one elected lane issues the MMAs (the three column shifts of a group read the
+// same window through a descriptor start moved by 16 B per cell); all four warps run the epilogue,
+// which reads the accumulators back with tcgen05.ld and stores them.  Every copy completes on its
+// stage's mbarrier, and every wait on an mbarrier is bounded and sets a status flag when it runs
+// out.
+//
+// Split products: 3xTF32 (Ootomo & Yokota, 2022) writes x = x_hi + x_lo with x_hi rounded to TF32
+// and keeps A_hi B_hi + A_hi B_lo + A_lo B_hi, about FP32 accuracy; BF16x3 writes x = hi + mid +
+// lo in BF16 and keeps the six products down to 2^-16.
 //
 // The monopole-log term of b'_0, sum_d M_0 (log|w0| + ln s), carries the largest part of phi; it
 // stays out of the GEMM (its (0, 0) operator entry is zero): k_prep_tc sums it in float-float
 // from the FP32 moment grid before the GEMM, in every mode, and the epilogue adds the GEMM's part
 // to it; a TF32 or BF16 product of a large M_0 with the log would lose more than the error bound
-// allows on clustered systems.  Every wait on
-// an mbarrier is bounded and sets a status flag when it runs out.
+// allows on clustered systems.
 
 #include <cuda_bf16.h>
 
@@ -46,7 +51,7 @@ constexpr int kTile = 128;        // targets per tile (MMA M)
 constexpr int kWin = kTile + 2;   // source cells per window
 constexpr int kThreads = 128;
 constexpr int kMinLevel = 6;      // coarser levels stay on the CUDA cores (see fmm_tc_kmin)
-constexpr int kMaxRows = 8;       // tiles per CTA: 8 accumulators of 64 columns fill tensor memory
+constexpr int kMaxRows = 8;       // tiles per CTA at most (also bounded by the 512 tensor-memory columns)
 constexpr int kSrcPad = 1024;     // cells after each source array: flat tiles past the last row read there
 constexpr unsigned kSpin = 1u << 24;
 
