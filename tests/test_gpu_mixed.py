@@ -60,6 +60,22 @@ def test_mixed_full_size_uniform_1m(oracle_mod):
     assert err < MIXED_TOL
 
 
+@pytest.mark.parametrize("precision,lev,p", [("fp32", 3, 30), ("3xtf32", 6, 20), ("bf16x3", 6, 20)])
+def test_single_particle_coincident_and_edges(oracle_mod, precision, lev, p):
+    """One particle: no far field and no pair, so phi is exactly 0.  Then particles on the corners
+    and edges of the box (x = 5 falls in the last square), a coincident pair (r^2 = 0 contributes
+    nothing) and an interior point, with the tensor-core levels in play for the split modes."""
+    from gpu_util import run_fmm
+    phi, _ = run_fmm(np.array([[2.0, 3.0]]), np.array([1.5]), lev, p, precision=precision)
+    assert phi[0] == 0.0
+    xy = np.array([[0.0, 0.0], [5.0, 5.0], [5.0, 0.0], [0.0, 5.0], [2.5, 2.5], [2.5, 2.5], [1.25, 3.75]])
+    q = np.array([1.0, -1.0, 0.5, 0.25, 2.0, -3.0, 0.75])
+    phi, _ = run_fmm(xy, q, lev, p, precision=precision)
+    err = rel_l2(phi, oracle_mod.shiftfree(xy, q, lev, p))
+    print(f"{precision} edges and duplicates, levels={lev} p={p}: rel L2 vs oracle {err:.3e}")
+    assert err < MIXED_TOL
+
+
 @pytest.mark.parametrize("precision,tol", [("3xtf32", MIXED_TOL), ("tf32", 1e-3), ("bf16x3", MIXED_TOL),
                                            ("bf16", 1e-2)])
 @pytest.mark.parametrize("case", [
@@ -68,7 +84,7 @@ def test_mixed_full_size_uniform_1m(oracle_mod):
     (200000, 8, 16, "annulus", 9),      # p = 16 (K = N = 48 with padding)
 ])
 def test_tensor_core_m2l_matches_oracle(oracle_mod, precision, tol, case):
-    """M2L of levels 7..8 on tcgen05 (TF32 / split 3xTF32, BF16 / split BF16x3), levels 2..6 on the
+    """M2L of levels 6..8 on tcgen05 (TF32 / split 3xTF32, BF16 / split BF16x3), levels 2..5 on the
     CUDA cores."""
     from gpu_util import run_fmm
     n, lev, p, fam, seed = case
@@ -102,8 +118,8 @@ def test_tensor_core_full_size_uniform_1m(oracle_mod, precision):
     (60000, 7, 20, "gmm", 15),          # 64-wide rows, the largest flat-tiled level
 ])
 def test_tensor_core_modes_coarse_levels(oracle_mod, precision, tol, case):
-    """Levels 2..6 on the CUDA cores (a warp per four targets); level 7 on tcgen05, whose 64-wide
-    parity sub-grid rows are read as one flat array of 128-target tiles."""
+    """Levels 2..5 on the CUDA cores; levels 6 and 7 on tcgen05, whose 32- and 64-wide parity
+    sub-grid rows are read as one flat array of 128-target tiles."""
     from gpu_util import run_fmm
     n, lev, p, fam, seed = case
     xy, q = getattr(inputs, fam)(n, inputs.config_seed(0, 300 + seed))
@@ -116,7 +132,7 @@ def test_tensor_core_modes_coarse_levels(oracle_mod, precision, tol, case):
 
 def test_crowded_squares_split_over_warps(oracle_mod):
     """Clustered charges (32 Gaussians, sigma down to 0.01) on a uniform tree: finest squares with
-    thousands of particles, whose near field is split into blocks of 32 targets over many warps."""
+    thousands of particles, whose near field is split into blocks of 24 targets over many warps."""
     from gpu_util import run_fmm
     xy, q = inputs.gmm(100000, inputs.config_seed(2, 7))
     phi, st = run_fmm(xy, q, 6, 16, precision="fp32")
