@@ -64,7 +64,7 @@ typedef enum {
 /* Arithmetic of the hot path.  FMM_FP64 runs every stage in FP64.  The mixed
  * modes run particle-side stages (P2M, L2P, P2P) in FP32 on coordinates local
  * to each square, keep the cross-level sum and the final phi in FP64, and run
- * M2L as stated: FP32 on the CUDA cores, or, for levels 7 and finer, on the
+ * M2L as stated: FP32 on the CUDA cores, or, for levels 6 and finer, on the
  * tensor cores (tcgen05) with FP32 accumulation in TF32 or BF16, where the x3
  * forms split each operand into parts to recover FP32-level accuracy
  * (3xTF32: hi + lo, three products; BF16x3: hi + mid + lo, six products).
@@ -104,7 +104,9 @@ typedef struct {
  *   n          1 <= n <= 2^31 - 1.
  *   levels     0 <= levels <= 12 (levels 0 and 1 have no far field: the
  *              interaction list exists from level 2, Sec. 2.1 item 5).
- *   p          1 <= p <= 40 (FP64 and mixed modes alike).
+ *   p          1 <= p <= 40 (FP64, FP32 and the batched form); the tensor-core
+ *              modes (TF32, 3xTF32, BF16, BF16x3) take p <= 31 and return
+ *              FMM_ERR_UNSUPPORTED above.
  *   box        side of the computation box (the paper's 5), > 0 and finite.
  *   precision  an fmm_precision value.
  *   stream     cudaStream_t to enqueue on (NULL = legacy default stream).
