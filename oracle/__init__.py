@@ -72,6 +72,7 @@ def _load():
             "oracle_l2l": (None, [vp, i32, d, d, vp]),
             "oracle_binom": (d, [i32, i32]),
             "oracle_interaction_list": (i32, [i32, i32, i32, vp, vp]),
+            "oracle_finest_squares": (i32, [i64, vp, i32, d, vp, vp]),
             "oracle_set_threads": (None, [i32]),
             "oracle_get_threads": (i32, []),
         }
@@ -208,6 +209,17 @@ def l2l(b, z0) -> np.ndarray:
 
 def binom(n: int, r: int) -> float:
     return float(_load().oracle_binom(n, r))
+
+
+def finest_squares(xy, levels: int, box: float = 5.0):
+    """(ix, iy) of each particle's finest square: floor(x 2^l / box) in FP64, in that order,
+    clamped to [0, 2^l - 1] (the tree of Sec. 2.1 items 1-4; points on an edge or on x = box
+    take the reading floor/clamp)."""
+    xy = _f64(xy).reshape(-1, 2)
+    ix = np.empty(xy.shape[0], dtype=np.int32)
+    iy = np.empty(xy.shape[0], dtype=np.int32)
+    _check(_load().oracle_finest_squares(xy.shape[0], _ptr(xy), int(levels), float(box), _ptr(ix), _ptr(iy)))
+    return ix, iy
 
 
 def interaction_list(bx: int, by: int, k: int):

@@ -316,6 +316,17 @@ static int finest_coord(double x, int levels, double box) {
     return (int)f;
 }
 
+/* The finest square of each particle by the rule above (Sec. 2.1 items 1-4 with the
+ * floor/clamp reading for points on an edge or on x = box): ix[i], iy[i] in [0, 2^l - 1]. */
+int oracle_finest_squares(int64_t n, const double *xy, int levels, double box, int *ix, int *iy) {
+    if (n < 0 || levels < 0 || levels > 12 || !(box > 0.0)) return ORACLE_ERR_ARG;
+    for (int64_t i = 0; i < n; ++i) {
+        ix[i] = finest_coord(xy[2 * i], levels, box);
+        iy[i] = finest_coord(xy[2 * i + 1], levels, box);
+    }
+    return ORACLE_OK;
+}
+
 static int tree_build(tree_t *t, int64_t n, const double *xy, int levels, int p, double box) {
     memset(t, 0, sizeof(*t));
     if (n < 0 || levels < 0 || levels > 12 || p < 1 || p > ORACLE_MAXP || !(box > 0.0)) return ORACLE_ERR_ARG;

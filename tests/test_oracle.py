@@ -167,6 +167,46 @@ def test_interaction_list_bruteforce(oracle_mod):
 
 # ---------------------------------------------------------------- whole method
 
+def _edge_points(levels, box, count, seed):
+    """Points on and one ulp either side of the square edges x = k box / 2^l, k = 0 .. 2^l."""
+    side = 1 << levels
+    k = (inputs.u01(seed, 0, count) * (side + 1)).astype(np.int64)
+    e = np.minimum(k * (box / side), box)
+    lo = np.maximum(np.nextafter(e, -np.inf), 0.0)
+    hi = np.minimum(np.nextafter(e, np.inf), box)
+    x = np.concatenate([e, lo, hi, [0.0, box]])
+    y = np.roll(x, 7)
+    return np.stack([x, y], axis=1)
+
+
+@pytest.mark.parametrize("levels,box", [(2, 5.0), (8, 5.0), (10, 5.0), (12, 5.0), (6, 4.0), (12, 3.0)])
+def test_finest_squares_against_exact_rationals(oracle_mod, levels, box):
+    """Binning (Sec. 2.1 items 1-4, read as floor(x 2^l / box) in FP64, clamped): against the exact
+    rational quotient.  Away from an integer by more than the FP64 division's rounding, the square is
+    floor of the exact quotient; within it, the quotient may round onto the integer, so either
+    neighbour is allowed.  x = box falls in the last square, x = 0 in the first; on a power-of-two box
+    every edge is exact and belongs to the square above it."""
+    from fractions import Fraction
+    side = 1 << levels
+    xy = np.concatenate([_edge_points(levels, box, 300, levels), inputs.uniform(500, 60 + levels)[0] * (box / 5.0)])
+    xy = np.minimum(xy, box)
+    ix, iy = oracle_mod.finest_squares(xy, levels, box)
+    fb = Fraction(box)
+    for v, got in zip(np.concatenate([xy[:, 0], xy[:, 1]]), np.concatenate([ix, iy])):
+        qx = Fraction(float(v)) * side / fb
+        fl = qx.numerator // qx.denominator
+        want = {min(max(fl, 0), side - 1)}
+        nearest = round(qx)
+        if abs(qx - nearest) <= Fraction(1, 1 << 50) * max(1, nearest):
+            want |= {min(max(nearest - 1, 0), side - 1), min(max(nearest, 0), side - 1)}
+        assert int(got) in want, (float(v), int(got), want)
+    assert oracle_mod.finest_squares(np.array([[box, 0.0]]), levels, box)[0][0] == side - 1
+    if box == 4.0:
+        k = np.arange(side)
+        e = k * (box / side)
+        assert np.array_equal(oracle_mod.finest_squares(np.stack([e, e], 1), levels, box)[0], k)
+
+
 def test_levels_0_and_1_are_the_direct_sum(oracle_mod):
     """No interaction lists exist above level 2, so the FMM is the near field alone (Sec. 2.1 item 5)."""
     xy, q = inputs.uniform(64, 21)
