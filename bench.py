@@ -6,7 +6,7 @@ M2L, L2P for every level, P2P + final phi in input order) through the C ABI
 call fmm_potential followed by fmm_sync, on inputs already resident in HBM.
 The default workload is 1,048,576 particles uniform in [0,5]^2, q ~ U[-1,1],
 a uniform quadtree of 8 levels and expansion order p = 20, computed in the
-mixed-precision form with the BF16x3 tensor-core M2L (the fastest form that
+mixed-precision form with the BF16x2 tensor-core M2L (the fastest form that
 meets the 1e-6 error bound); the plain FP64 GPU path is timed beside it.
 
 Timing: W warm-up steps, then exactly K steps timed with CUDA events on the
@@ -59,8 +59,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uniform_1m_l8_p20", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="bf16x3",
-                    help="fp32 (CUDA-core M2L), 3xtf32 / tf32 or bf16x3 / bf16 (tensor-core M2L from level 6), fp64")
+    ap.add_argument("--precision", default="bf16x2",
+                    help="fp32 (CUDA-core M2L), 3xtf32 / tf32 or bf16x3 / bf16x2 / bf16 (tensor-core M2L from "
+                         "level 6), fp64")
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=20)
@@ -153,8 +154,8 @@ def roofline_for(stage, stats, ms, w, peaks, sm_clock_mhz, precision, traffic):
                 "work_per_launch": f"{pairs} ordered pairs, one lg2 each"}
     if stage == "m2l":
         flops = m2l_pairs(w["levels"]) * 8 * p1 * p1
-        if precision in ("tf32", "3xtf32", "bf16", "bf16x3"):
-            # the stage runs levels >= 7 on the tensor cores and the coarser ones on the CUDA cores;
+        if precision in ("tf32", "3xtf32", "bf16", "bf16x2", "bf16x3"):
+            # the stage runs levels >= 6 on the tensor cores and the coarser ones on the CUDA cores;
             # algorithmic flops of all levels over the stage time, against the tensor peak of the
             # operand type (measured dense bf16; x the nominal TF32/BF16 ratio of 1/2 for TF32)
             bf = precision.startswith("bf16")
@@ -331,7 +332,7 @@ def run_ours(args):
                                                               args.steps, args.warmup, flush, stream)
     barrier()
     clk = clocks.stop()
-    ms_step = max_over_ranks(float(np.mean(ms)), dev)
+    ms_step = max_over_ranks(float(np.median(ms)), dev)   # the median step (mean reported beside it)
     value = job_rate(w["n"], ws, ms_step * 1e-3)
 
     # accuracy gate: FP64 direct sum at 4096 sampled targets (on the GPU)
@@ -392,7 +393,7 @@ def run_ours(args):
         p64, phi64, ms64, st64, l64, _, _ = time_plan(binding, torch, w, "fp64", xy_d, q_d, args.fp64_steps, 2,
                                                       flush, stream)
         err64 = float(torch.linalg.norm(phi64[idx_d] - ref) / torch.linalg.norm(ref))
-        m64 = max_over_ranks(float(np.mean(ms64)), dev)
+        m64 = max_over_ranks(float(np.median(ms64)), dev)
         fp64 = {"value": job_rate(w["n"], ws, m64 * 1e-3), "ms_per_step": m64, "rel_l2_err": err64,
                 "stage_ms": {k: float(np.mean(v)) for k, v in st64.items()}}
         p64.close()
@@ -409,7 +410,8 @@ def run_ours(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_step, "ms_per_step_mean": max_over_ranks(float(np.mean(ms)), dev),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
             "data": "synthetic (seeded SplitMix64: uniform positions in [0,5]^2, q ~ U[-1,1])",
             "config": {"workload": args.workload, "n": w["n"], "levels": w["levels"], "p": w["p"],
@@ -497,6 +499,23 @@ def run_batched(binding, torch, dev, nsys, steps, warmup):
 
 # ---------------------------------------------------------------- CPU oracle
 
+def cpu_model():
+    """The host CPU's model name (lscpu), for the CPU baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+        for line in out.splitlines():
+            if line.startswith("Vendor ID"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 def cpu_baseline(w, xy, q, max_runs=3, budget_s=30.0):
     """The oracle as it stands on the host cores: all threads, then one thread where a run fits the
     remaining budget (it reports `one_thread`, the same metric from a single core)."""
@@ -509,7 +528,7 @@ def cpu_baseline(w, xy, q, max_runs=3, budget_s=30.0):
         t_total += time.perf_counter() - t
         runs += 1
     cores = oracle.get_threads()
-    res = {"value": runs * w["n"] / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+    res = {"value": runs * w["n"] / t_total, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
            "sample": f"full workload (N={w['n']}, levels={w['levels']}, p={w['p']}), {runs} run(s) of the FP64 "
                      f"C oracle's shift-free FMM, OpenMP over independent outputs"}
     # one thread: expected about cores x the time of one all-core run
@@ -562,7 +581,7 @@ def run_reference(args):
             "config": {"workload": args.workload, "n": w["n"], "levels": w["levels"], "p": w["p"],
                        "precision": "fp64", "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-                             "sample": desc},
+                             "cpu_model": cpu_model(), "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

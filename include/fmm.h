@@ -67,7 +67,8 @@ typedef enum {
  * M2L as stated: FP32 on the CUDA cores, or, for levels 6 and finer, on the
  * tensor cores (tcgen05) with FP32 accumulation in TF32 or BF16, where the x3
  * forms split each operand into parts to recover FP32-level accuracy
- * (3xTF32: hi + lo, three products; BF16x3: hi + mid + lo, six products).
+ * (3xTF32: hi + lo, three products; BF16x2: hi + lo in BF16, three products;
+ * BF16x3: hi + mid + lo, six products).
  * Measured relative L2 error against the FP64 oracle at 2^20 uniform
  * particles, levels 8, p = 20: FP32 / 3xTF32 / BF16x3 about 2e-7, TF32 about
  * 3e-6, BF16 about 2e-5. */
@@ -77,7 +78,8 @@ typedef enum {
     FMM_MIXED_TF32 = 2,
     FMM_MIXED_3XTF32 = 3,
     FMM_MIXED_BF16 = 4,
-    FMM_MIXED_BF16X3 = 5
+    FMM_MIXED_BF16X3 = 5,
+    FMM_MIXED_BF16X2 = 6
 } fmm_precision;
 
 /* Per-call statistics of the last completed fmm_potential (valid after fmm_sync). */
@@ -105,7 +107,7 @@ typedef struct {
  *   levels     0 <= levels <= 12 (levels 0 and 1 have no far field: the
  *              interaction list exists from level 2, Sec. 2.1 item 5).
  *   p          1 <= p <= 40 (FP64, FP32 and the batched form); the tensor-core
- *              modes (TF32, 3xTF32, BF16, BF16x3) take p <= 31 and return
+ *              modes (TF32, 3xTF32, BF16, BF16x2, BF16x3) take p <= 31 and return
  *              FMM_ERR_UNSUPPORTED above.
  *   box        side of the computation box (the paper's 5), > 0 and finite.
  *   precision  an fmm_precision value.
@@ -141,6 +143,23 @@ fmm_status fmm_sync(fmm_plan_t plan);
 
 /* Copy the statistics of the last synced call into *out (host struct). */
 fmm_status fmm_plan_stats(fmm_plan_t plan, fmm_stats* out);
+
+/* The finest square each particle of the last fmm_potential call was binned into (Sec. 2.1
+ * items 1-4: ix = floor(x 2^levels / box) evaluated in FP64 in that order and clamped to
+ * [0, 2^levels - 1], likewise iy), as the Morton key ix_0 iy_0 ix_1 iy_1 ... (bit 2b of the key
+ * is bit b of ix, bit 2b + 1 is bit b of iy), in input order.
+ *   keys  device, uint32_t[n], owned by the caller.
+ * Asynchronous on the plan's stream (a device-to-device copy); allocates nothing.  Valid once
+ * a call has been enqueued; FMM_ERR_INVALID_ARG for a null pointer. */
+fmm_status fmm_leaf_keys(fmm_plan_t plan, uint32_t* keys);
+
+/* Error-path test hook (no counterpart in the paper): with enable != 0, later calls run the
+ * tensor-core M2L kernel with its copy producers switched off and its bounded mbarrier waits cut
+ * to 4096 polls, so its first wait runs out with no copy or MMA in flight; the kernel then stores
+ * nothing, frees its tensor memory and returns, phi is left unwritten and fmm_sync returns
+ * FMM_ERR_TIMEOUT.  enable = 0 restores normal calls.  FMM_ERR_UNSUPPORTED for a plan that runs
+ * no tensor-core level (an FP64 or FP32 plan, or levels < 6); FMM_ERR_INVALID_ARG for NULL. */
+fmm_status fmm_inject_timeout(fmm_plan_t plan, int enable);
 
 /* Free the plan and every device buffer it owns.  NULL is ignored. */
 void fmm_plan_destroy(fmm_plan_t plan);
@@ -266,7 +285,11 @@ fmm_status fmm_select(fmm_selector_t sel, const double* xy, int64_t n, double bo
  * memory belongs to another allocator, a plugin that may not own allocations -- and
  * fmm_plan allocates.  This entry point creates no plan and allocates nothing: its
  * workspaces live in one fixed device array of 8.5 MB inside libfmm.so, which every GPU
- * that loads the library reserves until the process exits.
+ * that loads the library reserves until the process exits.  The CUDA runtime reserves it
+ * when the library's module is loaded on a device; with lazy loading (the default) that is
+ * the first call of this entry point or of any library kernel there, so a caller whose
+ * allocator later claims the free memory should make one call before it does.  If that
+ * reservation fails the call returns FMM_ERR_OOM.
  *   n, levels, p, box   as for fmm_plan, FP64 only, limited to 1 <= n <= 65536,
  *                       0 <= levels <= 6 and 1 <= p <= 20; larger requests return
  *                       FMM_ERR_INVALID_ARG and touch nothing.
@@ -275,7 +298,8 @@ fmm_status fmm_select(fmm_selector_t sel, const double* xy, int64_t n, double bo
  * The call waits for `stream` and returns the device checks' status (phi is left unwritten
  * when a particle is outside the box or a value is not finite).  The first call on a device
  * looks up the array's device address and creates the stage events for that device; make
- * that first call before any stream capture.  Every call on a device shares the one array,
+ * that first call before any stream capture.  A CUDA error already pending on the calling
+ * thread is left for its owner: the call returns FMM_ERR_CUDA without clearing it.  Every call on a device shares the one array,
  * so calls that overlap on the GPU (other threads, other streams) race and must be
  * serialised by the caller. */
 fmm_status fmm_potential_noalloc(int64_t n, int levels, int p, double box, const double* xy,

@@ -31,9 +31,10 @@ FMM_MIXED_TF32 = 2
 FMM_MIXED_3XTF32 = 3
 FMM_MIXED_BF16 = 4
 FMM_MIXED_BF16X3 = 5
+FMM_MIXED_BF16X2 = 6
 
 PRECISIONS = {"fp64": FMM_FP64, "fp32": FMM_MIXED_FP32, "tf32": FMM_MIXED_TF32, "3xtf32": FMM_MIXED_3XTF32,
-              "bf16": FMM_MIXED_BF16, "bf16x3": FMM_MIXED_BF16X3}
+              "bf16": FMM_MIXED_BF16, "bf16x2": FMM_MIXED_BF16X2, "bf16x3": FMM_MIXED_BF16X3}
 
 # Every entry point include/fmm.h declares, with (restype, argtypes).
 _vp, _i64, _i32, _d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -58,6 +59,8 @@ SIGNATURES = {
     "fmm_potential_host": (_i32, [_vp, _vp, _vp, _vp]),
     "fmm_sync": (_i32, [_vp]),
     "fmm_plan_stats": (_i32, [_vp, ctypes.POINTER(fmm_stats)]),
+    "fmm_leaf_keys": (_i32, [_vp, _vp]),
+    "fmm_inject_timeout": (_i32, [_vp, _i32]),
     "fmm_plan_destroy": (None, [_vp]),
     "fmm_status_string": (ctypes.c_char_p, [_i32]),
     "fmm_direct_targets": (_i32, [_i64, _vp, _vp, _i64, _vp, _vp, _vp]),
@@ -176,6 +179,16 @@ def fmm_plan_stats(plan: int) -> dict:
     st = fmm_stats()
     _check(_lib.fmm_plan_stats(plan, ctypes.byref(st)), "fmm_plan_stats")
     return st.as_dict()
+
+
+def fmm_leaf_keys(plan: int, keys):
+    """Copy the last call's finest-square Morton keys (uint32, input order) into a device buffer."""
+    _check(_lib.fmm_leaf_keys(plan, _ptr(keys)), "fmm_leaf_keys")
+
+
+def fmm_inject_timeout(plan: int, enable: bool):
+    """Error-path test hook: make the tensor-core M2L's first bounded wait run out (see fmm.h)."""
+    _check(_lib.fmm_inject_timeout(plan, 1 if enable else 0), "fmm_inject_timeout")
 
 
 def fmm_plan_destroy(plan: int):
@@ -385,6 +398,14 @@ class Plan:
 
     def stats(self):
         return fmm_plan_stats(self.handle)
+
+    def leaf_keys(self):
+        """The last call's finest-square Morton keys (int32 tensor holding the uint32 bits)."""
+        import torch
+        keys = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        fmm_leaf_keys(self.handle, keys)
+        torch.cuda.synchronize()
+        return keys
 
     def close(self):
         if getattr(self, "handle", None):

@@ -48,7 +48,7 @@ void build_operators(int p, std::vector<cd>& T) {
         }
 }
 
-bool valid_precision(int v) { return v >= FMM_FP64 && v <= FMM_MIXED_BF16X3; }
+bool valid_precision(int v) { return v >= FMM_FP64 && v <= FMM_MIXED_BF16X2; }
 
 template <class T>
 fmm_status dev_alloc(fmm_plan_s* pl, T** ptr, size_t bytes) {
@@ -216,7 +216,7 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     if (cudaMemcpy(pl->T64, T.data(), sizeof(double2) * T.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         FMM_TRY(FMM_ERR_CUDA);
     if (precision == FMM_MIXED_TF32 || precision == FMM_MIXED_3XTF32 || precision == FMM_MIXED_BF16 ||
-        precision == FMM_MIXED_BF16X3) {
+        precision == FMM_MIXED_BF16X3 || precision == FMM_MIXED_BF16X2) {
         std::vector<double> tre(T.size()), tim(T.size());
         for (size_t i = 0; i < T.size(); ++i) {
             tre[i] = T[i].real();
@@ -344,6 +344,20 @@ fmm_status fmm_sync(fmm_plan_t plan) {
     if (f & FMM_FLAG_NONFINITE) return FMM_ERR_NONFINITE;
     if (f & FMM_FLAG_OUT_OF_BOX) return FMM_ERR_OUT_OF_BOX;
     if (f & FMM_FLAG_TIMEOUT) return FMM_ERR_TIMEOUT;
+    return FMM_OK;
+}
+
+fmm_status fmm_leaf_keys(fmm_plan_t plan, uint32_t* keys) {
+    if (!plan || !keys) return FMM_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    return cudaMemcpyAsync(keys, plan->keys, sizeof(uint32_t) * (size_t)plan->n, cudaMemcpyDeviceToDevice,
+                           plan->stream) == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
+}
+
+fmm_status fmm_inject_timeout(fmm_plan_t plan, int enable) {
+    if (!plan) return FMM_ERR_INVALID_ARG;
+    if (plan->tc == nullptr || plan->levels < fmm_tc_kmin()) return FMM_ERR_UNSUPPORTED;
+    plan->test_stall = enable != 0;
     return FMM_OK;
 }
 

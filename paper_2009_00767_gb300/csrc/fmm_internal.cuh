@@ -126,6 +126,7 @@ struct fmm_plan_s {
     int launches;
     fmm_stats last;
     uint64_t workspace_bytes;
+    int test_stall;       // fmm_inject_timeout: the tensor-core M2L's producers issue nothing
 };
 
 // --- Morton helpers ----------------------------------------------------------------------------

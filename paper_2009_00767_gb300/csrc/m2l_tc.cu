@@ -1,5 +1,5 @@
 // m2l_tc.cu -- M2L (D-bar-1 of Sec. 2.2.1) on the 5th-generation tensor cores (tcgen05) for the
-// levels from 6 down, in TF32 or BF16, unsplit or split (3xTF32, BF16x3), with FP32 accumulation
+// levels from 6 down, in TF32 or BF16, unsplit or split (3xTF32, BF16x2, BF16x3), with FP32 accumulation
 // in tensor memory.
 //
 // For one level k and one parity class c = (px, py) of target squares, the conversion of the
@@ -28,8 +28,9 @@
 // out.
 //
 // Split products: 3xTF32 (Ootomo & Yokota, 2022) writes x = x_hi + x_lo with x_hi rounded to TF32
-// and keeps A_hi B_hi + A_hi B_lo + A_lo B_hi, about FP32 accuracy; BF16x3 writes x = hi + mid +
-// lo in BF16 and keeps the six products down to 2^-16.
+// and keeps A_hi B_hi + A_hi B_lo + A_lo B_hi, about FP32 accuracy; BF16x2 does the same with two
+// BF16 parts (16 significant bits, the dropped lo lo term at 2^-16 of the product) at twice the
+// TF32 rate; BF16x3 writes x = hi + mid + lo in BF16 and keeps the six products down to 2^-16.
 //
 // The monopole-log term of b'_0, sum_d M_0 (log|w0| + ln s), carries the largest part of phi; it
 // stays out of the GEMM (its (0, 0) operator entry is zero): k_prep_tc sums it in float-float
@@ -53,7 +54,8 @@ constexpr int kThreads = 128;
 constexpr int kMinLevel = 6;      // coarser levels stay on the CUDA cores (see fmm_tc_kmin)
 constexpr int kMaxRows = 8;       // tiles per CTA at most (also bounded by the 512 tensor-memory columns)
 constexpr int kSrcPad = 1024;     // cells after each source array: flat tiles past the last row read there
-constexpr unsigned kSpin = 1u << 24;
+constexpr unsigned kSpin = 1u << 24;      // polls of a bounded wait (each poll may suspend briefly)
+constexpr unsigned kTestSpin = 1u << 12;  // the error-path test's limit
 
 struct TcGroup {
     int qx, qy, sy, nops, slot0;
@@ -79,6 +81,8 @@ struct TcArgs {
     int nseg, tiles, rows, tmem_cols;
     int levels, p;
     unsigned int* status;
+    unsigned spin;    // polls of a bounded mbarrier wait before it gives up
+    int stall;        // error-path test: the producers issue nothing, so the first wait runs out
 };
 
 // flat start (halo coordinates) of tile T of a parity sub-grid of width w2
@@ -99,8 +103,8 @@ __host__ __device__ __forceinline__ int tiles_of_level(int k) {
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity) {
-    for (unsigned it = 0; it < kSpin; ++it) {
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, unsigned spin) {
+    for (unsigned it = 0; it < spin; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred P;\n\t"
@@ -265,18 +269,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
         // operator producer: each group's operators (its offsets are consecutive slots) as soon
         // as the stage's previous group has been consumed; lane 0 posts the byte count, then the
         // lanes copy 16-byte-aligned slices in parallel
-        for (int g = 0; g < 12; ++g) {
+        int posted = 0;   // groups whose copies were issued
+        for (int g = 0; g < 12 && !a.stall; ++g) {
             const TcGroup& G = a.groups[cls][g];
             const int so = g % NSO, uso = g / NSO;
             const uint32_t bytes = (uint32_t)G.nops * OP_BYTES;
             if (lane == 0) {
-                if (g >= NSO && !wait_bar(su32(&ops_empty[so]), (uint32_t)((uso - 1) & 1))) ok = false;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&ops_full[so])),
-                             "r"(bytes)
-                             : "memory");
+                // a stage's arrival is posted only together with its copies
+                if (g >= NSO && !wait_bar(su32(&ops_empty[so]), (uint32_t)((uso - 1) & 1), a.spin))
+                    ok = false;
+                else
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                     su32(&ops_full[so])),
+                                 "r"(bytes)
+                                 : "memory");
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
+            posted = g + 1;
             const uint32_t units = bytes / 16u, per = (units + 31u) / 32u;
             const uint32_t u0 = min(units, (uint32_t)lane * per), u1 = min(units, u0 + per);
             if (u1 > u0) {
@@ -288,23 +298,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                     : "memory");
             }
         }
-        __syncwarp();
+        // before the CTA may exit: every copy issued has landed (each stage's last posted phase
+        // completes only after its earlier ones)
+        if (lane == 0)
+            for (int g = posted - NSO > 0 ? posted - NSO : 0; g < posted; ++g)
+                if (!wait_bar(su32(&ops_full[g % NSO]), (uint32_t)((g / NSO) & 1), a.spin)) ok = false;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
     } else if (warp == 0) {
         // window producer: lane 0 waits for a free stage and posts its byte count, then the lanes
         // issue the window's bulk copies in parallel (one K chunk of one part each); every copy
         // completes on the stage's full barrier, so the producer runs ahead of the MMAs
-        for (int i = 0; i < NWIN; ++i) {
+        int posted = 0;   // windows whose copies were issued
+        for (int i = 0; i < NWIN && !a.stall; ++i) {
             const int g = i / nrows, t = i % nrows;
             const TcGroup& G = a.groups[cls][g];
             const int sw = i % NSW, usw = i / NSW;
             if (lane == 0) {
-                if (i >= NSW && !wait_bar(su32(&win_empty[sw]), (uint32_t)((usw - 1) & 1))) ok = false;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&win_full[sw])),
-                             "r"((uint32_t)(NP * A_BYTES))
-                             : "memory");
+                if (i >= NSW && !wait_bar(su32(&win_empty[sw]), (uint32_t)((usw - 1) & 1), a.spin))
+                    ok = false;
+                else
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                     su32(&win_full[sw])),
+                                 "r"((uint32_t)(NP * A_BYTES))
+                                 : "memory");
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
+            posted = i + 1;
             if (lane < NP * KC) {
                 // chunk j of part `part` of the 130 cells from the window's flat start: 2080
                 // contiguous bytes (past a chunk's end it reads the next chunk or the zero pad,
@@ -322,7 +342,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                     : "memory");
             }
         }
-        __syncwarp();
+        if (lane == 0)
+            for (int i = posted - NSW > 0 ? posted - NSW : 0; i < posted; ++i)
+                if (!wait_bar(su32(&win_full[i % NSW]), (uint32_t)((i / NSW) & 1), a.spin)) ok = false;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
     } else if (warp == 1) {
         // MMA issuer: the whole warp runs the loop (waits, descriptors) in step, one elected lane
         // issues the MMAs and commits
@@ -331,9 +354,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
             const TcGroup& G = a.groups[cls][g];
             const int so = g % NSO, uso = g / NSO;
             const int sw = i % NSW, usw = i / NSW;
-            if (t == 0 && !wait_bar(su32(&ops_full[so]), (uint32_t)(uso & 1))) ok = false;
-            if (!wait_bar(su32(&win_full[sw]), (uint32_t)(usw & 1))) ok = false;
+            if (t == 0 && !wait_bar(su32(&ops_full[so]), (uint32_t)(uso & 1), a.spin)) ok = false;
+            if (ok && !wait_bar(su32(&win_full[sw]), (uint32_t)(usw & 1), a.spin)) ok = false;
             ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;   // nothing more is issued; the producers' own waits then run out
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // descriptors: the window's and the group's base descriptors once, then constant
             // offsets in 16-byte units on the start-address field (shared addresses stay below
@@ -342,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
             const uint64_t bDesc = smem_desc(su32(ops_buf + so * OPS_STAGE), ROWS * 16, 128);
             const uint32_t acc_t = tmem + (uint32_t)t * ACC_COLS;
             const int nops = G.nops;
-            for (int o = 0; o < nops && ok; ++o) {
+            for (int o = 0; o < nops; ++o) {
                 const uint64_t ad0 = aDesc + (uint64_t)(1 + G.sx[o]);   // column shift: one 16-byte cell
                 const uint64_t bd0 = bDesc + (uint64_t)(o * (OP_BYTES / 16));
                 const uint32_t acc0 = (g | o) != 0;
@@ -361,11 +385,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
             commit_elect(su32(&win_empty[sw]));
             if (t == nrows - 1) commit_elect(su32(&ops_empty[so]));
         }
-        // the final commit tracks every MMA issued above
+        // the final commit tracks every MMA issued above (it arrives at once if none was)
         commit_elect(su32(done_bar));
         __syncwarp();
     }
-    if (!ok) atomicOr(a.status, FMM_FLAG_TIMEOUT);
     // warp w holds accumulator rows (targets) 32w..32w+31 of every tile: each thread's targets,
     // and the monopole-log part of their Re b'_0 that k_prep_tc left in B, loaded while the MMAs
     // run (kept in registers: the tile loops are unrolled over kMaxRows)
@@ -387,13 +410,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
             }
         }
     }
-    const bool done = wait_bar(su32(done_bar), 0);
+    // Every issued copy has landed (the producers waited for them); the MMAs are done once
+    // done_bar completes.  If any wait of the CTA ran out, nothing is read back or stored.
+    const bool done = wait_bar(su32(done_bar), 0, a.spin);
+    const bool fail = __syncthreads_or(!ok || !done) != 0;
+    if (fail && threadIdx.x == 0) atomicOr(a.status, FMM_FLAG_TIMEOUT);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     // ---- epilogue
 #pragma unroll
     for (int t = 0; t < kMaxRows; ++t) {
-        if (t >= nrows) break;
+        if (t >= nrows || fail) break;
         constexpr int SW = stack_width(NP);
         float v[SW * N];
 #pragma unroll
@@ -404,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
 #pragma unroll
             for (int c = 0; c < N; ++c) v[c] += v[N + c];   // the column blocks of the stacked products
         }
-        if (done && bt[t] != nullptr) {
+        if (bt[t] != nullptr) {
             // Re b'_0: the GEMM's part added to the monopole-log term
             float2* B = bt[t];
             B[0] = ff_add_f(b0[t], v[0]);
@@ -415,7 +442,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    if (warp == 0) {
+        // MMAs still in flight after a wait that ran out: one more bounded wait before the
+        // tensor memory they write is freed
+        if (fail) wait_bar(su32(done_bar), 0, a.spin);
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
 }
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -594,10 +626,13 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
     const int p1 = pl->p + 1;
     const int H = ((p1 + 7) / 8) * 8;
     if (H != 8 && H != 16 && H != 24 && H != 32) return -2;
-    const bool bf = pl->precision == FMM_MIXED_BF16 || pl->precision == FMM_MIXED_BF16X3;
+    const bool bf = pl->precision == FMM_MIXED_BF16 || pl->precision == FMM_MIXED_BF16X2 ||
+                    pl->precision == FMM_MIXED_BF16X3;
     const int kc = bf ? H / 4 : H / 2;
     const int per = bf ? 8 : 4, elem = bf ? 2 : 4;
-    const int np = pl->precision == FMM_MIXED_3XTF32 ? 2 : (pl->precision == FMM_MIXED_BF16X3 ? 3 : 1);
+    const int np = (pl->precision == FMM_MIXED_3XTF32 || pl->precision == FMM_MIXED_BF16X2)
+                       ? 2
+                       : (pl->precision == FMM_MIXED_BF16X3 ? 3 : 1);
     FmmTc* tc = new FmmTc();
     memset(tc, 0, sizeof(FmmTc));
     tc->h = H;
@@ -742,6 +777,8 @@ static int launch_tc(fmm_plan_s* pl, const MixedLevels& lv) {
     a.levels = L;
     a.p = pl->p;
     a.status = pl->d_status;
+    a.spin = pl->test_stall ? kTestSpin : kSpin;
+    a.stall = pl->test_stall;
     // the tiles of a class, finest level first; rows per CTA so that the four classes fill the
     // SMs about once (at most kMaxRows: more tiles make more waves)
     int tiles = 0, nseg = 0;
@@ -781,7 +818,9 @@ int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv) {
     if (!tc || pl->levels < kMinLevel) return 0;
 #define FMM_TC_CASES(H)                                                                                     \
     case H:                                                                                                 \
-        if (tc->bf) return tc->np == 3 ? launch_tc<H, true, 3>(pl, lv) : launch_tc<H, true, 1>(pl, lv);    \
+        if (tc->bf)                                                                                         \
+            return tc->np == 3 ? launch_tc<H, true, 3>(pl, lv)                                              \
+                               : (tc->np == 2 ? launch_tc<H, true, 2>(pl, lv) : launch_tc<H, true, 1>(pl, lv)); \
         return tc->np == 2 ? launch_tc<H, false, 2>(pl, lv) : launch_tc<H, false, 1>(pl, lv);
     switch (tc->h) {
         FMM_TC_CASES(8)

@@ -712,7 +712,7 @@ int fmm_m2l_bucket(int p1) {
 
 int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     if (pl->precision != FMM_MIXED_FP32 && pl->precision != FMM_MIXED_TF32 && pl->precision != FMM_MIXED_3XTF32 &&
-        pl->precision != FMM_MIXED_BF16 && pl->precision != FMM_MIXED_BF16X3)
+        pl->precision != FMM_MIXED_BF16 && pl->precision != FMM_MIXED_BF16X3 && pl->precision != FMM_MIXED_BF16X2)
         return -2;
     // in the tensor-core modes the tensor-core M2L takes the levels from fmm_tc_kmin() on
     const bool use_tc = pl->tc != nullptr && pl->levels >= fmm_tc_kmin();

@@ -6,8 +6,11 @@
 // that shares a device with an allocator that owns all free memory (a framework's caching
 // pool), or a plugin that may not create allocations of its own.  fmm_potential needs a plan,
 // and fmm_plan allocates; this entry point needs none.  Its scratch is the static array below,
-// which the CUDA runtime reserves on every device when the library's module is loaded there
-// and keeps until the process exits.
+// which the CUDA runtime reserves on a device when the library's module is loaded there and
+// keeps until the process exits.  With lazy module loading (the CUDA default) that happens at
+// the first use of the library on the device -- this entry point's first call, or the first
+// library kernel -- so a caller whose allocator claims the free memory later should make one
+// call first.
 //
 // Host code sees `g_noalloc_scratch` only as a host-side stand-in symbol, not as a device
 // address: a kernel handed that name faults or, where the GPU can reach host memory, uses the
@@ -114,9 +117,19 @@ fmm_status setup(int dev, void** scratch, cudaEvent_t** events) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
         void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return FMM_ERR_CUDA;
+        const cudaError_t r = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (r != cudaSuccess || !ptr) {
+            // the module (and with it the array) could not be loaded on this device
+            return r == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA;
+        }
         for (int e = 0; e < 6; ++e)
-            if (cudaEventCreate(&g_events[dev][e]) != cudaSuccess) return FMM_ERR_CUDA;
+            if (cudaEventCreate(&g_events[dev][e]) != cudaSuccess) {
+                for (int f = 0; f < e; ++f) {   // a later call starts the set-up again
+                    cudaEventDestroy(g_events[dev][f]);
+                    g_events[dev][f] = nullptr;
+                }
+                return FMM_ERR_CUDA;
+            }
         g_scratch_ptr[dev] = ptr;
     }
     *scratch = g_scratch_ptr[dev];
@@ -156,8 +169,10 @@ extern "C" fmm_status fmm_potential_noalloc(int64_t n, int levels, int p, double
         cudaMemsetAsync(pl.d_counters, 0, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long), st) != cudaSuccess)
         return FMM_ERR_CUDA;
     const int nops = 49 * (p + 1) * (p + 1);
+    // an error left pending by the caller's own earlier work is not this call's to report or clear
+    if (cudaPeekAtLastError() != cudaSuccess) return FMM_ERR_CUDA;
     k_build_ops_f64<<<(nops + 255) / 256, 256, 0, st>>>(p, pl.T64);
-    if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) return FMM_ERR_CUDA;
     cudaEventRecord(pl.ev[0], st);
     if (fmm_launch_sort(&pl, xy, q) < 0 || fmm_launch_fp64(&pl, phi) < 0) return FMM_ERR_CUDA;
 

@@ -31,7 +31,7 @@ from . import binding, inputs
 FALLBACK = (8, 20)
 P_GRID = (8, 12, 16, 20, 24, 28, 32)
 DEFAULT_PRECISION = "fp32"
-TENSOR_CORE = ("tf32", "3xtf32", "bf16", "bf16x3")   # these take p + 1 <= 32 coefficients
+TENSOR_CORE = ("tf32", "3xtf32", "bf16", "bf16x2", "bf16x3")   # these take p + 1 <= 32 coefficients
 LOG10_SCALE = 8.0           # the network predicts log10(error) / 8
 ERR_FLOOR = 1e-8            # errors below this are labelled at the floor
 

@@ -7,7 +7,7 @@ L2), and against the single-system mixed path.
 import numpy as np
 import pytest
 
-from conftest import rel_l2
+from conftest import check_parity
 from paper_2009_00767_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -48,9 +48,7 @@ def test_batch_matches_oracle_per_system(oracle_mod):
     off = np.concatenate([[0], np.cumsum(n)])
     for i, (ni, li, fam) in enumerate(SPEC):
         ref = oracle_mod.shiftfree(xys[i], qs[i], li, 12)
-        err = rel_l2(phi[off[i]:off[i + 1]], ref)
-        print(f"batch system {i}: N={ni} levels={li} {fam}: rel L2 {err:.3e}")
-        assert err < MIXED_TOL
+        check_parity(phi[off[i]:off[i + 1]], ref, MIXED_TOL, f"batch system {i}: N={ni} levels={li} {fam}")
 
 
 def test_batch_equals_single_plans_and_survives_autotune():
@@ -69,11 +67,11 @@ def test_batch_equals_single_plans_and_survives_autotune():
         g = binding.fmm_batch_autotune(b.handle, xy, q, phi)
         assert g in (1, 2, 4, 8, 16)
         second = b.potential(xy, q).cpu().numpy()
-    assert rel_l2(second, first) < MIXED_TOL
+    check_parity(second, first, MIXED_TOL, "batch after autotune vs before")
     for i in range(len(spec)):
         with binding.Plan(n[i], lev[i], 16, 5.0, "fp32") as plan:
             single = plan.potential(xy[off[i]:off[i + 1]].contiguous(), q[off[i]:off[i + 1]].contiguous()).cpu().numpy()
-        assert rel_l2(second[off[i]:off[i + 1]], single) < MIXED_TOL
+        check_parity(second[off[i]:off[i + 1]], single, MIXED_TOL, f"batch system {i} vs its single-system plan")
 
 
 def test_batch_device_checks():
