@@ -130,75 +130,90 @@ def m2l_pairs(levels, kmin=2):
 TC_KMIN = 6   # the tensor-core M2L takes levels 6 and finer
 
 
+TC_PRECISIONS = ("tf32", "3xtf32", "bf16", "bf16x2", "bf16x3")
+
+
+def _tensor_peak(peaks, precision):
+    bf = precision.startswith("bf16")
+    peak = peaks.get("bf16_tflops", 1939.8) / (1.0 if bf else 2.0)
+    basis = "measured bf16 dense (MEASURED_PEAKS.json)" + ("" if bf else " x the nominal TF32/BF16 ratio 1/2")
+    return peak, basis
+
+
 def roofline_for(stage, stats, ms, w, peaks, sm_clock_mhz, precision, traffic):
+    """Roofline of one kernel (or stage) from its device time `ms`: algorithmic work per launch over
+    the time, against the measured (or derived) peak of the unit that bounds it.  Particle stages
+    (P2M, L2P) carry both their FP32-FMA fraction and their HBM fraction."""
+    if ms <= 0:
+        return None
     p1 = w["p"] + 1
-    n = w["n"]
-    if stage == "m2l_tc":
-        # the tensor-core kernel alone: algorithmic flops of its levels (split products not counted)
-        # against the tensor peak of the operand type
-        flops = m2l_pairs(w["levels"], TC_KMIN) * 8 * p1 * p1
-        bf = precision.startswith("bf16")
-        peak = peaks.get("bf16_tflops", 1939.8) / (1.0 if bf else 2.0)
-        ach = flops / (ms * 1e-3) / 1e12
-        return {"kernel": "k_m2l_tc", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": traffic,
-                "peak_basis": "measured bf16 dense (MEASURED_PEAKS.json)" + ("" if bf else " x 1/2 for TF32"),
-                "work_per_launch": f"{flops:.4g} flop = IL pairs of levels {TC_KMIN}..{w['levels']} x 8 (p+1)^2"}
-    if stage == "p2p_kernel":
+    n, L = w["n"], w["levels"]
+    fma_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_clock_mhz * 1e6 / 1e12
+    fma_basis = f"FP32 FMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_clock_mhz:.0f} MHz"
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    sec = ms * 1e-3
+
+    def out(kernel, bound, ach, peak, unit, work, **extra):
+        d = {"kernel": kernel, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+             "traffic": traffic, "work_per_launch": work, "ms": ms}
+        d.update(extra)
+        return d
+
+    def grid_bytes(k0, k1, per_cell):
+        return sum(((1 << k) ** 2) * per_cell for k in range(max(2, k0), k1 + 1))
+
+    if stage in ("m2l_tc", "m2l_fine") and precision in TC_PRECISIONS:
+        flops = m2l_pairs(L, TC_KMIN) * 8 * p1 * p1
+        peak, basis = _tensor_peak(peaks, precision)
+        name = "k_m2l_tc" if stage == "m2l_tc" else "k_prep_tc + k_m2l_tc"
+        return out(name, "tensor", flops / sec / 1e12, peak, "TFLOP/s",
+                   f"{flops:.4g} flop = IL pairs of levels {TC_KMIN}..{L} x 8 (p+1)^2 (split products not counted)",
+                   peak_basis=basis)
+    if stage in ("m2l_coarse", "m2l_fine", "m2l"):
+        k0, k1 = (2, min(L, 5)) if stage == "m2l_coarse" else ((6, L) if stage == "m2l_fine" else (2, L))
+        flops = m2l_pairs(L, k0) * 8 * p1 * p1 - (m2l_pairs(L, k1 + 1) * 8 * p1 * p1 if k1 < L else 0)
+        if precision == "fp64":
+            return None
+        return out({"m2l_coarse": "k_m2l_coarse", "m2l_fine": "k_m2l_f32", "m2l": "m2l"}[stage], "alu",
+                   flops / sec / 1e12, fma_peak, "TFLOP/s", f"{flops:.4g} flop = IL pairs of levels {k0}..{k1} x 8 (p+1)^2",
+                   peak_basis=fma_basis)
+    if stage in ("p2p_kernel", "p2p"):
         pairs = stats["p2p_pairs"]
         peak = N_SMS * MUFU_PER_SM * sm_clock_mhz * 1e6 / 1e12   # Tlg2/s
-        ach = pairs / (ms * 1e-3) / 1e12
-        return {"kernel": "k_p2p_mixed", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tlg2/s",
-                "frac": ach / peak, "traffic": traffic,
-                "peak_basis": f"MUFU lg2: {N_SMS} SMs x {MUFU_PER_SM}/clk x {sm_clock_mhz:.0f} MHz",
-                "work_per_launch": f"{pairs} ordered pairs, one lg2 each"}
-    if stage == "m2l":
-        flops = m2l_pairs(w["levels"]) * 8 * p1 * p1
-        if precision in ("tf32", "3xtf32", "bf16", "bf16x2", "bf16x3"):
-            # the stage runs levels >= 6 on the tensor cores and the coarser ones on the CUDA cores;
-            # algorithmic flops of all levels over the stage time, against the tensor peak of the
-            # operand type (measured dense bf16; x the nominal TF32/BF16 ratio of 1/2 for TF32)
-            bf = precision.startswith("bf16")
-            peak = peaks.get("bf16_tflops", 1939.8) / (1.0 if bf else 2.0)
-            ach = flops / (ms * 1e-3) / 1e12
-            return {"kernel": "m2l", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": traffic,
-                    "peak_basis": "measured bf16 dense (MEASURED_PEAKS.json)" + ("" if bf else " x 1/2 for TF32"),
-                    "work_per_launch": f"{flops:.4g} flop = IL pairs x 8 (p+1)^2 (split products not counted)"}
-        if precision in ("fp32", "fp64"):
-            lanes = FP32_LANES_PER_SM if precision == "fp32" else None
-            if lanes is None:
-                return None
-            peak = N_SMS * lanes * 2 * sm_clock_mhz * 1e6 / 1e12
-            ach = flops / (ms * 1e-3) / 1e12
-            return {"kernel": "m2l", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": traffic,
-                    "peak_basis": f"FP32 FMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_clock_mhz:.0f} MHz",
-                    "work_per_launch": f"{flops:.4g} flop = IL pairs x 8 (p+1)^2"}
-    if stage == "p2p":
-        pairs = stats["p2p_pairs"]
-        peak = N_SMS * MUFU_PER_SM * sm_clock_mhz * 1e6 / 1e12   # Tlg2/s
-        ach = pairs / (ms * 1e-3) / 1e12
-        return {"kernel": "p2p", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tlg2/s",
-                "frac": ach / peak, "traffic": traffic,
-                "peak_basis": f"MUFU lg2: {N_SMS} SMs x {MUFU_PER_SM}/clk x {sm_clock_mhz:.0f} MHz",
-                "work_per_launch": f"{pairs} ordered pairs, one lg2 each"}
-    if stage in ("p2m", "l2p") and precision != "fp64":
-        # FP32 power chains / Horner: 8p flops per particle per level (levels 2..L), against the
-        # FP32 FMA peak
-        flops = 8 * w["p"] * n * (w["levels"] - 1)
-        peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_clock_mhz * 1e6 / 1e12
-        ach = flops / (ms * 1e-3) / 1e12
-        return {"kernel": stage, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": traffic,
-                "peak_basis": f"FP32 FMA: {N_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_clock_mhz:.0f} MHz",
-                "work_per_launch": f"{flops:.4g} flop = 8p per particle per level, levels 2..{w['levels']}"}
+        return out("k_p2p_mixed" if stage == "p2p_kernel" else "p2p", "alu", pairs / sec / 1e12, peak, "Tlg2/s",
+                   f"{pairs} ordered pairs, one lg2 each (the survey's unit; the symmetric kernel evaluates the "
+                   f"forward-neighbour pairs once for both sides, about 0.56 lg2 per ordered pair)",
+                   peak_basis=f"MUFU lg2: {N_SMS} SMs x {MUFU_PER_SM}/clk x {sm_clock_mhz:.0f} MHz")
+    if stage in ("p2m_fine", "p2m_coarse", "l2p", "p2m") and precision != "fp64":
+        if stage == "p2m_fine":
+            lev = range(max(2, L - 2), L + 1)
+            nbytes = 16 * n + grid_bytes(L - 2, L, p1 * 8)
+            what = "16 B particle in, FP32 moment grids out"
+        elif stage == "p2m_coarse":
+            lev = range(2, L - 2)
+            nbytes = 20 * n + grid_bytes(2, L - 3, p1 * 24)
+            what = "16 B particle + 4 B key in, FP64 + FP32 moment grids"
+        elif stage == "l2p":
+            lev = range(2, L + 1)
+            nbytes = 44 * n + grid_bytes(2, L, p1 * 8)
+            what = "16 B particle + 4 B key + 8 B near in, 8 B phi + 8 B near reset out, local grids in"
+        else:
+            lev = range(2, L + 1)
+            nbytes = 20 * n
+            what = "particles in"
+        flops = 8 * w["p"] * n * len(lev)
+        if flops == 0:
+            return None
+        ach_b = nbytes / sec / 1e9
+        return out(stage, "alu", flops / sec / 1e12, fma_peak, "TFLOP/s",
+                   f"{flops:.4g} flop = 8p per particle per level, {len(lev)} levels", peak_basis=fma_basis,
+                   hbm={"achieved": ach_b, "peak": hbm, "unit": "GB/s", "frac": ach_b / hbm,
+                        "bytes": nbytes, "what": what})
     # sort (and the FP64 path's P2M / L2P): HBM bytes per launch
-    nbytes = {"sort": n * (24 + 4 + 4 + 4 + 4 + 16 + 4 + 24), "p2m": n * 20, "l2p": n * (20 + 8)}[stage]
-    ach = nbytes / (ms * 1e-3) / 1e9
-    peak = peaks.get("hbm_gbs", 6800.0)
-    return {"kernel": stage, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": traffic, "work_per_launch": f"{nbytes} bytes"}
+    nbytes = {"sort": n * (24 + 4 + 4 + 4 + 4 + 16 + 4 + 24), "p2m": n * 20, "l2p": n * (20 + 8)}.get(stage)
+    if nbytes is None:
+        return None
+    return out(stage, "hbm", nbytes / sec / 1e9, hbm, "GB/s", f"{nbytes} bytes")
 
 
 # ---------------------------------------------------------------- clocks
@@ -278,7 +293,8 @@ def time_plan(binding, torch, w, precision, xy_d, q_d, steps, warmup, flush, str
         binding.fmm_potential(plan.handle, xy_d, q_d, phi)
         plan.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    stage_ms = {k: [] for k in ("sort", "p2m", "m2l", "l2p", "p2p", "m2l_tc", "p2p_kernel")}
+    stage_ms = {k: [] for k in ("sort", "p2m", "m2l", "l2p", "p2p", "m2l_tc", "p2p_kernel", "p2m_fine", "p2m_coarse",
+                                "m2l_fine", "m2l_coarse")}
     launches = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -296,6 +312,32 @@ def time_plan(binding, torch, w, precision, xy_d, q_d, steps, warmup, flush, str
     wall = time.perf_counter() - t0
     ms = [a.elapsed_time(b) for a, b in ev]
     return plan, phi, ms, stage_ms, launches, wall, st
+
+
+KERNELS_ALONE = ("sort", "p2m_fine", "p2m_coarse", "m2l_coarse", "m2l_fine", "m2l_tc", "p2p_kernel", "l2p")
+
+
+def time_kernels_alone(binding, torch, plan, xy_d, q_d, phi, steps, warmup, flush, stream):
+    """Each kernel's device time with the stages run one after the other on the plan's stream
+    (fmm_set_concurrency(plan, 1)); the timed step overlaps them on three streams, where a kernel's
+    own span also holds the time it waits for SMs the others hold.  Medians over `steps` calls, L2
+    flushed before each."""
+    binding.fmm_set_concurrency(plan.handle, 1)
+    rec = {k: [] for k in KERNELS_ALONE + ("total",)}
+    try:
+        for i in range(warmup + steps):
+            flush.zero_()
+            binding.fmm_potential(plan.handle, xy_d, q_d, phi)
+            plan.sync()
+            if i < warmup:
+                continue
+            st = plan.stats()
+            for k in KERNELS_ALONE:
+                rec[k].append(st["ms_" + k])
+            rec["total"].append(st["ms_total"])
+    finally:
+        binding.fmm_set_concurrency(plan.handle, 3)
+    return {k: float(np.median(v)) for k, v in rec.items()}
 
 
 def run_ours(args):
@@ -346,27 +388,39 @@ def run_ours(args):
     got = phi[idx_d]
     err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
 
-    # per-stage device times, the two kernels the library times alone, and the dominant one's
-    # roofline (a single kernel where one is timed alone, else the stage)
-    stage_avg = {k: float(np.mean(stage_ms[k])) for k in ("sort", "p2m", "m2l", "l2p", "p2p")}
+    # per-stage device times in the timed (overlapped) step, each kernel's time alone from a serial
+    # pass, and the rooflines from the times alone (the dominant kernel: the longest alone)
+    stage_avg = {k: float(np.mean(stage_ms[k])) for k in ("sort", "p2m", "m2l", "l2p", "p2p", "p2m_fine", "p2m_coarse",
+                                                          "m2l_fine", "m2l_coarse")}
     kern_avg = {k: float(np.mean(stage_ms[k])) for k in ("m2l_tc", "p2p_kernel")}
-    cands = {k: stage_avg[k] for k in ("sort", "p2m", "l2p")}
-    cands.update({"m2l_tc": kern_avg["m2l_tc"]} if kern_avg["m2l_tc"] > 0 else {"m2l": stage_avg["m2l"]})
-    cands.update({"p2p_kernel": kern_avg["p2p_kernel"]} if kern_avg["p2p_kernel"] > 0 else {"p2p": stage_avg["p2p"]})
-    # the dominant kernel: among the kernels the library times alone where it does (the stage
-    # times hold several kernels, and the P2M stage's also the near field running beside it on the
-    # second stream), else among the stages
-    single = {k: v for k, v in cands.items() if k in ("m2l_tc", "p2p_kernel")}
-    dom = max(single or cands, key=(single or cands).get)
+    alone = None
+    if args.precision != "fp64":
+        alone = time_kernels_alone(binding, torch, plan, xy_d, q_d, phi, max(5, min(args.steps, 50)), 3, flush,
+                                   stream)
+        cands = {k: alone[k] for k in KERNELS_ALONE if alone[k] > 0}
+    else:
+        cands = {k: stage_avg[k] for k in ("sort", "p2m", "m2l", "l2p", "p2p")}
+    # the dominant kernel: the longest single kernel timed alone (the sort, the coarse P2M and the
+    # fine M2L stage are several kernels each)
+    singles = [k for k in ("p2m_fine", "m2l_coarse", "m2l_tc", "p2p_kernel", "l2p") if k in cands]
+    dom = max(singles or [k for k in cands if k != "sort"], key=cands.get)
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    roof = roofline_for(dom, last, cands[dom], w, peaks, sm_max, args.precision, load_traffic(dom))
-    roof_all = {k: roofline_for(k, last, v, w, peaks, sm_max, args.precision, load_traffic(k)) for k, v in cands.items()}
+    in_step = dict(stage_avg, m2l_tc=kern_avg["m2l_tc"], p2p_kernel=kern_avg["p2p_kernel"], l2p=stage_avg["l2p"])
+    roof_all = {}
+    for k, v in cands.items():
+        r = roofline_for(k, last, v, w, peaks, sm_max, args.precision, load_traffic(k))
+        if r is not None:
+            r["timing"] = "kernel alone (serial pass, CUDA events)" if alone else "stage in the timed step"
+            if k in in_step:
+                r["in_step_ms"] = in_step[k]
+            roof_all[k] = r
+    roof = roof_all.get(dom)
     # the arithmetic units measured by the library's own probes (a few ms, after the timed region),
     # beside the peaks derived from unit counts and the maximum clock
     probe = {"fp32_tflops": binding.fmm_probe_peak(binding.FMM_PROBE_FP32_FMA) / 1e12,
              "mufu_tlg2_per_s": binding.fmm_probe_peak(binding.FMM_PROBE_MUFU_LG2) / 1e12,
              "fp64_tflops": binding.fmm_probe_peak(binding.FMM_PROBE_FP64_FMA) / 1e12}
-    for r in [roof] + list(roof_all.values()):
+    for r in roof_all.values():
         if r and r.get("bound") == "alu":
             r["peak_probe"] = probe["mufu_tlg2_per_s"] if r["unit"] == "Tlg2/s" else probe["fp32_tflops"]
 
@@ -418,7 +472,8 @@ def run_ours(args):
                        "precision": args.precision, "parallelism": f"replicas x{ws}",
                        "l2": "256 MB buffer written between timed steps (outside the events)"},
             "rel_l2_err": err, "meets_error_bound": err <= ERR_BOUND,
-            "stage_ms": stage_avg, "kernel_ms": kern_avg, "roofline": roof, "roofline_stages": roof_all,
+            "stage_ms": stage_avg, "kernel_ms": kern_avg, "kernel_ms_alone": alone, "roofline": roof,
+            "roofline_stages": roof_all,
             "gpu_launches": launches, "e2e": e2e, "fp64_gpu": fp64, "alu_peaks_probe": probe,
             "speedup_vs_fp64_gpu": (value / fp64["value"]) if fp64 else None,
             "cpu_baseline": cpu, "batched": batched, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],

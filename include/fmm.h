@@ -98,6 +98,14 @@ typedef struct {
     uint64_t workspace_bytes;  /* device memory the plan owns */
     double ms_m2l_tc;          /* the tensor-core M2L kernel alone (0 when none ran) */
     double ms_p2p_kernel;      /* the mixed path's near-field kernel alone (0 when none ran) */
+    /* Mixed path: after the fine levels' P2M the near field, the coarse levels' chain (P2M of
+     * levels 2..levels-3, its FP32 conversion, M2L of levels 2..5) and the fine levels' M2L run
+     * on three streams at once, so ms_p2m and ms_m2l above are sums of these spans and the
+     * stages overlap in time.  FP64 path: ms_m2l_fine = ms_m2l, the others 0. */
+    double ms_p2m_fine;        /* P2M of the finest three levels */
+    double ms_p2m_coarse;      /* P2M of the coarser levels and their FP32 conversion */
+    double ms_m2l_fine;        /* M2L of levels 6 and finer (tensor-core prep + kernel, or FP32) */
+    double ms_m2l_coarse;      /* M2L of levels 2..5 on the CUDA cores */
 } fmm_stats;
 
 /* Create a plan for exactly n particles, a quadtree of depth `levels` over
@@ -118,6 +126,13 @@ typedef struct {
  * FMM_ERR_CUDA on failure. */
 fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box,
                     int precision, void* stream);
+
+/* How many streams a mixed-precision call spreads its work over: 3 (the default: after the
+ * fine levels' P2M the near field, the coarse levels' chain and the fine levels' M2L run at
+ * once on the plan's stream and two streams of its own, joined back before L2P) or 1 (every
+ * kernel in turn on the plan's stream, so that fmm_plan_stats times each kernel alone).  The
+ * results are the same either way.  FMM_ERR_INVALID_ARG for another count or a NULL plan. */
+fmm_status fmm_set_concurrency(fmm_plan_t plan, int streams);
 
 /* Change the stream later calls enqueue on. */
 fmm_status fmm_set_stream(fmm_plan_t plan, void* stream);

@@ -46,7 +46,9 @@ class fmm_stats(ctypes.Structure):
                 ("ms_m2l", ctypes.c_double), ("ms_l2p", ctypes.c_double), ("ms_p2p", ctypes.c_double),
                 ("p2p_pairs", ctypes.c_int64), ("max_leaf", ctypes.c_int64), ("kernel_launches", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_uint64), ("ms_m2l_tc", ctypes.c_double),
-                ("ms_p2p_kernel", ctypes.c_double)]
+                ("ms_p2p_kernel", ctypes.c_double), ("ms_p2m_fine", ctypes.c_double),
+                ("ms_p2m_coarse", ctypes.c_double), ("ms_m2l_fine", ctypes.c_double),
+                ("ms_m2l_coarse", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -55,6 +57,7 @@ class fmm_stats(ctypes.Structure):
 SIGNATURES = {
     "fmm_plan": (_i32, [ctypes.POINTER(_vp), _i64, _i32, _i32, _d, _i32, _vp]),
     "fmm_set_stream": (_i32, [_vp, _vp]),
+    "fmm_set_concurrency": (_i32, [_vp, _i32]),
     "fmm_potential": (_i32, [_vp, _vp, _vp, _vp]),
     "fmm_potential_host": (_i32, [_vp, _vp, _vp, _vp]),
     "fmm_sync": (_i32, [_vp]),
@@ -156,6 +159,11 @@ def fmm_plan(n: int, levels: int, p: int, box: float = 5.0, precision="fp64", st
 
 def fmm_set_stream(plan: int, stream=None):
     _check(_lib.fmm_set_stream(plan, _stream_handle(stream)), "fmm_set_stream")
+
+
+def fmm_set_concurrency(plan: int, streams: int):
+    """3: the mixed path's stages overlap on three streams (default); 1: one after the other."""
+    _check(_lib.fmm_set_concurrency(plan, int(streams)), "fmm_set_concurrency")
 
 
 def fmm_potential(plan: int, xy, q, phi):

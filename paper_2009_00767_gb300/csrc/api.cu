@@ -82,11 +82,13 @@ void free_plan(fmm_plan_s* pl) {
     fmm_tc_destroy(pl);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     if (pl->h_counters) cudaFreeHost(pl->h_counters);
-    for (int e = 0; e < 10; ++e)
+    for (int e = 0; e < 15; ++e)
         if (pl->ev[e]) cudaEventDestroy(pl->ev[e]);
     if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
     if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+    if (pl->ev_join3) cudaEventDestroy(pl->ev_join3);
     if (pl->stream2) cudaStreamDestroy(pl->stream2);
+    if (pl->stream3) cudaStreamDestroy(pl->stream3);
     cudaSetDevice(prev);
     delete pl;
 }
@@ -253,13 +255,15 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->d_xy_stage, sizeof(double) * 2 * n));
     FMM_TRY(dev_alloc(pl, &pl->d_q_stage, sizeof(double) * n));
     FMM_TRY(dev_alloc(pl, &pl->d_phi_stage, sizeof(double) * n));
-    for (int e = 0; e < 10; ++e)
+    for (int e = 0; e < 15; ++e)
         if (cudaEventCreate(&pl->ev[e]) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
     if (precision != FMM_FP64) {
-        // the mixed path's near field runs on a second stream of the plan's own
+        // the mixed path's near field and coarse levels run on streams of the plan's own
         if (cudaStreamCreateWithFlags(&pl->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&pl->stream3, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev_join3, cudaEventDisableTiming) != cudaSuccess)
             FMM_TRY(FMM_ERR_CUDA);
     }
 #undef FMM_TRY
@@ -269,6 +273,12 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     pl->last.precision = precision;
     pl->last.workspace_bytes = pl->workspace_bytes;
     *out = pl;
+    return FMM_OK;
+}
+
+fmm_status fmm_set_concurrency(fmm_plan_t plan, int streams) {
+    if (!plan || (streams != 1 && streams != 3)) return FMM_ERR_INVALID_ARG;
+    plan->serial = streams == 1;
     return FMM_OK;
 }
 
@@ -312,23 +322,33 @@ fmm_status fmm_sync(fmm_plan_t plan) {
         return FMM_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
     if (plan->events_recorded) {
-        float ms[5] = {0, 0, 0, 0, 0};
-        for (int e = 0; e < 5; ++e) cudaEventElapsedTime(&ms[e], plan->ev[e], plan->ev[e + 1]);
-        float tot = 0;
-        cudaEventElapsedTime(&tot, plan->ev[0], plan->ev[5]);
-        plan->last.ms_sort = ms[0];
-        plan->last.ms_p2m = ms[1];
-        plan->last.ms_m2l = ms[2];
-        plan->last.ms_l2p = ms[3];
-        plan->last.ms_p2p = ms[4];   // FP64 path: the P2P stage; the mixed path's is set below
-        plan->last.ms_total = tot;
-        float kt = 0.f;
-        plan->last.ms_m2l_tc = (plan->ev_kernels & 1) && cudaEventElapsedTime(&kt, plan->ev[6], plan->ev[7]) ==
-                                                              cudaSuccess ? kt : 0.0;
-        plan->last.ms_p2p_kernel = (plan->ev_kernels & 2) && cudaEventElapsedTime(&kt, plan->ev[8], plan->ev[9]) ==
-                                                                  cudaSuccess ? kt : 0.0;
-        // the mixed path's P2P runs beside P2M and M2L on the second stream: its stage is its kernel
-        if (plan->ev_kernels & 2) plan->last.ms_p2p = plan->last.ms_p2p_kernel;
+        auto span = [&](int a, int b) -> double {
+            float t = 0.f;
+            return cudaEventElapsedTime(&t, plan->ev[a], plan->ev[b]) == cudaSuccess ? (double)t : 0.0;
+        };
+        const int kb = plan->ev_kernels;
+        plan->last.ms_total = span(0, 5);
+        plan->last.ms_sort = span(0, 1);
+        plan->last.ms_m2l_tc = (kb & 1) ? span(6, 7) : 0.0;
+        plan->last.ms_p2p_kernel = (kb & 2) ? span(8, 9) : 0.0;
+        if (plan->precision == FMM_FP64) {
+            plan->last.ms_p2m = span(1, 2);
+            plan->last.ms_m2l = span(2, 3);
+            plan->last.ms_l2p = span(3, 4);
+            plan->last.ms_p2p = span(4, 5);
+            plan->last.ms_p2m_fine = plan->last.ms_p2m_coarse = plan->last.ms_m2l_coarse = 0.0;
+            plan->last.ms_m2l_fine = plan->last.ms_m2l;
+        } else {
+            // three streams overlap: each stage is the sum of its kernels' own spans
+            plan->last.ms_p2m_fine = span(1, 2);
+            plan->last.ms_p2m_coarse = (kb & 4) ? span(10, 11) : 0.0;
+            plan->last.ms_m2l_fine = span(14, 3);
+            plan->last.ms_m2l_coarse = (kb & 8) ? span(12, 13) : 0.0;
+            plan->last.ms_p2m = plan->last.ms_p2m_fine + plan->last.ms_p2m_coarse;
+            plan->last.ms_m2l = plan->last.ms_m2l_fine + plan->last.ms_m2l_coarse;
+            plan->last.ms_l2p = span(4, 5);
+            plan->last.ms_p2p = plan->last.ms_p2p_kernel;
+        }
         plan->ev_kernels = 0;
         unsigned long long pairs = 0, mx = 0;
         for (int c = 0; c < FMM_COUNTER_SLOTS; ++c) {

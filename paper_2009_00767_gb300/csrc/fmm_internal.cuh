@@ -118,10 +118,19 @@ struct fmm_plan_s {
     double* d_q_stage;
     double* d_phi_stage;
 
-    cudaStream_t stream2;          // mixed path: the near field runs here, beside P2M and M2L
-    cudaEvent_t ev_fork, ev_join;  // untimed: stream -> stream2 after the sort, back before L2P
-    cudaEvent_t ev[10];   // stage boundaries [0..5]; the tensor-core M2L kernel [6, 7]; the P2P kernel [8, 9]
-    int ev_kernels;       // bit 0: [6, 7] recorded this call, bit 1: [8, 9]
+    // Mixed path: after the fine P2M the work forks three ways -- the near field on stream2, the
+    // coarse levels' chain (P2M, conversion, M2L of levels 2..5) on stream3, the fine levels' M2L
+    // on the plan's stream -- and joins back before L2P.
+    cudaStream_t stream2, stream3;
+    cudaEvent_t ev_fork, ev_join, ev_join3;   // untimed fork / join events
+    // Timing events.  FP64 path: stage boundaries [0..5] (sort, P2M, M2L, L2P, P2P).  Mixed path:
+    // [0] start, [1] sort done, [2] fine P2M done, [14] fine M2L start, [3] fine M2L done, [4] L2P
+    // start (after the joins), [5] end, all on the plan's stream; [6, 7] the tensor-core M2L
+    // kernel; [8, 9] the near-field kernel (stream2); [10, 11] the coarse P2M and its conversion,
+    // [12, 13] the coarse M2L (stream3).
+    cudaEvent_t ev[15];
+    int ev_kernels;       // bits: 1 [6, 7], 2 [8, 9], 4 [10, 11], 8 [12, 13] recorded this call
+    int serial;           // fmm_set_concurrency(plan, 1): every stage on the plan's stream
     int events_recorded;
     int launches;
     fmm_stats last;

@@ -600,10 +600,11 @@ __device__ __forceinline__ float l2p_split_horner(const float2 (&b)[P1B], float2
 template <int P1B, bool kExact>
 __global__ void __launch_bounds__(128)
 k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int p,
-            MixedLevels lv, FmmLevelPtrs g, const float2* __restrict__ near, const unsigned int* __restrict__ status,
+            MixedLevels lv, FmmLevelPtrs g, const double* __restrict__ near, const unsigned int* __restrict__ status,
             double* __restrict__ phi) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double nd = near[i];
     const float4 P = sp[i];
     const uint32_t key = skey[i];
     const uint32_t ix = fmm_compact2(key), iy = fmm_compact2(key >> 1);
@@ -623,26 +624,27 @@ k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
         far = ff_add(far, ff_add_f(b[0], v));         // b[0] = Re b'_0 as (hi, lo)
     }
     if (*(volatile const unsigned int*)status != 0u) return;   // inputs failed the device checks
-    phi[__float_as_int(P.w)] = p2p_phi(far, near[i]);
+    phi[__float_as_int(P.w)] = p2p_phi(far, fmm_d2ff_bits(nd));
 }
 
 // -------------------------------------------------------------------------------- P2P
 // One warp per block of up to FMM_P2P_BLOCK targets of one finest square (the block -> square map
 // spares the warp a search); crowded squares spread over as many warps as they have blocks.  The
-// block's near field is p2p_near (p2p_block.cuh); it is stored per sorted particle (log2 r^2 units,
-// float-float) for L2P to finish phi.  The kernel needs only the sort's output, so it runs on a
-// second stream beside P2M and M2L.  (A persistent variant that ran each block's lookups one block
-// ahead measured no faster: the time goes to the blocks' own work.)
+// block's near field is p2p_near_sym (p2p_block.cuh): the own square in full and the four forward
+// neighbours once for both sides, every result added in FP64 to the per-particle accumulator
+// `acc` (log2 r^2 units, sorted order; cleared at the start of each call), which L2P adds to phi.
+// The kernel needs only the sort's output, so it runs on a second stream beside P2M and M2L.
 constexpr int kP2PWarps = 4;
 
-__global__ void __launch_bounds__(kP2PWarps * 32, 6)
+__global__ void __launch_bounds__(kP2PWarps * 32, 8)
 k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
             const uint32_t* __restrict__ bstart, const uint2* __restrict__ bmap, uint32_t nleaf, int levels,
-            float s_leaf, float2* __restrict__ near_out, unsigned int* __restrict__ status,
+            float s_leaf, double* __restrict__ acc, unsigned int* __restrict__ status,
             unsigned long long* __restrict__ counters) {
     __shared__ __align__(16) float4 tgt[kP2PWarps][16];   // zero past the block's targets
-    __shared__ __align__(16) int4 seg[kP2PWarps][8];      // neighbours in slot order: {index - slot, ox, oy, -}
-    static_assert(FMM_P2P_BLOCK <= 24, "p2p_near takes blocks of up to 24 targets");
+    __shared__ __align__(16) float2 tq[kP2PWarps][16];
+    __shared__ __align__(16) int4 seg[kP2PWarps][4];      // forward neighbours: {index - slot, ox, oy, -}
+    static_assert(FMM_P2P_BLOCK <= 24, "p2p_near_sym takes blocks of up to 24 targets");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t w = (uint32_t)blockIdx.x * kP2PWarps + warp;
     // the map has an entry for every warp of the grid (its size is the grid's bound), so it is
@@ -654,14 +656,15 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
     const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
     const uint32_t b0 = t0 + (uint32_t)FMM_P2P_BLOCK * lt.y;
     const int T = (int)min((uint32_t)FMM_P2P_BLOCK, t1 - b0);
-    uint32_t nsrc;
-    const float2 near = p2p_near(sp, leaf_start, leaf, t0, t1, b0, T, levels, s_leaf, tgt[warp], seg[warp], lane, &nsrc);
+    uint32_t pairs;
+    const float2 near = p2p_near_sym(sp, leaf_start, leaf, t0, t1, b0, T, levels, s_leaf, tgt[warp], tq[warp],
+                                     seg[warp], lane, acc, &pairs);
     if (lane == 0) {
         const unsigned slot = leaf % FMM_COUNTER_SLOTS;
-        atomicAdd(&counters[slot], (unsigned long long)T * nsrc - (unsigned long long)T);
+        atomicAdd(&counters[slot], (unsigned long long)pairs);
         atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)(t1 - t0));
     }
-    if (lane < T) near_out[b0 + lane] = near;
+    if (lane < T) atomicAdd(acc + b0 + lane, fmm_f2d_bits(near.x) + fmm_f2d_bits(near.y));
 }
 
 }  // namespace
@@ -669,7 +672,11 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
 // The near field on the plan's second stream: forked from the plan's stream at this point of its
 // work (any point after the sort will do), joined back before L2P.
 int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv) {
-    cudaStream_t st = pl->stream, s2 = pl->stream2;
+    cudaStream_t st = pl->stream, s2 = pl->serial ? pl->stream : pl->stream2;
+    // the near-field accumulator starts at zero: cleared on stream2 as soon as the call starts (the
+    // start event follows the previous call's L2P, its last reader), beside the sort and fine P2M
+    if (s2 != st && cudaStreamWaitEvent(s2, pl->ev[0], 0) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(pl->phi_far, 0, sizeof(double) * (size_t)pl->n, s2) != cudaSuccess) return -1;
     if (cudaEventRecord(pl->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(s2, pl->ev_fork, 0) != cudaSuccess)
         return -1;
     const int L = pl->levels;
@@ -681,8 +688,7 @@ int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv) {
     const unsigned blocks = (unsigned)((wmax + kP2PWarps - 1) / kP2PWarps);
     cudaEventRecord(pl->ev[8], s2);
     k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, s2>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, pl->blk_map, nleaf,
-                                                  L, lv.s_leaf, reinterpret_cast<float2*>(pl->phi_far), pl->d_status,
-                                                  pl->d_counters);
+                                                  L, lv.s_leaf, pl->phi_far, pl->d_status, pl->d_counters);
     cudaEventRecord(pl->ev[9], s2);
     pl->ev_kernels |= 2;
     if (cudaEventRecord(pl->ev_join, s2) != cudaSuccess) return -1;
@@ -716,37 +722,50 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
         return -2;
     // in the tensor-core modes the tensor-core M2L takes the levels from fmm_tc_kmin() on
     const bool use_tc = pl->tc != nullptr && pl->levels >= fmm_tc_kmin();
-    cudaStream_t st = pl->stream;
+    cudaStream_t st = pl->stream, s3 = pl->serial ? pl->stream : pl->stream3;
     const int64_t n = pl->n;
     const int L = pl->levels, p = pl->p, p1 = p + 1;
     const MixedLevels lv = fmm_make_levels(pl);
     int launches = 0;
-    const float2* near = reinterpret_cast<const float2*>(pl->phi_far);   // near field per sorted particle
+    const double* near = pl->phi_far;   // near-field accumulator per sorted particle
     cudaEventRecord(pl->ev[1], st);
+    // fine levels: the finest kFineLevels; coarser ones by the particle-parallel kernel
+    const int kf = L - (kFineLevels - 1) > 2 ? L - (kFineLevels - 1) : 2;
+    const int kc_max = kf - 1;   // the coarse FP64 grids are zero here (k_prep_a32 re-zeroes them)
+    const int kw = L < kM2LWarpMaxLevel ? L : kM2LWarpMaxLevel;   // levels 2..kw: the coarse M2L kernel
     if (L >= 2) {
-        // fine levels: the finest kFineLevels; coarser ones by the particle-parallel kernel
-        const int kf = L - (kFineLevels - 1) > 2 ? L - (kFineLevels - 1) : 2;
-        const int kc_max = kf - 1;   // the coarse FP64 grids are zero here (k_prep_a32 re-zeroes them)
         const unsigned fblocks = (unsigned)(((2ull << (2 * L)) + 127) / 128);   // two lanes per finest square
-        const unsigned cblocks = (unsigned)((n + 4 * kCoarseChunk - 1) / (4 * kCoarseChunk));
-        // the near field forks after the fine P2M kernel: it then runs beside the coarse P2M and the
-        // M2L's smaller kernels (forked at the sort it slowed the register-heavy fine P2M; forked at
-        // the tensor-core kernel it slowed that kernel's single MMA-issuing thread)
         switch (pl->p1b) {
 #define FMM_P2M(PB)                                                                                          \
-    case PB:                                                                                                 \
-        k_p2m_fine<PB><<<fblocks, 128, 0, st>>>(pl->sorted32, pl->leaf_start, L, p, lv, pl->grids);           \
-        if (fmm_launch_p2p_concurrent(pl, lv) < 0) return -1;                                                \
-        if (kc_max >= 2)                                                                                     \
-            k_p2m_coarse<PB><<<cblocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, kc_max, p, lv,     \
-                                                      pl->grids);                                            \
-        break;
+    case PB: k_p2m_fine<PB><<<fblocks, 128, 0, st>>>(pl->sorted32, pl->leaf_start, L, p, lv, pl->grids); break;
             FMM_P2M(9) FMM_P2M(13) FMM_P2M(17) FMM_P2M(21) FMM_P2M(25) FMM_P2M(33) FMM_P2M(41)
 #undef FMM_P2M
             default: return -2;
         }
-        launches += kc_max >= 2 ? 3 : 2;   // with the near-field kernel
+        ++launches;
+    }
+    cudaEventRecord(pl->ev[2], st);
+    // Fork after the fine P2M: the near field (stream2) needs only the sort; the coarse levels'
+    // chain (stream3) needs the sort and, for the coarse M2L, the fine levels' moments of levels
+    // up to 5; the fine levels' M2L stays here.  All three join before L2P.  (With
+    // fmm_set_concurrency(plan, 1) they run one after the other on the plan's stream.)
+    const int r = fmm_launch_p2p_concurrent(pl, lv);   // records ev_fork on the plan's stream
+    if (r < 0) return -1;
+    launches += r;
+    if (L >= 2) {
+        if (cudaStreamWaitEvent(s3, pl->ev_fork, 0) != cudaSuccess) return -1;
+        cudaEventRecord(pl->ev[10], s3);
         if (kc_max >= 2) {
+            const unsigned cblocks = (unsigned)((n + 4 * kCoarseChunk - 1) / (4 * kCoarseChunk));
+            switch (pl->p1b) {
+#define FMM_P2MC(PB)                                                                                         \
+    case PB:                                                                                                 \
+        k_p2m_coarse<PB><<<cblocks, 128, 0, s3>>>(pl->sorted32, pl->sorted_key, n, L, kc_max, p, lv, pl->grids); \
+        break;
+                FMM_P2MC(9) FMM_P2MC(13) FMM_P2MC(17) FMM_P2MC(21) FMM_P2MC(25) FMM_P2MC(33) FMM_P2MC(41)
+#undef FMM_P2MC
+                default: return -2;
+            }
             PrepA32Args pa{};
             int64_t acc = 0;
             for (int k = 2; k <= kc_max; ++k) {
@@ -758,18 +777,17 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
             pa.base[kc_max + 1] = acc;
             pa.kmax = kc_max;
             pa.p1 = p1;
-            k_prep_a32<<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(pa);
-            ++launches;
+            k_prep_a32<<<(unsigned)((acc + 255) / 256), 256, 0, s3>>>(pa);
+            launches += 2;
         }
-    }
-    cudaEventRecord(pl->ev[2], st);
-    if (L >= 2) {
+        cudaEventRecord(pl->ev[11], s3);
+        cudaEventRecord(pl->ev[12], s3);
         // coarse levels: a CTA per 4 x kM2LWarpTargets targets of one class
         M2LWarpArgs wa;
         wa.g = pl->grids;
         wa.T = pl->T32;
         wa.p = p;
-        wa.kw = L < kM2LWarpMaxLevel ? L : kM2LWarpMaxLevel;
+        wa.kw = kw;
         int wacc = 0;
         for (int k = 0; k <= FMM_MAX_LEVELS + 1; ++k) wa.cbase[k] = 0;
         for (int k = 2; k <= wa.kw; ++k) {
@@ -778,23 +796,28 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
         }
         wa.cbase[wa.kw + 1] = wacc;
         switch (pl->p1b) {
-            case 9: launch_m2l_coarse<9>(wa, lv, wacc, st); break;
-            case 13: launch_m2l_coarse<13>(wa, lv, wacc, st); break;
-            case 17: launch_m2l_coarse<17>(wa, lv, wacc, st); break;
-            case 21: launch_m2l_coarse<21>(wa, lv, wacc, st); break;
-            case 25: launch_m2l_coarse<25>(wa, lv, wacc, st); break;
-            case 33: launch_m2l_coarse<33>(wa, lv, wacc, st); break;
-            case 41: launch_m2l_coarse<41>(wa, lv, wacc, st); break;
+            case 9: launch_m2l_coarse<9>(wa, lv, wacc, s3); break;
+            case 13: launch_m2l_coarse<13>(wa, lv, wacc, s3); break;
+            case 17: launch_m2l_coarse<17>(wa, lv, wacc, s3); break;
+            case 21: launch_m2l_coarse<21>(wa, lv, wacc, s3); break;
+            case 25: launch_m2l_coarse<25>(wa, lv, wacc, s3); break;
+            case 33: launch_m2l_coarse<33>(wa, lv, wacc, s3); break;
+            case 41: launch_m2l_coarse<41>(wa, lv, wacc, s3); break;
             default: return -2;
         }
         ++launches;
-        // finer levels: one thread per target, or the tensor cores
+        cudaEventRecord(pl->ev[13], s3);
+        pl->ev_kernels |= 4 | 8;
+        if (cudaEventRecord(pl->ev_join3, s3) != cudaSuccess) return -1;
+
+        // finer levels on the plan's stream: one thread per target, or the tensor cores
+        cudaEventRecord(pl->ev[14], st);
         M2LMixedArgs a;
         a.g = pl->grids;
         a.T = pl->T32;
         a.levels = L;
         a.p = p;
-        a.kmin = wa.kw + 1;
+        a.kmin = kw + 1;
         a.kmax = use_tc ? fmm_tc_kmin() - 1 : L;
         int acc = 0;
         for (int k = 0; k <= FMM_MAX_LEVELS + 1; ++k) a.cta_base[k] = 0;
@@ -823,13 +846,11 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
             launches += t;
         }
     }
-    if (L < 2) {   // no far field: the near field alone
-        const int r = fmm_launch_p2p_concurrent(pl, lv);
-        if (r < 0) return -1;
-        launches += r;
-    }
+    if (L < 2) cudaEventRecord(pl->ev[14], st);
     cudaEventRecord(pl->ev[3], st);
     if (cudaStreamWaitEvent(st, pl->ev_join, 0) != cudaSuccess) return -1;   // the near field is done
+    if (L >= 2 && cudaStreamWaitEvent(st, pl->ev_join3, 0) != cudaSuccess) return -1;   // and the coarse levels
+    cudaEventRecord(pl->ev[4], st);
     {
         const unsigned blocks = (unsigned)((n + 127) / 128);
         switch (pl->p1b) {
@@ -848,7 +869,6 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
         }
         ++launches;
     }
-    cudaEventRecord(pl->ev[4], st);
     cudaEventRecord(pl->ev[5], st);
     if (cudaGetLastError() != cudaSuccess) return -1;
     return launches;

@@ -217,6 +217,176 @@ __device__ __forceinline__ float2 p2p_near(const float4* __restrict__ sp, const 
     return p2p_near_nb(sp, t0, t1, b0, T, p2p_neighbour(ls, leaf, levels, lane), s_leaf, tgt, seg, lane, nsrc);
 }
 
+// ---------------------------------------------------------------- symmetric near field
+// The pair term log r^2 is symmetric, so each pair of adjacent squares is evaluated once: the
+// block's targets take their own square in full (both orders, as above) and only the four
+// "forward" neighbours E (+1, 0), NE (+1, +1), N (0, +1) and NW (-1, +1); the other four
+// neighbours are covered by the squares that have this one as their forward neighbour.  For a
+// forward pair the logarithm serves both sides: q_s L goes to the target (register partials, as
+// above) and q_t L to the source, summed over the block's targets in the lane that holds the
+// source and added to the source's accumulator with one FP64 atomic per lane and chunk.
+
+// Forward neighbour `lane` (< 4: E, NE, N, NW) of finest square `leaf`: its first sorted particle
+// and count (an empty range outside the domain and on the other lanes).
+__device__ __forceinline__ uint2 p2p_forward(const uint32_t* __restrict__ ls, uint32_t leaf, int levels, int lane) {
+    uint32_t first = 0, cnt = 0;
+    if (lane < 4) {
+        const int side = 1 << levels;
+        const int jx = (int)fmm_compact2(leaf) + (lane == 3 ? -1 : (lane == 2 ? 0 : 1));
+        const int jy = (int)fmm_compact2(leaf >> 1) + (lane == 0 ? 0 : 1);
+        if (jx >= 0 && jy >= 0 && jx < side && jy < side) {
+            const uint32_t nl = fmm_morton((uint32_t)jx, (uint32_t)jy);
+            first = ls[nl];
+            cnt = ls[nl + 1] - first;
+        }
+    }
+    return make_uint2(first, cnt);
+}
+
+// The block's sources: the own square's particles [t0, t0 + n_own) in nch_own chunks, then the
+// four forward neighbours' in lane order (seg[b]: sorted index minus slot, frame shift; thr:
+// first slot of forward neighbours 1..3).
+struct P2PSymSources {
+    const float4* sp;
+    const int4* seg;
+    uint32_t thr[3];
+    uint32_t t0, n_own, nch_own, n_fw;
+
+    // source of chunk c for this lane in the target square's frame, and for a forward chunk its
+    // sorted index (0xffffffff past the end, where q = 0)
+    __device__ __forceinline__ float4 load(uint32_t c, int lane, uint32_t* idx) const {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        *idx = 0xffffffffu;
+        if (c < nch_own) {
+            const uint32_t s = 32u * c + (uint32_t)lane;
+            if (s < n_own) v = sp[t0 + s];
+        } else {
+            const uint32_t s = 32u * (c - nch_own) + (uint32_t)lane;
+            if (s < n_fw) {
+                const int b = (s >= thr[0] ? 1 : 0) + (s >= thr[1] ? 1 : 0) + (s >= thr[2] ? 1 : 0);
+                const int4 g = seg[b];
+                *idx = s + (uint32_t)g.x;
+                v = sp[*idx];
+                v.x += __int_as_float(g.y);
+                v.y += __int_as_float(g.z);
+            }
+        }
+        return v;
+    }
+};
+
+// one forward chunk: the lane's source against the NP target pairs, both sides; returns the
+// source's sum over the block's targets (targets past the block's end have q = 0)
+template <int NP>
+__device__ __forceinline__ float p2p_chunk_sym(float2 (&part)[NP], const float4* __restrict__ tg,
+                                               const float2* __restrict__ tq, float4 src) {
+    const float2 nsx = make_float2(-src.x, -src.x), nsy = make_float2(-src.y, -src.y);
+    const float2 q2 = make_float2(src.z, src.z);
+    const float2 tiny = make_float2(0x1p-100f, 0x1p-100f);
+    float2 sacc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int tp = 0; tp < NP; ++tp) {
+        const float4 t = tg[tp];
+        const float2 dx = __fadd2_rn(make_float2(t.x, t.y), nsx);
+        const float2 dy = __fadd2_rn(make_float2(t.z, t.w), nsy);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, tiny));
+        const float2 lg = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
+        part[tp] = __ffma2_rn(q2, lg, part[tp]);
+        sacc = __ffma2_rn(tq[tp], lg, sacc);
+    }
+    return sacc.x + sacc.y;
+}
+
+// the block's own-square and forward-neighbour sums: returns target `lane`'s sum (log2 r^2 units,
+// float-float) and adds each forward source's sum to acc[its sorted index]
+template <int NP>
+__device__ __forceinline__ float2 p2p_block_sym(const P2PSymSources& S, const float4* __restrict__ tg,
+                                                const float2* __restrict__ tq, int lane, double* __restrict__ acc) {
+    constexpr int W = NP <= 2 ? 4 : (NP <= 4 ? 8 : (NP <= 8 ? 16 : 32));
+    const uint32_t nch = S.nch_own + (S.n_fw + 31u) / 32u;
+    float2 near = make_float2(0.f, 0.f);
+    for (uint32_t r0 = 0; r0 < nch; r0 += kP2PRun) {
+        const uint32_t r1 = min(nch, r0 + (uint32_t)kP2PRun);
+        float2 part[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) part[i] = make_float2(0.f, 0.f);
+        uint32_t idx;
+        float4 cur = S.load(r0, lane, &idx);
+        for (uint32_t c = r0; c < r1; ++c) {
+            uint32_t nidx = idx;
+            const float4 nxt = (c + 1 < r1) ? S.load(c + 1, lane, &nidx) : cur;
+            if (c < S.nch_own) {
+                p2p_chunk<true, NP>(part, tg, cur);
+            } else {
+                const float ssum = p2p_chunk_sym<NP>(part, tg, tq, cur);
+                if (idx != 0xffffffffu) atomicAdd(acc + idx, fmm_f2d_bits(ssum));
+            }
+            cur = nxt;
+            idx = nidx;
+        }
+        near = ff_add_f(near, warp_reduce_scatter<W, NP>(part, lane));
+    }
+    return near;
+}
+
+// Symmetric near field of the targets [b0, b0 + T) (T <= 24) of finest square `leaf` with
+// particles [t0, t1): target `lane`'s own-square and forward sum (log2 r^2 units, float-float) is
+// returned, the forward sources' shares go to acc.  *pairs receives the ordered pairs covered
+// (both directions of every forward pair).  tgt (16 float4), tq (16 float2) and seg (4 int4) are
+// the warp's shared memory.
+__device__ __forceinline__ float2 p2p_near_sym(const float4* __restrict__ sp, const uint32_t* __restrict__ ls,
+                                               uint32_t leaf, uint32_t t0, uint32_t t1, uint32_t b0, int T,
+                                               int levels, float s_leaf, float4* tgt, float2* tq, int4* seg,
+                                               int lane, double* __restrict__ acc, uint32_t* pairs) {
+    const uint2 nb = p2p_forward(ls, leaf, levels, lane);
+    const uint32_t n_own = t1 - t0;
+    uint32_t incl = nb.y;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t excl = incl - nb.y;
+    const uint32_t n_fw = __shfl_sync(0xffffffffu, incl, 3);
+    if (lane < 4) {
+        const float ox = (float)(lane == 3 ? -1 : (lane == 2 ? 0 : 1)) * s_leaf;
+        const float oy = (float)(lane == 0 ? 0 : 1) * s_leaf;
+        seg[lane] = make_int4((int)(nb.x - excl), __float_as_int(ox), __float_as_int(oy), 0);
+    }
+    P2PSymSources S;
+    S.sp = sp;
+    S.seg = seg;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) S.thr[i] = __shfl_sync(0xffffffffu, excl, i + 1);
+    S.t0 = t0;
+    S.n_own = n_own;
+    S.nch_own = (n_own + 31u) / 32u;
+    S.n_fw = n_fw;
+    *pairs = (uint32_t)T * (n_own + 2u * n_fw) - (uint32_t)T;
+    {
+        float x = 0.f, y = 0.f, q = 0.f;
+        if (lane < T) {
+            const float4 P = sp[b0 + lane];
+            x = P.x;
+            y = P.y;
+            q = P.z;
+        }
+        float* t = reinterpret_cast<float*>(&tgt[lane >> 1]);
+        t[lane & 1] = x;
+        t[2 + (lane & 1)] = y;
+        reinterpret_cast<float*>(&tq[lane >> 1])[lane & 1] = q;
+    }
+    __syncwarp();
+    switch ((T + 3) >> 2) {
+        case 1: return p2p_block_sym<2>(S, tgt, tq, lane, acc);
+        case 2: return p2p_block_sym<4>(S, tgt, tq, lane, acc);
+        case 3: return p2p_block_sym<6>(S, tgt, tq, lane, acc);
+        case 4: return p2p_block_sym<8>(S, tgt, tq, lane, acc);
+        case 5: return p2p_block_sym<10>(S, tgt, tq, lane, acc);
+        default: return p2p_block_sym<12>(S, tgt, tq, lane, acc);
+    }
+}
+
 // phi = far + near x ln2 / 2 (the float-float factor turns sum q log2 r^2 into sum q ln r)
 __device__ __forceinline__ double p2p_phi(float2 far, float2 near) {
     const float2 v = ff_add(far, ff_mul(near, make_float2(0.3465736f, -9.523271e-10f)));

@@ -173,3 +173,27 @@ def test_tensor_core_wait_timeout_is_reported_and_recoverable(oracle_mod):
     with binding.Plan(1000, 4, 8, 5.0, "bf16x3") as plan:   # no tensor-core level: nothing to inject
         with pytest.raises(binding.FmmError):
             binding.fmm_inject_timeout(plan.handle, True)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2"])
+def test_one_stream_and_three_streams_agree(oracle_mod, precision):
+    """fmm_set_concurrency(plan, 1) runs the stages one after the other on the plan's stream; the
+    result meets the same bound as the overlapped default, and the per-kernel times are filled."""
+    import torch
+    from gpu_util import to_dev
+    from paper_2009_00767_gb300 import binding
+    xy, q = inputs.gmm(120000, inputs.config_seed(0, 402))
+    txy, tq = to_dev(xy, q)
+    ref = oracle_mod.shiftfree(xy, q, 7, 16)
+    with binding.Plan(120000, 7, 16, 5.0, precision) as plan:
+        three = plan.potential(txy, tq).cpu().numpy()
+        binding.fmm_set_concurrency(plan.handle, 1)
+        one = plan.potential(txy, tq).cpu().numpy()
+        st = plan.stats()
+        with pytest.raises(binding.FmmError):
+            binding.fmm_set_concurrency(plan.handle, 2)
+    check_parity(three, ref, MIXED_TOL, f"{precision} three streams")
+    check_parity(one, ref, MIXED_TOL, f"{precision} one stream")
+    for k in ("ms_sort", "ms_p2m_fine", "ms_p2m_coarse", "ms_m2l_coarse", "ms_m2l_fine", "ms_p2p_kernel", "ms_l2p"):
+        assert st[k] > 0.0, k
+    assert st["ms_total"] >= st["ms_sort"] + st["ms_p2p_kernel"] + st["ms_l2p"]
