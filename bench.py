@@ -65,9 +65,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--fp64-steps", type=int, default=20)
-    ap.add_argument("--batched", action="store_true",
-                    help="also time the batched form on 1024 systems (N log-uniform in [1024, 262144]) "
-                         "against a loop of single-system launches")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched form (1024 systems, N log-uniform in [1024, 262144], against a loop "
+                         "of single-system launches)")
     ap.add_argument("--batched-systems", type=int, default=1024)
     return ap.parse_args()
 
@@ -454,8 +454,9 @@ def run_ours(args):
     plan.close()
 
     batched = None
-    if args.batched:
-        batched = run_batched(binding, torch, dev, args.batched_systems, max(3, min(args.steps, 20)), 3)
+    if not args.no_batched and args.precision != "fp64":
+        batched = run_batched(binding, torch, dev, args.batched_systems, max(5, min(args.steps, 20)), 3,
+                              args.precision)
 
     cpu = None
     if rank == 0 and not args.no_cpu and ws == 1:
@@ -507,30 +508,51 @@ def batched_workload(nsys, seed=20094767):
     return ns, levels, np.concatenate(xys), np.concatenate(qs)
 
 
-def run_batched(binding, torch, dev, nsys, steps, warmup):
+def run_batched(binding, torch, dev, nsys, steps, warmup, precision):
+    """The batched form: one graph replay per step over all systems (launch shapes picked by the
+    library's autotuner), against a loop of single-system plans of the same precision over the same
+    systems; accuracy against the FP64 direct sum at sampled targets of sampled systems."""
     ns, levels, xy, q = batched_workload(nsys)
     total = int(ns.sum())
     xy_d = torch.from_numpy(xy).to(dev)
     q_d = torch.from_numpy(q).to(dev)
     phi = torch.empty(total, dtype=torch.float64, device=dev)
-    b = binding.Batch(ns, levels, 16)
-    grid_mult = binding.fmm_batch_autotune(b.handle, xy_d, q_d, phi)
+    b = binding.Batch(ns, levels, 16, precision=precision)
+    binding.fmm_batch_autotune_cached(b.handle, xy_d, q_d, phi, None)
+    tuning = binding.fmm_batch_tuning(b.handle)
     for _ in range(warmup):
         binding.fmm_batch_potential(b.handle, xy_d, q_d, phi)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    ms_steps = []
     for _ in range(steps):
+        e0.record()
         binding.fmm_batch_potential(b.handle, xy_d, q_d, phi)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_batch = e0.elapsed_time(e1) / steps
+        e1.record()
+        torch.cuda.synchronize()
+        ms_steps.append(e0.elapsed_time(e1))
+    ms_batch = float(np.median(ms_steps))
     binding.fmm_batch_sync(b.handle)
     launches = binding.fmm_batch_launches(b.handle)
     b.close()
-    # the same systems as a loop of single-system plans (one launch sequence per system)
+    # accuracy: 8 systems spread over the size range, 256 sampled targets each
+    from paper_2009_00767_gb300 import inputs
     off = np.concatenate([[0], np.cumsum(ns)])
-    plans = [binding.Plan(int(ns[i]), int(levels[i]), 16, 5.0, "fp32") for i in range(nsys)]
+    order = np.argsort(ns)
+    errs = []
+    for i in order[np.linspace(0, nsys - 1, 8).astype(int)]:
+        n_i = int(ns[i])
+        idx = np.unique((inputs.u01(5150 + int(i), 0, min(256, n_i)) * n_i).astype(np.int64))
+        idx_d = torch.from_numpy(idx).to(dev)
+        ref = torch.empty(idx.shape[0], dtype=torch.float64, device=dev)
+        xs, qs_ = xy_d[off[i]:off[i + 1]].contiguous(), q_d[off[i]:off[i + 1]].contiguous()
+        binding.fmm_direct_targets(xs, qs_, idx_d, ref)
+        torch.cuda.synchronize()
+        got = phi[off[i]:off[i + 1]][idx_d]
+        errs.append({"system": int(i), "n": n_i, "levels": int(levels[i]),
+                     "rel_l2_err": float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))})
+    # the same systems as a loop of single-system plans (one launch sequence per system)
+    plans = [binding.Plan(int(ns[i]), int(levels[i]), 16, 5.0, precision) for i in range(nsys)]
     views = [(xy_d[off[i]:off[i + 1]], q_d[off[i]:off[i + 1]], phi[off[i]:off[i + 1]]) for i in range(nsys)]
     for _ in range(max(1, warmup // 2)):
         for pl, (x, qq, ph) in zip(plans, views):
@@ -548,8 +570,10 @@ def run_batched(binding, torch, dev, nsys, steps, warmup):
         pl.close()
     return {"systems": nsys, "particles": total, "ms_per_step": ms_batch, "value": total / (ms_batch * 1e-3),
             "unit": UNIT, "loop_ms_per_step": ms_loop, "loop_value": total / (ms_loop * 1e-3),
-            "speedup_vs_loop": ms_loop / ms_batch, "graph_launches_per_step": launches, "grid_mult": grid_mult,
-            "precision": "fp32", "p": 16}
+            "speedup_vs_loop": ms_loop / ms_batch, "graph_launches_per_step": launches, "tuning": tuning,
+            "precision": precision, "p": 16, "rel_l2_err_max": max(e["rel_l2_err"] for e in errs),
+            "meets_error_bound": all(e["rel_l2_err"] <= ERR_BOUND for e in errs), "sampled_systems": errs,
+            "timing": "CUDA events around each graph replay, median of the steps"}
 
 
 # ---------------------------------------------------------------- CPU oracle

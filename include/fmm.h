@@ -210,14 +210,18 @@ fmm_status fmm_probe_peak(int unit, double* ops_per_s, void* stream);
 /* ---------------------------------------------------------------------------------------
  * Batched form: many independent systems of uneven size, each an independent instance of
  * the method above (its own box [0, box]^2 and quadtree depth), evaluated by one launch per
- * stage that spans all systems, replayed as one CUDA graph.  Mixed FP32 precision only.
+ * stage that spans all systems, replayed as one CUDA graph.  M2L of levels 2..5 runs on the
+ * CUDA cores in FP32; in the tensor-core precisions every system's levels 6 and finer run in
+ * one tcgen05 launch whose tiles come from any system.  The near field is the symmetric one
+ * of the single-system path, on a second branch of the graph beside P2M and M2L.
  * --------------------------------------------------------------------------------------- */
 typedef struct fmm_batch_s* fmm_batch_t;
 
 /* Create a batch plan for nsys systems (1 <= nsys <= 1536; total particles < 2^31).
  *   n[i], levels[i]  host arrays: particles (>= 1) and quadtree depth (0..12) of system i.
  *   p, box           expansion order and box side shared by all systems.
- *   precision        FMM_MIXED_FP32 (others return FMM_ERR_UNSUPPORTED).
+ *   precision        FMM_MIXED_FP32, or a tensor-core precision (FMM_MIXED_TF32, _3XTF32,
+ *                    _BF16, _BF16X2, _BF16X3; p <= 31); FMM_FP64 returns FMM_ERR_UNSUPPORTED.
  *   stream           cudaStream_t the calls run on (NULL = default stream).
  * Allocates every workspace, builds the operators and captures the launch sequence into a
  * CUDA graph. */
@@ -233,11 +237,26 @@ fmm_status fmm_batch_potential(fmm_batch_t batch, const double* xy, const double
  * last sync and clear it.  ms (may be NULL) receives the device time of the last call. */
 fmm_status fmm_batch_sync(fmm_batch_t batch, double* ms);
 
-/* Time the batch on the given inputs for several persistent grid sizes (blocks per SM),
- * keep the fastest and rebuild the graph.  grid_mult_out (may be NULL) receives it.  Runs
- * and waits for several calls on the batch's stream. */
+/* Autotuner: times the batch on the given inputs (device arrays as for fmm_batch_potential)
+ * for every launch shape of a small grid -- persistent blocks per SM of the grid-stride
+ * kernels (2, 4, 8), tensor-core M2L tiles per CTA (the default, 2, 4; tensor-core
+ * precisions only) and near-field targets per block (16, 24) -- keeps the fastest and
+ * rebuilds the graph.  grid_mult_out (may be NULL) receives the blocks per SM.  Runs and
+ * waits for about 70 calls on the batch's stream. */
 fmm_status fmm_batch_autotune(fmm_batch_t batch, const double* xy, const double* q, double* phi,
                               int* grid_mult_out);
+
+/* As fmm_batch_autotune, with a cache: cache_path (may be NULL: no cache) names a text file
+ * of lines "key grid_mult tc_rows p2p_block ms", the key naming the device (name, SMs,
+ * driver version), p, the precision and the batch's shape (systems, total particles to a
+ * power of two, systems per depth).  A line with this batch's key is applied without timing;
+ * otherwise the search runs and its result is appended.  The file is created if missing. */
+fmm_status fmm_batch_autotune_cached(fmm_batch_t batch, const double* xy, const double* q, double* phi,
+                                     const char* cache_path);
+
+/* The batch's current launch shape and the autotuner's best time (0 before a search); any
+ * pointer may be NULL. */
+fmm_status fmm_batch_tuning(fmm_batch_t batch, int* grid_mult, int* tc_rows, int* p2p_block, double* ms);
 
 /* Kernels (and memsets) the batch graph launches per call, or -1 for NULL. */
 int fmm_batch_launches(fmm_batch_t batch);

@@ -73,6 +73,9 @@ SIGNATURES = {
     "fmm_batch_potential": (_i32, [_vp, _vp, _vp, _vp]),
     "fmm_batch_sync": (_i32, [_vp, ctypes.POINTER(_d)]),
     "fmm_batch_autotune": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(_i32)]),
+    "fmm_batch_autotune_cached": (_i32, [_vp, _vp, _vp, _vp, ctypes.c_char_p]),
+    "fmm_batch_tuning": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                ctypes.POINTER(_d)]),
     "fmm_batch_launches": (_i32, [_vp]),
     "fmm_batch_destroy": (None, [_vp]),
     "fmm_selector_dims": (_i32, [ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -253,6 +256,22 @@ def fmm_batch_autotune(batch: int, xy, q, phi) -> int:
     g = _i32(0)
     _check(_lib.fmm_batch_autotune(batch, _ptr(xy), _ptr(q), _ptr(phi), ctypes.byref(g)), "fmm_batch_autotune")
     return g.value
+
+
+def fmm_batch_autotune_cached(batch: int, xy, q, phi, cache_path=None):
+    """Autotune with a cache file (None: no cache); see include/fmm.h."""
+    _check(_lib.fmm_batch_autotune_cached(batch, _ptr(xy), _ptr(q), _ptr(phi),
+                                          None if cache_path is None else str(cache_path).encode()),
+           "fmm_batch_autotune_cached")
+
+
+def fmm_batch_tuning(batch: int) -> dict:
+    """The batch's launch shape: persistent blocks per SM, tensor-core tiles per CTA (0 = default),
+    near-field targets per block, and the autotuner's best time in ms (0 before a search)."""
+    g, r, k, ms = _i32(), _i32(), _i32(), _d()
+    _check(_lib.fmm_batch_tuning(batch, ctypes.byref(g), ctypes.byref(r), ctypes.byref(k), ctypes.byref(ms)),
+           "fmm_batch_tuning")
+    return {"grid_mult": g.value, "tc_rows": r.value, "p2p_block": k.value, "ms": ms.value}
 
 
 def fmm_batch_launches(batch: int) -> int:

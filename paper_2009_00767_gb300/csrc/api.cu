@@ -50,6 +50,21 @@ void build_operators(int p, std::vector<cd>& T) {
 
 bool valid_precision(int v) { return v >= FMM_FP64 && v <= FMM_MIXED_BF16X2; }
 
+}  // namespace
+
+void fmm_build_operators_f64(int p, std::vector<double>& re, std::vector<double>& im) {
+    std::vector<cd> T;
+    build_operators(p, T);
+    re.resize(T.size());
+    im.resize(T.size());
+    for (size_t i = 0; i < T.size(); ++i) {
+        re[i] = T[i].real();
+        im[i] = T[i].imag();
+    }
+}
+
+namespace {
+
 template <class T>
 fmm_status dev_alloc(fmm_plan_s* pl, T** ptr, size_t bytes) {
     *ptr = nullptr;
@@ -217,8 +232,7 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->T64, sizeof(double2) * T.size()));
     if (cudaMemcpy(pl->T64, T.data(), sizeof(double2) * T.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         FMM_TRY(FMM_ERR_CUDA);
-    if (precision == FMM_MIXED_TF32 || precision == FMM_MIXED_3XTF32 || precision == FMM_MIXED_BF16 ||
-        precision == FMM_MIXED_BF16X3 || precision == FMM_MIXED_BF16X2) {
+    if (fmm_tc_precision(precision)) {
         std::vector<double> tre(T.size()), tim(T.size());
         for (size_t i = 0; i < T.size(); ++i) {
             tre[i] = T[i].real();

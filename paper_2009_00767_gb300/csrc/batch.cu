@@ -3,15 +3,22 @@
 //
 // Every system is an independent instance of the method (its own box [0, box]^2, its own
 // quadtree depth); the particles of all systems are concatenated in system order.  The stages
-// are the single-system ones (sort, P2M per level, FP32 M2L, L2P per level, P2P), each run as
-// one grid-stride (persistent) kernel over a flattened work space that spans all systems.  A
-// work item finds its system by binary search over per-system prefix counts held in shared
-// memory.  One exclusive scan over the concatenated finest-square populations gives every
-// system's CSR offsets already shifted by the system's first particle.  The sequence of launches
-// is captured once into a CUDA graph; the call's array pointers live in a small device block
-// written before each replay, so one graph serves every call.
+// are the single-system ones (sort, P2M per level, M2L, L2P per level, P2P), each run as one
+// grid-stride (persistent) kernel over a flattened work space that spans all systems.  A work
+// item finds its system by binary search over per-system prefix counts held in shared memory.
+// One exclusive scan over the concatenated finest-square populations gives every system's CSR
+// offsets already shifted by the system's first particle.  M2L runs levels 2..5 on the CUDA cores
+// in FP32 and, in the tensor-core precisions, every system's levels 6 and finer in one tcgen05
+// launch whose tiles come from any system (one segment per system and level).  The near field is
+// the symmetric one of the single-system path, on a second branch of the graph beside P2M and M2L;
+// L2P then adds each particle's near field and writes phi.  The sequence of launches is captured
+// once into a CUDA graph; the call's array pointers live in a small device block written before
+// each replay, so one graph serves every call.  fmm_batch_autotune times candidate launch shapes
+// (persistent blocks per SM, tensor-core tiles per CTA, near-field targets per block).
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "mixed_common.cuh"
@@ -23,6 +30,7 @@ constexpr int kT = 128;   // threads per block of every batched kernel
 constexpr int kCoarseChunk = 256;
 constexpr int kLaneMax = 128;
 constexpr int kFineMean = 64;
+constexpr int kP2PBlockMin = 16;   // the smallest near-field block the autotuner tries
 
 struct BatchSys {
     long long p_off;                       // first particle of the system (input and sorted order)
@@ -63,8 +71,10 @@ struct BatchArgs {
     float2* a32;     // all moment grids (FP32; coarse region first, same cells as a64)
     float2* b32;     // local coefficients
     const float2* T; // FP32 operators [49][P1B][P1B]
-    float2* far;
+    double* acc;     // near field per sorted particle (log2 r^2 units), zeroed at the start of a call
     unsigned int* status;
+    int m2l_kmax;    // levels 2..m2l_kmax of each system run in kb_m2l_f32 (the tensor cores take the rest)
+    int p2p_block;   // near-field targets per block (16 or 24)
 };
 
 // largest s with pre[s] <= w, for pre[0] = 0 <= w < pre[nsys]
@@ -341,7 +351,8 @@ __global__ void __launch_bounds__(kT) kb_m2l_f32(BatchArgs a, MixedLevels lv) {
         const BatchSys& S = a.sys[s];
         long long rel = cta - pre[s];
         int k = 2;
-        for (; k < S.levels; ++k) {
+        const int kmax = S.levels < a.m2l_kmax ? S.levels : a.m2l_kmax;
+        for (; k < kmax; ++k) {
             const long long w2 = 1ll << (k - 1);
             const long long cnt = 4 * ((w2 * w2 + kT - 1) / kT);
             if (rel < cnt) break;
@@ -396,15 +407,20 @@ __global__ void __launch_bounds__(kT) kb_m2l_f32(BatchArgs a, MixedLevels lv) {
     }
 }
 
-// -------------------------------------------------------------------------------- L2P
+// -------------------------------------------------------------------------------- L2P + final phi
+// One thread per particle: the levels' local expansions summed in float-float, the particle's near
+// field (kb_p2p, already complete) added, phi written in input order unless the checks failed.
 template <int P1B>
 __global__ void __launch_bounds__(kT) kb_l2p(BatchArgs a, MixedLevels lv) {
     extern __shared__ long long pre[];
     load_prefix(pre, a.wp_part, a.nsys);
     const long long total = pre[a.nsys];
     const int p1 = a.p + 1;
-    for (long long i = (long long)blockIdx.x * kT + threadIdx.x; i < total; i += (long long)gridDim.x * kT) {
+    const bool bad = *(volatile const unsigned int*)a.status != 0u;
+    double* phi = a.call->phi;
+    for (long long i = (long long)blockIdx.x * kT + threadIdx.x; i < total && !bad; i += (long long)gridDim.x * kT) {
         const BatchSys& S = a.sys[find_sys(pre, a.nsys, i)];
+        const double nd = a.acc[i];
         const float4 P = a.sorted32[i];
         const uint32_t key = a.sorted_key[i];
         const uint32_t ix = fmm_compact2(key), iy = fmm_compact2(key >> 1);
@@ -426,22 +442,23 @@ __global__ void __launch_bounds__(kT) kb_l2p(BatchArgs a, MixedLevels lv) {
             }
             far = ff_add(far, ff_add_f(b[0], fmaf(u.x, w.x, -u.y * w.y)));
         }
-        a.far[i] = far;
+        phi[S.p_off + __float_as_int(P.w)] = p2p_phi(far, fmm_d2ff_bits(nd));
     }
 }
 
-// One warp per near-field block of any system (blocks of up to FMM_P2P_BLOCK targets, the block
-// map giving the square), grid-stride; the block's near field is p2p_near (p2p_block.cuh), as in
-// the single-system path.
-__global__ void __launch_bounds__(kT) kb_p2p(BatchArgs a, MixedLevels lv) {
+// One warp per near-field block of any system (blocks of up to p2p_block targets, the block map
+// giving the square), grid-stride; the block's near field is p2p_near_sym (p2p_block.cuh), as in
+// the single-system path: the own square in full, the four forward neighbours once for both sides,
+// every result added in FP64 to the per-particle accumulator.
+__global__ void __launch_bounds__(kT, 8) kb_p2p(BatchArgs a, MixedLevels lv) {
     extern __shared__ long long pre[];
     __shared__ __align__(16) float4 tgt[kT / 32][16];
-    __shared__ __align__(16) int4 seg[kT / 32][8];
+    __shared__ __align__(16) float2 tq[kT / 32][16];
+    __shared__ __align__(16) int4 seg[kT / 32][4];
     load_prefix(pre, a.wp_leaf, a.nsys);
     const long long total = a.bstart[a.nl];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool bad = *(volatile const unsigned int*)a.status != 0u;
-    double* phi = a.call->phi;
     for (long long w = (long long)blockIdx.x * (kT / 32) + warp; w < total && !bad;
          w += (long long)gridDim.x * (kT / 32)) {
         const uint2 lt = a.bmap[w];
@@ -450,20 +467,14 @@ __global__ void __launch_bounds__(kT) kb_p2p(BatchArgs a, MixedLevels lv) {
         const uint32_t leaf = (uint32_t)((long long)lt.x - pre[s]);
         const uint32_t* ls = a.leaf_start + S.leaf_off;
         const uint32_t t0 = ls[leaf], t1 = ls[leaf + 1];
-        const uint32_t b0 = t0 + (uint32_t)FMM_P2P_BLOCK * lt.y;
-        const int T = (int)min((uint32_t)FMM_P2P_BLOCK, t1 - b0);
-        int idx = 0;
-        float2 far = make_float2(0.f, 0.f);
-        if (lane < T) {
-            idx = __float_as_int(a.sorted32[b0 + lane].w);
-            far = a.far[b0 + lane];
-        }
+        const uint32_t b0 = t0 + (uint32_t)a.p2p_block * lt.y;
+        const int T = (int)min((uint32_t)a.p2p_block, t1 - b0);
         const float s_leaf = a.box_ff.x * __int_as_float((127 - S.levels) << 23);
-        uint32_t nsrc;
-        const float2 near =
-            p2p_near(a.sorted32, ls, leaf, t0, t1, b0, T, S.levels, s_leaf, tgt[warp], seg[warp], lane, &nsrc);
-        if (lane < T) phi[S.p_off + idx] = p2p_phi(far, near);
-        __syncwarp();   // tgt and seg are rewritten by the next block
+        uint32_t pairs;
+        const float2 near = p2p_near_sym(a.sorted32, ls, leaf, t0, t1, b0, T, S.levels, s_leaf, tgt[warp], tq[warp],
+                                         seg[warp], lane, a.acc, &pairs);
+        if (lane < T) atomicAdd(a.acc + b0 + lane, fmm_f2d_bits(near.x) + fmm_f2d_bits(near.y));
+        __syncwarp();   // tgt, tq and seg are rewritten by the next block
     }
 }
 
@@ -475,7 +486,12 @@ struct fmm_batch_s {
     double box;
     long long nt, nl, coarse_cells, a_cells, b_cells;
     cudaStream_t stream;
+    int precision;
     int grid_mult;                    // persistent blocks per SM (autotuned)
+    int tc_rows;                      // tensor-core tiles per CTA, 0 = the kernel's default (autotuned)
+    int p2p_block;                    // near-field targets per block, 16 or 24 (autotuned)
+    double tuned_ms;                  // the autotuner's best time (0 before a search)
+    FmmTc* tc;                        // tensor-core M2L of levels 6 and finer (tensor-core precisions)
     std::vector<BatchSys> host_sys;
     BatchSys* d_sys;
     long long* d_pre;                 // 5 prefix arrays, (nsys + 1) each
@@ -485,7 +501,8 @@ struct fmm_batch_s {
     uint2* bmap;
     float4* sorted32;
     double* a64;
-    float2 *a32, *b32, *far;
+    float2 *a32, *b32;
+    double* acc;                      // near field per sorted particle
     float2* T32;
     unsigned int* d_status;
     unsigned int* h_status;
@@ -504,7 +521,8 @@ void batch_free(fmm_batch_s* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     void* bufs[] = {b->d_sys, b->d_pre, b->d_call, b->keys, b->rank, b->counts, b->leaf_start, b->block_sums,
                     b->leaf_nb, b->bstart, b->bmap,
-                    b->sorted_key, b->sorted32, b->a64, b->a32, b->b32, b->far, b->T32, b->d_status};
+                    b->sorted_key, b->sorted32, b->a64, b->a32, b->b32, b->acc, b->T32, b->d_status};
+    fmm_tc_free(b->tc);
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (b->h_call) cudaFreeHost(b->h_call);
@@ -526,14 +544,19 @@ bool balloc(fmm_batch_s* b, T** p, size_t bytes) {
     return true;
 }
 
+// The call's launches: the sort on st, then two branches -- the near field on st2, P2M and M2L on
+// st -- joined before L2P.  (st2 == st runs them in turn.)
 template <int P1B>
-int enqueue_batch_kernels(fmm_batch_s* b, const BatchArgs& a, const MixedLevels& lv, cudaStream_t st) {
+int enqueue_batch_kernels(fmm_batch_s* b, const BatchArgs& a, const MixedLevels& lv, cudaStream_t st,
+                          cudaStream_t st2, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     const unsigned grid = (unsigned)(sms * b->grid_mult);
     const size_t pre_bytes = sizeof(long long) * (b->nsys + 1);
     int launches = 0;
-    if (cudaMemsetAsync(b->counts, 0, sizeof(uint32_t) * b->nl, st) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(b->counts, 0, sizeof(uint32_t) * b->nl, st) != cudaSuccess ||
+        cudaMemsetAsync(b->acc, 0, sizeof(double) * b->nt, st) != cudaSuccess)
+        return -1;
     if (b->coarse_cells > 0 &&
         cudaMemsetAsync(b->a64, 0, sizeof(double2) * b->coarse_cells * (b->p + 1), st) != cudaSuccess)
         return -1;
@@ -543,8 +566,18 @@ int enqueue_batch_kernels(fmm_batch_s* b, const BatchArgs& a, const MixedLevels&
     if (sc < 0) return -1;
     launches += sc;
     kb_scatter<<<grid, kT, pre_bytes, st>>>(a);
+    ++launches;
+    // the near field needs only the sorted particles
+    if (st2 != st && (cudaEventRecord(ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(st2, ev_fork, 0) != cudaSuccess))
+        return -1;
+    const int lb = fmm_launch_leaf_blocks(b->leaf_start, b->nl, (uint32_t)b->p2p_block, b->leaf_nb, b->block_sums,
+                                          b->bstart, b->bmap, st2);
+    if (lb < 0) return -1;
+    kb_p2p<<<grid, kT, pre_bytes, st2>>>(a, lv);
+    launches += lb + 1;
+    if (st2 != st && cudaEventRecord(ev_join, st2) != cudaSuccess) return -1;
     kb_p2m_fine<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
-    launches += 2;
+    ++launches;
     if (b->coarse_cells > 0) {
         kb_p2m_coarse<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
         kb_prep_a32<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(b->a64), b->a32,
@@ -552,16 +585,19 @@ int enqueue_batch_kernels(fmm_batch_s* b, const BatchArgs& a, const MixedLevels&
         launches += 2;
     }
     kb_m2l_f32<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
+    ++launches;
+    if (b->tc) {
+        const int t = fmm_tc_enqueue(b->tc, lv, st, b->d_status, 0, b->tc_rows, nullptr, nullptr);
+        if (t < 0) return -1;
+        launches += t;
+    }
+    if (st2 != st && cudaStreamWaitEvent(st, ev_join, 0) != cudaSuccess) return -1;
     kb_l2p<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
-    const int lb = fmm_launch_leaf_blocks(b->leaf_start, b->nl, (uint32_t)FMM_P2P_BLOCK, b->leaf_nb, b->block_sums,
-                                          b->bstart, b->bmap, st);
-    if (lb < 0) return -1;
-    kb_p2p<<<grid, kT, pre_bytes, st>>>(a, lv);
-    launches += 3 + lb;
+    ++launches;
     return cudaGetLastError() == cudaSuccess ? launches : -1;
 }
 
-int enqueue_all(fmm_batch_s* b, cudaStream_t st) {
+int enqueue_all(fmm_batch_s* b, cudaStream_t st, cudaStream_t st2, cudaEvent_t ev_fork, cudaEvent_t ev_join) {
     BatchArgs a{};
     const long long stride = b->nsys + 1;
     a.sys = b->d_sys;
@@ -589,20 +625,22 @@ int enqueue_all(fmm_batch_s* b, cudaStream_t st) {
     a.a32 = b->a32;
     a.b32 = b->b32;
     a.T = b->T32;
-    a.far = b->far;
+    a.acc = b->acc;
     a.status = b->d_status;
+    a.m2l_kmax = b->tc ? fmm_tc_kmin() - 1 : FMM_MAX_LEVELS;
+    a.p2p_block = b->p2p_block;
     fmm_plan_s shim{};
     shim.box = b->box;
     shim.levels = 0;
     const MixedLevels lv = fmm_make_levels(&shim);
     switch (b->p1b) {
-        case 9: return enqueue_batch_kernels<9>(b, a, lv, st);
-        case 13: return enqueue_batch_kernels<13>(b, a, lv, st);
-        case 17: return enqueue_batch_kernels<17>(b, a, lv, st);
-        case 21: return enqueue_batch_kernels<21>(b, a, lv, st);
-        case 25: return enqueue_batch_kernels<25>(b, a, lv, st);
-        case 33: return enqueue_batch_kernels<33>(b, a, lv, st);
-        case 41: return enqueue_batch_kernels<41>(b, a, lv, st);
+        case 9: return enqueue_batch_kernels<9>(b, a, lv, st, st2, ev_fork, ev_join);
+        case 13: return enqueue_batch_kernels<13>(b, a, lv, st, st2, ev_fork, ev_join);
+        case 17: return enqueue_batch_kernels<17>(b, a, lv, st, st2, ev_fork, ev_join);
+        case 21: return enqueue_batch_kernels<21>(b, a, lv, st, st2, ev_fork, ev_join);
+        case 25: return enqueue_batch_kernels<25>(b, a, lv, st, st2, ev_fork, ev_join);
+        case 33: return enqueue_batch_kernels<33>(b, a, lv, st, st2, ev_fork, ev_join);
+        case 41: return enqueue_batch_kernels<41>(b, a, lv, st, st2, ev_fork, ev_join);
         default: return -2;
     }
 }
@@ -617,16 +655,29 @@ fmm_status build_graph(fmm_batch_s* b) {
         cudaGraphDestroy(b->graph);
         b->graph = nullptr;
     }
-    cudaStream_t cap;
-    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return FMM_ERR_CUDA;
-    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaStreamDestroy(cap);
+    cudaStream_t cap = nullptr, cap2 = nullptr;
+    cudaEvent_t evf = nullptr, evj = nullptr;
+    auto release = [&]() {
+        if (cap) cudaStreamDestroy(cap);
+        if (cap2) cudaStreamDestroy(cap2);
+        if (evf) cudaEventDestroy(evf);
+        if (evj) cudaEventDestroy(evj);
+    };
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&evf, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&evj, cudaEventDisableTiming) != cudaSuccess) {
+        release();
         return FMM_ERR_CUDA;
     }
-    const int n = enqueue_all(b, cap);
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        release();
+        return FMM_ERR_CUDA;
+    }
+    const int n = enqueue_all(b, cap, cap2, evf, evj);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cap, &g);
-    cudaStreamDestroy(cap);
+    release();
     if (n < 0 || e != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
@@ -651,6 +702,49 @@ fmm_status batch_run(fmm_batch_s* b, const double* xy, const double* q, double* 
     return FMM_OK;
 }
 
+// The autotuner's cache key: the device (name, SM count, driver version), the order, the precision,
+// and the batch's shape (system count, total particles to the nearest power of two, systems per
+// quadtree depth).  Spaces become underscores so the key is one token.
+std::string tune_key(const fmm_batch_s* b) {
+    cudaDeviceProp prop;
+    memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, b->device);
+    int drv = 0;
+    cudaDriverGetVersion(&drv);
+    int hist[FMM_MAX_LEVELS + 1] = {};
+    for (const BatchSys& S : b->host_sys) ++hist[S.levels];
+    int lg = 0;
+    while ((1ll << (lg + 1)) <= b->nt) ++lg;
+    std::string key = prop.name;
+    for (char& c : key)
+        if (c == ' ' || c == '|') c = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "|sm%d|drv%d|p%d|prec%d|nsys%d|N2^%d|depths", prop.multiProcessorCount, drv, b->p,
+             b->precision, b->nsys, lg);
+    key += buf;
+    for (int k = 0; k <= FMM_MAX_LEVELS; ++k)
+        if (hist[k]) {
+            snprintf(buf, sizeof(buf), ":%dx%d", k, hist[k]);
+            key += buf;
+        }
+    return key;
+}
+
+// device time of the current shape: one warm-up replay, then the sum of three
+fmm_status time_shape(fmm_batch_s* b, const double* xy, const double* q, double* phi, double* ms_out) {
+    fmm_status s = build_graph(b);
+    if (s != FMM_OK) return s;
+    double tot = 0.0;
+    for (int rep = 0; rep < 4; ++rep) {
+        double ms = 0.0;
+        if ((s = batch_run(b, xy, q, phi)) != FMM_OK) return s;
+        if ((s = fmm_batch_sync(b, &ms)) != FMM_OK) return s;
+        if (rep > 0) tot += ms;
+    }
+    *ms_out = tot / 3.0;
+    return FMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -661,7 +755,7 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
     if (!out || nsys < 1 || nsys > 1536 || !n || !levels || p < 1 || p > FMM_MAX_P || !(box > 0.0) ||
         !(box < 1e300))
         return FMM_ERR_INVALID_ARG;
-    if (precision != FMM_MIXED_FP32) return FMM_ERR_UNSUPPORTED;
+    if (precision != FMM_MIXED_FP32 && !fmm_tc_precision(precision)) return FMM_ERR_UNSUPPORTED;
     long long nt = 0;
     for (int i = 0; i < nsys; ++i) {
         if (n[i] < 1 || n[i] > 2147483647LL || levels[i] < 0 || levels[i] > FMM_MAX_LEVELS) return FMM_ERR_INVALID_ARG;
@@ -675,7 +769,11 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
     b->p = p;
     b->box = box;
     b->stream = static_cast<cudaStream_t>(stream);
+    b->precision = precision;
     b->grid_mult = 4;
+    b->tc_rows = 0;
+    b->p2p_block = FMM_P2P_BLOCK;
+    const int m2l_kmax = fmm_tc_precision(precision) ? fmm_tc_kmin() - 1 : FMM_MAX_LEVELS;
     b->p1b = fmm_m2l_bucket(p + 1);
     if (b->p1b < 0) {
         delete b;
@@ -722,7 +820,7 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
         pre[2 * s1 + i + 1] = pre[2 * s1 + i] + fine;
         pre[3 * s1 + i + 1] = pre[3 * s1 + i] + (S.kf > 2 && S.levels >= 2 ? (S.n + kCoarseChunk - 1) / kCoarseChunk : 0);
         long long m2l = 0;
-        for (int k = 2; k <= S.levels; ++k) {
+        for (int k = 2; k <= S.levels && k <= m2l_kmax; ++k) {
             const long long w2 = 1ll << (k - 1);
             m2l += 4 * ((w2 * w2 + kT - 1) / kT);
         }
@@ -738,10 +836,10 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
               balloc(b, &b->counts, 4 * nl) && balloc(b, &b->leaf_start, 4 * (nl + 1)) &&
               balloc(b, &b->block_sums, 4 * ((size_t)fmm_scan_blocks(nl) + 1)) && balloc(b, &b->sorted_key, 4 * nt) &&
               balloc(b, &b->leaf_nb, 4 * nl) && balloc(b, &b->bstart, 4 * (nl + 1)) &&
-              balloc(b, &b->bmap, sizeof(uint2) * ((size_t)nl + (size_t)nt / FMM_P2P_BLOCK + 1)) &&
+              balloc(b, &b->bmap, sizeof(uint2) * ((size_t)nl + (size_t)nt / kP2PBlockMin + 1)) &&
               balloc(b, &b->sorted32, 16 * nt) && balloc(b, &b->a64, sizeof(double2) * coarse * p1) &&
               balloc(b, &b->a32, sizeof(float2) * b->a_cells * p1) && balloc(b, &b->b32, sizeof(float2) * bcells * p1) &&
-              balloc(b, &b->far, sizeof(float2) * nt) && balloc(b, &b->d_status, sizeof(unsigned int));
+              balloc(b, &b->acc, sizeof(double) * nt) && balloc(b, &b->d_status, sizeof(unsigned int));
     if (!ok) {
         batch_free(b);
         return FMM_ERR_OOM;
@@ -761,6 +859,30 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
         if (!ok) {
             batch_free(b);
             return FMM_ERR_CUDA;
+        }
+    }
+    // the tensor-core M2L: every system's levels 6 and finer, one segment each
+    if (fmm_tc_precision(precision)) {
+        std::vector<double> tre, tim;
+        fmm_build_operators_f64(p, tre, tim);
+        int err = 0;
+        uint64_t bytes = 0;
+        b->tc = fmm_tc_new(p, precision, tre, tim, &err, &bytes);
+        if (!b->tc) {
+            batch_free(b);
+            return err == -2 ? FMM_ERR_UNSUPPORTED : FMM_ERR_CUDA;
+        }
+        std::vector<FmmTcLevel> lev;
+        for (int i = 0; i < nsys; ++i) {
+            const BatchSys& S = b->host_sys[i];
+            for (int k = S.levels; k >= fmm_tc_kmin(); --k)
+                lev.push_back({b->a32 + S.a_off[k] * p1, b->b32 + S.b_off[k] * p1, k});
+        }
+        const int r = fmm_tc_set_levels(b->tc, lev, &bytes);
+        b->workspace_bytes += bytes;
+        if (r < 0) {
+            batch_free(b);
+            return FMM_ERR_OOM;
         }
     }
     if (cudaMemcpy(b->d_sys, b->host_sys.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -806,29 +928,79 @@ fmm_status fmm_batch_sync(fmm_batch_t b, double* ms) {
 }
 
 fmm_status fmm_batch_autotune(fmm_batch_t b, const double* xy, const double* q, double* phi, int* grid_mult_out) {
+    const fmm_status s = fmm_batch_autotune_cached(b, xy, q, phi, nullptr);
+    if (s == FMM_OK && grid_mult_out) *grid_mult_out = b->grid_mult;
+    return s;
+}
+
+fmm_status fmm_batch_autotune_cached(fmm_batch_t b, const double* xy, const double* q, double* phi,
+                                     const char* cache_path) {
     if (!b || !xy || !q || !phi) return FMM_ERR_INVALID_ARG;
-    const int cand[] = {1, 2, 4, 8, 16};
-    int best = b->grid_mult;
-    double best_ms = 1e30;
-    for (int c : cand) {
-        b->grid_mult = c;
-        fmm_status s = build_graph(b);
-        if (s != FMM_OK) return s;
-        double tot = 0.0;
-        for (int rep = 0; rep < 4; ++rep) {
-            double ms = 0.0;
-            if ((s = batch_run(b, xy, q, phi)) != FMM_OK) return s;
-            if ((s = fmm_batch_sync(b, &ms)) != FMM_OK) return s;
-            if (rep > 0) tot += ms;   // the first replay warms up
-        }
-        if (tot < best_ms) {
-            best_ms = tot;
-            best = c;
+    const std::string key = tune_key(b);
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[1024];
+            bool hit = false;
+            while (!hit && fgets(line, sizeof(line), f)) {
+                char k[768];
+                int gm = 0, rows = 0, blk = 0;
+                double ms = 0.0;
+                if (sscanf(line, "%767s %d %d %d %lf", k, &gm, &rows, &blk, &ms) == 5 && key == k && gm >= 1 &&
+                    gm <= 16 && rows >= 0 && rows <= 8 && (blk == 16 || blk == 24)) {
+                    b->grid_mult = gm;
+                    b->tc_rows = rows;
+                    b->p2p_block = blk;
+                    b->tuned_ms = ms;
+                    hit = true;
+                }
+            }
+            fclose(f);
+            if (hit) return build_graph(b);
         }
     }
-    b->grid_mult = best;
-    if (grid_mult_out) *grid_mult_out = best;
+    const int gms[] = {2, 4, 8};
+    const int rows_tc[] = {0, 2, 4};
+    const int blks[] = {16, 24};
+    int best_gm = b->grid_mult, best_rows = b->tc_rows, best_blk = b->p2p_block;
+    double best_ms = 1e30;
+    for (int gm : gms)
+        for (int rows : rows_tc) {
+            if (!b->tc && rows != 0) continue;
+            for (int blk : blks) {
+                b->grid_mult = gm;
+                b->tc_rows = rows;
+                b->p2p_block = blk;
+                double ms = 0.0;
+                const fmm_status s = time_shape(b, xy, q, phi, &ms);
+                if (s != FMM_OK) return s;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_gm = gm;
+                    best_rows = rows;
+                    best_blk = blk;
+                }
+            }
+        }
+    b->grid_mult = best_gm;
+    b->tc_rows = best_rows;
+    b->p2p_block = best_blk;
+    b->tuned_ms = best_ms;
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), best_gm, best_rows, best_blk, best_ms);
+            fclose(f);
+        }
+    }
     return build_graph(b);
+}
+
+fmm_status fmm_batch_tuning(fmm_batch_t b, int* grid_mult, int* tc_rows, int* p2p_block, double* ms) {
+    if (!b) return FMM_ERR_INVALID_ARG;
+    if (grid_mult) *grid_mult = b->grid_mult;
+    if (tc_rows) *tc_rows = b->tc_rows;
+    if (p2p_block) *p2p_block = b->p2p_block;
+    if (ms) *ms = b->tuned_ms;
+    return FMM_OK;
 }
 
 int fmm_batch_launches(fmm_batch_t b) { return b ? b->launches : -1; }

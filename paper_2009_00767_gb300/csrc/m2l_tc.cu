@@ -65,25 +65,44 @@ struct TcGroup {
 
 constexpr int kMaxParts = 3;     // split parts of an operand: TF32 x2 (hi, lo), BF16 x3 (hi, mid, lo)
 
+// One segment = the grids of one level of one system (a plan has one system; a batch many).  The
+// tiles of a class are the segments' tiles one after the other (the same list in every class):
+// segment j owns tiles tile0 .. segs[j + 1].tile0 - 1, and the prep kernel's cells
+// cell0 .. cell0 + 4 w2^2 - 1 (w2 = 2^(k-1), four parity sub-grids).
+struct TcSeg {
+    const float2* a32;                // FP32 moment grid of the level, (2^k + 6)^2 cells (3-cell halo)
+    uint8_t* src[kMaxParts];          // split sources [q][KC][w2+2][w2+2][16 bytes] (1-cell zero halo)
+    float2* B;                        // local coefficients of the level, (2^k)^2 cells
+    long long cell0;                  // first prep cell
+    int k;                            // level
+    int tile0;                        // first tile
+};
+
 struct TcArgs {
-    // [part][level] -> [q][KC][w2+2][w2+2][16 bytes] (1-cell zero halo); a 16-byte K chunk holds 4
-    // TF32 or 8 BF16 values
-    const uint8_t* src[kMaxParts][FMM_MAX_LEVELS + 1];
+    const TcSeg* segs;                // [nseg] in device memory, tile0 increasing
     // [class][27 slots][KC][NP * N rows][16 bytes], scale-free: within a K chunk the operator's parts
     // are stacked along N (rows part * N + n), so one MMA can take several parts at once
     const uint8_t* ops;
-    float2* B[FMM_MAX_LEVELS + 1];
     TcGroup groups[4][12];
-    // the tiles of one class, finest level first: level seg_level[j] owns tiles
-    // seg_start[j] .. seg_start[j + 1] - 1; CTA b takes tiles c * rows .. of class b % 4, c = b / 4
-    int seg_start[FMM_MAX_LEVELS + 2];
-    int seg_level[FMM_MAX_LEVELS + 1];
+    // CTA b takes tiles c * rows .. of class b % 4, c = b / 4
     int nseg, tiles, rows, tmem_cols;
-    int levels, p;
+    int p;
     unsigned int* status;
     unsigned spin;    // polls of a bounded mbarrier wait before it gives up
     int stall;        // error-path test: the producers issue nothing, so the first wait runs out
 };
+
+// the segment holding item x (a tile or a prep cell) of an increasing start table: binary search
+template <typename F>
+__device__ __forceinline__ int find_seg(int nseg, long long x, F start) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start(mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 // flat start (halo coordinates) of tile T of a parity sub-grid of width w2
 __host__ __device__ __forceinline__ int tile_start(int w2, int T) {
@@ -223,6 +242,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done_bar + 1);
     int* tile_k = reinterpret_cast<int*>(tmem_holder + 1);   // [kMaxRows] level of each tile
     int* tile_P = tile_k + kMaxRows;                           // [kMaxRows] flat start of each tile
+    // [kMaxRows][kMaxParts + 1]: each tile's source arrays and its level's local grid
+    uint8_t** tile_ptr = reinterpret_cast<uint8_t**>(((uintptr_t)(tile_P + kMaxRows) + 7) & ~(uintptr_t)7);
+    static_assert(8 * (2 * NSO + 2 * NSW + 1) + 4 + 8 * kMaxRows + 8 + 8 * kMaxRows * (kMaxParts + 1) <= 512,
+                  "barriers and tile tables fit the 512 bytes tc_bytes reserves");
 
     // ---- which tiles
     const int cls = blockIdx.x & 3;
@@ -232,11 +255,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x < nrows) {
         const int tau = t0 + threadIdx.x;
-        int j = 0;
-        while (j + 1 < a.nseg && tau >= a.seg_start[j + 1]) ++j;
-        const int k = a.seg_level[j];
+        const TcSeg& S = a.segs[find_seg(a.nseg, tau, [&](int j) { return (long long)a.segs[j].tile0; })];
+        const int k = S.k;
         tile_k[threadIdx.x] = k;
-        tile_P[threadIdx.x] = tile_start(1 << (k - 1), tau - a.seg_start[j]);
+        tile_P[threadIdx.x] = tile_start(1 << (k - 1), tau - S.tile0);
+#pragma unroll
+        for (int part = 0; part < kMaxParts; ++part) tile_ptr[threadIdx.x * (kMaxParts + 1) + part] = S.src[part];
+        tile_ptr[threadIdx.x * (kMaxParts + 1) + kMaxParts] = reinterpret_cast<uint8_t*>(S.B);
     }
     const uint32_t TMEM_COLS = (uint32_t)a.tmem_cols;
 
@@ -334,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
                 const int k = tile_k[t];
                 const size_t W2P = ((size_t)1 << (k - 1)) + 2;
                 const size_t start = (size_t)(tile_P[t] - 1 + G.sy * (int)W2P);   // flat, >= 0
-                const uint8_t* src = a.src[part][k] + (((size_t)q * KC + j) * W2P * W2P + start) * 16;
+                const uint8_t* src = tile_ptr[t * (kMaxParts + 1) + part] + (((size_t)q * KC + j) * W2P * W2P + start) * 16;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         su32(win_buf + sw * WIN_STAGE + part * A_BYTES + j * (kWin * 16))),
@@ -405,7 +430,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
             const int pos = tile_P[t] + 32 * warp + lane;
             const int x = pos % W2P - 1, y = pos / W2P - 1;   // sub-grid cell; halo cells are dropped
             if (x >= 0 && x < w2 && y < w2) {
-                bt[t] = a.B[k] + ((size_t)(2 * y + py) * (1u << k) + (2 * x + px)) * p1;
+                bt[t] = reinterpret_cast<float2*>(tile_ptr[t * (kMaxParts + 1) + kMaxParts]) +
+                        ((size_t)(2 * y + py) * (1u << k) + (2 * x + px)) * p1;
                 b0[t] = bt[t][0];
             }
         }
@@ -486,12 +512,11 @@ __device__ __forceinline__ float2 mono_sum(const float2* __restrict__ A32, const
 }
 
 struct PrepArgs {
-    const float2* a32[FMM_MAX_LEVELS + 1];
-    uint4* out[kMaxParts][FMM_MAX_LEVELS + 1];
-    float2* B[FMM_MAX_LEVELS + 1];
+    const TcSeg* segs;
+    int nseg;
+    long long cells;                      // cells of all segments
     float2 logc[FMM_MAX_LEVELS + 1][49];
-    long long base[FMM_MAX_LEVELS + 2];   // first cell (over all four parities) of each level
-    int kmin, levels, p1;
+    int p1;
 };
 
 // FP32 moment grid (3-cell halo) -> the GEMM's source layout, one thread per cell of a parity
@@ -507,15 +532,15 @@ template <int H, bool BF, int NP>
 __global__ void k_prep_tc(const __grid_constant__ PrepArgs a) {
     constexpr int KC = BF ? H / 4 : H / 2, PER = BF ? 8 : 4;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.base[a.levels + 1]) return;
-    int k = a.kmin;
-    while (g >= a.base[k + 1]) ++k;
-    const int64_t e = g - a.base[k];
+    if (g >= a.cells) return;
+    const TcSeg& S = a.segs[find_seg(a.nseg, g, [&](int j) { return a.segs[j].cell0; })];
+    const int k = S.k;
+    const int64_t e = g - S.cell0;
     const int w2 = 1 << (k - 1), W2P = w2 + 2, p1 = a.p1;
     const int col = (int)(e % w2), row = (int)((e / w2) % w2), q = (int)(e / ((int64_t)w2 * w2));
     const int x = 2 * col + (q & 1), y = 2 * row + (q >> 1);
     const int W = fmm_grid_width(k);
-    const float2* src = a.a32[k] + ((size_t)(y + FMM_HALO) * W + (x + FMM_HALO)) * p1;
+    const float2* src = S.a32 + ((size_t)(y + FMM_HALO) * W + (x + FMM_HALO)) * p1;
     float vals[2 * H];
 #pragma unroll
     for (int j = 0; j < H; ++j) {
@@ -548,17 +573,18 @@ __global__ void k_prep_tc(const __grid_constant__ PrepArgs a) {
         }
         const size_t at = ((size_t)q * KC + c) * (size_t)W2P * W2P + cell;
 #pragma unroll
-        for (int part = 0; part < NP; ++part) a.out[part][k][at] = make_uint4(w[part][0], w[part][1], w[part][2], w[part][3]);
+        for (int part = 0; part < NP; ++part)
+            reinterpret_cast<uint4*>(S.src[part])[at] = make_uint4(w[part][0], w[part][1], w[part][2], w[part][3]);
     }
     const size_t c0 = (size_t)(y + FMM_HALO) * W + (x + FMM_HALO);
     float2 mono;
     switch (q) {
-        case 0: mono = mono_sum<0, 0>(a.a32[k], a.logc[k], c0, W, p1); break;
-        case 1: mono = mono_sum<1, 0>(a.a32[k], a.logc[k], c0, W, p1); break;
-        case 2: mono = mono_sum<0, 1>(a.a32[k], a.logc[k], c0, W, p1); break;
-        default: mono = mono_sum<1, 1>(a.a32[k], a.logc[k], c0, W, p1); break;
+        case 0: mono = mono_sum<0, 0>(S.a32, a.logc[k], c0, W, p1); break;
+        case 1: mono = mono_sum<1, 0>(S.a32, a.logc[k], c0, W, p1); break;
+        case 2: mono = mono_sum<0, 1>(S.a32, a.logc[k], c0, W, p1); break;
+        default: mono = mono_sum<1, 1>(S.a32, a.logc[k], c0, W, p1); break;
     }
-    a.B[k][((size_t)y * (1u << k) + x) * p1] = mono;   // Re b'_0 as float-float, the GEMM's part to come
+    S.B[((size_t)y * (1u << k) + x) * p1] = mono;   // Re b'_0 as float-float, the GEMM's part to come
 }
 
 // host-side round to nearest TF32 (ties away), the rounding cvt.rna.tf32.f32 does on the device
@@ -587,11 +613,12 @@ float bf16_bits_to_float(uint16_t b) {
 }
 
 // shared-memory plan: two operator stages and as many window stages (2 to 4) as fit, else one
-// operator stage and two window stages; 128 bytes of alignment slack and 256 bytes of barriers
+// operator stage and two window stages; 128 bytes of alignment slack and 512 bytes of barriers
+// and per-tile tables
 template <int H, bool BF, int NP>
 constexpr size_t tc_bytes(int nso, int nsw) {
     constexpr int KC = BF ? H / 4 : H / 2;
-    return (size_t)nso * NP * 3 * (KC * (2 * H) * 16) + (size_t)nsw * NP * (KC * kWin * 16) + 128 + 256;
+    return (size_t)nso * NP * 3 * (KC * (2 * H) * 16) + (size_t)nsw * NP * (KC * kWin * 16) + 128 + 512;
 }
 template <int H, bool BF, int NP>
 constexpr int tc_nso() {
@@ -608,11 +635,14 @@ constexpr int tc_nsw() {
 
 // ---------------------------------------------------------------- plan-side state
 struct FmmTc {
-    int h, kc, np, sms;
-    bool bf;                                    // BF16 operands (else TF32)
-    uint8_t* ops;                               // one scale-free copy, the parts stacked
-    uint8_t* src[kMaxParts][FMM_MAX_LEVELS + 1];
-    TcArgs args;   // tables, filled at plan time
+    int h, kc, np, sms, p, precision;
+    bool bf;                       // BF16 operands (else TF32)
+    uint8_t* ops;                  // one scale-free copy, the parts stacked
+    uint8_t* src_all;              // every segment's split source arrays
+    TcSeg* d_segs;                 // the segment table in device memory
+    std::vector<TcSeg> segs;       // host copy
+    long long cells;               // prep cells of all segments
+    TcArgs args;                   // tables, filled at plan time
 };
 
 // The tensor cores take levels kMinLevel and finer.  The coarse levels carry most of the far
@@ -620,30 +650,56 @@ struct FmmTc {
 // each MMA) loses more there than FP32 FMAs; they hold few targets, so the CUDA cores take them.
 int fmm_tc_kmin() { return kMinLevel; }
 
-// Allocate and build the tensor-core M2L state for the plan's precision (TF32, 3xTF32, BF16 or
-// BF16x3).  Returns 0, or a negative value on failure (-1 CUDA error, -2 unsupported p).
-int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vector<double>& Tim) {
-    const int p1 = pl->p + 1;
+bool fmm_tc_precision(int precision) {
+    return precision == FMM_MIXED_TF32 || precision == FMM_MIXED_3XTF32 || precision == FMM_MIXED_BF16 ||
+           precision == FMM_MIXED_BF16X2 || precision == FMM_MIXED_BF16X3;
+}
+
+void fmm_tc_free(FmmTc* tc) {
+    if (!tc) return;
+    if (tc->ops) cudaFree(tc->ops);
+    if (tc->src_all) cudaFree(tc->src_all);
+    if (tc->d_segs) cudaFree(tc->d_segs);
+    delete tc;
+}
+
+// The operators and class tables of a tensor-core precision (TF32, 3xTF32, BF16, BF16x2 or BF16x3)
+// at order p, from the FP64 operators Tre/Tim ([49][p+1][p+1]).  *err: 0, -1 (CUDA error) or -2
+// (unsupported p); *bytes grows by the device memory taken.
+FmmTc* fmm_tc_new(int p, int precision, const std::vector<double>& Tre, const std::vector<double>& Tim, int* err,
+                  uint64_t* bytes) {
+    *err = 0;
+    const int p1 = p + 1;
     const int H = ((p1 + 7) / 8) * 8;
-    if (H != 8 && H != 16 && H != 24 && H != 32) return -2;
-    const bool bf = pl->precision == FMM_MIXED_BF16 || pl->precision == FMM_MIXED_BF16X2 ||
-                    pl->precision == FMM_MIXED_BF16X3;
+    if (!fmm_tc_precision(precision) || (H != 8 && H != 16 && H != 24 && H != 32)) {
+        *err = -2;
+        return nullptr;
+    }
+    const bool bf = precision == FMM_MIXED_BF16 || precision == FMM_MIXED_BF16X2 || precision == FMM_MIXED_BF16X3;
     const int kc = bf ? H / 4 : H / 2;
     const int per = bf ? 8 : 4, elem = bf ? 2 : 4;
-    const int np = (pl->precision == FMM_MIXED_3XTF32 || pl->precision == FMM_MIXED_BF16X2)
+    const int np = (precision == FMM_MIXED_3XTF32 || precision == FMM_MIXED_BF16X2)
                        ? 2
-                       : (pl->precision == FMM_MIXED_BF16X3 ? 3 : 1);
+                       : (precision == FMM_MIXED_BF16X3 ? 3 : 1);
     FmmTc* tc = new FmmTc();
-    memset(tc, 0, sizeof(FmmTc));
     tc->h = H;
     tc->kc = kc;
     tc->np = np;
     tc->bf = bf;
-    pl->tc = tc;
+    tc->p = p;
+    tc->precision = precision;
+    tc->ops = nullptr;
+    tc->src_all = nullptr;
+    tc->d_segs = nullptr;
+    tc->cells = 0;
+    memset(&tc->args, 0, sizeof(TcArgs));
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&tc->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return -1;
+        cudaDeviceGetAttribute(&tc->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        *err = -1;
+        fmm_tc_free(tc);
+        return nullptr;
+    }
     const int N = 2 * H, K = 2 * H;
 
     // class tables: 12 groups (source parity qx, qy and row shift sy) of 1..3 offsets each
@@ -670,7 +726,11 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
                     }
                     slots[cls] += G.nops;
                 }
-        if (slots[cls] != 27) return -1;
+        if (slots[cls] != 27) {
+            *err = -1;
+            fmm_tc_free(tc);
+            return nullptr;
+        }
     }
     // operators, real block form, [part][class][slot][KC][N][16 bytes]: scale-free, so one copy
     // serves every level; the monopole-log entry (0, 0) is left out (summed in float-float by
@@ -719,109 +779,129 @@ int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vec
                         }
                 }
             }
-        if (cudaMalloc(&tc->ops, opsz) != cudaSuccess) return -1;
-        pl->workspace_bytes += opsz;
-        if (cudaMemcpy(tc->ops, hostops.data(), opsz, cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+        if (cudaMalloc(&tc->ops, opsz) != cudaSuccess ||
+            cudaMemcpy(tc->ops, hostops.data(), opsz, cudaMemcpyHostToDevice) != cudaSuccess) {
+            *err = -1;
+            fmm_tc_free(tc);
+            return nullptr;
+        }
+        *bytes += opsz;
         tc->args.ops = tc->ops;
     }
-    // source buffers (chunk-major, 1-cell zero halo, kSrcPad zero cells after), levels kMinLevel..L
-    for (int k = kMinLevel; k <= pl->levels; ++k) {
-        const size_t w2p = ((size_t)1 << (k - 1)) + 2;
-        const size_t bytes = ((size_t)4 * w2p * w2p * kc + kSrcPad) * 16;
-        for (int part = 0; part < np; ++part) {
-            if (cudaMalloc(&tc->src[part][k], bytes) != cudaSuccess) return -1;
-            pl->workspace_bytes += bytes;
-            if (cudaMemset(tc->src[part][k], 0, bytes) != cudaSuccess) return -1;
-            tc->args.src[part][k] = tc->src[part][k];
-        }
+    tc->args.p = p;
+    return tc;
+}
+
+// The levels the tensor cores convert, one segment each (kMinLevel <= k): their FP32 moment grids
+// and local grids.  Allocates the split source arrays (chunk-major, 1-cell zero halo, kSrcPad zero
+// cells after each: flat tiles past a sub-grid's last row read there) and uploads the segment
+// table.  Returns 0 or -1.
+int fmm_tc_set_levels(FmmTc* tc, const std::vector<FmmTcLevel>& levels, uint64_t* bytes) {
+    tc->segs.clear();
+    size_t total = 0;
+    std::vector<size_t> part_bytes;
+    for (const FmmTcLevel& L : levels) {
+        if (L.k < kMinLevel || L.k > FMM_MAX_LEVELS) return -1;
+        const size_t w2p = ((size_t)1 << (L.k - 1)) + 2;
+        part_bytes.push_back(((size_t)4 * w2p * w2p * tc->kc + kSrcPad) * 16);
+        total += part_bytes.back() * tc->np;
     }
+    if (total > 0) {
+        if (cudaMalloc(&tc->src_all, total) != cudaSuccess || cudaMemset(tc->src_all, 0, total) != cudaSuccess)
+            return -1;
+        *bytes += total;
+    }
+    size_t off = 0;
+    long long cells = 0;
+    int tiles = 0;
+    for (size_t i = 0; i < levels.size(); ++i) {
+        TcSeg S;
+        memset(&S, 0, sizeof(S));
+        S.a32 = levels[i].a32;
+        S.B = levels[i].B;
+        S.k = levels[i].k;
+        for (int part = 0; part < tc->np; ++part) {
+            S.src[part] = tc->src_all + off;
+            off += part_bytes[i];
+        }
+        S.cell0 = cells;
+        S.tile0 = tiles;
+        cells += 4ll << (2 * (S.k - 1));
+        tiles += tiles_of_level(S.k);
+        tc->segs.push_back(S);
+    }
+    tc->cells = cells;
+    tc->args.nseg = (int)tc->segs.size();
+    tc->args.tiles = tiles;
+    if (!tc->segs.empty()) {
+        if (cudaMalloc(&tc->d_segs, sizeof(TcSeg) * tc->segs.size()) != cudaSuccess ||
+            cudaMemcpy(tc->d_segs, tc->segs.data(), sizeof(TcSeg) * tc->segs.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+            return -1;
+        *bytes += sizeof(TcSeg) * tc->segs.size();
+    }
+    tc->args.segs = tc->d_segs;
     return 0;
 }
 
-void fmm_tc_destroy(fmm_plan_s* pl) {
-    FmmTc* tc = pl->tc;
-    if (!tc) return;
-    if (tc->ops) cudaFree(tc->ops);
-    for (int part = 0; part < kMaxParts; ++part) {
-        for (int k = 0; k <= FMM_MAX_LEVELS; ++k)
-            if (tc->src[part][k]) cudaFree(tc->src[part][k]);
-    }
-    delete tc;
-    pl->tc = nullptr;
-}
+namespace {
 
 template <int H, bool BF, int NP>
-static int launch_tc(fmm_plan_s* pl, const MixedLevels& lv) {
-    FmmTc* tc = pl->tc;
-    cudaStream_t st = pl->stream;
-    const int L = pl->levels, p1 = pl->p + 1;
+int launch_tc(FmmTc* tc, const MixedLevels& lv, cudaStream_t st, unsigned int* status, int stall, int rows_max,
+              cudaEvent_t e0, cudaEvent_t e1) {
+    if (tc->args.nseg == 0) return 0;
     {
-        PrepArgs pa{};
-        long long acc = 0;
-        for (int k = kMinLevel; k <= L; ++k) {
-            pa.a32[k] = reinterpret_cast<const float2*>(pl->grids.A32[k]);
-            for (int part = 0; part < NP; ++part) pa.out[part][k] = reinterpret_cast<uint4*>(tc->src[part][k]);
-            pa.B[k] = reinterpret_cast<float2*>(pl->grids.B[k]);
-            pa.base[k] = acc;
-            acc += 4ll << (2 * (k - 1));
-        }
-        pa.base[L + 1] = acc;
-        pa.kmin = kMinLevel;
-        pa.levels = L;
-        pa.p1 = p1;
+        PrepArgs pa;
+        memset(&pa, 0, sizeof(pa));
+        pa.segs = tc->d_segs;
+        pa.nseg = tc->args.nseg;
+        pa.cells = tc->cells;
+        pa.p1 = tc->p + 1;
         memcpy(pa.logc, lv.logc, sizeof(pa.logc));
-        k_prep_tc<H, BF, NP><<<(unsigned)((acc + 255) / 256), 256, 0, st>>>(pa);
+        k_prep_tc<H, BF, NP><<<(unsigned)((tc->cells + 255) / 256), 256, 0, st>>>(pa);
     }
     TcArgs& a = tc->args;
-    for (int k = 0; k <= FMM_MAX_LEVELS; ++k) a.B[k] = reinterpret_cast<float2*>(pl->grids.B[k]);
-    a.levels = L;
-    a.p = pl->p;
-    a.status = pl->d_status;
-    a.spin = pl->test_stall ? kTestSpin : kSpin;
-    a.stall = pl->test_stall;
-    // the tiles of a class, finest level first; rows per CTA so that the four classes fill the
-    // SMs about once (at most kMaxRows: more tiles make more waves)
-    int tiles = 0, nseg = 0;
-    for (int k = L; k >= kMinLevel; --k) {
-        a.seg_start[nseg] = tiles;
-        a.seg_level[nseg] = k;
-        ++nseg;
-        tiles += tiles_of_level(k);
-    }
-    a.seg_start[nseg] = tiles;
-    a.nseg = nseg;
-    a.tiles = tiles;
+    a.status = status;
+    a.spin = stall ? kTestSpin : kSpin;
+    a.stall = stall;
+    // rows (tiles) per CTA so that the four classes fill the SMs about once (at most kMaxRows or
+    // rows_max: more tiles make more waves)
     const int per_class_ctas = tc->sms / 4 > 0 ? tc->sms / 4 : 1;
     constexpr int ACC = acc_cols(2 * H, NP);
-    const int max_rows = 512 / ACC < kMaxRows ? 512 / ACC : kMaxRows;   // accumulators fit tensor memory
-    a.rows = (tiles + per_class_ctas - 1) / per_class_ctas;
+    int max_rows = 512 / ACC < kMaxRows ? 512 / ACC : kMaxRows;   // accumulators fit tensor memory
+    if (rows_max > 0 && rows_max < max_rows) max_rows = rows_max;
+    a.rows = (a.tiles + per_class_ctas - 1) / per_class_ctas;
     if (a.rows > max_rows) a.rows = max_rows;
     if (a.rows < 1) a.rows = 1;
     int cols = 32;
     while (cols < a.rows * ACC) cols <<= 1;
     a.tmem_cols = cols;
-    const int items = (tiles + a.rows - 1) / a.rows;
+    const int items = (a.tiles + a.rows - 1) / a.rows;
     constexpr int NSO = tc_nso<H, BF, NP>(), NSW = tc_nsw<H, BF, NP>();
     const size_t shm = tc_bytes<H, BF, NP>(NSO, NSW);
     auto kern = k_m2l_tc<H, BF, NP, NSO, NSW>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
-    cudaEventRecord(pl->ev[6], st);
+    if (e0) cudaEventRecord(e0, st);
     kern<<<4 * items, kThreads, shm, st>>>(a);
-    cudaEventRecord(pl->ev[7], st);
-    pl->ev_kernels |= 1;
-    return 2;
+    if (e1) cudaEventRecord(e1, st);
+    return cudaGetLastError() == cudaSuccess ? 2 : -1;
 }
 
-// Launch prep + tensor-core M2L for levels 2..L; returns kernels launched or -1.
-int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv) {
-    const FmmTc* tc = pl->tc;
-    if (!tc || pl->levels < kMinLevel) return 0;
+}  // namespace
+
+// Prep + tensor-core M2L of every segment on stream st; returns the kernels launched or -1.
+// rows_max (> 0) caps the tiles per CTA (an autotuned shape; 0: the default).
+int fmm_tc_enqueue(FmmTc* tc, const MixedLevels& lv, cudaStream_t st, unsigned int* status, int stall, int rows_max,
+                   cudaEvent_t e0, cudaEvent_t e1) {
+    if (!tc) return 0;
 #define FMM_TC_CASES(H)                                                                                     \
     case H:                                                                                                 \
         if (tc->bf)                                                                                         \
-            return tc->np == 3 ? launch_tc<H, true, 3>(pl, lv)                                              \
-                               : (tc->np == 2 ? launch_tc<H, true, 2>(pl, lv) : launch_tc<H, true, 1>(pl, lv)); \
-        return tc->np == 2 ? launch_tc<H, false, 2>(pl, lv) : launch_tc<H, false, 1>(pl, lv);
+            return tc->np == 3 ? launch_tc<H, true, 3>(tc, lv, st, status, stall, rows_max, e0, e1)         \
+                               : (tc->np == 2 ? launch_tc<H, true, 2>(tc, lv, st, status, stall, rows_max, e0, e1) \
+                                              : launch_tc<H, true, 1>(tc, lv, st, status, stall, rows_max, e0, e1)); \
+        return tc->np == 2 ? launch_tc<H, false, 2>(tc, lv, st, status, stall, rows_max, e0, e1)           \
+                           : launch_tc<H, false, 1>(tc, lv, st, status, stall, rows_max, e0, e1);
     switch (tc->h) {
         FMM_TC_CASES(8)
         FMM_TC_CASES(16)
@@ -830,4 +910,36 @@ int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv) {
         default: return -1;
     }
 #undef FMM_TC_CASES
+}
+
+// ---------------------------------------------------------------- the single-system plan
+// Allocate and build the tensor-core M2L state for the plan's precision, its levels kMinLevel..L
+// finest first.  Returns 0, or a negative value on failure (-1 CUDA error, -2 unsupported p).
+int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vector<double>& Tim) {
+    int err = 0;
+    uint64_t bytes = 0;
+    FmmTc* tc = fmm_tc_new(pl->p, pl->precision, Tre, Tim, &err, &bytes);
+    pl->workspace_bytes += bytes;
+    if (!tc) return err;
+    pl->tc = tc;
+    std::vector<FmmTcLevel> lev;
+    for (int k = pl->levels; k >= kMinLevel; --k)
+        lev.push_back({reinterpret_cast<const float2*>(pl->grids.A32[k]), reinterpret_cast<float2*>(pl->grids.B[k]), k});
+    bytes = 0;
+    const int r = fmm_tc_set_levels(tc, lev, &bytes);
+    pl->workspace_bytes += bytes;
+    return r;
+}
+
+void fmm_tc_destroy(fmm_plan_s* pl) {
+    fmm_tc_free(pl->tc);
+    pl->tc = nullptr;
+}
+
+// Launch prep + tensor-core M2L for levels kMinLevel..L; returns kernels launched or -1.
+int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv) {
+    if (!pl->tc || pl->levels < kMinLevel) return 0;
+    const int r = fmm_tc_enqueue(pl->tc, lv, pl->stream, pl->d_status, pl->test_stall, 0, pl->ev[6], pl->ev[7]);
+    if (r > 0) pl->ev_kernels |= 1;
+    return r;
 }

@@ -74,9 +74,24 @@ inline MixedLevels fmm_make_levels(const fmm_plan_s* pl) {
 
 // tensor-core M2L (m2l_tc.cu)
 #include <vector>
+// one level of one system for the tensor cores: its FP32 moment grid (3-cell halo) and local grid
+struct FmmTcLevel {
+    const float2* a32;
+    float2* B;
+    int k;
+};
+bool fmm_tc_precision(int precision);
+FmmTc* fmm_tc_new(int p, int precision, const std::vector<double>& Tre, const std::vector<double>& Tim, int* err,
+                  uint64_t* bytes);
+int fmm_tc_set_levels(FmmTc* tc, const std::vector<FmmTcLevel>& levels, uint64_t* bytes);
+void fmm_tc_free(FmmTc* tc);
+int fmm_tc_enqueue(FmmTc* tc, const MixedLevels& lv, cudaStream_t st, unsigned int* status, int stall, int rows_max,
+                   cudaEvent_t e0, cudaEvent_t e1);
 int fmm_tc_create(fmm_plan_s* pl, const std::vector<double>& Tre, const std::vector<double>& Tim);
 void fmm_tc_destroy(fmm_plan_s* pl);
 int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv);
+// the FP64 M2L operators T[49][p+1][p+1] (api.cu), real and imaginary parts
+void fmm_build_operators_f64(int p, std::vector<double>& re, std::vector<double>& im);
 // the near field on the plan's second stream (mixed.cu); kernels launched, or -1
 int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv);
 int fmm_tc_kmin();
