@@ -14,7 +14,10 @@ Every function cites the part of arXiv 2009.00767 it follows:
   with the near field of Sec. 2.1 E-2;
 * :func:`classical` -- Greengard's scheme as recalled in Sec. 2.1
   (U-1, U-2, D-1, D-2, E-1, E-2);
-* single-step expansions (P2M, M2L, L2P, M2M, L2L) of the paper's ref. [101].
+* single-step expansions (P2M, M2L, L2P, M2M, L2L) of the paper's ref. [101];
+* :func:`direct_field`, :func:`shiftfree_field` -- the force field E = -grad phi
+  (Sec. 3's timings cover "potential and force fields"): the definition, and
+  the shift-free method differentiated term by term.
 """
 from __future__ import annotations
 
@@ -73,6 +76,10 @@ def _load():
             "oracle_binom": (d, [i32, i32]),
             "oracle_interaction_list": (i32, [i32, i32, i32, vp, vp]),
             "oracle_finest_squares": (i32, [i64, vp, i32, d, vp, vp]),
+            "oracle_direct_field": (i32, [i64, vp, vp, vp]),
+            "oracle_direct_field_targets": (i32, [i64, vp, vp, i64, vp, vp]),
+            "oracle_shiftfree_field": (i32, [i64, vp, vp, i32, i32, d, vp, vp]),
+            "oracle_local_eval_deriv": (d, [vp, i32, d, d, d, d, vp]),
             "oracle_set_threads": (None, [i32]),
             "oracle_get_threads": (i32, []),
         }
@@ -142,6 +149,46 @@ def shiftfree(xy, q, levels: int, p: int, box: float = 5.0, per_level: bool = Fa
         return phi, lev
     _check(_load().oracle_shiftfree(n, _ptr(xy), _ptr(q), levels, p, box, _ptr(phi)))
     return phi
+
+
+def direct_field(xy, q) -> np.ndarray:
+    """E_i = -grad phi = -sum_{j != i, r > 0} q_j (z_i - z_j) / |z_i - z_j|^2, shape [N, 2]."""
+    xy = _f64(xy).reshape(-1, 2)
+    q = _f64(q).reshape(-1)
+    E = np.empty((q.shape[0], 2))
+    _check(_load().oracle_direct_field(q.shape[0], _ptr(xy), _ptr(q), _ptr(E)))
+    return E
+
+
+def direct_field_targets(xy, q, targets) -> np.ndarray:
+    """The direct field at the listed particle indices only, shape [len(targets), 2]."""
+    xy = _f64(xy).reshape(-1, 2)
+    q = _f64(q).reshape(-1)
+    t = np.ascontiguousarray(targets, dtype=np.int64)
+    E = np.empty((t.shape[0], 2))
+    _check(_load().oracle_direct_field_targets(q.shape[0], _ptr(xy), _ptr(q), t.shape[0], _ptr(t), _ptr(E)))
+    return E
+
+
+def shiftfree_field(xy, q, levels: int, p: int, box: float = 5.0):
+    """(phi, E): the shift-free FMM's potential and field E = -grad phi, the local expansions
+    differentiated term by term (E = (-Re f', Im f') for phi = Re f) plus the direct near field."""
+    xy = _f64(xy).reshape(-1, 2)
+    q = _f64(q).reshape(-1)
+    n = q.shape[0]
+    phi = np.empty(n)
+    E = np.empty((n, 2))
+    _check(_load().oracle_shiftfree_field(n, _ptr(xy), _ptr(q), levels, p, box, _ptr(phi), _ptr(E)))
+    return phi, E
+
+
+def local_eval_deriv(b, centre, z) -> complex:
+    """f'(z) = sum_{l>=1} l b_l (z - c)^(l-1) of a local expansion about ``centre``."""
+    br = _c2r(b)
+    im = ctypes.c_double(0.0)
+    re = _load().oracle_local_eval_deriv(_ptr(br), len(b) - 1, centre.real, centre.imag, z.real, z.imag,
+                                         ctypes.byref(im))
+    return complex(re, im.value)
 
 
 def classical(xy, q, levels: int, p: int, box: float = 5.0) -> np.ndarray:

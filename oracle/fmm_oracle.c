@@ -46,6 +46,13 @@
  * contribute 0; the interaction lists of ALL levels 2..l are converted (the
  * text's "k < l" would drop the finest level's well-separated pairs).
  *
+ * Force field (Sec. 3: the paper's timings cover "potential and force
+ * fields"): E = -grad phi.  With phi = Re f(z), f analytic, grad phi =
+ * (Re f', -Im f'), so E = (-Re f'(z), Im f'(z)); oracle_direct_field is the
+ * definition, E_i = -sum_{j != i, r > 0} q_j (z_i - z_j) / |z_i - z_j|^2, and
+ * oracle_shiftfree_field differentiates the same method term by term (each
+ * level's local expansion, sum_l l b_l (z - c)^(l-1), plus the near field).
+ *
  * Loops over independent outputs carry OpenMP pragmas; no reduction crosses
  * threads, so results do not depend on the thread count.
  */
@@ -448,6 +455,62 @@ static void near_field(const tree_t *t, const double *xy, const double *q, doubl
 }
 
 /* ------------------------------------------------------------------------ */
+/* force field E = -grad phi                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* grad phi contribution at (xi, yi) of a charge qj at (xj, yj): qj (z_i - z_j) / r^2; 0 at r = 0 */
+static void pair_grad(double xi, double yi, double xj, double yj, double qj, double *gx, double *gy) {
+    double dx = xi - xj, dy = yi - yj;
+    double r2 = dx * dx + dy * dy;
+    if (r2 > 0.0) { *gx += qj * dx / r2; *gy += qj * dy / r2; }
+}
+
+/* E at targets[t]: E[2t] = Ex, E[2t+1] = Ey. */
+int oracle_direct_field_targets(int64_t n, const double *xy, const double *q,
+                                int64_t n_targets, const int64_t *targets, double *E) {
+    if (n < 0 || n_targets < 0) return ORACLE_ERR_ARG;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n_targets; ++t) {
+        int64_t i = targets[t];
+        double gx = 0.0, gy = 0.0;
+        for (int64_t j = 0; j < n; ++j)
+            if (j != i) pair_grad(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1], q[j], &gx, &gy);
+        E[2 * t] = -gx;
+        E[2 * t + 1] = -gy;
+    }
+    return ORACLE_OK;
+}
+
+int oracle_direct_field(int64_t n, const double *xy, const double *q, double *E) {
+    if (n < 0) return ORACLE_ERR_ARG;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double gx = 0.0, gy = 0.0;
+        for (int64_t j = 0; j < n; ++j)
+            if (j != i) pair_grad(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1], q[j], &gx, &gy);
+        E[2 * i] = -gx;
+        E[2 * i + 1] = -gy;
+    }
+    return ORACLE_OK;
+}
+
+/* f'(z) of a local expansion about c: sum_{l>=1} l b_l (z - c)^(l-1) */
+static cplx local_eval_deriv(const cplx *b, int p, cplx c, cplx z) {
+    cplx u = z - c;
+    cplx acc = 0.0;
+    for (int l = p; l >= 1; --l) acc = acc * u + (double)l * b[l];
+    return acc;
+}
+
+double oracle_local_eval_deriv(const double *b_in, int p, double cx, double cy, double x, double y, double *im) {
+    cplx b[ORACLE_MAXP + 1];
+    for (int m = 0; m <= p; ++m) b[m] = b_in[2 * m] + I * b_in[2 * m + 1];
+    cplx d = local_eval_deriv(b, p, cx + I * cy, x + I * y);
+    *im = cimag(d);
+    return creal(d);
+}
+
+/* ------------------------------------------------------------------------ */
 /* shift-free FMM (Sec. 2.2.1)                                               */
 /* ------------------------------------------------------------------------ */
 
@@ -493,6 +556,60 @@ int oracle_shiftfree(int64_t n, const double *xy, const double *q, int levels, i
 /* ------------------------------------------------------------------------ */
 /* classical Greengard FMM with shifts (Sec. 2.1)                            */
 /* ------------------------------------------------------------------------ */
+
+/* The shift-free FMM with the field: phi as oracle_shiftfree, and E = -grad phi from the same
+ * local expansions (differentiated) and the same near field (E[2i] = Ex, E[2i+1] = Ey). */
+int oracle_shiftfree_field(int64_t n, const double *xy, const double *q, int levels, int p, double box,
+                           double *phi, double *E) {
+    binom_init();
+    tree_t t;
+    int rc = tree_build(&t, n, xy, levels, p, box);
+    if (rc) return rc;
+    double *gx = calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *gy = calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!gx || !gy) { free(gx); free(gy); tree_free(&t); return ORACLE_ERR_NOMEM; }
+    for (int64_t i = 0; i < n; ++i) phi[i] = 0.0;
+    for (int k = 2; k <= levels; ++k) {
+        cplx *a = moments_from_particles(&t, xy, q, k);
+        if (!a) { free(gx); free(gy); tree_free(&t); return ORACLE_ERR_NOMEM; }
+        cplx *b = locals_from_interaction_lists(&t, a, k);
+        free(a);
+        if (!b) { free(gx); free(gy); tree_free(&t); return ORACLE_ERR_NOMEM; }
+        int sh = levels - k, side = 1 << k;
+        #pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            int bx = t.ix[i] >> sh, by = t.iy[i] >> sh;
+            const cplx *bl = b + (size_t)(bx + by * side) * (p + 1);
+            cplx c = box_centre(bx, by, k, box), z = xy[2 * i] + I * xy[2 * i + 1];
+            phi[i] += local_eval(bl, p, c, z);
+            cplx d = local_eval_deriv(bl, p, c, z);     /* grad = (Re f', -Im f') */
+            gx[i] += creal(d);
+            gy[i] -= cimag(d);
+        }
+        free(b);
+    }
+    near_field(&t, xy, q, phi);
+    int side = t.side;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        double sx = 0.0, sy = 0.0;
+        for (int ny = t.iy[i] - 1; ny <= t.iy[i] + 1; ++ny)
+            for (int nx = t.ix[i] - 1; nx <= t.ix[i] + 1; ++nx) {
+                if (nx < 0 || ny < 0 || nx >= side || ny >= side) continue;
+                int64_t leaf = (int64_t)nx + (int64_t)ny * side;
+                for (int64_t r = t.start[leaf]; r < t.start[leaf + 1]; ++r) {
+                    int64_t j = t.order[r];
+                    if (j != i) pair_grad(xy[2 * i], xy[2 * i + 1], xy[2 * j], xy[2 * j + 1], q[j], &sx, &sy);
+                }
+            }
+        E[2 * i] = -(gx[i] + sx);
+        E[2 * i + 1] = -(gy[i] + sy);
+    }
+    free(gx);
+    free(gy);
+    tree_free(&t);
+    return ORACLE_OK;
+}
 
 int oracle_classical(int64_t n, const double *xy, const double *q, int levels, int p, double box, double *phi) {
     binom_init();

@@ -311,3 +311,77 @@ def test_a_dropped_level_is_caught(oracle_mod):
     d = oracle_mod.direct(xy, q)
     assert rel_l2(phi, d) < 1e-8
     assert rel_l2(phi - lev[4], d) > 1e-3
+
+
+# ---------------------------------------------------------------- force field E = -grad phi
+
+def _probe_phi(oracle_mod, xy, q, z, levels=None, p=None):
+    """phi at a zero-charge probe particle placed at z (it moves nothing else): the direct sum, or
+    the shift-free FMM when levels and p are given."""
+    xyp = np.vstack([xy, [[z.real, z.imag]]])
+    qp = np.concatenate([q, [0.0]])
+    if levels is None:
+        return oracle_mod.direct(xyp, qp)[-1]
+    return oracle_mod.shiftfree(xyp, qp, levels, p)[-1]
+
+
+def _probe_field(oracle_mod, xy, q, z, levels=None, p=None):
+    xyp = np.vstack([xy, [[z.real, z.imag]]])
+    qp = np.concatenate([q, [0.0]])
+    if levels is None:
+        return oracle_mod.direct_field(xyp, qp)[-1]
+    return oracle_mod.shiftfree_field(xyp, qp, levels, p)[1][-1]
+
+
+@pytest.mark.parametrize("levels,p", [(None, None), (3, 6), (4, 12), (5, 20)])
+def test_field_is_minus_the_gradient_of_phi(oracle_mod, levels, p):
+    """E = -grad phi by central differences of the oracle's own phi at a zero-charge probe, for the
+    direct sum and for the shift-free FMM at low and high order (the FMM field is the derivative of
+    the FMM potential whatever p is, so the match does not depend on the truncation)."""
+    xy, q = inputs.uniform(600, 41)
+    h = 1e-5
+    for z in (1.3 + 2.2j, 3.71 + 0.45j, 4.05 + 4.6j):
+        # keep the probe inside one finest square for the FMM (its expansions are per square)
+        if levels is not None:
+            s = 5.0 / (1 << levels)
+            z = complex((np.floor(z.real / s) + 0.5) * s, (np.floor(z.imag / s) + 0.5) * s)
+        gx = (_probe_phi(oracle_mod, xy, q, z + h, levels, p) - _probe_phi(oracle_mod, xy, q, z - h, levels, p)) / (2 * h)
+        gy = (_probe_phi(oracle_mod, xy, q, z + 1j * h, levels, p) -
+              _probe_phi(oracle_mod, xy, q, z - 1j * h, levels, p)) / (2 * h)
+        E = _probe_field(oracle_mod, xy, q, z, levels, p)
+        assert np.allclose(E, [-gx, -gy], rtol=1e-6, atol=1e-6 * np.hypot(gx, gy)), (E, -gx, -gy)
+
+
+@pytest.mark.parametrize("n,R", [(7, 1.3), (12, 0.8), (40, 2.2)])
+def test_field_at_ngon_vertices_closed_form(oracle_mod, n, R):
+    """Unit charges at the vertices of a regular n-gon: sum_{m=1}^{n-1} 1/(1 - w^m) = (n-1)/2 for the
+    n-th roots of unity w, so f'(z_k) = (n-1) / (2 R w^k) and E(z_k) = -(n-1)/(2R) (cos t_k, sin t_k),
+    radial.  Direct sum and the FMM at p = 50."""
+    xy, q = _ngon(n, R, "unit")
+    t = 2.0 * np.pi * np.arange(n) / n
+    want = -(n - 1) / (2.0 * R) * np.stack([np.cos(t), np.sin(t)], axis=1)
+    assert np.allclose(oracle_mod.direct_field(xy, q), want, rtol=1e-12, atol=1e-12)
+    _, E = oracle_mod.shiftfree_field(xy, q, 3, 50)
+    assert np.allclose(E, want, rtol=1e-10, atol=1e-10 * (n - 1) / (2 * R))
+
+
+def test_local_expansion_derivative_converges_to_the_source_field(oracle_mod):
+    """f'(z) of the local expansion of one far charge (P2M then M2L) tends to 1 / (z - z_s)."""
+    zs = 0.31 + 0.22j
+    cs, ct = 0.25 + 0.25j, 1.75 + 0.75j          # squares of side 0.5, three sides apart along x
+    for z in (1.6 + 0.9j, 1.95 + 0.55j):
+        errs = []
+        for p in (6, 12, 24):
+            a = oracle_mod.p2m(np.array([[zs.real, zs.imag]]), np.array([1.0]), cs, p)
+            b = oracle_mod.m2l(a, cs - ct)
+            errs.append(abs(oracle_mod.local_eval_deriv(b, ct, z) - 1.0 / (z - zs)))
+        assert errs[2] < 1e-9 and errs[1] < errs[0]
+
+
+def test_field_shiftfree_matches_direct_at_high_order(oracle_mod):
+    xy, q = inputs.gmm(3000, 43)
+    _, E = oracle_mod.shiftfree_field(xy, q, 5, 40)
+    ref = oracle_mod.direct_field(xy, q)
+    assert rel_l2(E, ref) < 1e-11
+    idx = np.array([0, 17, 2999])
+    assert np.allclose(oracle_mod.direct_field_targets(xy, q, idx), ref[idx], rtol=0, atol=1e-13 * np.abs(ref).max())
