@@ -145,6 +145,17 @@ fmm_status fmm_set_stream(fmm_plan_t plan, void* stream);
  * errors are reported by fmm_sync.  Coincident particles (r = 0) contribute 0. */
 fmm_status fmm_potential(fmm_plan_t plan, const double* xy, const double* q, double* phi);
 
+/* phi and the force field E = -grad phi at every particle, in input order (Sec. 3: the paper
+ * times the method for "potential and force fields").  With phi = Re f(z), f analytic, grad phi
+ * = (Re f', -Im f'): the far field differentiates each level's local expansion (sum over l of
+ * l b_l w^(l-1) / s_k for w = (z - c) / s_k), the near field adds q_j (z - z_j) / |z - z_j|^2 of
+ * the own and adjacent squares' particles; coincident particles contribute 0.
+ *   xy, q, phi  as for fmm_potential.
+ *   field       device, double[n][2]: (Ex, Ey) of particle i at field[2i], field[2i + 1];
+ *               written only if the device checks pass.
+ * Asynchronous on the plan's stream; allocates nothing.  Every precision. */
+fmm_status fmm_potential_field(fmm_plan_t plan, const double* xy, const double* q, double* phi, double* field);
+
 /* As fmm_potential, with HOST arrays: copies xy and q to plan-owned device
  * buffers, runs the method and copies phi back, then waits for the stream.
  * Host arrays may be pageable or pinned (pinned is faster).  Returns the

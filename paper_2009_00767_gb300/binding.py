@@ -60,6 +60,7 @@ SIGNATURES = {
     "fmm_set_concurrency": (_i32, [_vp, _i32]),
     "fmm_potential": (_i32, [_vp, _vp, _vp, _vp]),
     "fmm_potential_host": (_i32, [_vp, _vp, _vp, _vp]),
+    "fmm_potential_field": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "fmm_sync": (_i32, [_vp]),
     "fmm_plan_stats": (_i32, [_vp, ctypes.POINTER(fmm_stats)]),
     "fmm_leaf_keys": (_i32, [_vp, _vp]),
@@ -172,6 +173,11 @@ def fmm_set_concurrency(plan: int, streams: int):
 def fmm_potential(plan: int, xy, q, phi):
     """Enqueue phi = potential(xy, q) on the plan's stream; device buffers (float64)."""
     _check(_lib.fmm_potential(plan, _ptr(xy), _ptr(q), _ptr(phi)), "fmm_potential")
+
+
+def fmm_potential_field(plan: int, xy, q, phi, field):
+    """Enqueue phi and the field E = -grad phi ([n][2], float64) on the plan's stream; device buffers."""
+    _check(_lib.fmm_potential_field(plan, _ptr(xy), _ptr(q), _ptr(phi), _ptr(field)), "fmm_potential_field")
 
 
 def fmm_potential_host(plan: int, xy, q, phi):
@@ -413,6 +419,18 @@ class Plan:
         if sync:
             fmm_sync(self.handle)
         return phi
+
+    def potential_field(self, xy, q, phi=None, field=None, sync=True):
+        """(phi, E): the potential and the force field E = -grad phi, shape [n] and [n, 2]."""
+        import torch
+        if phi is None:
+            phi = torch.empty(self.n, dtype=torch.float64, device=xy.device)
+        if field is None:
+            field = torch.empty((self.n, 2), dtype=torch.float64, device=xy.device)
+        fmm_potential_field(self.handle, xy, q, phi, field)
+        if sync:
+            fmm_sync(self.handle)
+        return phi, field
 
     def potential_host(self, xy, q, phi=None):
         if phi is None:

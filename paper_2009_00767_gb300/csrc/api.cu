@@ -85,7 +85,8 @@ void free_plan(fmm_plan_s* pl) {
     cudaSetDevice(pl->device);
     void* bufs[] = {pl->keys, pl->rank, pl->counts, pl->leaf_start, pl->block_sums, pl->leaf_bstart,
                     pl->blk_map, pl->sorted_key,
-                    pl->sorted64, pl->sorted32, pl->phi_far, pl->T64, pl->T32, pl->d_status,
+                    pl->sorted64, pl->sorted32, pl->sorted_lo, pl->phi_far, pl->near_grad, pl->T64, pl->T32,
+                    pl->d_status,
                     pl->d_counters, pl->d_xy_stage, pl->d_q_stage, pl->d_phi_stage};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -131,7 +132,7 @@ fmm_status reset_accumulators(fmm_plan_s* pl, cudaStream_t st) {
     return FMM_OK;
 }
 
-fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* phi) {
+fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* phi, double* field = nullptr) {
     cudaStream_t st = pl->stream;
     if (cudaMemsetAsync(pl->d_counters, 0, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long), st) != cudaSuccess)
         return FMM_ERR_CUDA;
@@ -141,9 +142,9 @@ fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* ph
     }
     pl->ev_kernels = 0;
     cudaEventRecord(pl->ev[0], st);
-    int launches = fmm_launch_sort(pl, xy, q);
+    int launches = fmm_launch_sort(pl, xy, q, field != nullptr && pl->precision != FMM_FP64);
     if (launches < 0) return FMM_ERR_CUDA;
-    int more = pl->precision == FMM_FP64 ? fmm_launch_fp64(pl, phi) : fmm_launch_mixed(pl, phi);
+    int more = pl->precision == FMM_FP64 ? fmm_launch_fp64(pl, phi, field) : fmm_launch_mixed(pl, phi, field);
     if (more == -2) return FMM_ERR_UNSUPPORTED;
     if (more < 0) return FMM_ERR_CUDA;
     pl->launches = launches + more;
@@ -215,6 +216,9 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     else
         FMM_TRY(dev_alloc(pl, &pl->sorted32, sizeof(float4) * n));
     FMM_TRY(dev_alloc(pl, &pl->phi_far, sizeof(double) * n));
+    // the field's gradient accumulator (near field in the mixed path, far field in the FP64 path)
+    FMM_TRY(dev_alloc(pl, &pl->near_grad, sizeof(double2) * n));
+    if (precision != FMM_FP64) FMM_TRY(dev_alloc(pl, &pl->sorted_lo, sizeof(float2) * n));
     const size_t bcplx = precision == FMM_FP64 ? sizeof(double2) : sizeof(float2);
     for (int k = 2; k <= levels; ++k) {
         const size_t W = (size_t)fmm_grid_width(k);
@@ -306,6 +310,12 @@ fmm_status fmm_potential(fmm_plan_t plan, const double* xy, const double* q, dou
     if (!plan || !xy || !q || !phi) return FMM_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
     return enqueue(plan, xy, q, phi);
+}
+
+fmm_status fmm_potential_field(fmm_plan_t plan, const double* xy, const double* q, double* phi, double* field) {
+    if (!plan || !xy || !q || !phi || !field) return FMM_ERR_INVALID_ARG;
+    DeviceGuard g(plan->device);
+    return enqueue(plan, xy, q, phi, field);
 }
 
 fmm_status fmm_potential_host(fmm_plan_t plan, const double* xy_host, const double* q_host, double* phi_host) {

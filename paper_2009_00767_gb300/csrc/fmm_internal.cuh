@@ -99,10 +99,11 @@ struct fmm_plan_s {
     uint32_t* sorted_key;
     fmm_p64* sorted64;
     float4* sorted32;
-
+    float2* sorted_lo;           // mixed path, field calls: the local coordinates' FP32 rounding residues
     FmmLevelPtrs grids;
     size_t a_bytes[FMM_MAX_LEVELS + 1];
-    double* phi_far;                  // FP64 path: far field; mixed path: near field (float2 per particle)
+    double* phi_far;                  // FP64 path: far field; mixed path: near-field accumulator per particle
+    double2* near_grad;               // mixed path: near-field gradient accumulator (fmm_potential_field)
 
     double2* T64;       // FP64 operators [49][p+1][p+1]
     float2* T32;        // FP32 operators [49][p1b][p1b], zero-padded, [d][0][0] = 0 (mixed SIMT M2L)
@@ -191,6 +192,12 @@ static __device__ __forceinline__ bool finite_bits(double x) {
     return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
+// the rounding error of s = fl(a + b) (Knuth's TwoSum): a + b = s + err exactly
+static __device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+    const float bb = s - a;
+    return (a - (s - bb)) + (b - bb);
+}
+
 // a * (s.x + s.y) as an FP32 pair (FMA-exact product of the high word)
 static __device__ __forceinline__ float2 scatter_mul(float a, float2 s) {
     const float h = a * s.x;
@@ -201,7 +208,8 @@ static __device__ __forceinline__ float2 scatter_mul(float a, float2 s) {
 
 
 // --- launchers (each returns the number of kernels it launched, or -1 on a launch error) ---------
-int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q);
+// with_lo: also the rounding residues of the mixed path's local coordinates (sorted_lo)
+int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q, bool with_lo = false);
 int fmm_scan_blocks(int64_t m);
 int fmm_launch_scan(const uint32_t* counts, int64_t m, uint32_t* block_sums, uint32_t* leaf_start, uint32_t n_total,
                     cudaStream_t st);
@@ -227,8 +235,8 @@ static __device__ __forceinline__ uint32_t fmm_warp_search(const uint32_t* pre, 
     }
     return lo;
 }
-int fmm_launch_fp64(fmm_plan_s* pl, double* phi);
-int fmm_launch_mixed(fmm_plan_s* pl, double* phi);
+int fmm_launch_fp64(fmm_plan_s* pl, double* phi, double* field = nullptr);
+int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field);
 int fmm_m2l_bucket(int p1);
 int fmm_launch_direct_f64(int64_t n, const double* xy, const double* q, int64_t nt, const int64_t* targets,
                           double* phi_t, cudaStream_t stream);

@@ -130,14 +130,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_m2l_f64(M2LArgs a) {
 }
 
 // -------------------------------------------------------------------------------- L2P
+// kField: also the far field's gradient, grad phi = (Re f', -Im f') with f'(z) = sum_l l b_l w^(l-1) / s
+// (one Horner pass for the expansion and its derivative), per sorted particle into grad_far.
+template <bool kField>
 __global__ void k_l2p_f64(const fmm_p64* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n,
-                          int levels, int p, double box, FmmLevelPtrs g, double* __restrict__ phi_far) {
+                          int levels, int p, double box, FmmLevelPtrs g, double* __restrict__ phi_far,
+                          double2* __restrict__ grad_far) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const fmm_p64 P = sp[i];
     const uint32_t key = skey[i];
     const int p1 = p + 1;
-    double far = 0.0;
+    double far = 0.0, gx = 0.0, gy = 0.0;
     for (int k = 2; k <= levels; ++k) {
         const uint32_t kk = key >> (2 * (levels - k));
         const double s = box / (double)(1 << k);
@@ -146,26 +150,41 @@ __global__ void k_l2p_f64(const fmm_p64* __restrict__ sp, const uint32_t* __rest
         const double wx = (P.x - ((double)bx + 0.5) * s) * inv_s;
         const double wy = (P.y - ((double)by + 0.5) * s) * inv_s;
         const double2* Bt = reinterpret_cast<const double2*>(g.B[k]) + ((size_t)by * (1u << k) + bx) * p1;
-        double2 acc = Bt[p];
+        double2 acc = Bt[p], d = make_double2(0.0, 0.0);
         for (int l = p - 1; l >= 0; --l) {
             const double2 b = Bt[l];
+            if (kField) {   // d <- d w + acc before acc moves on: d ends as the derivative
+                const double dr = fma(d.x, wx, fma(-d.y, wy, acc.x));
+                const double di = fma(d.x, wy, fma(d.y, wx, acc.y));
+                d.x = dr;
+                d.y = di;
+            }
             const double r = fma(acc.x, wx, fma(-acc.y, wy, b.x));
             const double im = fma(acc.x, wy, fma(acc.y, wx, b.y));
             acc.x = r;
             acc.y = im;
         }
         far += acc.x;
+        if (kField) {
+            gx += d.x * inv_s;
+            gy -= d.y * inv_s;
+        }
     }
     phi_far[i] = far;
+    if (kField) grad_far[i] = make_double2(gx, gy);
 }
 
 // -------------------------------------------------------------------------------- P2P + final phi
 // One warp per finest square.  With T targets (T <= 32) the warp is split into 32 / T' groups
 // (T' = T rounded up to a power of two) that take interleaved sources, then combine by shuffles.
+// kField: also the near field's gradient q_j (z_i - z_j) / r^2, added to grad_far; the field
+// E = -grad phi goes to field[2 i], field[2 i + 1] in input order.
+template <bool kField>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_p2p_f64(const fmm_p64* __restrict__ sp, const uint32_t* __restrict__ leaf_start, int levels,
           const double* __restrict__ phi_far, double* __restrict__ phi, const unsigned int* __restrict__ status,
-          unsigned long long* __restrict__ counters) {
+          unsigned long long* __restrict__ counters, const double2* __restrict__ grad_far,
+          double* __restrict__ field) {
     const int lane = threadIdx.x & 31;
     const uint32_t leaf = (uint32_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const uint32_t nleaf = 1u << (2 * levels);
@@ -203,17 +222,37 @@ k_p2p_f64(const fmm_p64* __restrict__ sp, const uint32_t* __restrict__ leaf_star
         const bool active = ti < T;
         const uint32_t gi = t0 + (active ? ti : 0);
         const fmm_p64 Pi = sp[gi];
-        double acc = 0.0;
+        double acc = 0.0, ax = 0.0, ay = 0.0;
         for (int b = 0; b < nn; ++b) {
             for (uint32_t j = ns0[b] + grp; j < ns1[b]; j += groups) {
                 const fmm_p64 Pj = sp[j];
                 const double dx = Pi.x - Pj.x, dy = Pi.y - Pj.y;
                 const double r2 = fma(dx, dx, dy * dy);
-                if (j != gi && r2 > 0.0) acc = fma(Pj.q, 0.5 * log(r2), acc);
+                if (j != gi && r2 > 0.0) {
+                    acc = fma(Pj.q, 0.5 * log(r2), acc);
+                    if (kField) {
+                        const double w = Pj.q / r2;
+                        ax = fma(w, dx, ax);
+                        ay = fma(w, dy, ay);
+                    }
+                }
             }
         }
-        for (int o = tp; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (active && grp == 0) phi[(int64_t)Pi.w] = phi_far[gi] + acc;
+        for (int o = tp; o < 32; o <<= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (kField) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            }
+        }
+        if (active && grp == 0) {
+            phi[(int64_t)Pi.w] = phi_far[gi] + acc;
+            if (kField) {
+                const double2 gf = grad_far[gi];
+                field[2 * (int64_t)Pi.w] = -(gf.x + ax);
+                field[2 * (int64_t)Pi.w + 1] = -(gf.y + ay);
+            }
+        }
     }
 }
 
@@ -242,7 +281,7 @@ __global__ void k_direct_f64(int64_t n, const double2* __restrict__ xy, const do
 
 }  // namespace
 
-int fmm_launch_fp64(fmm_plan_s* pl, double* phi) {
+int fmm_launch_fp64(fmm_plan_s* pl, double* phi, double* field) {
     cudaStream_t st = pl->stream;
     const int64_t n = pl->n;
     const int L = pl->levels, p = pl->p;
@@ -286,7 +325,12 @@ int fmm_launch_fp64(fmm_plan_s* pl, double* phi) {
     // L2P
     {
         const unsigned blocks = (unsigned)((n + 127) / 128);
-        k_l2p_f64<<<blocks, 128, 0, st>>>(pl->sorted64, pl->sorted_key, n, L, p, pl->box, pl->grids, pl->phi_far);
+        if (field)
+            k_l2p_f64<true><<<blocks, 128, 0, st>>>(pl->sorted64, pl->sorted_key, n, L, p, pl->box, pl->grids,
+                                                    pl->phi_far, pl->near_grad);
+        else
+            k_l2p_f64<false><<<blocks, 128, 0, st>>>(pl->sorted64, pl->sorted_key, n, L, p, pl->box, pl->grids,
+                                                     pl->phi_far, nullptr);
         ++launches;
     }
     cudaEventRecord(pl->ev[4], st);
@@ -294,8 +338,14 @@ int fmm_launch_fp64(fmm_plan_s* pl, double* phi) {
     {
         const uint32_t nleaf = 1u << (2 * L);
         const unsigned blocks = (nleaf + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        k_p2p_f64<<<blocks, kWarpsPerBlock * 32, 0, st>>>(pl->sorted64, pl->leaf_start, L, pl->phi_far, phi,
-                                                          pl->d_status, pl->d_counters);
+        if (field)
+            k_p2p_f64<true><<<blocks, kWarpsPerBlock * 32, 0, st>>>(pl->sorted64, pl->leaf_start, L, pl->phi_far, phi,
+                                                                    pl->d_status, pl->d_counters, pl->near_grad,
+                                                                    field);
+        else
+            k_p2p_f64<false><<<blocks, kWarpsPerBlock * 32, 0, st>>>(pl->sorted64, pl->leaf_start, L, pl->phi_far,
+                                                                     phi, pl->d_status, pl->d_counters, nullptr,
+                                                                     nullptr);
         ++launches;
     }
     cudaEventRecord(pl->ev[5], st);

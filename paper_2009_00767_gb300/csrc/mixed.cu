@@ -627,6 +627,50 @@ k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
     phi[__float_as_int(P.w)] = p2p_phi(far, fmm_d2ff_bits(nd));
 }
 
+// L2P with the field: per level the local expansion F(w) = sum_{l>=1} b'_l w^l and its derivative by
+// one Horner pass (q <- q w + b_l, d <- d w + q), f'(z) = F'(w) / s_k, grad phi = (Re f', -Im f'),
+// levels summed in float-float; E = -(far + near gradient) written as (Ex, Ey) in input order.
+template <int P1B>
+__global__ void __launch_bounds__(128)
+k_l2p_field(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int p,
+            MixedLevels lv, FmmLevelPtrs g, const double* __restrict__ near, const double2* __restrict__ nearg,
+            const unsigned int* __restrict__ status, double* __restrict__ phi, double* __restrict__ field) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double nd = near[i];
+    const double2 ng = nearg[i];
+    const float4 P = sp[i];
+    const uint32_t key = skey[i];
+    const uint32_t ix = fmm_compact2(key), iy = fmm_compact2(key >> 1);
+    const int p1 = p + 1;
+    float2 far = make_float2(0.f, 0.f), gx = make_float2(0.f, 0.f), gy = make_float2(0.f, 0.f);
+    for (int k = 2; k <= levels; ++k) {
+        const int sh = levels - k;
+        const float2 w = level_w(P.x, P.y, ix, iy, sh, lv.inv_s[k]);
+        const size_t t = (size_t)(iy >> sh) * (1u << k) + (ix >> sh);
+        const float2* Bt = reinterpret_cast<const float2*>(g.B[k]) + t * p1;
+        float2 b[P1B];
+#pragma unroll
+        for (int l = 0; l < P1B; ++l) b[l] = l < p1 ? __ldg(Bt + l) : make_float2(0.f, 0.f);
+        float2 q = b[P1B - 1], d = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = P1B - 2; l >= 1; --l) {
+            d = cfma(d, w, q);
+            q = cfma(q, w, b[l]);
+        }
+        d = cfma(d, w, q);                                  // F'(w)
+        const float v = fmaf(q.x, w.x, -q.y * w.y);        // Re F(w)
+        far = ff_add(far, ff_add_f(b[0], v));
+        gx = ff_add_f(gx, d.x * lv.inv_s[k]);
+        gy = ff_add_f(gy, -d.y * lv.inv_s[k]);
+    }
+    if (*(volatile const unsigned int*)status != 0u) return;   // inputs failed the device checks
+    const int idx = __float_as_int(P.w);
+    phi[idx] = p2p_phi(far, fmm_d2ff_bits(nd));
+    field[2 * (int64_t)idx] = -(fmm_f2d_bits(gx.x) + fmm_f2d_bits(gx.y) + ng.x);
+    field[2 * (int64_t)idx + 1] = -(fmm_f2d_bits(gy.x) + fmm_f2d_bits(gy.y) + ng.y);
+}
+
 // -------------------------------------------------------------------------------- P2P
 // One warp per block of up to FMM_P2P_BLOCK targets of one finest square (the block -> square map
 // spares the warp a search); crowded squares spread over as many warps as they have blocks.  The
@@ -667,16 +711,52 @@ k_p2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
     if (lane < T) atomicAdd(acc + b0 + lane, fmm_f2d_bits(near.x) + fmm_f2d_bits(near.y));
 }
 
+// The near field with the gradient (fmm_potential_field): p2p_near_sym_field, the gradient sums
+// added to accg beside phi's to acc.  Three accumulators per target: fewer warps per SM.
+__global__ void __launch_bounds__(kP2PWarps * 32, 4)
+k_p2p_field(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start,
+            const uint32_t* __restrict__ bstart, const uint2* __restrict__ bmap, uint32_t nleaf, int levels,
+            float s_leaf, const float2* __restrict__ lo, double* __restrict__ acc, double2* __restrict__ accg,
+            unsigned int* __restrict__ status, unsigned long long* __restrict__ counters) {
+    __shared__ __align__(16) float4 tgt[kP2PWarps][16];
+    __shared__ __align__(16) float4 tlo[kP2PWarps][16];
+    __shared__ __align__(16) float2 tq[kP2PWarps][16];
+    __shared__ __align__(16) int4 seg[kP2PWarps][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t w = (uint32_t)blockIdx.x * kP2PWarps + warp;
+    const uint2 lt = bmap[w];
+    if (w >= bstart[nleaf]) return;
+    if (*(volatile const unsigned int*)status != 0u) return;
+    const uint32_t leaf = lt.x;
+    const uint32_t t0 = leaf_start[leaf], t1 = leaf_start[leaf + 1];
+    const uint32_t b0 = t0 + (uint32_t)FMM_P2P_BLOCK * lt.y;
+    const int T = (int)min((uint32_t)FMM_P2P_BLOCK, t1 - b0);
+    uint32_t pairs;
+    const NearField nf = p2p_near_sym_field(sp, lo, leaf_start, leaf, t0, t1, b0, T, levels, s_leaf, tgt[warp],
+                                            tlo[warp], tq[warp], seg[warp], lane, acc, accg, &pairs);
+    if (lane == 0) {
+        const unsigned slot = leaf % FMM_COUNTER_SLOTS;
+        atomicAdd(&counters[slot], (unsigned long long)pairs);
+        atomicMax(&counters[FMM_COUNTER_SLOTS + slot], (unsigned long long)(t1 - t0));
+    }
+    if (lane < T) {
+        atomicAdd(acc + b0 + lane, fmm_f2d_bits(nf.phi.x) + fmm_f2d_bits(nf.phi.y));
+        atomicAdd(&accg[b0 + lane].x, fmm_f2d_bits(nf.gx.x) + fmm_f2d_bits(nf.gx.y));
+        atomicAdd(&accg[b0 + lane].y, fmm_f2d_bits(nf.gy.x) + fmm_f2d_bits(nf.gy.y));
+    }
+}
+
 }  // namespace
 
 // The near field on the plan's second stream: forked from the plan's stream at this point of its
 // work (any point after the sort will do), joined back before L2P.
-int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv) {
+int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv, bool with_field) {
     cudaStream_t st = pl->stream, s2 = pl->serial ? pl->stream : pl->stream2;
     // the near-field accumulator starts at zero: cleared on stream2 as soon as the call starts (the
     // start event follows the previous call's L2P, its last reader), beside the sort and fine P2M
     if (s2 != st && cudaStreamWaitEvent(s2, pl->ev[0], 0) != cudaSuccess) return -1;
     if (cudaMemsetAsync(pl->phi_far, 0, sizeof(double) * (size_t)pl->n, s2) != cudaSuccess) return -1;
+    if (with_field && cudaMemsetAsync(pl->near_grad, 0, sizeof(double2) * (size_t)pl->n, s2) != cudaSuccess) return -1;
     if (cudaEventRecord(pl->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(s2, pl->ev_fork, 0) != cudaSuccess)
         return -1;
     const int L = pl->levels;
@@ -687,8 +767,13 @@ int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv) {
     const uint64_t wmax = (uint64_t)nleaf + (uint64_t)(n / FMM_P2P_BLOCK) + 1;
     const unsigned blocks = (unsigned)((wmax + kP2PWarps - 1) / kP2PWarps);
     cudaEventRecord(pl->ev[8], s2);
-    k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, s2>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, pl->blk_map, nleaf,
-                                                  L, lv.s_leaf, pl->phi_far, pl->d_status, pl->d_counters);
+    if (with_field)
+        k_p2p_field<<<blocks, kP2PWarps * 32, 0, s2>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, pl->blk_map,
+                                                      nleaf, L, lv.s_leaf, pl->sorted_lo, pl->phi_far, pl->near_grad,
+                                                      pl->d_status, pl->d_counters);
+    else
+        k_p2p_mixed<<<blocks, kP2PWarps * 32, 0, s2>>>(pl->sorted32, pl->leaf_start, pl->leaf_bstart, pl->blk_map,
+                                                      nleaf, L, lv.s_leaf, pl->phi_far, pl->d_status, pl->d_counters);
     cudaEventRecord(pl->ev[9], s2);
     pl->ev_kernels |= 2;
     if (cudaEventRecord(pl->ev_join, s2) != cudaSuccess) return -1;
@@ -716,7 +801,7 @@ int fmm_m2l_bucket(int p1) {
     return -1;
 }
 
-int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
+int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field) {
     if (pl->precision != FMM_MIXED_FP32 && pl->precision != FMM_MIXED_TF32 && pl->precision != FMM_MIXED_3XTF32 &&
         pl->precision != FMM_MIXED_BF16 && pl->precision != FMM_MIXED_BF16X3 && pl->precision != FMM_MIXED_BF16X2)
         return -2;
@@ -749,7 +834,7 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     // chain (stream3) needs the sort and, for the coarse M2L, the fine levels' moments of levels
     // up to 5; the fine levels' M2L stays here.  All three join before L2P.  (With
     // fmm_set_concurrency(plan, 1) they run one after the other on the plan's stream.)
-    const int r = fmm_launch_p2p_concurrent(pl, lv);   // records ev_fork on the plan's stream
+    const int r = fmm_launch_p2p_concurrent(pl, lv, field != nullptr);   // records ev_fork on the plan's stream
     if (r < 0) return -1;
     launches += r;
     if (L >= 2) {
@@ -851,7 +936,20 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi) {
     if (cudaStreamWaitEvent(st, pl->ev_join, 0) != cudaSuccess) return -1;   // the near field is done
     if (L >= 2 && cudaStreamWaitEvent(st, pl->ev_join3, 0) != cudaSuccess) return -1;   // and the coarse levels
     cudaEventRecord(pl->ev[4], st);
-    {
+    if (field != nullptr) {
+        const unsigned blocks = (unsigned)((n + 127) / 128);
+        switch (pl->p1b) {
+#define FMM_L2PF(PB)                                                                                         \
+    case PB:                                                                                                 \
+        k_l2p_field<PB><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids, near,      \
+                                                pl->near_grad, pl->d_status, phi, field);                    \
+        break;
+            FMM_L2PF(9) FMM_L2PF(13) FMM_L2PF(17) FMM_L2PF(21) FMM_L2PF(25) FMM_L2PF(33) FMM_L2PF(41)
+#undef FMM_L2PF
+            default: return -2;
+        }
+        ++launches;
+    } else {
         const unsigned blocks = (unsigned)((n + 127) / 128);
         switch (pl->p1b) {
 #define FMM_L2P(PB)                                                                                          \

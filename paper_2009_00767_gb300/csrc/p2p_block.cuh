@@ -28,6 +28,13 @@ __device__ __forceinline__ float mufu_lg2(float x) {
     return r;
 }
 
+// 1 / x on the MUFU unit (within one ulp)
+__device__ __forceinline__ float mufu_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Sum of v[l & (W - 1)] over the warp's lanes, returned in lane l (v[t] = p[t / 2].x or .y for
 // t < 2 NP, 0 beyond).  The low log2(W) lane bits scatter (at the step with mask m a lane keeps
 // the half of its live entries whose bit m matches its own and sends the other half to its
@@ -384,6 +391,197 @@ __device__ __forceinline__ float2 p2p_near_sym(const float4* __restrict__ sp, co
         case 4: return p2p_block_sym<8>(S, tgt, tq, lane, acc);
         case 5: return p2p_block_sym<10>(S, tgt, tq, lane, acc);
         default: return p2p_block_sym<12>(S, tgt, tq, lane, acc);
+    }
+}
+
+// ---------------------------------------------------------------- near field with the field
+// The same symmetric scheme with grad phi beside phi: a pair adds q_s log2 r^2 to the target's
+// phi and q_s (dx, dy) / r^2 to its gradient (dx, dy = target - source), and for a forward pair q_t
+// log2 r^2 and -q_t (dx, dy) / r^2 to the source's; 1 / r^2 comes from the MUFU reciprocal.  A
+// coincident own-square pair (r^2 = 0) gives 0 to both.  The field of a close pair goes as 1 / r,
+// so FP32 square-local coordinates alone (about 1e-9 of the box) would limit it; each coordinate
+// also carries its FP32 rounding residue (written by the sort for field calls), and a pair's
+// difference takes the high words (exact for close pairs) plus the residues' difference.
+struct NearField {
+    float2 phi, gx, gy;   // float-float sums of target `lane`
+};
+
+template <bool kOwn, int NP>
+__device__ __forceinline__ float3 p2p_chunk_field(float2 (&pp)[NP], float2 (&px)[NP], float2 (&py)[NP],
+                                                  const float4* __restrict__ tg, const float4* __restrict__ tl,
+                                                  const float2* __restrict__ tq, float4 src, float2 slo) {
+    const float2 nsx = make_float2(-src.x, -src.x), nsy = make_float2(-src.y, -src.y);
+    const float2 nlx = make_float2(-slo.x, -slo.x), nly = make_float2(-slo.y, -slo.y);
+    const float2 q2 = make_float2(src.z, src.z);
+    const float2 tiny = make_float2(0x1p-100f, 0x1p-100f);
+    float2 sp = make_float2(0.f, 0.f), sx = make_float2(0.f, 0.f), sy = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int tp = 0; tp < NP; ++tp) {
+        const float4 t = tg[tp], u = tl[tp];
+        // the coordinates' high words differ exactly for close pairs; the low words carry the rest
+        const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(t.x, t.y), nsx), __fadd2_rn(make_float2(u.x, u.y), nlx));
+        const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(t.z, t.w), nsy), __fadd2_rn(make_float2(u.z, u.w), nly));
+        float2 r2, lg, iv;
+        if (kOwn) {
+            r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+            lg = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
+            iv = make_float2(mufu_rcp(r2.x), mufu_rcp(r2.y));
+            lg.x = r2.x > 0.f ? lg.x : 0.f;
+            lg.y = r2.y > 0.f ? lg.y : 0.f;
+            iv.x = r2.x > 0.f ? iv.x : 0.f;
+            iv.y = r2.y > 0.f ? iv.y : 0.f;
+        } else {
+            r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, tiny));
+            lg = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
+            iv = make_float2(mufu_rcp(r2.x), mufu_rcp(r2.y));
+        }
+        const float2 wx = __fmul2_rn(dx, iv), wy = __fmul2_rn(dy, iv);   // (dx, dy) / r^2
+        pp[tp] = __ffma2_rn(q2, lg, pp[tp]);
+        px[tp] = __ffma2_rn(q2, wx, px[tp]);
+        py[tp] = __ffma2_rn(q2, wy, py[tp]);
+        if (!kOwn) {
+            const float2 qt = tq[tp];
+            sp = __ffma2_rn(qt, lg, sp);
+            sx = __ffma2_rn(qt, wx, sx);
+            sy = __ffma2_rn(qt, wy, sy);
+        }
+    }
+    return make_float3(sp.x + sp.y, -(sx.x + sx.y), -(sy.x + sy.y));   // the source's phi and gradient
+}
+
+// the source of chunk c with its coordinates' low words (frame shift by TwoSum), for the field
+__device__ __forceinline__ float4 load_lo(const P2PSymSources& S, const float2* __restrict__ lo, uint32_t c, int lane,
+                                          uint32_t* idx, float2* vlo) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    *vlo = make_float2(0.f, 0.f);
+    *idx = 0xffffffffu;
+    if (c < S.nch_own) {
+        const uint32_t s = 32u * c + (uint32_t)lane;
+        if (s < S.n_own) {
+            v = S.sp[S.t0 + s];
+            *vlo = lo[S.t0 + s];
+        }
+    } else {
+        const uint32_t s = 32u * (c - S.nch_own) + (uint32_t)lane;
+        if (s < S.n_fw) {
+            const int b = (s >= S.thr[0] ? 1 : 0) + (s >= S.thr[1] ? 1 : 0) + (s >= S.thr[2] ? 1 : 0);
+            const int4 g = S.seg[b];
+            *idx = s + (uint32_t)g.x;
+            v = S.sp[*idx];
+            float2 l = lo[*idx];
+            const float ox = __int_as_float(g.y), oy = __int_as_float(g.z);
+            const float sx = v.x + ox, sy = v.y + oy;
+            l.x += two_sum_err(v.x, ox, sx);
+            l.y += two_sum_err(v.y, oy, sy);
+            v.x = sx;
+            v.y = sy;
+            *vlo = l;
+        }
+    }
+    return v;
+}
+
+template <int NP>
+__device__ __forceinline__ NearField p2p_block_sym_field(const P2PSymSources& S, const float2* __restrict__ lo,
+                                                         const float4* __restrict__ tg, const float4* __restrict__ tl,
+                                                         const float2* __restrict__ tq, int lane,
+                                                         double* __restrict__ acc, double2* __restrict__ accg) {
+    constexpr int W = NP <= 2 ? 4 : (NP <= 4 ? 8 : (NP <= 8 ? 16 : 32));
+    const uint32_t nch = S.nch_own + (S.n_fw + 31u) / 32u;
+    NearField out;
+    out.phi = out.gx = out.gy = make_float2(0.f, 0.f);
+    for (uint32_t r0 = 0; r0 < nch; r0 += kP2PRun) {
+        const uint32_t r1 = min(nch, r0 + (uint32_t)kP2PRun);
+        float2 pp[NP], px[NP], py[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) pp[i] = px[i] = py[i] = make_float2(0.f, 0.f);
+        uint32_t idx;
+        float2 clo;
+        float4 cur = load_lo(S, lo, r0, lane, &idx, &clo);
+        for (uint32_t c = r0; c < r1; ++c) {
+            uint32_t nidx = idx;
+            float2 nlo = clo;
+            const float4 nxt = (c + 1 < r1) ? load_lo(S, lo, c + 1, lane, &nidx, &nlo) : cur;
+            if (c < S.nch_own) {
+                p2p_chunk_field<true, NP>(pp, px, py, tg, tl, tq, cur, clo);
+            } else {
+                const float3 sv = p2p_chunk_field<false, NP>(pp, px, py, tg, tl, tq, cur, clo);
+                if (idx != 0xffffffffu) {
+                    atomicAdd(acc + idx, fmm_f2d_bits(sv.x));
+                    atomicAdd(&accg[idx].x, fmm_f2d_bits(sv.y));
+                    atomicAdd(&accg[idx].y, fmm_f2d_bits(sv.z));
+                }
+            }
+            cur = nxt;
+            idx = nidx;
+            clo = nlo;
+        }
+        out.phi = ff_add_f(out.phi, warp_reduce_scatter<W, NP>(pp, lane));
+        out.gx = ff_add_f(out.gx, warp_reduce_scatter<W, NP>(px, lane));
+        out.gy = ff_add_f(out.gy, warp_reduce_scatter<W, NP>(py, lane));
+    }
+    return out;
+}
+
+// p2p_near_sym with the gradient: target `lane`'s phi (log2 r^2 units) and grad phi sums; the
+// forward sources' shares go to acc and accg.
+__device__ __forceinline__ NearField p2p_near_sym_field(const float4* __restrict__ sp, const float2* __restrict__ lo,
+                                                        const uint32_t* __restrict__ ls, uint32_t leaf, uint32_t t0,
+                                                        uint32_t t1, uint32_t b0, int T, int levels, float s_leaf,
+                                                        float4* tgt, float4* tlo, float2* tq, int4* seg, int lane,
+                                                        double* __restrict__ acc, double2* __restrict__ accg,
+                                                        uint32_t* pairs) {
+    const uint2 nb = p2p_forward(ls, leaf, levels, lane);
+    const uint32_t n_own = t1 - t0;
+    uint32_t incl = nb.y;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t excl = incl - nb.y;
+    const uint32_t n_fw = __shfl_sync(0xffffffffu, incl, 3);
+    if (lane < 4) {
+        const float ox = (float)(lane == 3 ? -1 : (lane == 2 ? 0 : 1)) * s_leaf;
+        const float oy = (float)(lane == 0 ? 0 : 1) * s_leaf;
+        seg[lane] = make_int4((int)(nb.x - excl), __float_as_int(ox), __float_as_int(oy), 0);
+    }
+    P2PSymSources S;
+    S.sp = sp;
+    S.seg = seg;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) S.thr[i] = __shfl_sync(0xffffffffu, excl, i + 1);
+    S.t0 = t0;
+    S.n_own = n_own;
+    S.nch_own = (n_own + 31u) / 32u;
+    S.n_fw = n_fw;
+    *pairs = (uint32_t)T * (n_own + 2u * n_fw) - (uint32_t)T;
+    {
+        float x = 0.f, y = 0.f, q = 0.f;
+        float2 l = make_float2(0.f, 0.f);
+        if (lane < T) {
+            const float4 P = sp[b0 + lane];
+            x = P.x;
+            y = P.y;
+            q = P.z;
+            l = lo[b0 + lane];
+        }
+        float* t = reinterpret_cast<float*>(&tgt[lane >> 1]);
+        t[lane & 1] = x;
+        t[2 + (lane & 1)] = y;
+        float* u = reinterpret_cast<float*>(&tlo[lane >> 1]);
+        u[lane & 1] = l.x;
+        u[2 + (lane & 1)] = l.y;
+        reinterpret_cast<float*>(&tq[lane >> 1])[lane & 1] = q;
+    }
+    __syncwarp();
+    switch ((T + 3) >> 2) {
+        case 1: return p2p_block_sym_field<2>(S, lo, tgt, tlo, tq, lane, acc, accg);
+        case 2: return p2p_block_sym_field<4>(S, lo, tgt, tlo, tq, lane, acc, accg);
+        case 3: return p2p_block_sym_field<6>(S, lo, tgt, tlo, tq, lane, acc, accg);
+        case 4: return p2p_block_sym_field<8>(S, lo, tgt, tlo, tq, lane, acc, accg);
+        case 5: return p2p_block_sym_field<10>(S, lo, tgt, tlo, tq, lane, acc, accg);
+        default: return p2p_block_sym_field<12>(S, lo, tgt, tlo, tq, lane, acc, accg);
     }
 }
 

@@ -224,7 +224,7 @@ template <bool kMixed>
 __global__ void k_scatter(const double2* __restrict__ xy, const double* __restrict__ q, int64_t n, int levels,
                           float2 s_ff, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank,
                           const uint32_t* __restrict__ leaf_start, uint32_t* __restrict__ sorted_key,
-                          fmm_p64* __restrict__ s64, float4* __restrict__ s32) {
+                          fmm_p64* __restrict__ s64, float4* __restrict__ s32, float2* __restrict__ s32_lo) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t key = keys[i];
@@ -238,9 +238,12 @@ __global__ void k_scatter(const double2* __restrict__ xy, const double* __restri
         const float2 cx = scatter_mul((float)fmm_compact2(key) + 0.5f, s_ff);
         const float2 cy = scatter_mul((float)fmm_compact2(key >> 1) + 0.5f, s_ff);
         const float2 xf = fmm_d2ff_bits(p.x), yf = fmm_d2ff_bits(p.y), qf = fmm_d2ff_bits(qq);
-        const float dx = (xf.x - cx.x) + (xf.y - cx.y);   // the high words are close: little is lost
-        const float dy = (yf.x - cy.x) + (yf.y - cy.y);
+        const float hx = xf.x - cx.x, hy = yf.x - cy.x;   // exact: the high words are close
+        const float lx = xf.y - cx.y, ly = yf.y - cy.y;
+        const float dx = hx + lx, dy = hy + ly;
         s32[pos] = make_float4(dx, dy, qf.x + qf.y, __int_as_float((int)i));
+        // the rounding residue of the local coordinates, for the field's near pairs (TwoSum)
+        if (s32_lo) s32_lo[pos] = make_float2(two_sum_err(hx, lx, dx), two_sum_err(hy, ly, dy));
     } else {
         s64[pos] = fmm_p64{p.x, p.y, qq, (double)i};
     }
@@ -248,7 +251,7 @@ __global__ void k_scatter(const double2* __restrict__ xy, const double* __restri
 
 }  // namespace
 
-int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
+int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q, bool with_lo) {
     const int64_t n = pl->n;
     const int64_t m = (int64_t)1 << (2 * pl->levels);
     cudaStream_t st = pl->stream;
@@ -288,11 +291,11 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q) {
     if (pl->precision == FMM_FP64)
         k_scatter<false><<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, s_ff,
                                               pl->keys, pl->rank, pl->leaf_start, pl->sorted_key, pl->sorted64,
-                                              pl->sorted32);
+                                              pl->sorted32, nullptr);
     else
         k_scatter<true><<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, s_ff,
                                              pl->keys, pl->rank, pl->leaf_start, pl->sorted_key, pl->sorted64,
-                                             pl->sorted32);
+                                             pl->sorted32, with_lo ? pl->sorted_lo : nullptr);
     ++launches;
     if (cudaGetLastError() != cudaSuccess) return -1;
     return launches;
