@@ -69,6 +69,7 @@ def parse():
                     help="skip the batched form (1024 systems, N log-uniform in [1024, 262144], against a loop "
                          "of single-system launches)")
     ap.add_argument("--batched-systems", type=int, default=1024)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned (levels, p) selector's leg")
     return ap.parse_args()
 
 
@@ -458,6 +459,10 @@ def run_ours(args):
         batched = run_batched(binding, torch, dev, args.batched_systems, max(5, min(args.steps, 20)), 3,
                               args.precision)
 
+    learned = None
+    if not args.no_learned and args.precision != "fp64":
+        learned = run_learned(binding, torch, dev, args.precision, flush)
+
     cpu = None
     if rank == 0 and not args.no_cpu and ws == 1:
         cpu = cpu_baseline(w, xy, q)
@@ -477,7 +482,7 @@ def run_ours(args):
             "roofline_stages": roof_all,
             "gpu_launches": launches, "e2e": e2e, "fp64_gpu": fp64, "alu_peaks_probe": probe,
             "speedup_vs_fp64_gpu": (value / fp64["value"]) if fp64 else None,
-            "cpu_baseline": cpu, "batched": batched, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+            "cpu_baseline": cpu, "batched": batched, "learned": learned, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                                             "reasons": clk["reasons"], "samples": clk["samples"]},
             "wall_s_timed": wall,
         }
@@ -574,6 +579,70 @@ def run_batched(binding, torch, dev, nsys, steps, warmup, precision):
             "precision": precision, "p": 16, "rel_l2_err_max": max(e["rel_l2_err"] for e in errs),
             "meets_error_bound": all(e["rel_l2_err"] <= ERR_BOUND for e in errs), "sampled_systems": errs,
             "timing": "CUDA events around each graph replay, median of the steps"}
+
+
+# ---------------------------------------------------------------- learned selector
+
+# held out (training seeds start at 700000, evaluation at 710000): two systems of each family --
+# uniform (990001, 990007), Gaussian mixture (990005, 990006), annulus (990002, 990003)
+LEARNED_SEEDS = (990001, 990007, 990005, 990006, 990002, 990003)
+
+
+def run_learned(binding, torch, dev, precision, flush, steps=20):
+    """The learned form: for held-out systems of the selector's family (N log-uniform in [2^16, 2^20],
+    uniform / Gaussian mixture / annulus), the trained network's (levels, p) pick against the fixed
+    (8, 20) and the no-network rule, each timed (median of `steps` calls, L2 flushed) and judged by
+    the FP64 direct sum at 1024 sampled targets."""
+    from paper_2009_00767_gb300 import inputs, selector
+    model = os.path.join(ROOT, "paper_2009_00767_gb300", "selector_gb300.bin")
+    if not os.path.exists(model):
+        return None
+    sel = binding.Selector(hidden=64, seed=1)
+    sel.load(model)
+    p_rule = selector.calibrate_p(ERR_BOUND, precision)   # the rule's p, calibrated live
+    rows = []
+    for sd in LEARNED_SEEDS:
+        name, xy, q = selector.system(sd)
+        n = int(q.shape[0])
+        xy_d = torch.from_numpy(xy).to(dev)
+        q_d = torch.from_numpy(q).to(dev)
+        idx = np.unique((inputs.u01(sd, 78, 1024) * n).astype(np.int64))
+        idx_d = torch.from_numpy(idx).to(dev)
+        ref = torch.empty(idx.shape[0], dtype=torch.float64, device=dev)
+        binding.fmm_direct_targets(xy_d, q_d, idx_d, ref)
+        torch.cuda.synchronize()
+        lev, p, fb = sel.select(xy_d, ERR_BOUND, 0.3)
+        row = {"seed": sd, "family": name, "n": n, "pick": [lev, p], "fallback_used": fb}
+        for key, (cl, cp) in (("pick", (lev, p)), ("fallback", selector.FALLBACK),
+                              ("rule", (selector.heuristic_levels(n), p_rule))):
+            phi = torch.empty(n, dtype=torch.float64, device=dev)
+            with binding.Plan(n, cl, cp, 5.0, precision) as plan:
+                for _ in range(3):
+                    binding.fmm_potential(plan.handle, xy_d, q_d, phi)
+                plan.sync()
+                ms = []
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                for _ in range(steps):
+                    flush.zero_()
+                    e0.record()
+                    binding.fmm_potential(plan.handle, xy_d, q_d, phi)
+                    e1.record()
+                    plan.sync()
+                    ms.append(e0.elapsed_time(e1))
+            row[f"ms_{key}"] = float(np.median(ms))
+            row[f"err_{key}"] = float(torch.linalg.norm(phi[idx_d] - ref) / torch.linalg.norm(ref))
+            if key == "rule":
+                row["rule"] = [cl, cp]
+        rows.append(row)
+    sel.close()
+    tot = {k: sum(r[f"ms_{k}"] for r in rows) for k in ("pick", "fallback", "rule")}
+    total_n = sum(r["n"] for r in rows)
+    return {"systems": rows, "precision": precision, "value": total_n / (tot["pick"] * 1e-3), "unit": UNIT,
+            "ms_total": tot, "speedup_vs_fallback": tot["fallback"] / tot["pick"],
+            "speedup_vs_rule": tot["rule"] / tot["pick"],
+            "meets_error_bound": all(r["err_pick"] <= ERR_BOUND for r in rows),
+            "rule_basis": f"no network: levels round(log4(N/16)), p {p_rule} = the smallest grid p meeting 1e-6 "
+                          f"on a 2^18 uniform calibration system"}
 
 
 # ---------------------------------------------------------------- CPU oracle

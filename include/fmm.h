@@ -318,7 +318,8 @@ fmm_status fmm_selector_save(fmm_selector_t sel, const char* path);
 fmm_status fmm_selector_load(fmm_selector_t sel, const char* path);
 
 /* Choose (levels, p) for xy (device, [n][2]): candidates levels = round(log4(n/16)) - 2 .. + 2
- * (clamped to 2..11) x p = 8, 12, .., 32; returns the cheapest predicted time among those
+ * (clamped to 2..11) x p = 8, 12, .., 28 (every precision takes them); returns the cheapest
+ * predicted time among those
  * whose predicted log10 error is at most log10(target_err) - margin_decades, else the fixed
  * fallback (8, 20) with *used_fallback = 1. */
 fmm_status fmm_select(fmm_selector_t sel, const double* xy, int64_t n, double box, double target_err,

@@ -427,7 +427,7 @@ fmm_status fmm_selector_load(fmm_selector_t s, const char* path) {
 }
 
 // Pick (levels, p) for the system xy: candidates levels = l0 - 2 .. l0 + 2 (l0 = round(log4(n / 16)),
-// clamped to 2..11) x p = 8, 12, ..., 32; the cheapest predicted time among those whose predicted
+// clamped to 2..11) x p = 8, 12, ..., 28; the cheapest predicted time among those whose predicted
 // log10 error is at most log10(target_err) - margin_decades; else the fallback (8, 20).
 fmm_status fmm_select(fmm_selector_t s, const double* xy, int64_t n, double box, double target_err,
                       double margin_decades, int* levels_out, int* p_out, int* used_fallback) {
@@ -439,7 +439,7 @@ fmm_status fmm_select(fmm_selector_t s, const double* xy, int64_t n, double box,
     std::vector<int> cl, cp;
     for (int l = l0 - 2; l <= l0 + 2; ++l) {
         if (l < 2 || l > 11) continue;
-        for (int p = 8; p <= 32; p += 4) {
+        for (int p = 8; p <= 28; p += 4) {
             cl.push_back(l);
             cp.push_back(p);
         }

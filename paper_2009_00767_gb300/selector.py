@@ -7,9 +7,14 @@ predicted to meet a requested accuracy, or the fixed fallback (8, 20).
 
 Its training tuples are generated by the method itself: for each synthetic system, every
 candidate of the grid is run through ``fmm_potential`` (in the precision given, by default the
-mixed FP32 form, which takes every p of fmm_select's grid), timed with CUDA events,
-and measured against the library's FP64 direct sum (``fmm_direct_targets``) on sampled targets.  The
-network is then fitted by the library's own forward / backward / Adam kernels.
+BF16x2 tensor-core form the benchmark quotes), timed with CUDA events, and measured against the
+library's FP64 direct sum (``fmm_direct_targets``) on sampled targets.  The network is then
+fitted by the library's own forward / backward / Adam kernels.
+
+``evaluate`` compares, on held-out systems, the learned pick with the fixed fallback, with a
+rule that uses no network (levels = round(log4(N / 16)), p = the smallest of the grid that meets
+the target on a uniform calibration system), and with the best candidate an exhaustive search of
+the grid finds (its regret).
 
 Workload of the tuples: N log-uniform in [2^16, 2^20]; families uniform, Gaussian mixture
 (K in [4, 64], sigma log-uniform in [0.02, 0.5], out-of-box draws redrawn) and annulus
@@ -29,8 +34,8 @@ import numpy as np
 from . import binding, inputs
 
 FALLBACK = (8, 20)
-P_GRID = (8, 12, 16, 20, 24, 28, 32)
-DEFAULT_PRECISION = "fp32"
+P_GRID = (8, 12, 16, 20, 24, 28)   # the p candidates of fmm_select
+DEFAULT_PRECISION = "bf16x2"
 TENSOR_CORE = ("tf32", "3xtf32", "bf16", "bf16x2", "bf16x3")   # these take p + 1 <= 32 coefficients
 LOG10_SCALE = 8.0           # the network predicts log10(error) / 8
 ERR_FLOOR = 1e-8            # errors below this are labelled at the floor
@@ -130,21 +135,74 @@ def best_feasible(meta_rows, target):
     return min(ok, key=lambda r: r["ms"]) if ok else None
 
 
-def evaluate(sel, seeds, target=1e-6, margin=0.3, precision=DEFAULT_PRECISION):
-    """Learned pick vs the fixed fallback on held-out systems, both measured against the FP64 direct sum."""
+def heuristic_levels(n):
+    """The depth that puts about 16 particles in a finest square, clamped to [2, 11]."""
+    return min(11, max(2, int(round(math.log(n / 16.0) / math.log(4.0)))))
+
+
+def calibrate_p(target=1e-6, precision=DEFAULT_PRECISION, n=1 << 18, seed=880001):
+    """The rule's p: the smallest p of the grid whose error on a uniform system of n particles (at
+    the rule's depth) meets the target, judged by the FP64 direct sum."""
     import torch
+    xy, q = inputs.uniform(n, seed)
+    xy_d = torch.from_numpy(xy).to("cuda")
+    q_d = torch.from_numpy(q).to("cuda")
+    idx_d, ref = reference_targets(torch, xy_d, q_d, n, seed)
+    for p in P_GRID:
+        err, _ = run_candidate(torch, xy_d, q_d, idx_d, ref, heuristic_levels(n), p, precision)
+        if err <= target:
+            return p
+    return P_GRID[-1]
+
+
+def evaluate(sel, seeds, target=1e-6, margin=0.3, precision=DEFAULT_PRECISION, exhaustive=False, p_rule=None):
+    """Learned pick vs the fixed fallback on held-out systems, both measured against the FP64 direct
+    sum; with ``exhaustive`` also the rule without a network (p_rule: its calibrated p) and the best
+    feasible candidate of the whole grid (the pick's regret = ms_pick / ms_best - 1)."""
+    import torch
+    if exhaustive and p_rule is None:
+        p_rule = calibrate_p(target, precision)
     rows = []
     for sd in seeds:
         name, xy, q = system(sd)
+        n = int(q.shape[0])
         xy_d = torch.from_numpy(xy).to("cuda")
         q_d = torch.from_numpy(q).to("cuda")
         lev, p, fb = sel.select(xy_d, target, margin)
-        idx_d, ref = reference_targets(torch, xy_d, q_d, q.shape[0], sd)
+        idx_d, ref = reference_targets(torch, xy_d, q_d, n, sd)
         err_l, ms_l = run_candidate(torch, xy_d, q_d, idx_d, ref, lev, p, precision)
         err_f, ms_f = run_candidate(torch, xy_d, q_d, idx_d, ref, *FALLBACK, precision)
-        rows.append({"seed": sd, "family": name, "n": int(q.shape[0]), "pick": [lev, p], "fallback_used": fb,
-                     "err_pick": err_l, "ms_pick": ms_l, "err_fallback": err_f, "ms_fallback": ms_f})
+        row = {"seed": sd, "family": name, "n": n, "pick": [lev, p], "fallback_used": fb,
+               "err_pick": err_l, "ms_pick": ms_l, "err_fallback": err_f, "ms_fallback": ms_f}
+        if exhaustive:
+            grid = []
+            for cl, cp in candidates(n, precision):
+                e, m = (err_l, ms_l) if (cl, cp) == (lev, p) else run_candidate(torch, xy_d, q_d, idx_d, ref, cl,
+                                                                               cp, precision)
+                grid.append({"levels": cl, "p": cp, "err": e, "ms": m})
+            best = best_feasible(grid, target)
+            hl = heuristic_levels(n)
+            err_h, ms_h = run_candidate(torch, xy_d, q_d, idx_d, ref, hl, p_rule, precision)
+            row.update({"rule": [hl, p_rule], "err_rule": err_h, "ms_rule": ms_h,
+                        "best": [best["levels"], best["p"]] if best else None,
+                        "ms_best": best["ms"] if best else None,
+                        "regret": (ms_l / best["ms"] - 1.0) if best else None})
+        rows.append(row)
     return rows
+
+
+def summary(rows, target=1e-6):
+    """Totals over held-out rows: time and the count meeting the target for each way of choosing."""
+    out = {"systems": len(rows)}
+    for key in ("pick", "fallback", "rule"):
+        if f"ms_{key}" in rows[0]:
+            out[key] = {"ms_total": sum(r[f"ms_{key}"] for r in rows),
+                        "met": sum(r[f"err_{key}"] <= target for r in rows)}
+    if rows and rows[0].get("ms_best") is not None:
+        out["best"] = {"ms_total": sum(r["ms_best"] for r in rows if r["ms_best"] is not None)}
+        reg = [r["regret"] for r in rows if r["regret"] is not None]
+        out["regret"] = {"mean": float(np.mean(reg)), "max": float(np.max(reg)), "median": float(np.median(reg))}
+    return out
 
 
 def main(argv=None):
@@ -171,15 +229,14 @@ def main(argv=None):
         losses.append(sel.train(X, T, 500, lr=1e-3 if chunk < 8 else 3e-4))
         print(f"epoch {(chunk + 1) * 500}: loss {losses[-1]:.5f}")
     sel.save(a.out)
-    ev = evaluate(sel, range(a.seed0 + 10_000, a.seed0 + 10_000 + a.eval_systems), precision=a.precision)
-    rep = {"train_tuples": int(X.shape[0]), "precision": a.precision, "losses": losses, "eval": ev}
+    ev = evaluate(sel, range(a.seed0 + 10_000, a.seed0 + 10_000 + a.eval_systems), precision=a.precision,
+                  exhaustive=True)
+    rep = {"train_tuples": int(X.shape[0]), "precision": a.precision, "losses": losses, "eval": ev,
+           "summary": summary(ev)}
     if a.report:
         with open(a.report, "w") as f:
             json.dump(rep, f, indent=1)
-    met = sum(r["err_pick"] <= 1e-6 for r in ev)
-    t_l = sum(r["ms_pick"] for r in ev)
-    t_f = sum(r["ms_fallback"] for r in ev)
-    print(f"held-out: {met}/{len(ev)} picks meet 1e-6; total ms learned {t_l:.2f} vs fallback {t_f:.2f}")
+    print("held-out:", json.dumps(summary(ev)))
 
 
 def build_lib():

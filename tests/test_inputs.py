@@ -35,8 +35,10 @@ def test_families_stay_in_the_box(fam):
 
 def test_selector_candidates_follow_the_precision():
     from paper_2009_00767_gb300 import selector
-    c32 = selector.candidates(1 << 20)                   # FP32 form: the whole p grid
-    ctc = selector.candidates(1 << 20, "bf16x3")         # tensor-core forms: p + 1 <= 32
-    assert max(p for _, p in c32) == 32 and max(p for _, p in ctc) == 28
+    c32 = selector.candidates(1 << 20, "fp32")           # the grid fmm_select scores: p = 8 .. 28
+    ctc = selector.candidates(1 << 20, "bf16x3")         # tensor-core forms take p + 1 <= 32: the same grid
+    assert max(p for _, p in c32) == 28 and max(p for _, p in ctc) == 28
+    assert sorted({p for _, p in c32}) == [8, 12, 16, 20, 24, 28]
     assert {lev for lev, _ in c32} == {6, 7, 8, 9, 10}   # round(log4(N / 16)) = 8, +-2
+    assert selector.heuristic_levels(1 << 20) == 8 and selector.heuristic_levels(100) == 2
     assert all(2 <= lev <= 11 for lev, _ in selector.candidates(1 << 10))
