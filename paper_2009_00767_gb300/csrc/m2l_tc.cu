@@ -443,7 +443,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
     if (fail && threadIdx.x == 0) atomicOr(a.status, FMM_FLAG_TIMEOUT);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    // ---- epilogue
+    // ---- epilogue: each thread's target row (p + 1 complex values, slot 0 the float-float Re b'_0)
+    // goes through a per-warp staging area in the window buffers (idle once the MMAs are done), then
+    // each row is stored by the lanes over its coefficients: 168 contiguous bytes per store at p = 20
+    // instead of one row per thread at a stride of two cells
+    const int RS = 2 * p1 + 1;   // staging row stride in floats (odd: no bank conflicts on the row writes)
+    static_assert((size_t)(kThreads / 32) * 32 * (2 * H + 1) * 4 <= (size_t)NSW * WIN_STAGE,
+                  "the epilogue's staging rows fit the window buffers");
+    float* stage = reinterpret_cast<float*>(win_buf) + (size_t)warp * 32 * RS;
 #pragma unroll
     for (int t = 0; t < kMaxRows; ++t) {
         if (t >= nrows || fail) break;
@@ -457,14 +464,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_m2l_tc(const __grid_constant__ 
 #pragma unroll
             for (int c = 0; c < N; ++c) v[c] += v[N + c];   // the column blocks of the stacked products
         }
-        if (bt[t] != nullptr) {
-            // Re b'_0: the GEMM's part added to the monopole-log term
-            float2* B = bt[t];
-            B[0] = ff_add_f(b0[t], v[0]);
+        float* row = stage + lane * RS;
+        const float2 r0 = ff_add_f(b0[t], v[0]);   // Re b'_0: the GEMM's part added to the monopole-log term
+        row[0] = r0.x;
+        row[1] = r0.y;
 #pragma unroll
-            for (int l = 1; l < H; ++l)
-                if (l < p1) B[l] = make_float2(v[l], v[H + l]);
+        for (int l = 1; l < H; ++l)
+            if (l < p1) {
+                row[2 * l] = v[l];
+                row[2 * l + 1] = v[H + l];
+            }
+        __syncwarp();
+        const unsigned long long mine = reinterpret_cast<unsigned long long>(bt[t]);
+        for (int r = 0; r < 32; ++r) {
+            float2* B = reinterpret_cast<float2*>(__shfl_sync(0xffffffffu, mine, r));
+            if (B != nullptr && lane < p1) B[lane] = make_float2(stage[r * RS + 2 * lane], stage[r * RS + 2 * lane + 1]);
         }
+        __syncwarp();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
