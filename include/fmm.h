@@ -159,9 +159,22 @@ fmm_status fmm_potential_field(fmm_plan_t plan, const double* xy, const double* 
 /* As fmm_potential, with HOST arrays: copies xy and q to plan-owned device
  * buffers, runs the method and copies phi back, then waits for the stream.
  * Host arrays may be pageable or pinned (pinned is faster).  Returns the
- * device-detected status, like fmm_sync. */
+ * device-detected status, like fmm_sync; after a device-detected error the
+ * contents of phi_host are unspecified.  Equivalent to fmm_potential_host_async
+ * followed by fmm_sync. */
 fmm_status fmm_potential_host(fmm_plan_t plan, const double* xy_host, const double* q_host,
                               double* phi_host);
+
+/* fmm_potential_host without the wait: enqueues the uploads, the method and the download of phi
+ * and returns.  The host arrays must stay valid, and xy_host / q_host unmodified, until the
+ * next fmm_sync returns; phi_host is written when the call's work completes.  The plan holds two
+ * staging sets, so in the mixed precisions successive calls overlap: a call's inputs go up (in
+ * chunks, each binned as it lands) while the previous call computes, and its phi comes down while
+ * the next one computes.  The device link carries about 200 GB/s each way on GB300, so this
+ * overlap, not a faster copy, is what hides the transfers.  fmm_sync waits for every call since
+ * the previous one and returns the first device-detected error among them. */
+fmm_status fmm_potential_host_async(fmm_plan_t plan, const double* xy_host, const double* q_host,
+                                    double* phi_host);
 
 /* Wait for the plan's stream; return the first device-detected error of the
  * calls since the previous fmm_sync (FMM_OK if none) and clear it. */

@@ -60,6 +60,7 @@ SIGNATURES = {
     "fmm_set_concurrency": (_i32, [_vp, _i32]),
     "fmm_potential": (_i32, [_vp, _vp, _vp, _vp]),
     "fmm_potential_host": (_i32, [_vp, _vp, _vp, _vp]),
+    "fmm_potential_host_async": (_i32, [_vp, _vp, _vp, _vp]),
     "fmm_potential_field": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "fmm_sync": (_i32, [_vp]),
     "fmm_plan_stats": (_i32, [_vp, ctypes.POINTER(fmm_stats)]),
@@ -183,6 +184,11 @@ def fmm_potential_field(plan: int, xy, q, phi, field):
 def fmm_potential_host(plan: int, xy, q, phi):
     """Host buffers (numpy float64 or pinned CPU tensors); waits and returns the device status."""
     _check(_lib.fmm_potential_host(plan, _ptr(xy), _ptr(q), _ptr(phi)), "fmm_potential_host")
+
+
+def fmm_potential_host_async(plan: int, xy, q, phi):
+    """Host buffers, without waiting: the arrays must stay valid until the next fmm_sync."""
+    _check(_lib.fmm_potential_host_async(plan, _ptr(xy), _ptr(q), _ptr(phi)), "fmm_potential_host_async")
 
 
 def fmm_sync(plan: int, check: bool = True) -> int:

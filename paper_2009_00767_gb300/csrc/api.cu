@@ -50,6 +50,10 @@ void build_operators(int p, std::vector<cd>& T) {
 
 bool valid_precision(int v) { return v >= FMM_FP64 && v <= FMM_MIXED_BF16X2; }
 
+// fmm_potential_host: inputs of at least kHostChunkMin particles go up in kHostChunks chunks
+constexpr size_t kHostChunkMin = 1 << 16;
+constexpr int kHostChunks = 4;
+
 }  // namespace
 
 void fmm_build_operators_f64(int p, std::vector<double>& re, std::vector<double>& im) {
@@ -87,7 +91,8 @@ void free_plan(fmm_plan_s* pl) {
                     pl->blk_map, pl->sorted_key,
                     pl->sorted64, pl->sorted32, pl->sorted_lo, pl->phi_far, pl->near_grad, pl->T64, pl->T32,
                     pl->d_status,
-                    pl->d_counters, pl->d_xy_stage, pl->d_q_stage, pl->d_phi_stage};
+                    pl->d_counters, pl->d_xy_stage[0], pl->d_q_stage[0], pl->d_phi_stage[0], pl->d_xy_stage[1],
+                    pl->d_q_stage[1], pl->d_phi_stage[1]};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (int k = 0; k <= FMM_MAX_LEVELS; ++k) {
@@ -105,6 +110,12 @@ void free_plan(fmm_plan_s* pl) {
     if (pl->ev_join3) cudaEventDestroy(pl->ev_join3);
     if (pl->stream2) cudaStreamDestroy(pl->stream2);
     if (pl->stream3) cudaStreamDestroy(pl->stream3);
+    if (pl->s_up) cudaStreamDestroy(pl->s_up);
+    if (pl->s_down) cudaStreamDestroy(pl->s_down);
+    cudaEvent_t evs[] = {pl->ev_sorted, pl->ev_stage_free[0], pl->ev_stage_free[1], pl->ev_up_done, pl->ev_l2p_done,
+                         pl->ev_down_done[0], pl->ev_down_done[1]};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
     cudaSetDevice(prev);
     delete pl;
 }
@@ -132,7 +143,9 @@ fmm_status reset_accumulators(fmm_plan_s* pl, cudaStream_t st) {
     return FMM_OK;
 }
 
-fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* phi, double* field = nullptr) {
+// The call's first steps, up to the start event: counters and, after a call that failed to enqueue,
+// the mixed path's accumulators back to zero.
+fmm_status enqueue_prologue(fmm_plan_s* pl) {
     cudaStream_t st = pl->stream;
     if (cudaMemsetAsync(pl->d_counters, 0, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long), st) != cudaSuccess)
         return FMM_ERR_CUDA;
@@ -142,8 +155,25 @@ fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* ph
     }
     pl->ev_kernels = 0;
     cudaEventRecord(pl->ev[0], st);
-    int launches = fmm_launch_sort(pl, xy, q, field != nullptr && pl->precision != FMM_FP64);
+    return FMM_OK;
+}
+
+// binned: the prologue ran and the particles were binned already (fmm_potential_host)
+fmm_status enqueue(fmm_plan_s* pl, const double* xy, const double* q, double* phi, double* field = nullptr,
+                   bool binned = false) {
+    if (!binned) {
+        const fmm_status s = enqueue_prologue(pl);
+        if (s != FMM_OK) return s;
+    }
+    int launches = fmm_launch_sort(pl, xy, q, field != nullptr && pl->precision != FMM_FP64, binned);
     if (launches < 0) return FMM_ERR_CUDA;
+    if (pl->ev_sorted) {
+        // the inputs, keys, ranks and populations are free for the next host call's uploads
+        if (cudaEventRecord(pl->ev_sorted, pl->stream) != cudaSuccess ||
+            cudaEventRecord(pl->ev_stage_free[pl->stage_next], pl->stream) != cudaSuccess)
+            return FMM_ERR_CUDA;
+    }
+    if (binned) launches += pl->host_chunks;   // the binning kernels of the chunks
     int more = pl->precision == FMM_FP64 ? fmm_launch_fp64(pl, phi, field) : fmm_launch_mixed(pl, phi, field);
     if (more == -2) return FMM_ERR_UNSUPPORTED;
     if (more < 0) return FMM_ERR_CUDA;
@@ -270,9 +300,11 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     if (cudaMallocHost(reinterpret_cast<void**>(&pl->h_counters), 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long)) !=
         cudaSuccess)
         FMM_TRY(FMM_ERR_OOM);
-    FMM_TRY(dev_alloc(pl, &pl->d_xy_stage, sizeof(double) * 2 * n));
-    FMM_TRY(dev_alloc(pl, &pl->d_q_stage, sizeof(double) * n));
-    FMM_TRY(dev_alloc(pl, &pl->d_phi_stage, sizeof(double) * n));
+    for (int b = 0; b < 2; ++b) {
+        FMM_TRY(dev_alloc(pl, &pl->d_xy_stage[b], sizeof(double) * 2 * n));
+        FMM_TRY(dev_alloc(pl, &pl->d_q_stage[b], sizeof(double) * n));
+        FMM_TRY(dev_alloc(pl, &pl->d_phi_stage[b], sizeof(double) * n));
+    }
     for (int e = 0; e < 15; ++e)
         if (cudaEventCreate(&pl->ev[e]) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
     if (precision != FMM_FP64) {
@@ -281,8 +313,14 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
             cudaStreamCreateWithFlags(&pl->stream3, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&pl->ev_join3, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&pl->ev_join3, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&pl->s_up, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&pl->s_down, cudaStreamNonBlocking) != cudaSuccess)
             FMM_TRY(FMM_ERR_CUDA);
+        cudaEvent_t* evs[] = {&pl->ev_sorted, &pl->ev_stage_free[0], &pl->ev_stage_free[1], &pl->ev_up_done,
+                              &pl->ev_l2p_done, &pl->ev_down_done[0], &pl->ev_down_done[1]};
+        for (cudaEvent_t* e : evs)
+            if (cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
     }
 #undef FMM_TRY
     pl->last.n = n;
@@ -318,19 +356,68 @@ fmm_status fmm_potential_field(fmm_plan_t plan, const double* xy, const double* 
     return enqueue(plan, xy, q, phi, field);
 }
 
-fmm_status fmm_potential_host(fmm_plan_t plan, const double* xy_host, const double* q_host, double* phi_host) {
+fmm_status fmm_potential_host_async(fmm_plan_t plan, const double* xy_host, const double* q_host, double* phi_host) {
     if (!plan || !xy_host || !q_host || !phi_host) return FMM_ERR_INVALID_ARG;
     DeviceGuard g(plan->device);
     cudaStream_t st = plan->stream;
     const size_t n = (size_t)plan->n;
-    if (cudaMemcpyAsync(plan->d_xy_stage, xy_host, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, st) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(plan->d_q_stage, q_host, sizeof(double) * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return FMM_ERR_CUDA;
-    fmm_status s = enqueue(plan, plan->d_xy_stage, plan->d_q_stage, plan->d_phi_stage);
+    const int b = plan->stage_next;
+    double *xy = plan->d_xy_stage[b], *q = plan->d_q_stage[b], *phi = plan->d_phi_stage[b];
+    fmm_status s;
+    if (plan->precision == FMM_FP64 || plan->serial) {
+        // one stream: upload, method, download in turn
+        if (cudaMemcpyAsync(xy, xy_host, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(q, q_host, sizeof(double) * n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        if ((s = enqueue(plan, xy, q, phi)) != FMM_OK) return s;
+        if (cudaMemcpyAsync(phi_host, phi, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return FMM_ERR_CUDA;
+    } else {
+        // Mixed path.  Upload stream: once this set's inputs are free (the call two back scattered
+        // them) and the previous call's sort has released the keys, ranks and populations, the
+        // inputs go up in chunks, each binned as it lands -- beside the previous call's compute.
+        // Plan's stream: the rest of the method once the uploads are in (and, before L2P writes this
+        // set's phi, once the call two back has downloaded it).  Download stream: phi, after L2P.
+        cudaStream_t up = plan->s_up, down = plan->s_down;
+        if (cudaStreamWaitEvent(up, plan->ev_stage_free[b], 0) != cudaSuccess ||
+            cudaStreamWaitEvent(up, plan->ev_sorted, 0) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        const bool reset = !plan->clean;   // a failed earlier call: the populations are reset first
+        if ((s = enqueue_prologue(plan)) != FMM_OK) return s;
+        if (reset && (cudaEventRecord(plan->ev_fork, st) != cudaSuccess ||
+                      cudaStreamWaitEvent(up, plan->ev_fork, 0) != cudaSuccess))
+            return FMM_ERR_CUDA;
+        const int chunks = n >= kHostChunkMin ? kHostChunks : 1;
+        for (int c = 0; c < chunks; ++c) {
+            const size_t i0 = n * c / chunks, i1 = n * (c + 1) / chunks;
+            if (cudaMemcpyAsync(xy + 2 * i0, xy_host + 2 * i0, sizeof(double) * 2 * (i1 - i0), cudaMemcpyHostToDevice,
+                                up) != cudaSuccess ||
+                cudaMemcpyAsync(q + i0, q_host + i0, sizeof(double) * (i1 - i0), cudaMemcpyHostToDevice, up) !=
+                    cudaSuccess ||
+                fmm_launch_bin_range(plan, xy, q, (int64_t)i0, (int64_t)i1, up) < 0)
+                return FMM_ERR_CUDA;
+        }
+        if (cudaEventRecord(plan->ev_up_done, up) != cudaSuccess ||
+            cudaStreamWaitEvent(st, plan->ev_up_done, 0) != cudaSuccess ||
+            cudaStreamWaitEvent(st, plan->ev_down_done[b], 0) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        plan->host_chunks = chunks;
+        s = enqueue(plan, xy, q, phi, nullptr, true);
+        plan->host_chunks = 0;
+        if (s != FMM_OK) return s;
+        if (cudaEventRecord(plan->ev_l2p_done, st) != cudaSuccess ||
+            cudaStreamWaitEvent(down, plan->ev_l2p_done, 0) != cudaSuccess ||
+            cudaMemcpyAsync(phi_host, phi, sizeof(double) * n, cudaMemcpyDeviceToHost, down) != cudaSuccess ||
+            cudaEventRecord(plan->ev_down_done[b], down) != cudaSuccess)
+            return FMM_ERR_CUDA;
+    }
+    plan->stage_next = b ^ 1;
+    return FMM_OK;
+}
+
+fmm_status fmm_potential_host(fmm_plan_t plan, const double* xy_host, const double* q_host, double* phi_host) {
+    const fmm_status s = fmm_potential_host_async(plan, xy_host, q_host, phi_host);
     if (s != FMM_OK) return s;
-    if (cudaMemcpyAsync(phi_host, plan->d_phi_stage, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return FMM_ERR_CUDA;
     return fmm_sync(plan);
 }
 
@@ -345,6 +432,7 @@ fmm_status fmm_sync(fmm_plan_t plan) {
         cudaMemsetAsync(plan->d_status, 0, sizeof(unsigned int), st) != cudaSuccess)
         return FMM_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return FMM_ERR_CUDA;
+    if (plan->s_down && cudaStreamSynchronize(plan->s_down) != cudaSuccess) return FMM_ERR_CUDA;
     if (plan->events_recorded) {
         auto span = [&](int a, int b) -> double {
             float t = 0.f;

@@ -115,9 +115,17 @@ struct fmm_plan_s {
     unsigned int* h_status;           // pinned
     unsigned long long* h_counters;   // pinned [128]
 
-    double* d_xy_stage;
-    double* d_q_stage;
-    double* d_phi_stage;
+    // host-array calls: two staging sets, so a call's uploads overlap the previous call's compute
+    double* d_xy_stage[2];
+    double* d_q_stage[2];
+    double* d_phi_stage[2];
+    int stage_next;                          // the set the next host call uses
+    int host_chunks;                         // chunks the current host call binned itself
+    cudaStream_t s_up, s_down;               // mixed path: uploads + binning, result downloads
+    cudaEvent_t ev_sorted;                   // the sort no longer needs keys, ranks or populations
+    cudaEvent_t ev_stage_free[2];            // the set's inputs were consumed (scatter done)
+    cudaEvent_t ev_up_done, ev_l2p_done;     // a host call's uploads / compute are complete
+    cudaEvent_t ev_down_done[2];             // the set's result was downloaded
 
     // Mixed path: after the fine P2M the work forks three ways -- the near field on stream2, the
     // coarse levels' chain (P2M, conversion, M2L of levels 2..5) on stream3, the fine levels' M2L
@@ -208,8 +216,10 @@ static __device__ __forceinline__ float2 scatter_mul(float a, float2 s) {
 
 
 // --- launchers (each returns the number of kernels it launched, or -1 on a launch error) ---------
-// with_lo: also the rounding residues of the mixed path's local coordinates (sorted_lo)
-int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q, bool with_lo = false);
+// with_lo: also the rounding residues of the mixed path's local coordinates (sorted_lo); binned: the
+// particles were already binned (fmm_launch_bin_range over all of them)
+int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q, bool with_lo = false, bool binned = false);
+int fmm_launch_bin_range(fmm_plan_s* pl, const double* xy, const double* q, int64_t i0, int64_t i1, cudaStream_t s);
 int fmm_scan_blocks(int64_t m);
 int fmm_launch_scan(const uint32_t* counts, int64_t m, uint32_t* block_sums, uint32_t* leaf_start, uint32_t n_total,
                     cudaStream_t st);

@@ -19,10 +19,11 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__global__ void k_bin(const double2* __restrict__ xy, const double* __restrict__ q, int64_t n, int levels,
+// particles [i0, n)
+__global__ void k_bin(const double2* __restrict__ xy, const double* __restrict__ q, int64_t i0, int64_t n, int levels,
                       double box, float scale_over_box32, uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
                       uint32_t* __restrict__ counts, unsigned int* __restrict__ status) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double2 p = xy[i];
     double qq = q[i];
@@ -251,20 +252,32 @@ __global__ void k_scatter(const double2* __restrict__ xy, const double* __restri
 
 }  // namespace
 
-int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q, bool with_lo) {
+// Bin particles [i0, i1) on stream s (key, rank in its square, device checks); the populations
+// must start at zero.
+int fmm_launch_bin_range(fmm_plan_s* pl, const double* xy, const double* q, int64_t i0, int64_t i1, cudaStream_t s) {
+    if (i1 <= i0) return 0;
+    const int tb = 256;
+    const unsigned nblk = (unsigned)((i1 - i0 + tb - 1) / tb);
+    const float scale_over_box32 = (float)((double)(1 << pl->levels) / pl->box);
+    k_bin<<<nblk, tb, 0, s>>>(reinterpret_cast<const double2*>(xy), q, i0, i1, pl->levels, pl->box, scale_over_box32,
+                              pl->keys, pl->rank, pl->counts, pl->d_status);
+    return cudaGetLastError() == cudaSuccess ? 1 : -1;
+}
+
+int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q, bool with_lo, bool binned) {
     const int64_t n = pl->n;
     const int64_t m = (int64_t)1 << (2 * pl->levels);
     cudaStream_t st = pl->stream;
     int launches = 0;
-    // the mixed path's scan returns counts to zero for the next call
-    if (pl->precision == FMM_FP64 && cudaMemsetAsync(pl->counts, 0, sizeof(uint32_t) * m, st) != cudaSuccess)
-        return -1;
     const int tb = 256;
     const unsigned nblk = (unsigned)((n + tb - 1) / tb);
-    const float scale_over_box32 = (float)((double)(1 << pl->levels) / pl->box);
-    k_bin<<<nblk, tb, 0, st>>>(reinterpret_cast<const double2*>(xy), q, n, pl->levels, pl->box, scale_over_box32,
-                               pl->keys, pl->rank, pl->counts, pl->d_status);
-    ++launches;
+    if (!binned) {
+        // the mixed path's scan returns counts to zero for the next call
+        if (pl->precision == FMM_FP64 && cudaMemsetAsync(pl->counts, 0, sizeof(uint32_t) * m, st) != cudaSuccess)
+            return -1;
+        if (fmm_launch_bin_range(pl, xy, q, 0, n, st) < 0) return -1;
+        ++launches;
+    }
     const int nb = pl->scan_blocks;
     if (pl->precision == FMM_FP64) {
         k_scan_reduce<<<nb, kScanThreads, 0, st>>>(pl->counts, m, pl->block_sums);

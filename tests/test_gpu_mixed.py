@@ -197,3 +197,46 @@ def test_one_stream_and_three_streams_agree(oracle_mod, precision):
     for k in ("ms_sort", "ms_p2m_fine", "ms_p2m_coarse", "ms_m2l_coarse", "ms_m2l_fine", "ms_p2p_kernel", "ms_l2p"):
         assert st[k] > 0.0, k
     assert st["ms_total"] >= st["ms_sort"] + st["ms_p2p_kernel"] + st["ms_l2p"]
+
+
+@pytest.mark.parametrize("n", [70000, 1 << 18])
+def test_host_entry_point_chunked_copies(oracle_mod, n):
+    """fmm_potential_host in the mixed path sends the inputs up in four chunks on two streams, each
+    binned as it lands; the result matches the device-array call and the oracle, and a failed
+    check in the last chunk is still reported."""
+    from gpu_util import to_dev
+    from paper_2009_00767_gb300 import binding
+    xy, q = inputs.gmm(n, inputs.config_seed(0, 403))
+    with binding.Plan(n, 7, 16, 5.0, "bf16x2") as plan:
+        host = plan.potential_host(xy, q)
+        txy, tq = to_dev(xy, q)
+        dev = plan.potential(txy, tq).cpu().numpy()
+        bad = xy.copy()
+        bad[n - 3] = (6.0, 1.0)
+        out = np.full(n, 5.0)
+        with pytest.raises(binding.FmmError):
+            plan.potential_host(bad, q, out)
+        assert plan.sync(check=False) == binding.FMM_OK   # the error was reported and cleared
+        again = plan.potential_host(xy, q)
+    check_parity(host, dev, MIXED_TOL, f"host entry N={n} vs the device call")
+    check_parity(again, dev, MIXED_TOL, f"host entry N={n} after a failed call")
+    check_parity(host, oracle_mod.shiftfree(xy, q, 7, 16), MIXED_TOL, f"host entry N={n} vs the oracle")
+
+
+def test_host_calls_in_flight(oracle_mod):
+    """Three fmm_potential_host_async calls on two alternating input sets before one fmm_sync: the
+    uploads of each call overlap the previous call's compute (two staging sets), and each result
+    is the one of its own inputs."""
+    import torch
+    from paper_2009_00767_gb300 import binding
+    n = 150000
+    sets = [inputs.uniform(n, inputs.config_seed(0, 404)), inputs.gmm(n, inputs.config_seed(0, 405))]
+    host = [(torch.from_numpy(xy).pin_memory(), torch.from_numpy(q).pin_memory()) for xy, q in sets]
+    outs = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3)]
+    with binding.Plan(n, 7, 16, 5.0, "bf16x2") as plan:
+        for i in range(3):
+            binding.fmm_potential_host_async(plan.handle, host[i % 2][0], host[i % 2][1], outs[i])
+        assert plan.sync(check=False) == binding.FMM_OK
+    refs = [oracle_mod.shiftfree(xy, q, 7, 16) for xy, q in sets]
+    for i in range(3):
+        check_parity(outs[i].numpy(), refs[i % 2], MIXED_TOL, f"host call {i} in flight")
