@@ -272,7 +272,7 @@ class ClockSampler:
 # ---------------------------------------------------------------- our arm
 
 def load_traffic(stage):
-    """ncu DRAM bytes per launch for a kernel, if captured on the current source of its file."""
+    """ncu DRAM bytes per launch for a kernel, if captured on the current source of its files."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -280,9 +280,10 @@ def load_traffic(stage):
         rec = json.load(open(path)).get(stage)
         if not rec:
             return None
-        src = os.path.join(ROOT, "paper_2009_00767_gb300", "csrc", rec["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return rec["bytes_per_launch"] if h == rec["sha"] else None
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_2009_00767_gb300", "csrc", f), "rb").read())
+        return rec["bytes_per_launch"] if h.hexdigest()[:16] == rec["sha"] else None
     except Exception:
         return None
 
