@@ -17,7 +17,12 @@ Every function cites the part of arXiv 2009.00767 it follows:
 * single-step expansions (P2M, M2L, L2P, M2M, L2L) of the paper's ref. [101];
 * :func:`direct_field`, :func:`shiftfree_field` -- the force field E = -grad phi
   (Sec. 3's timings cover "potential and force fields"): the definition, and
-  the shift-free method differentiated term by term.
+  the shift-free method differentiated term by term;
+* :func:`lag_literal`, :func:`lag_node`, :func:`lag_direct` (``lagrange_oracle.c``)
+  -- the paper's own realisation with charges at Lagrange nodes (Appendix,
+  STEP1-STEP5, Eq. 1-2) in 2D (log kernel) and 3D (Coulomb): the literal
+  U-bar / B = M^T M_b M / D-bar steps, the same bilinear forms with the change
+  of basis applied on the particle side, and the definition.
 """
 from __future__ import annotations
 
@@ -30,6 +35,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fmm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "lagrange_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -42,11 +48,11 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile fmm_oracle.c into liboracle.so (gcc, -O2, OpenMP)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    """Compile fmm_oracle.c and lagrange_oracle.c into liboracle.so (gcc, -O2, OpenMP)."""
+    if not force and os.path.exists(_LIB) and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-o", tmp] + _SRCS + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -80,6 +86,14 @@ def _load():
             "oracle_direct_field_targets": (i32, [i64, vp, vp, i64, vp, vp]),
             "oracle_shiftfree_field": (i32, [i64, vp, vp, i32, i32, d, vp, vp]),
             "oracle_local_eval_deriv": (d, [vp, i32, d, d, d, d, vp]),
+            "oracle_lag_weights1": (None, [d, vp]),
+            "oracle_lag_weights": (i32, [i32, i32, vp, d, vp, vp]),
+            "oracle_lag_matrix_M": (i32, [i32, i32, vp, d, vp]),
+            "oracle_lag_direct": (i32, [i32, i32, i64, vp, vp, vp]),
+            "oracle_lag_direct_targets": (i32, [i32, i32, i64, vp, vp, i64, vp, vp]),
+            "oracle_lag_literal": (i32, [i32, i32, i64, vp, vp, i32, d, i32, vp]),
+            "oracle_lag_node": (i32, [i32, i32, i64, vp, vp, i32, d, i32, vp]),
+            "oracle_lag_cells": (i32, [i32, i64, vp, i32, d, vp]),
             "oracle_set_threads": (None, [i32]),
             "oracle_get_threads": (i32, []),
         }
@@ -274,3 +288,92 @@ def interaction_list(bx: int, by: int, k: int):
     sy = np.zeros(27, dtype=np.int32)
     cnt = _load().oracle_interaction_list(bx, by, k, _ptr(sx), _ptr(sy))
     return list(zip(sx[:cnt].tolist(), sy[:cnt].tolist()))
+
+
+# ------------------------------------------------------------ charges at Lagrange nodes (Appendix)
+
+LAG_NODES = (-2.0, -1.0, 1.0, 2.0)   # Eq. 2's node coordinates, in units of (side / 5)
+
+
+def _pos(pos):
+    pos = _f64(pos)
+    if pos.ndim != 2 or pos.shape[1] not in (2, 3):
+        raise ValueError("positions must have shape [N, 2] or [N, 3]")
+    return pos, pos.shape[1]
+
+
+def lag_weights1(x: float) -> np.ndarray:
+    """Eq. 1: the Lagrange basis f_i(x) on the nodes {-2, -1, 1, 2}."""
+    w = np.empty(4)
+    _load().oracle_lag_weights1(float(x), _ptr(w))
+    return w
+
+
+def lag_weights(dim: int, level: int, cell, pos, box: float = 5.0) -> np.ndarray:
+    """STEP2: the unit-charge node weights f_i(x) f_j(y) [f_k(z)] of ``pos`` in the square
+    (cube) ``cell`` of ``level`` (node index i + 4j + 16k)."""
+    c = np.ascontiguousarray(cell, dtype=np.int32)
+    p = _f64(pos).reshape(-1)
+    w = np.empty(4 ** dim)
+    _check(_load().oracle_lag_weights(int(dim), int(level), _ptr(c), float(box), _ptr(p), _ptr(w)))
+    return w
+
+
+def lag_matrix_M(dim: int, level: int, cell, box: float = 5.0) -> np.ndarray:
+    """STEP4: M_m, whose column l is h_m of a unit charge at the root box's node l."""
+    c = np.ascontiguousarray(cell, dtype=np.int32)
+    d = 4 ** dim
+    M = np.empty((d, d))
+    _check(_load().oracle_lag_matrix_M(int(dim), int(level), _ptr(c), float(box), _ptr(M)))
+    return M
+
+
+def lag_direct(pos, q, kernel: int = 0) -> np.ndarray:
+    """phi_i = sum_{j != i} q_j K(c_i, c_j): K = log r in 2D, 1/r in 3D (kernel 0), or the
+    test polynomial (kernel 1)."""
+    pos, dim = _pos(pos)
+    q = _f64(q).reshape(-1)
+    phi = np.empty(q.shape[0])
+    _check(_load().oracle_lag_direct(dim, int(kernel), q.shape[0], _ptr(pos), _ptr(q), _ptr(phi)))
+    return phi
+
+
+def lag_direct_targets(pos, q, targets, kernel: int = 0) -> np.ndarray:
+    pos, dim = _pos(pos)
+    q = _f64(q).reshape(-1)
+    t = np.ascontiguousarray(targets, dtype=np.int64)
+    phi = np.empty(t.shape[0])
+    _check(_load().oracle_lag_direct_targets(dim, int(kernel), q.shape[0], _ptr(pos), _ptr(q), t.shape[0],
+                                             _ptr(t), _ptr(phi)))
+    return phi
+
+
+def lag_literal(pos, q, levels: int, box: float = 5.0, kernel: int = 0, skip_level: int = -1) -> np.ndarray:
+    """The paper's literal steps: v_c = h_{m^0}(c), U-bar-1/U-bar-2 sums, D-bar-1 with
+    B = M_{m_i}^T M_b M_m formed per pair, D-bar-2 sums, F(v) = L_{m^l}(v), plus the near field."""
+    pos, dim = _pos(pos)
+    q = _f64(q).reshape(-1)
+    phi = np.empty(q.shape[0])
+    _check(_load().oracle_lag_literal(dim, int(kernel), q.shape[0], _ptr(pos), _ptr(q), int(levels), float(box),
+                                      int(skip_level), _ptr(phi)))
+    return phi
+
+
+def lag_node(pos, q, levels: int, box: float = 5.0, kernel: int = 0, skip_level: int = -1) -> np.ndarray:
+    """The same bilinear forms with M_m applied on the particle side: node charges per level
+    straight from the charges, node-to-node M_b over each interaction list, node potentials
+    interpolated back at the charges, plus the near field."""
+    pos, dim = _pos(pos)
+    q = _f64(q).reshape(-1)
+    phi = np.empty(q.shape[0])
+    _check(_load().oracle_lag_node(dim, int(kernel), q.shape[0], _ptr(pos), _ptr(q), int(levels), float(box),
+                                   int(skip_level), _ptr(phi)))
+    return phi
+
+
+def lag_cells(pos, levels: int, box: float = 5.0) -> np.ndarray:
+    """The finest cell of every charge, floor(x 2^l / box) per axis in FP64, clamped."""
+    pos, dim = _pos(pos)
+    cell = np.empty(pos.shape, dtype=np.int32)
+    _check(_load().oracle_lag_cells(dim, pos.shape[0], _ptr(pos), int(levels), float(box), _ptr(cell)))
+    return cell

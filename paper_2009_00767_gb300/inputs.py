@@ -18,7 +18,10 @@ square box of side 5, Sec. 2.1 item 1 and Sec. 3) with charges q ~ U[-1, 1]:
                    equal weights; draws outside the box are redrawn (a
                    truncated normal) rather than clamped, so no duplicate
                    points pile up on the box edges;
-* ``annulus``   -- radius uniform in [1, 2] about (2.5, 2.5), angle uniform.
+* ``annulus``   -- radius uniform in [1, 2] about (2.5, 2.5), angle uniform;
+* ``paper_cube``  -- the paper's own experiments (Sec. 3): charges +1 or -1 with equal
+                   probability scattered uniformly in a cube (D = 3) or square (D = 2) of
+                   side 5.
 """
 from __future__ import annotations
 
@@ -107,6 +110,19 @@ def annulus(n: int, seed: int, r_lo: float = 1.0, r_hi: float = 2.0, centre: flo
     xy[:, 0] = centre + r * np.cos(t)
     xy[:, 1] = centre + r * np.sin(t)
     return xy, charges(n, seed)
+
+
+def signs(n: int, seed: int) -> np.ndarray:
+    """q = +1 or -1, each with probability 1/2."""
+    return np.where(u01(seed, 8, n) < 0.5, -1.0, 1.0)
+
+
+def paper_cube(n: int, seed: int, dim: int = 3, box: float = 5.0):
+    """Positions uniform in [0, box)^dim and q = +-1; returns (pos [n, dim] f64, q [n] f64)."""
+    pos = np.empty((n, dim))
+    for a in range(dim):
+        pos[:, a] = box * u01(seed, 31 + a, n)
+    return pos, signs(n, seed)
 
 
 def config_seed(config: int, replicate: int = 0) -> int:

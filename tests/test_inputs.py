@@ -42,3 +42,12 @@ def test_selector_candidates_follow_the_precision():
     assert {lev for lev, _ in c32} == {6, 7, 8, 9, 10}   # round(log4(N / 16)) = 8, +-2
     assert selector.heuristic_levels(1 << 20) == 8 and selector.heuristic_levels(100) == 2
     assert all(2 <= lev <= 11 for lev, _ in selector.candidates(1 << 10))
+
+
+def test_paper_cube_charges_are_signs_and_positions_in_the_box():
+    pos, q = inputs.paper_cube(20000, 5, 3)
+    assert pos.shape == (20000, 3) and pos.min() >= 0.0 and pos.max() < 5.0
+    assert set(np.unique(q).tolist()) == {-1.0, 1.0}
+    assert abs(q.mean()) < 0.03
+    pos2, q2 = inputs.paper_cube(20000, 5, 3)
+    assert np.array_equal(pos, pos2) and np.array_equal(q, q2)
