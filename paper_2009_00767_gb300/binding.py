@@ -1,4 +1,4 @@
-"""ctypes binding of include/fmm.h (libfmm.so): argument marshalling only.
+"""ctypes binding of include/fmm.h and include/fmm_lagrange.h (libfmm.so): argument marshalling only.
 
 Every function here has the name of the C entry point it calls and does no
 arithmetic of the method: all of it runs in the CUDA kernels of libfmm.so.
@@ -54,6 +54,22 @@ class fmm_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fmm_lag_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("dim", ctypes.c_int), ("levels", ctypes.c_int), ("form", ctypes.c_int),
+                ("ms_total", ctypes.c_double), ("ms_sort", ctypes.c_double), ("ms_up", ctypes.c_double),
+                ("ms_down", ctypes.c_double), ("ms_eval", ctypes.c_double), ("ms_p2p", ctypes.c_double),
+                ("p2p_pairs", ctypes.c_int64), ("m2l_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+FMM_LAG_NODE_F32 = 0
+FMM_LAG_NODE_F64 = 1
+FMM_LAG_LITERAL_F64 = 2
+LAG_FORMS = {"node_f32": FMM_LAG_NODE_F32, "node_f64": FMM_LAG_NODE_F64, "literal_f64": FMM_LAG_LITERAL_F64}
+
 SIGNATURES = {
     "fmm_plan": (_i32, [ctypes.POINTER(_vp), _i64, _i32, _i32, _d, _i32, _vp]),
     "fmm_set_stream": (_i32, [_vp, _vp]),
@@ -94,6 +110,14 @@ SIGNATURES = {
     "fmm_selector_load": (_i32, [_vp, ctypes.c_char_p]),
     "fmm_select": (_i32, [_vp, _vp, _i64, _d, _d, _d, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                           ctypes.POINTER(_i32)]),
+    "fmm_lag_plan": (_i32, [ctypes.POINTER(_vp), _i32, _i64, _i32, _d, _i32, _vp]),
+    "fmm_lag_potential": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+    "fmm_lag_sync": (_i32, [_vp]),
+    "fmm_lag_stats_get": (_i32, [_vp, ctypes.POINTER(fmm_lag_stats)]),
+    "fmm_lag_set_stream": (_i32, [_vp, _vp]),
+    "fmm_lag_cells": (_i32, [_vp, _vp]),
+    "fmm_lag_direct_targets": (_i32, [_i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "fmm_lag_plan_destroy": (None, [_vp]),
 }
 
 
@@ -474,3 +498,96 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ------------------------------------------------------------------- Lagrange-node form (fmm_lagrange.h)
+
+def fmm_lag_plan(dim: int, n_max: int, levels: int, box: float = 5.0, form="node_f32", stream=None) -> int:
+    f = LAG_FORMS[form] if isinstance(form, str) else int(form)
+    h = _vp()
+    _check(_lib.fmm_lag_plan(ctypes.byref(h), int(dim), int(n_max), int(levels), float(box), f,
+                             _stream_handle(stream)), "fmm_lag_plan")
+    return h.value
+
+
+def fmm_lag_potential(plan: int, pos, q, n: int, phi):
+    _check(_lib.fmm_lag_potential(plan, _ptr(pos), _ptr(q), int(n), _ptr(phi)), "fmm_lag_potential")
+
+
+def fmm_lag_sync(plan: int, check: bool = True) -> int:
+    st = _lib.fmm_lag_sync(plan)
+    if check:
+        _check(st, "fmm_lag_sync")
+    return st
+
+
+def fmm_lag_stats_get(plan: int) -> dict:
+    st = fmm_lag_stats()
+    _check(_lib.fmm_lag_stats_get(plan, ctypes.byref(st)), "fmm_lag_stats_get")
+    return st.as_dict()
+
+
+def fmm_lag_set_stream(plan: int, stream=None):
+    _check(_lib.fmm_lag_set_stream(plan, _stream_handle(stream)), "fmm_lag_set_stream")
+
+
+def fmm_lag_cells(plan: int, cells):
+    _check(_lib.fmm_lag_cells(plan, _ptr(cells)), "fmm_lag_cells")
+
+
+def fmm_lag_direct_targets(pos, q, targets, phi_t, stream=None):
+    dim = int(pos.shape[1])
+    _check(_lib.fmm_lag_direct_targets(dim, int(q.shape[0]), _ptr(pos), _ptr(q), int(targets.shape[0]),
+                                       _ptr(targets), _ptr(phi_t), _stream_handle(stream)), "fmm_lag_direct_targets")
+
+
+def fmm_lag_plan_destroy(plan: int):
+    _lib.fmm_lag_plan_destroy(plan)
+
+
+class LagPlan:
+    """Owner of one fmm_lag_plan handle (charges at Lagrange nodes, 2D log or 3D Coulomb)."""
+
+    def __init__(self, dim, n_max, levels, box=5.0, form="node_f32", stream=None):
+        self.dim, self.n_max, self.levels, self.box, self.form = int(dim), int(n_max), int(levels), float(box), form
+        self.handle = fmm_lag_plan(dim, n_max, levels, box, form, stream)
+
+    def potential(self, pos, q, phi=None, sync=True):
+        import torch
+        n = int(q.shape[0])
+        if phi is None:
+            phi = torch.empty(n, dtype=torch.float64, device=q.device)
+        fmm_lag_potential(self.handle, pos, q, n, phi)
+        if sync:
+            fmm_lag_sync(self.handle)
+        return phi
+
+    def sync(self, check=True):
+        return fmm_lag_sync(self.handle, check)
+
+    def stats(self):
+        return fmm_lag_stats_get(self.handle)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def cells(self, n):
+        import torch
+        c = torch.empty((int(n), self.dim), dtype=torch.int32, device="cuda")
+        fmm_lag_cells(self.handle, c)
+        torch.cuda.synchronize()
+        return c
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fmm_lag_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
