@@ -70,6 +70,9 @@ def parse():
                          "of single-system launches)")
     ap.add_argument("--batched-systems", type=int, default=1024)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned (levels, p) selector's leg")
+    ap.add_argument("--no-lagrange", action="store_true",
+                    help="skip the leg of the paper's own Lagrange-node form (3D Coulomb workloads of its "
+                         "Tables 1-3, the 2D comparison and the FP64-conditioning sweep)")
     return ap.parse_args()
 
 
@@ -466,6 +469,10 @@ def run_ours(args):
         p64.close()
     plan.close()
 
+    lagrange = None
+    if not args.no_lagrange and rank == 0:
+        lagrange = run_lagrange(binding, torch, dev, flush, peaks.get("sm_max_mhz", 2070.0))
+
     batched = None
     if not args.no_batched and args.precision != "fp64":
         batched = run_batched(binding, torch, dev, args.batched_systems, max(5, min(args.steps, 20)), 3,
@@ -494,7 +501,7 @@ def run_ours(args):
             "roofline_stages": roof_all,
             "gpu_launches": launches, "e2e": e2e, "fp64_gpu": fp64, "alu_peaks_probe": probe,
             "speedup_vs_fp64_gpu": (value / fp64["value"]) if fp64 else None,
-            "cpu_baseline": cpu, "batched": batched, "learned": learned, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+            "cpu_baseline": cpu, "batched": batched, "learned": learned, "lagrange": lagrange, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                                             "reasons": clk["reasons"], "samples": clk["samples"]},
             "wall_s_timed": wall,
         }
@@ -655,6 +662,112 @@ def run_learned(binding, torch, dev, precision, flush, steps=20):
             "meets_error_bound": all(r["err_pick"] <= ERR_BOUND for r in rows),
             "rule_basis": f"no network: levels round(log4(N/16)), p {p_rule} = the smallest grid p meeting 1e-6 "
                           f"on a 2^18 uniform calibration system"}
+
+
+# ---------------------------------------------------------------- Lagrange-node form (Appendix)
+
+# The paper's own experiments (Sec. 3, Tables 1-3): +-1 charges uniform in a cube of side 5, 64
+# nodes per cube, FP64 on one Core i7-9700; its total times are the context of these lines.
+LAGRANGE_WORKLOADS = [
+    {"name": "table1_3d_80k_l3", "dim": 3, "n": 80_000, "levels": 3, "paper_total_s": 9.4e-2, "paper_accuracy": 0.18e-2},
+    {"name": "table2_3d_200k_l3", "dim": 3, "n": 200_000, "levels": 3, "paper_total_s": 1.1e-1, "paper_accuracy": 0.40e-2},
+    {"name": "table3_3d_80k_l2", "dim": 3, "n": 80_000, "levels": 2, "paper_total_s": 1.4e-2, "paper_accuracy": 0.15e-2},
+    {"name": "2d_1m_l7", "dim": 2, "n": 1 << 20, "levels": 7},
+]
+
+
+def run_lagrange(binding, torch, dev, flush, sm_max_mhz, steps=20, steps64=3):
+    """The Lagrange-node form through include/fmm_lagrange.h: per workload each form's median step
+    (L2 flushed between steps), its stage times alone (serial pass), its error against the FP64
+    direct sum at sampled targets, and the near-field kernel's roofline; then, in 2D, the paper's
+    literal form against the node form level by level (its FP64 conditioning, Sec. 4 (3))."""
+    from paper_2009_00767_gb300 import inputs as inp
+    out = []
+    for wl in LAGRANGE_WORKLOADS:
+        dim, n, L = wl["dim"], wl["n"], wl["levels"]
+        pos, q = inp.paper_cube(n, inp.config_seed(30 + dim * 10 + L), dim)
+        tp = torch.from_numpy(pos).to(dev)
+        tq = torch.from_numpy(q).to(dev)
+        S = min(4096, n)
+        idx = np.unique((inp.u01(4343, 0, S) * n).astype(np.int64))
+        idx_d = torch.from_numpy(idx).to(dev)
+        ref = torch.empty(idx.shape[0], dtype=torch.float64, device=dev)
+        binding.fmm_lag_direct_targets(tp, tq, idx_d, ref)
+        torch.cuda.synchronize()
+        forms = ("node_f32",) if dim == 2 else ("node_f32", "node_f64", "literal_f64")
+        row = {"name": wl["name"], "dim": dim, "n": n, "levels": L, "forms": {}}
+        for form in forms:
+            k = steps if form == "node_f32" else steps64
+            with binding.LagPlan(dim, n, L, 5.0, form) as plan:
+                phi = torch.empty(n, dtype=torch.float64, device=dev)
+                for _ in range(2):
+                    plan.potential(tp, tq, phi)
+                ms = []
+                for _ in range(k):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    binding.fmm_lag_potential(plan.handle, tp, tq, n, phi)
+                    e1.record()
+                    plan.sync()
+                    ms.append(e0.elapsed_time(e1))
+                got = phi[idx_d]
+                err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+                mean_rel = float(torch.mean(torch.abs((got - ref) / ref)))
+                binding.fmm_lag_set_concurrency(plan.handle, 1)
+                alone = []
+                for _ in range(max(2, k // 2)):
+                    flush.zero_()
+                    plan.potential(tp, tq, phi)
+                    alone.append(plan.stats())
+                st = alone[-1]
+            med = float(np.median(ms))
+            stages = {key[3:]: float(np.median([a[key] for a in alone]))
+                      for key in ("ms_sort", "ms_up", "ms_down", "ms_eval", "ms_p2p")}
+            f = {"ms_per_step": med, "value": n / (med * 1e-3), "unit": UNIT, "rel_l2_vs_direct": err,
+                 "mean_abs_rel_err_vs_direct": mean_rel, "stages_alone_ms": stages,
+                 "p2p_pairs": st["p2p_pairs"], "m2l_pairs": st["m2l_pairs"],
+                 "workspace_bytes": st["workspace_bytes"]}
+            if form == "node_f32":
+                # the near-field kernel, the longest stage: ordered pairs per second against the MUFU
+                # rate (rsqrt in 3D, lg2 in 2D: 16 per clock per SM); the kernel evaluates each pair of
+                # adjacent cells once for both sides (about 0.5 MUFU op per ordered pair)
+                peak = N_SMS * MUFU_PER_SM * sm_max_mhz * 1e6 / 1e12
+                ach = st["p2p_pairs"] / (stages["p2p"] * 1e-3) / 1e12
+                f["roofline"] = {"kernel": "k_p2p32", "bound": "alu", "achieved": ach, "peak": peak,
+                                 "unit": "Tpairs/s", "frac": ach / peak, "traffic": None,
+                                 "work_per_launch": f"{st['p2p_pairs']} ordered pairs, one MUFU "
+                                                    f"{'rsqrt' if dim == 3 else 'lg2'} each (the survey's unit)",
+                                 "peak_basis": f"MUFU: {N_SMS} SMs x {MUFU_PER_SM}/clk x {sm_max_mhz:.0f} MHz",
+                                 "timing": "kernel alone (serial pass, CUDA events)"}
+            if "paper_total_s" in wl:
+                f["speedup_vs_paper_total"] = wl["paper_total_s"] / (med * 1e-3)
+            row["forms"][form] = f
+        if "paper_total_s" in wl:
+            row["paper"] = {"total_s": wl["paper_total_s"], "accuracy": wl["paper_accuracy"],
+                            "machine": "FP64 Fortran, one Intel Core i7-9700 (Sec. 3)"}
+        out.append(row)
+        del tp, tq
+    # FP64 conditioning of the literal form (2D, 2^16 charges): its error against the direct sum
+    # next to the node form's, level by level
+    cond = []
+    pos, q = inp.paper_cube(1 << 16, inp.config_seed(39), 2)
+    tp, tq = torch.from_numpy(pos).to(dev), torch.from_numpy(q).to(dev)
+    idx = np.unique((inp.u01(4444, 0, 2048) * pos.shape[0]).astype(np.int64))
+    idx_d = torch.from_numpy(idx).to(dev)
+    ref = torch.empty(idx.shape[0], dtype=torch.float64, device=dev)
+    binding.fmm_lag_direct_targets(tp, tq, idx_d, ref)
+    torch.cuda.synchronize()
+    for L in range(2, 8):
+        r = {"levels": L}
+        for form in ("node_f64", "literal_f64"):
+            with binding.LagPlan(2, pos.shape[0], L, 5.0, form) as plan:
+                phi = plan.potential(tp, tq)
+                r[form] = float(torch.linalg.norm(phi[idx_d] - ref) / torch.linalg.norm(ref))
+        cond.append(r)
+    return {"workloads": out, "fp64_conditioning_2d_64k": cond,
+            "data": "synthetic: +-1 charges uniform in a square/cube of side 5 (the paper's Sec. 3 setup)",
+            "timing": "median step, CUDA events on the stream, 256 MB L2 flush between steps"}
 
 
 # ---------------------------------------------------------------- CPU oracle

@@ -109,6 +109,12 @@ fmm_status fmm_lag_stats_get(fmm_lag_plan_t plan, fmm_lag_stats* out);
 /* Change the stream later calls enqueue on. */
 fmm_status fmm_lag_set_stream(fmm_lag_plan_t plan, void* stream);
 
+/* 2 (the default): the near field runs on a stream of the plan's own beside the far field, joined
+ * back before the final sum.  1: every kernel in turn on the plan's stream, so that the stage
+ * times of fmm_lag_stats_get are those of each stage alone.  Same results either way.
+ * FMM_ERR_INVALID_ARG for another count or a NULL plan. */
+fmm_status fmm_lag_set_concurrency(fmm_lag_plan_t plan, int streams);
+
 /* The finest cell of every charge of the last call, [n][dim] int32 device array, input order
  * (the binning the tree used, for bit-exact checks).  Enqueued on the plan's stream. */
 fmm_status fmm_lag_cells(fmm_lag_plan_t plan, int32_t* cells);

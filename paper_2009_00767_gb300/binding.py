@@ -115,6 +115,7 @@ SIGNATURES = {
     "fmm_lag_sync": (_i32, [_vp]),
     "fmm_lag_stats_get": (_i32, [_vp, ctypes.POINTER(fmm_lag_stats)]),
     "fmm_lag_set_stream": (_i32, [_vp, _vp]),
+    "fmm_lag_set_concurrency": (_i32, [_vp, _i32]),
     "fmm_lag_cells": (_i32, [_vp, _vp]),
     "fmm_lag_direct_targets": (_i32, [_i32, _i64, _vp, _vp, _i64, _vp, _vp, _vp]),
     "fmm_lag_plan_destroy": (None, [_vp]),
@@ -529,6 +530,10 @@ def fmm_lag_stats_get(plan: int) -> dict:
 
 def fmm_lag_set_stream(plan: int, stream=None):
     _check(_lib.fmm_lag_set_stream(plan, _stream_handle(stream)), "fmm_lag_set_stream")
+
+
+def fmm_lag_set_concurrency(plan: int, streams: int):
+    _check(_lib.fmm_lag_set_concurrency(plan, int(streams)), "fmm_lag_set_concurrency")
 
 
 def fmm_lag_cells(plan: int, cells):

@@ -32,6 +32,7 @@
 namespace {
 
 constexpr int kChunk = 128;      // charges per work item
+constexpr int kWarpChunk = 64;   // targets per near-field warp work item (two per lane)
 constexpr int kMaxLevels = 8;
 constexpr double kLn2 = 0.69314718055994530942;
 
@@ -71,6 +72,21 @@ __host__ __device__ inline double kernel64(int D, double r2) {
 
 constexpr unsigned kFlagOutOfBox = 1u, kFlagNonFinite = 2u;
 
+// The MUFU reciprocal square root and base-2 logarithm with subnormal inputs flushed to zero:
+// a near-field r^2 is never subnormal (coincident pairs give exactly 0, which both map to an
+// infinity that the own cell's mask removes), so the subnormal handling of rsqrtf / __log2f is
+// dead weight in the pair loop.
+__device__ __forceinline__ float mufu_rsqrt(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float mufu_lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 }  // namespace
 
 // A sorted charge of the FP64 forms: position and charge, one 32-byte load.
@@ -83,7 +99,7 @@ struct fmm_lag_plan_s {
     double box = 5.0;
     int64_t n_max = 0, nleaf = 1, last_n = 0;
     cudaStream_t st = nullptr, st2 = nullptr;
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[9] = {};   // 0 start, 1 far field start, 2 up done, 3 down done, 4 end, 5/6 p2p, 7 sorted
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint32_t* key = nullptr;       // [n_max] finest Morton key, input order
     uint32_t* rank = nullptr;      // [n_max] rank within the cell
@@ -91,6 +107,7 @@ struct fmm_lag_plan_s {
     int* count = nullptr;          // [nleaf]
     int* start = nullptr;          // [nleaf + 1]
     int* chunk_start = nullptr;    // [nleaf + 1]
+    int* wchunk_start = nullptr;   // [nleaf + 1] near-field warp chunks
     int* order = nullptr;          // [n_max] sorted -> input index
     float4* hi = nullptr;          // FP32 forms
     float4* lo = nullptr;
@@ -98,6 +115,7 @@ struct fmm_lag_plan_s {
     double* nearf = nullptr;       // [n_max] near field, sorted order
     unsigned* status = nullptr;
     unsigned long long* pairs = nullptr;   // near-field pair counter
+    int* next_item = nullptr;              // near-field work counter
     void* node[kMaxLevels + 1] = {};       // Q_k (node) or v_k (literal), d values per cell
     void* pot[kMaxLevels + 1] = {};        // psi_k (node) or u_k (literal)
     void* K = nullptr;                     // node forms: operators of levels 2..levels
@@ -109,6 +127,8 @@ struct fmm_lag_plan_s {
     uint64_t bytes = 0;
     int launches = 0;
     int grid_particles = 0;
+    bool serial = false;   // every kernel in turn on the plan's stream (per-kernel timing)
+    int grid_p2p = 0;      // resident blocks of the FP32 near-field kernel, all SMs
 };
 
 namespace {
@@ -142,36 +162,43 @@ __global__ void k_bin(const double* __restrict__ pos, const double* __restrict__
 
 // Exclusive scans of the populations and of the chunk counts, one block.
 __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ count, int nleaf, int* __restrict__ start,
-                                               int* __restrict__ chunk_start) {
-    __shared__ int s_n[1024], s_c[1024];
+                                               int* __restrict__ chunk_start, int* __restrict__ wchunk_start) {
+    __shared__ int s_n[1024], s_c[1024], s_w[1024];
     const int t = threadIdx.x;
     const int per = (nleaf + 1023) / 1024;
     const int b0 = min(nleaf, t * per), b1 = min(nleaf, b0 + per);
-    int sn = 0, sc = 0;
+    int sn = 0, sc = 0, sw = 0;
     for (int b = b0; b < b1; ++b) {
         sn += count[b];
         sc += (count[b] + kChunk - 1) / kChunk;
+        sw += (count[b] + kWarpChunk - 1) / kWarpChunk;
     }
     s_n[t] = sn;
     s_c[t] = sc;
+    s_w[t] = sw;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {   // Hillis-Steele inclusive scan
         const int vn = t >= off ? s_n[t - off] : 0, vc = t >= off ? s_c[t - off] : 0;
+        const int vw = t >= off ? s_w[t - off] : 0;
         __syncthreads();
         s_n[t] += vn;
         s_c[t] += vc;
+        s_w[t] += vw;
         __syncthreads();
     }
-    int rn = s_n[t] - sn, rc = s_c[t] - sc;
+    int rn = s_n[t] - sn, rc = s_c[t] - sc, rw = s_w[t] - sw;
     for (int b = b0; b < b1; ++b) {
         start[b] = rn;
         chunk_start[b] = rc;
+        wchunk_start[b] = rw;
         rn += count[b];
         rc += (count[b] + kChunk - 1) / kChunk;
+        rw += (count[b] + kWarpChunk - 1) / kWarpChunk;
     }
     if (t == 1023) {
         start[nleaf] = s_n[1023];
         chunk_start[nleaf] = s_c[1023];
+        wchunk_start[nleaf] = s_w[1023];
     }
 }
 
@@ -209,68 +236,180 @@ __device__ __forceinline__ int chunk_leaf(const int* __restrict__ chunk_start, i
 
 // ------------------------------------------------------------------------------ near field
 
-// Sec. 2.1 E-2 in FP32: each thread one target of the chunk, the own and adjacent cells'
-// charges streamed through shared memory; differences from two-word coordinates, so a close
-// pair's distance keeps about 48 bits; per tile FP32 sums added in FP64.
+// Sec. 2.1 E-2 in FP32, each pair of adjacent cells evaluated once for both sides.  A warp work
+// item is one chunk of up to 64 targets of a finest cell A, two per lane (i and i + 32), against a
+// group of A's "forward" cells: A itself and the neighbours B whose offset is positive in (z, y, x)
+// order (13 in 3D, 4 in 2D), so that every unordered pair of adjacent cells is met once.  For B != A
+// each 1/r (or log r) feeds the target, q_b / r, and the source, q_a / r: the lanes' source terms of
+// a 32-source tile are summed across the warp by a transposing butterfly (31 shuffles leave lane j
+// with source j's sum), then added to the source in FP64.  A itself is evaluated one-sided with the
+// r > 0 mask (only there can a pair sit at distance 0).  The two targets of a lane run in packed
+// FP32x2 against one source, staged negated and duplicated, (-x, -x, -y, -y), so that every
+// difference is one FADD2; differences come from two-word coordinates, (hi_t - hi_s) + (lo_t - lo_s),
+// so a close pair's distance keeps about 48 bits.  Empty slots hold far zero charges.  Sums are FP32
+// within a tile and FP64 across tiles, and meet in FP64 atomics.
+template <int D, bool kMask>
+__device__ __forceinline__ float2 p2p_tile(const float4* __restrict__ s_a, const float4* __restrict__ s_b,
+                                           const float4* __restrict__ s_c, const float2* __restrict__ s_d, int m,
+                                           float2 tx, float2 ty, float2 tz, float2 ux, float2 uy, float2 uz) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int j = 0; j < m; ++j) {
+        const float4 A = s_a[j], B = s_b[j], C = s_c[j];
+        const float2 dx = __fadd2_rn(__fadd2_rn(tx, make_float2(A.x, A.y)), __fadd2_rn(ux, make_float2(C.x, C.y)));
+        const float2 dy = __fadd2_rn(__fadd2_rn(ty, make_float2(A.z, A.w)), __fadd2_rn(uy, make_float2(C.z, C.w)));
+        float2 r2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+        if constexpr (D == 3) {
+            const float2 E = s_d[j];
+            const float2 dz = __fadd2_rn(__fadd2_rn(tz, make_float2(B.x, B.y)), __fadd2_rn(uz, E));
+            r2 = __ffma2_rn(dz, dz, r2);
+        }
+        float2 k;
+        if constexpr (D == 3) {
+            k = make_float2(mufu_rsqrt(r2.x), mufu_rsqrt(r2.y));
+        } else {
+            k = make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
+        }
+        if constexpr (kMask) {
+            k.x = r2.x > 0.f ? k.x : 0.f;
+            k.y = r2.y > 0.f ? k.y : 0.f;
+        }
+        acc = __ffma2_rn(make_float2(B.z, B.w), k, acc);
+    }
+    return acc;
+}
+
+constexpr int kSymTile = 32;     // sources per staged tile (one per lane for the butterfly)
+constexpr int kP2PWarps = 8;     // warps per block, each on its own work items
 template <int D>
-__global__ void __launch_bounds__(kChunk) k_p2p32(const float4* __restrict__ hi, const float4* __restrict__ lo,
-                                                  const int* __restrict__ start, const int* __restrict__ chunk_start,
-                                                  int nleaf, int L, double* __restrict__ nearf,
-                                                  unsigned long long* __restrict__ pairs) {
-    __shared__ float4 s_hi[kChunk], s_lo[kChunk];
-    const int total = chunk_start[nleaf];
+__host__ __device__ constexpr int fwd_group() { return D == 3 ? 4 : 5; }   // forward cells per work item
+
+// Forward cell f of a cell: f = 0 the cell itself, then the offsets o > 0 in (z, y, x) order.
+template <int D>
+__device__ __forceinline__ void fwd_offset(int f, int* o) {
+    o[0] = o[1] = o[2] = 0;
+    if (f == 0) return;
+    const int e = f - 1;
+    if constexpr (D == 3) {
+        if (e < 9) { o[0] = e % 3 - 1; o[1] = e / 3 - 1; o[2] = 1; }
+        else if (e < 12) { o[0] = e - 10; o[1] = 1; }
+        else { o[0] = 1; }
+    } else {
+        if (e < 3) { o[0] = e - 1; o[1] = 1; }
+        else { o[0] = 1; }
+    }
+}
+
+// v[j] on every lane in, lane j holds the sum over the warp of v[j] out.
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane) {
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            const float send = upper ? v[i] : v[i + w];
+            const float keep = upper ? v[i + w] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0];
+}
+
+template <int D>
+__global__ void __launch_bounds__(kP2PWarps * 32) k_p2p32(const float4* __restrict__ hi, const float4* __restrict__ lo,
+                                                          const int* __restrict__ start,
+                                                          const int* __restrict__ wchunk_start, int nleaf, int L,
+                                                          double* __restrict__ nearf,
+                                                          unsigned long long* __restrict__ pairs,
+                                                          int* __restrict__ next_item) {
+    constexpr int F = D == 3 ? 14 : 5, FG = fwd_group<D>(), G = (F + FG - 1) / FG;
+    __shared__ float4 s_a[kP2PWarps][kSymTile], s_b[kP2PWarps][kSymTile], s_c[kP2PWarps][kSymTile];
+    __shared__ float2 s_d[kP2PWarps][kSymTile];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int side = 1 << L;
+    const double scale = D == 2 ? 0.5 * kLn2 : 1.0;
+    const int64_t total = (int64_t)wchunk_start[nleaf] * G;
     unsigned long long my_pairs = 0;
-    for (int w = blockIdx.x; w < total; w += gridDim.x) {
-        const int b = chunk_leaf(chunk_start, nleaf, w);
-        const int t0 = start[b] + (w - chunk_start[b]) * kChunk, t1 = min(t0 + kChunk, start[b + 1]);
-        const int i = t0 + (int)threadIdx.x;
-        const bool act = i < t1;
-        const float4 th = act ? hi[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 tl = act ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // items are taken from a shared counter, so that the warps finish within one item of each other
+    for (;;) {
+        int64_t w = 0;
+        if (lane == 0) w = atomicAdd(next_item, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const int cidx = (int)(w / G), g = (int)(w % G);
+        const int b = chunk_leaf(wchunk_start, nleaf, cidx);
+        const int t0 = start[b] + (cidx - wchunk_start[b]) * kWarpChunk, t1 = min(t0 + kWarpChunk, start[b + 1]);
+        const int ia = t0 + lane, ib = ia + 32;
+        const bool va = ia < t1, vb = ib < t1;
+        // an empty target slot is a zero charge far outside the box
+        const float4 far_t = make_float4(-1.0e4f, -1.0e4f, -1.0e4f, 0.f), z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 ha = va ? hi[ia] : far_t, hb = vb ? hi[ib] : far_t;
+        const float4 la = va ? lo[ia] : z4, lb = vb ? lo[ib] : z4;
+        const float2 tx = make_float2(ha.x, hb.x), ty = make_float2(ha.y, hb.y), tz = make_float2(ha.z, hb.z);
+        const float2 ux = make_float2(la.x, lb.x), uy = make_float2(la.y, lb.y), uz = make_float2(la.z, lb.z);
+        const float2 qa = make_float2(ha.w, hb.w);
         int c[3];
         morton_dec(D, (uint32_t)b, c);
-        double acc = 0.0;
-        for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
-            for (int oy = -1; oy <= 1; ++oy)
-                for (int ox = -1; ox <= 1; ++ox) {
-                    const int nc[3] = {c[0] + ox, c[1] + oy, c[2] + oz};
-                    if (nc[0] < 0 || nc[0] >= side || nc[1] < 0 || nc[1] >= side) continue;
-                    if (D == 3 && (nc[2] < 0 || nc[2] >= side)) continue;
-                    const uint32_t nb = morton_enc(D, nc);
-                    const int s0 = start[nb], s1 = start[nb + 1];
-                    if (threadIdx.x == 0) my_pairs += (unsigned long long)(s1 - s0) * (unsigned long long)(t1 - t0);
-                    for (int s = s0; s < s1; s += kChunk) {
-                        __syncthreads();
-                        if (s + (int)threadIdx.x < s1) {
-                            s_hi[threadIdx.x] = hi[s + threadIdx.x];
-                            s_lo[threadIdx.x] = lo[s + threadIdx.x];
-                        }
-                        __syncthreads();
-                        const int m = min(kChunk, s1 - s);
-                        float a = 0.f;
-#pragma unroll 4
-                        for (int j = 0; j < m; ++j) {
-                            const float4 sh = s_hi[j], sl = s_lo[j];
-                            const float dx = (th.x - sh.x) + (tl.x - sl.x);
-                            const float dy = (th.y - sh.y) + (tl.y - sl.y);
-                            float r2 = fmaf(dx, dx, dy * dy);
-                            if constexpr (D == 3) {
-                                const float dz = (th.z - sh.z) + (tl.z - sl.z);
-                                r2 = fmaf(dz, dz, r2);
-                                const float ri = rsqrtf(r2);
-                                a = fmaf(sh.w, r2 > 0.f ? ri : 0.f, a);
-                            } else {
-                                const float lg = __log2f(r2);
-                                a = fmaf(sh.w, r2 > 0.f ? lg : 0.f, a);
-                            }
-                        }
-                        acc += (double)a;
-                    }
+        double acc_a = 0.0, acc_b = 0.0;
+#pragma unroll 1
+        for (int f = g * FG; f < min(F, (g + 1) * FG); ++f) {
+            int o[3];
+            fwd_offset<D>(f, o);
+            const int nc[3] = {c[0] + o[0], c[1] + o[1], c[2] + o[2]};
+            if (nc[0] < 0 || nc[0] >= side || nc[1] < 0 || nc[1] >= side) continue;
+            if (D == 3 && (nc[2] < 0 || nc[2] >= side)) continue;
+            const bool own = f == 0;
+            const uint32_t nb = morton_enc(D, nc);
+            const int s0 = start[nb], s1 = start[nb + 1];
+            if (lane == 0) my_pairs += (own ? 1ull : 2ull) * (unsigned long long)(s1 - s0) * (unsigned long long)(t1 - t0);
+            for (int s = s0; s < s1; s += kSymTile) {
+                const int m = min(kSymTile, s1 - s);
+                __syncwarp();
+                {
+                    const bool have = lane < m;
+                    const float4 h = have ? hi[s + lane] : make_float4(1.0e4f, 1.0e4f, 1.0e4f, 0.f);
+                    const float4 l = have ? lo[s + lane] : z4;
+                    s_a[wid][lane] = make_float4(-h.x, -h.x, -h.y, -h.y);
+                    s_b[wid][lane] = make_float4(-h.z, -h.z, h.w, h.w);
+                    s_c[wid][lane] = make_float4(-l.x, -l.x, -l.y, -l.y);
+                    s_d[wid][lane] = make_float2(-l.z, -l.z);
                 }
-        if (act) nearf[i] = D == 2 ? acc * (0.5 * kLn2) : acc;
+                __syncwarp();
+                if (own) {
+                    const float2 a2 = p2p_tile<D, true>(s_a[wid], s_b[wid], s_c[wid], s_d[wid], m, tx, ty, tz, ux, uy, uz);
+                    acc_a += (double)a2.x;
+                    acc_b += (double)a2.y;
+                    continue;
+                }
+                float cs[kSymTile];
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < kSymTile; ++j) {
+                    const float4 A = s_a[wid][j], B = s_b[wid][j], C = s_c[wid][j];
+                    const float2 dx = __fadd2_rn(__fadd2_rn(tx, make_float2(A.x, A.y)), __fadd2_rn(ux, make_float2(C.x, C.y)));
+                    const float2 dy = __fadd2_rn(__fadd2_rn(ty, make_float2(A.z, A.w)), __fadd2_rn(uy, make_float2(C.z, C.w)));
+                    float2 r2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+                    if constexpr (D == 3) {
+                        const float2 E = s_d[wid][j];
+                        const float2 dz = __fadd2_rn(__fadd2_rn(tz, make_float2(B.x, B.y)), __fadd2_rn(uz, E));
+                        r2 = __ffma2_rn(dz, dz, r2);
+                    }
+                    const float2 k = D == 3 ? make_float2(mufu_rsqrt(r2.x), mufu_rsqrt(r2.y))
+                                            : make_float2(mufu_lg2(r2.x), mufu_lg2(r2.y));
+                    acc = __ffma2_rn(make_float2(B.z, B.w), k, acc);
+                    const float2 t = __fmul2_rn(qa, k);
+                    cs[j] = t.x + t.y;
+                }
+                acc_a += (double)acc.x;
+                acc_b += (double)acc.y;
+                const float v = warp_transpose_sum(cs, lane);
+                if (lane < m) atomicAdd(nearf + s + lane, (double)v * scale);
+            }
+        }
+        if (va) atomicAdd(nearf + ia, acc_a * scale);
+        if (vb) atomicAdd(nearf + ib, acc_b * scale);
     }
-    if (threadIdx.x == 0 && my_pairs) atomicAdd(pairs, my_pairs);
+    if (lane == 0 && my_pairs) atomicAdd(pairs, my_pairs);
 }
 
 // The near field in FP64 (node and literal FP64 forms), same walk.
@@ -444,8 +583,8 @@ __global__ void __launch_bounds__(256) k_m2l(const T* __restrict__ K, const T* _
                 if (my < e0 || my >= e1) continue;
                 const int oidx = (ox + 3) + 7 * (oy + 3) + (D == 3 ? 49 * (oz + 3) : 0);
                 __syncthreads();
-                const T* Ko = K + (size_t)oidx * d * d;
-                for (int x = tid; x < d * d; x += NT) s_K[x] = Ko[x];
+                const float4* Ko = reinterpret_cast<const float4*>(K + (size_t)oidx * d * d);
+                for (int x = tid; x < d * d * (int)sizeof(T) / 16; x += NT) reinterpret_cast<float4*>(s_K)[x] = Ko[x];
                 for (int x = tid; x < d * TT; x += NT) {
                     const int tt = x / d, i = x % d;
                     const int P = tile * TT + tt;
@@ -738,8 +877,8 @@ fmm_status alloc(fmm_lag_plan_s* pl, T** p, size_t count) {
 void plan_free(fmm_lag_plan_s* pl) {
     if (!pl) return;
     cudaFree(pl->key); cudaFree(pl->rank); cudaFree(pl->skey); cudaFree(pl->count); cudaFree(pl->start);
-    cudaFree(pl->chunk_start); cudaFree(pl->order); cudaFree(pl->hi); cudaFree(pl->lo); cudaFree(pl->p64);
-    cudaFree(pl->nearf); cudaFree(pl->status); cudaFree(pl->pairs); cudaFree(pl->K);
+    cudaFree(pl->chunk_start); cudaFree(pl->wchunk_start); cudaFree(pl->order); cudaFree(pl->hi); cudaFree(pl->lo); cudaFree(pl->p64);
+    cudaFree(pl->nearf); cudaFree(pl->status); cudaFree(pl->pairs); cudaFree(pl->next_item); cudaFree(pl->K);
     for (int k = 0; k <= kMaxLevels; ++k) {
         cudaFree(pl->node[k]); cudaFree(pl->pot[k]); cudaFree(pl->pair_start[k]); cudaFree(pl->pair_src[k]);
         cudaFree(pl->B[k]);
@@ -795,7 +934,7 @@ fmm_status enqueue(fmm_lag_plan_s* pl, const double* pos, const double* q, int64
     }
     const unsigned gb = (unsigned)((n + 255) / 256);
     k_bin<D><<<gb, 256, 0, st>>>(pos, q, n, L, pl->box, pl->key, pl->rank, pl->count, pl->status);
-    k_scan<<<1, 1024, 0, st>>>(pl->count, (int)pl->nleaf, pl->start, pl->chunk_start);
+    k_scan<<<1, 1024, 0, st>>>(pl->count, (int)pl->nleaf, pl->start, pl->chunk_start, pl->wchunk_start);
     if (f64)
         k_scatter<D, true><<<gb, 256, 0, st>>>(pos, q, n, pl->key, pl->rank, pl->start, pl->skey, pl->order,
                                                 nullptr, nullptr, pl->p64);
@@ -803,21 +942,31 @@ fmm_status enqueue(fmm_lag_plan_s* pl, const double* pos, const double* q, int64
         k_scatter<D, false><<<gb, 256, 0, st>>>(pos, q, n, pl->key, pl->rank, pl->start, pl->skey, pl->order,
                                                  pl->hi, pl->lo, nullptr);
     launches += 3;
+    cudaEventRecord(pl->ev[7], st);
     cudaEventRecord(pl->ev[1], st);
-    // near field on the second stream
-    cudaEventRecord(pl->ev_fork, st);
-    cudaStreamWaitEvent(pl->st2, pl->ev_fork, 0);
-    cudaEventRecord(pl->ev[5], pl->st2);
+    // near field on the second stream (or in turn on the plan's stream in serial mode)
+    cudaStream_t p2p_st = pl->serial ? st : pl->st2;
+    if (!pl->serial) {
+        cudaEventRecord(pl->ev_fork, st);
+        cudaStreamWaitEvent(pl->st2, pl->ev_fork, 0);
+    }
     const unsigned gp = (unsigned)pl->grid_particles;
-    if (f64)
-        k_p2p64<D><<<gp, kChunk, 0, pl->st2>>>(pl->p64, pl->start, pl->chunk_start, (int)pl->nleaf, L, pl->nearf,
+    if (!f64) {
+        cudaMemsetAsync(pl->nearf, 0, sizeof(double) * (size_t)n, p2p_st);
+        cudaMemsetAsync(pl->next_item, 0, sizeof(int), p2p_st);
+    }
+    cudaEventRecord(pl->ev[5], p2p_st);
+    if (f64) {
+        k_p2p64<D><<<gp, kChunk, 0, p2p_st>>>(pl->p64, pl->start, pl->chunk_start, (int)pl->nleaf, L, pl->nearf,
                                                pl->pairs);
-    else
-        k_p2p32<D><<<gp, kChunk, 0, pl->st2>>>(pl->hi, pl->lo, pl->start, pl->chunk_start, (int)pl->nleaf, L,
-                                               pl->nearf, pl->pairs);
+    } else {
+        k_p2p32<D><<<(unsigned)pl->grid_p2p, kP2PWarps * 32, 0, p2p_st>>>(
+            pl->hi, pl->lo, pl->start, pl->wchunk_start, (int)pl->nleaf, L, pl->nearf, pl->pairs, pl->next_item);
+    }
     ++launches;
-    cudaEventRecord(pl->ev[6], pl->st2);
-    cudaEventRecord(pl->ev_join, pl->st2);
+    cudaEventRecord(pl->ev[6], p2p_st);
+    cudaEventRecord(pl->ev_join, p2p_st);
+    if (pl->serial) cudaEventRecord(pl->ev[1], st);   // the far-field stages start after the near field
 
     LevelPtrs nodes{}, pots{};
     for (int k = 0; k <= kMaxLevels; ++k) {
@@ -835,7 +984,7 @@ fmm_status enqueue(fmm_lag_plan_s* pl, const double* pos, const double* q, int64
             ++launches;
         }
         cudaEventRecord(pl->ev[2], st);
-        const int ngroups = D == 2 ? 3 : 9;
+        const int ngroups = D == 2 ? 3 : 27;
         for (int k = 2; k <= L; ++k) {
             const int pside = 1 << (k - 1);
             const int64_t nparent = ipow(pside, D);
@@ -926,6 +1075,11 @@ fmm_status fmm_lag_plan(fmm_lag_plan_t* out, int dim, int64_t n_max, int levels,
     int sms = 0;
     if (rc == FMM_OK) rc = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->dev));
     pl->grid_particles = std::max(1, sms) * 8;
+    int per_sm = 0;
+    if (rc == FMM_OK)
+        rc = cuda_status(dim == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p32<2>, kP2PWarps * 32, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_p2p32<3>, kP2PWarps * 32, 0));
+    pl->grid_p2p = std::max(1, sms) * std::max(1, per_sm);
     if (rc == FMM_OK) rc = cuda_status(cudaStreamCreateWithFlags(&pl->st2, cudaStreamNonBlocking));
     for (auto& e : pl->ev)
         if (rc == FMM_OK) rc = cuda_status(cudaEventCreate(&e));
@@ -940,8 +1094,10 @@ fmm_status fmm_lag_plan(fmm_lag_plan_t* out, int dim, int64_t n_max, int levels,
     if (rc == FMM_OK) rc = alloc(pl, &pl->count, (size_t)pl->nleaf);
     if (rc == FMM_OK) rc = alloc(pl, &pl->start, (size_t)pl->nleaf + 1);
     if (rc == FMM_OK) rc = alloc(pl, &pl->chunk_start, (size_t)pl->nleaf + 1);
+    if (rc == FMM_OK) rc = alloc(pl, &pl->wchunk_start, (size_t)pl->nleaf + 1);
     if (rc == FMM_OK) rc = alloc(pl, &pl->status, 1);
     if (rc == FMM_OK) rc = alloc(pl, &pl->pairs, 1);
+    if (rc == FMM_OK) rc = alloc(pl, &pl->next_item, 1);
     if (rc == FMM_OK && f64) rc = alloc(pl, &pl->p64, n);
     if (rc == FMM_OK && !f64) rc = alloc(pl, &pl->hi, n);
     if (rc == FMM_OK && !f64) rc = alloc(pl, &pl->lo, n);
@@ -1077,7 +1233,7 @@ fmm_status fmm_lag_stats_get(fmm_lag_plan_t pl, fmm_lag_stats* out) {
         return cudaEventElapsedTime(&ms, pl->ev[a], pl->ev[b]) == cudaSuccess ? (double)ms : 0.0;
     };
     out->ms_total = span(0, 4);
-    out->ms_sort = span(0, 1);
+    out->ms_sort = span(0, 7);
     out->ms_up = span(1, 2);
     out->ms_down = span(2, 3);
     out->ms_eval = span(3, 4);
@@ -1086,6 +1242,12 @@ fmm_status fmm_lag_stats_get(fmm_lag_plan_t pl, fmm_lag_stats* out) {
     if (cudaMemcpy(&pairs, pl->pairs, sizeof(pairs), cudaMemcpyDeviceToHost) != cudaSuccess) return FMM_ERR_CUDA;
     out->p2p_pairs = (int64_t)pairs;
     out->kernel_launches = pl->launches;
+    return FMM_OK;
+}
+
+fmm_status fmm_lag_set_concurrency(fmm_lag_plan_t pl, int streams) {
+    if (!pl || (streams != 1 && streams != 2)) return FMM_ERR_INVALID_ARG;
+    pl->serial = streams == 1;
     return FMM_OK;
 }
 
