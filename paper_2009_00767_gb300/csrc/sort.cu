@@ -16,7 +16,7 @@ namespace {
 
 constexpr int kScanThreads = 256;
 
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 2;   // small tiles: 128 blocks for 4^8 squares, each with little serial work
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // particles [i0, n)
