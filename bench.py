@@ -70,6 +70,9 @@ def parse():
                          "of single-system launches)")
     ap.add_argument("--batched-systems", type=int, default=1024)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned (levels, p) selector's leg")
+    ap.add_argument("--lagrange-only", action="store_true",
+                    help="run only the Lagrange-node leg (a profiling target); prints that leg's JSON")
+    ap.add_argument("--lagrange-steps", type=int, default=20)
     ap.add_argument("--no-lagrange", action="store_true",
                     help="skip the leg of the paper's own Lagrange-node form (3D Coulomb workloads of its "
                          "Tables 1-3, the 2D comparison and the FP64-conditioning sweep)")
@@ -471,7 +474,8 @@ def run_ours(args):
 
     lagrange = None
     if not args.no_lagrange and rank == 0:
-        lagrange = run_lagrange(binding, torch, dev, flush, peaks.get("sm_max_mhz", 2070.0))
+        lagrange = run_lagrange(binding, torch, dev, flush, peaks.get("sm_max_mhz", 2070.0),
+                                steps=args.lagrange_steps)
 
     batched = None
     if not args.no_batched and args.precision != "fp64":
@@ -859,10 +863,28 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_lagrange_only(args):
+    import torch
+    from paper_2009_00767_gb300 import binding, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    res = run_lagrange(binding, torch, dev, flush, peaks.get("sm_max_mhz", 2070.0), steps=args.lagrange_steps,
+                       steps64=max(1, min(3, args.lagrange_steps)))
+    print(json.dumps({"lagrange": res}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.lagrange_only:
+        run_lagrange_only(args)
     else:
         run_ours(args)
 
