@@ -70,6 +70,9 @@ def parse():
                          "of single-system launches)")
     ap.add_argument("--batched-systems", type=int, default=1024)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned (levels, p) selector's leg")
+    ap.add_argument("--no-clustered", action="store_true",
+                    help="skip the clustered leg (2^24 Gaussian-mixture particles, levels 10, p 24)")
+    ap.add_argument("--clustered-steps", type=int, default=5)
     ap.add_argument("--lagrange-only", action="store_true",
                     help="run only the Lagrange-node leg (a profiling target); prints that leg's JSON")
     ap.add_argument("--lagrange-steps", type=int, default=20)
@@ -472,6 +475,10 @@ def run_ours(args):
         p64.close()
     plan.close()
 
+    clustered = None
+    if not args.no_clustered and rank == 0 and args.workload != "gmm32_16m_l10_p24":
+        clustered = run_clustered(binding, torch, dev, args.precision, flush, args.clustered_steps, peaks)
+
     lagrange = None
     if not args.no_lagrange and rank == 0:
         lagrange = run_lagrange(binding, torch, dev, flush, peaks.get("sm_max_mhz", 2070.0),
@@ -505,7 +512,7 @@ def run_ours(args):
             "roofline_stages": roof_all,
             "gpu_launches": launches, "e2e": e2e, "fp64_gpu": fp64, "alu_peaks_probe": probe,
             "speedup_vs_fp64_gpu": (value / fp64["value"]) if fp64 else None,
-            "cpu_baseline": cpu, "batched": batched, "learned": learned, "lagrange": lagrange, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+            "cpu_baseline": cpu, "batched": batched, "learned": learned, "lagrange": lagrange, "clustered": clustered, "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                                             "reasons": clk["reasons"], "samples": clk["samples"]},
             "wall_s_timed": wall,
         }
@@ -515,6 +522,12 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------- batched form
+
+def batched_families(nsys, seed=20094767):
+    """True for the systems batched_workload draws uniform (the rest are Gaussian mixtures)."""
+    from paper_2009_00767_gb300 import inputs
+    return inputs.u01(seed, 32, nsys) < 0.5
+
 
 def batched_workload(nsys, seed=20094767):
     """1024 independent systems: N log-uniform in [1024, 262144], uniform or a Gaussian mixture
@@ -579,6 +592,32 @@ def run_batched(binding, torch, dev, nsys, steps, warmup, precision):
         got = phi[off[i]:off[i + 1]][idx_d]
         errs.append({"system": int(i), "n": n_i, "levels": int(levels[i]),
                      "rel_l2_err": float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))})
+    # the uniform half alone, as its own batch: the particles/s of the same form on the family of
+    # the single-system workload (the Gaussian-mixture half fills its leaves unevenly at ~16
+    # particles per leaf on average, so its near field dominates the mixed batch)
+    uni = np.nonzero(batched_families(nsys))[0]
+    off = np.concatenate([[0], np.cumsum(ns)])
+    sel = np.concatenate([np.arange(off[i], off[i + 1]) for i in uni])
+    xu, qu = xy_d[torch.from_numpy(sel).to(dev)].contiguous(), q_d[torch.from_numpy(sel).to(dev)].contiguous()
+    phu = torch.empty(sel.shape[0], dtype=torch.float64, device=dev)
+    bu = binding.Batch(ns[uni], levels[uni], 16, precision=precision)
+    binding.fmm_batch_autotune_cached(bu.handle, xu, qu, phu, None)
+    for _ in range(warmup):
+        binding.fmm_batch_potential(bu.handle, xu, qu, phu)
+    torch.cuda.synchronize()
+    msu = []
+    for _ in range(steps):
+        e0.record()
+        binding.fmm_batch_potential(bu.handle, xu, qu, phu)
+        e1.record()
+        torch.cuda.synchronize()
+        msu.append(e0.elapsed_time(e1))
+    binding.fmm_batch_sync(bu.handle)
+    bu.close()
+    ms_uni = float(np.median(msu))
+    uniform_subset = {"systems": int(uni.shape[0]), "particles": int(sel.shape[0]), "ms_per_step": ms_uni,
+                      "value": sel.shape[0] / (ms_uni * 1e-3), "unit": UNIT}
+    del xu, qu, phu
     # the same systems as a loop of single-system plans (one launch sequence per system)
     plans = [binding.Plan(int(ns[i]), int(levels[i]), 16, 5.0, precision) for i in range(nsys)]
     views = [(xy_d[off[i]:off[i + 1]], q_d[off[i]:off[i + 1]], phi[off[i]:off[i + 1]]) for i in range(nsys)]
@@ -599,6 +638,7 @@ def run_batched(binding, torch, dev, nsys, steps, warmup, precision):
     return {"systems": nsys, "particles": total, "ms_per_step": ms_batch, "value": total / (ms_batch * 1e-3),
             "unit": UNIT, "loop_ms_per_step": ms_loop, "loop_value": total / (ms_loop * 1e-3),
             "speedup_vs_loop": ms_loop / ms_batch, "graph_launches_per_step": launches, "tuning": tuning,
+            "uniform_subset": uniform_subset,
             "precision": precision, "p": 16, "rel_l2_err_max": max(e["rel_l2_err"] for e in errs),
             "meets_error_bound": all(e["rel_l2_err"] <= ERR_BOUND for e in errs), "sampled_systems": errs,
             "timing": "CUDA events around each graph replay, median of the steps"}
@@ -666,6 +706,43 @@ def run_learned(binding, torch, dev, precision, flush, steps=20):
             "meets_error_bound": all(r["err_pick"] <= ERR_BOUND for r in rows),
             "rule_basis": f"no network: levels round(log4(N/16)), p {p_rule} = the smallest grid p meeting 1e-6 "
                           f"on a 2^18 uniform calibration system"}
+
+
+# ---------------------------------------------------------------- clustered workload
+
+def run_clustered(binding, torch, dev, precision, flush, steps, peaks):
+    """The clustered configuration (2^24 particles, a mixture of 32 Gaussians, levels 10, p 24) in the
+    benchmarked precision: median step, error against the FP64 direct sum at 4096 sampled targets,
+    each stage's time alone and the near field's roofline.  On a uniform tree the clusters fill
+    their leaves with thousands of particles, so the near field dominates."""
+    w = WORKLOADS["gmm32_16m_l10_p24"]
+    xy, q = make_inputs(w)
+    xy_d, q_d = torch.from_numpy(xy).to(dev), torch.from_numpy(q).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    plan, phi, ms, stage_ms, launches, wall, last = time_plan(binding, torch, w, precision, xy_d, q_d, steps, 2,
+                                                              flush, stream)
+    from paper_2009_00767_gb300 import inputs as inp
+    idx = np.unique((inp.u01(4545, 0, 4096) * w["n"]).astype(np.int64))
+    idx_d = torch.from_numpy(idx).to(dev)
+    ref = torch.empty(idx.shape[0], dtype=torch.float64, device=dev)
+    binding.fmm_direct_targets(xy_d, q_d, idx_d, ref)
+    torch.cuda.synchronize()
+    err = float(torch.linalg.norm(phi[idx_d] - ref) / torch.linalg.norm(ref))
+    alone = time_kernels_alone(binding, torch, plan, xy_d, q_d, phi, max(2, steps), 1, flush, stream)
+    st = plan.stats()
+    plan.close()
+    med = float(np.median(ms))
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak = N_SMS * MUFU_PER_SM * sm_max * 1e6 / 1e12
+    ach = st["p2p_pairs"] / (alone["p2p_kernel"] * 1e-3) / 1e12 if alone["p2p_kernel"] > 0 else None
+    return {"workload": "gmm32_16m_l10_p24", "n": w["n"], "levels": w["levels"], "p": w["p"],
+            "precision": precision, "ms_per_step": med, "value": w["n"] / (med * 1e-3), "unit": UNIT,
+            "rel_l2_err": err, "meets_error_bound": err <= ERR_BOUND, "kernel_ms_alone": alone,
+            "max_leaf": st["max_leaf"], "p2p_pairs": st["p2p_pairs"],
+            "roofline_p2p": None if ach is None else {
+                "kernel": "k_p2p_mixed", "bound": "alu", "achieved": ach, "peak": peak, "unit": "Tlg2/s",
+                "frac": ach / peak, "work_per_launch": f"{st['p2p_pairs']} ordered pairs, one lg2 each",
+                "timing": "kernel alone (serial pass, CUDA events)"}}
 
 
 # ---------------------------------------------------------------- Lagrange-node form (Appendix)
