@@ -167,3 +167,27 @@ def test_papers_table2_size(oracle_mod, form, tol):
     check_parity(phi, ref, tol, f"{form} 200k 3D L3")
     t = np.linspace(0, 199_999, 64).astype(np.int64)
     assert rel_l2(phi[t], oracle_mod.lag_direct_targets(pos, q, t)) < 1e-3
+
+
+@pytest.mark.parametrize("dim,levels,n", [(2, 8, 200_000), (3, 4, 60_000), (3, 5, 100_000)])
+def test_node_forms_at_the_deepest_levels(oracle_mod, dim, levels, n):
+    # the deepest trees a plan accepts (2D level 8, 3D levels 4 and 5): many cells, few charges each
+    pos, q = inputs.paper_cube(n, 5000 + 10 * dim + levels, dim)
+    ref = oracle_mod.lag_node(pos, q, levels)
+    check_parity(run(pos, q, levels, "node_f64")[0], ref, TOL64, f"node_f64 D={dim} L={levels}")
+    check_parity(run(pos, q, levels, "node_f32")[0], ref, TOL32, f"node_f32 D={dim} L={levels}")
+
+
+def test_literal_form_at_its_deepest_level_runs():
+    # 2D level 7: the literal form's rounding swamps the result (the FP64 conditioning of Sec. 4
+    # (3)), but the call completes with finite values and the node form still holds
+    import torch
+    from paper_2009_00767_gb300 import binding
+    pos, q = inputs.paper_cube(30_000, 77, 2)
+    phi, st, _ = run(pos, q, 7, "literal_f64")
+    assert np.all(np.isfinite(phi))
+    assert st["m2l_pairs"] > 16384 * 20
+    with pytest.raises(binding.FmmError):
+        binding.LagPlan(2, 10, 8, 5.0, "literal_f64")
+    with pytest.raises(binding.FmmError):
+        binding.LagPlan(3, 10, 6, 5.0, "node_f32")
