@@ -103,6 +103,7 @@ void free_plan(fmm_plan_s* pl) {
     fmm_tc_destroy(pl);
     if (pl->h_status) cudaFreeHost(pl->h_status);
     if (pl->h_counters) cudaFreeHost(pl->h_counters);
+    if (pl->crowd_hint_h) cudaFreeHost(pl->crowd_hint_h);
     for (int e = 0; e < 15; ++e)
         if (pl->ev[e]) cudaEventDestroy(pl->ev[e]);
     if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
@@ -295,6 +296,10 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->d_status, sizeof(unsigned int)));
     FMM_TRY(dev_alloc(pl, &pl->d_counters, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long)));
     if (cudaMemset(pl->d_status, 0, sizeof(unsigned int)) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
+    if (cudaHostAlloc(reinterpret_cast<void**>(&pl->crowd_hint_h), sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&pl->crowd_hint_d), pl->crowd_hint_h, 0) != cudaSuccess)
+        FMM_TRY(FMM_ERR_CUDA);
+    *pl->crowd_hint_h = 0;
     if (cudaMallocHost(reinterpret_cast<void**>(&pl->h_status), sizeof(unsigned int)) != cudaSuccess)
         FMM_TRY(FMM_ERR_OOM);
     if (cudaMallocHost(reinterpret_cast<void**>(&pl->h_counters), 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long)) !=

@@ -42,6 +42,7 @@ struct __align__(32) fmm_p64 {
 // Near-field statistics are spread over this many counter slots (one update per CTA each) so
 // that no single L2 address serialises the updates.
 #define FMM_COUNTER_SLOTS 64
+#define FMM_LANE_MAX 128   // finest squares above this many particles are "crowded" in the fine P2M
 
 // Conversions between FP32 and FP64 by integer bit operations, so that they do not occupy
 // GB300's narrow FP64 pipe.  Zero, subnormal and out-of-range inputs flush to zero (their
@@ -114,6 +115,11 @@ struct fmm_plan_s {
     unsigned long long* d_counters;   // [0..63] near-field pair partials, [64..127] max leaf population
     unsigned int* h_status;           // pinned
     unsigned long long* h_counters;   // pinned [128]
+    // mixed path: set to 1 by the scan of a call that finds a finest square above FMM_LANE_MAX
+    // particles (mapped host memory, read without a sync by the next call's enqueue, which then
+    // sums crowded squares' fine-level moments with k_p2m_crowded instead of one warp each)
+    int* crowd_hint_h;
+    int* crowd_hint_d;
 
     // host-array calls: two staging sets, so a call's uploads overlap the previous call's compute
     double* d_xy_stage[2];

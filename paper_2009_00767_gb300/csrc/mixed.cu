@@ -41,7 +41,7 @@ constexpr int kM2LThreads = 128;
 // particles' terms in registers while the square stays the same and flush (a column sum over the
 // warp's lanes in shared memory, then FP64 atomics into the level's grid) when it changes.
 constexpr int kFineLevels = 3;
-constexpr int kLaneMax = 128;
+constexpr int kLaneMax = FMM_LANE_MAX;
 constexpr int kCoarseChunk = 256;
 
 // powers q w^m, m = 1..P1B-1 added into acc (entries at m >= p1 stay untouched: the caller masks)
@@ -85,7 +85,7 @@ template <int P1B, int G, int SH>
 __device__ __forceinline__ void p2m_fine_finish(const float2 (&acc)[P1B], float2 m0, const float4* __restrict__ sp,
                                                 uint32_t sq, uint32_t lo, uint32_t hi, bool valid, bool owner,
                                                 int levels, int p1, float inv_s, float ox, float oy, float* red,
-                                                int lane, FmmLevelPtrs g) {
+                                                int lane, FmmLevelPtrs g, bool ext) {
     constexpr int V = 2 * (P1B - 1);              // Re, Im of coefficients 1 .. P1B - 1
     constexpr int VP = (V + G - 1) / G * G;
     constexpr int B = VP / G;
@@ -98,7 +98,9 @@ __device__ __forceinline__ void p2m_fine_finish(const float2 (&acc)[P1B], float2
 #pragma unroll
     for (int m = 1; m < G; m <<= 1)
         m0 = ff_add(m0, make_float2(__shfl_xor_sync(0xffffffffu, m0.x, m), __shfl_xor_sync(0xffffffffu, m0.y, m)));
-    // crowded squares: the whole warp sums the particles, the owning group adds its share
+    // crowded squares: the whole warp sums the particles, the owning group adds its share (with
+    // `ext`, k_p2m_crowded adds their coefficients 1..p afterwards and the warp sums only the
+    // total charge, in float-float)
     unsigned todo = __ballot_sync(0xffffffffu, valid && large && owner);
     while (todo) {
         const int src = __ffs(todo) - 1;
@@ -109,18 +111,24 @@ __device__ __forceinline__ void p2m_fine_finish(const float2 (&acc)[P1B], float2
 #pragma unroll
         for (int m = 0; m < P1B; ++m) a2[m] = make_float2(0.f, 0.f);
         float2 mm = make_float2(0.f, 0.f);
-        for (uint32_t j = lo2 + lane; j < hi2; j += 32) {
-            const float4 P = sp[j];
-            mm = ff_add_f(mm, P.z);
-            add_powers<P1B>(a2, P.z, make_float2(fmaf(P.x, inv_s, ox2), fmaf(P.y, inv_s, oy2)));
+        if (ext) {
+            for (uint32_t j = lo2 + lane; j < hi2; j += 32) mm = ff_add_f(mm, sp[j].z);
+        } else {
+            for (uint32_t j = lo2 + lane; j < hi2; j += 32) {
+                const float4 P = sp[j];
+                mm = ff_add_f(mm, P.z);
+                add_powers<P1B>(a2, P.z, make_float2(fmaf(P.x, inv_s, ox2), fmaf(P.y, inv_s, oy2)));
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             mm = ff_add(mm, make_float2(__shfl_xor_sync(0xffffffffu, mm.x, o), __shfl_xor_sync(0xffffffffu, mm.y, o)));
+            if (!ext) {
 #pragma unroll
-            for (int m = 1; m < P1B; ++m) {
-                a2[m].x += __shfl_xor_sync(0xffffffffu, a2[m].x, o);
-                a2[m].y += __shfl_xor_sync(0xffffffffu, a2[m].y, o);
+                for (int m = 1; m < P1B; ++m) {
+                    a2[m].x += __shfl_xor_sync(0xffffffffu, a2[m].x, o);
+                    a2[m].y += __shfl_xor_sync(0xffffffffu, a2[m].y, o);
+                }
             }
         }
         if (lane == 0) {
@@ -188,7 +196,7 @@ __device__ __forceinline__ void add_powers_pair(float2 (&ar)[P1B], float2 (&ai)[
 template <int P1B>
 __global__ void __launch_bounds__(128, P1B <= 25 ? 4 : 1)
 k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_start, int levels, int p, MixedLevels lv,
-           FmmLevelPtrs g) {
+           FmmLevelPtrs g, int ext) {
     __shared__ float red[4][2 * P1B];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t t = blockIdx.x * 128u + threadIdx.x;
@@ -229,13 +237,97 @@ k_p2m_fine(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_star
         for (int m = 0; m < P1B; ++m) acc[m] = make_float2(ar[m].x + ar[m].y, ai[m].x + ai[m].y);
         if (sh == 0)
             p2m_fine_finish<P1B, 2, 0>(acc, m0, sp, sq, lo, hi, valid, owner, levels, p1, s, ox, oy, red[warp], lane,
-                                       g);
+                                       g, ext != 0);
         else if (sh == 1)
             p2m_fine_finish<P1B, 8, 1>(acc, m0, sp, sq, lo, hi, valid, owner, levels, p1, s, ox, oy, red[warp], lane,
-                                       g);
+                                       g, ext != 0);
         else
             p2m_fine_finish<P1B, 32, 2>(acc, m0, sp, sq, lo, hi, valid, owner, levels, p1, s, ox, oy, red[warp],
-                                        lane, g);
+                                        lane, g, ext != 0);
+    }
+}
+
+// Fine levels of crowded finest squares (above kLaneMax particles), spread over the whole grid
+// instead of one warp per square: each warp walks kCoarseChunk consecutive sorted particles, takes
+// those of crowded squares and, per fine level, adds their power chains in registers while their
+// level-k square stays the same, flushing (a warp butterfly sum, then FP32 atomics into the level's
+// FP32 grid) when it changes.  k_p2m_fine, run first in its `ext` mode, has stored every square's
+// other shares and the crowded squares' total charge, so these adds complete coefficients 1..p.
+template <int P1B>
+__global__ void __launch_bounds__(128)
+k_p2m_crowded(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, const uint32_t* __restrict__ leaf_start,
+              int64_t n, int levels, int p, MixedLevels lv, FmmLevelPtrs g) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = ((int64_t)blockIdx.x * 4 + warp) * kCoarseChunk;
+    if (base >= n) return;
+    const int p1 = p + 1;
+    uint32_t cmask = 0;   // bit r: particle base + 32 r + lane lies in a crowded finest square
+#pragma unroll
+    for (int r = 0; r < kCoarseChunk / 32; ++r) {
+        const int64_t j = base + 32 * r + lane;
+        if (j < n) {
+            const uint32_t key = skey[j];
+            if (leaf_start[key + 1] - leaf_start[key] > (uint32_t)kLaneMax) cmask |= 1u << r;
+        }
+    }
+    if (!__any_sync(0xffffffffu, cmask != 0u)) return;
+#pragma unroll 1
+    for (int sh = 0; sh < kFineLevels; ++sh) {
+        const int k = levels - sh;
+        if (k < 2) break;
+        const int W = fmm_grid_width(k);
+        float2* A = reinterpret_cast<float2*>(g.A32[k]);
+        const float inv_s = lv.inv_s[k];
+        float2 acc[P1B];
+#pragma unroll
+        for (int m = 0; m < P1B; ++m) acc[m] = make_float2(0.f, 0.f);
+        uint32_t cur = 0xffffffffu;   // the level-k square the sums belong to (warp-uniform)
+        auto flush = [&]() {
+#pragma unroll
+            for (int m = 1; m < P1B; ++m)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc[m].x += __shfl_xor_sync(0xffffffffu, acc[m].x, o);
+                    acc[m].y += __shfl_xor_sync(0xffffffffu, acc[m].y, o);
+                }
+            const size_t cell = (size_t)(fmm_compact2(cur >> 1) + FMM_HALO) * W + fmm_compact2(cur) + FMM_HALO;
+            float2* Ac = A + cell * p1;
+#pragma unroll
+            for (int m = 1; m < P1B; ++m) {
+                if (m < p1 && lane == (m & 31)) {
+                    atomicAdd(&Ac[m].x, acc[m].x);
+                    atomicAdd(&Ac[m].y, acc[m].y);
+                }
+                acc[m] = make_float2(0.f, 0.f);
+            }
+        };
+#pragma unroll 1
+        for (int r = 0; r < kCoarseChunk / 32; ++r) {
+            const bool act = (cmask >> r) & 1u;
+            const int64_t j = base + 32 * r + lane;
+            float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint32_t key = 0u, box = 0xffffffffu;
+            if (act) {
+                P = sp[j];
+                key = skey[j];
+                box = key >> (2 * sh);
+            }
+            // the keys are sorted, so the lanes of one square are consecutive: each pass takes the
+            // square of the first lane still to add, at most 32 passes
+            unsigned todo = __ballot_sync(0xffffffffu, act);
+            while (todo) {
+                const uint32_t first = __shfl_sync(0xffffffffu, box, __ffs(todo) - 1);
+                if (first != cur) {
+                    if (cur != 0xffffffffu) flush();
+                    cur = first;
+                }
+                const bool mine = ((todo >> lane) & 1u) && box == cur;
+                if (mine)
+                    add_powers<P1B>(acc, P.z, level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh, inv_s));
+                todo &= ~__ballot_sync(0xffffffffu, mine);
+            }
+        }
+        if (cur != 0xffffffffu) flush();
     }
 }
 
@@ -819,15 +911,26 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field) {
     const int kc_max = kf - 1;   // the coarse FP64 grids are zero here (k_prep_a32 re-zeroes them)
     const int kw = L < kM2LWarpMaxLevel ? L : kM2LWarpMaxLevel;   // levels 2..kw: the coarse M2L kernel
     if (L >= 2) {
+        // crowded squares (a previous call's scan found a finest square above kLaneMax particles):
+        // their fine-level coefficients come from k_p2m_crowded, spread over the grid; the hint is
+        // only a guess about this call's input, and either way the result is the same
+        const bool ext = pl->crowd_hint_h != nullptr && *(volatile int*)pl->crowd_hint_h != 0;
+        if (pl->crowd_hint_h) *(volatile int*)pl->crowd_hint_h = 0;
         const unsigned fblocks = (unsigned)(((2ull << (2 * L)) + 127) / 128);   // two lanes per finest square
+        const unsigned cwblocks = (unsigned)((n + 4 * kCoarseChunk - 1) / (4 * kCoarseChunk));
         switch (pl->p1b) {
 #define FMM_P2M(PB)                                                                                          \
-    case PB: k_p2m_fine<PB><<<fblocks, 128, 0, st>>>(pl->sorted32, pl->leaf_start, L, p, lv, pl->grids); break;
+    case PB:                                                                                                 \
+        k_p2m_fine<PB><<<fblocks, 128, 0, st>>>(pl->sorted32, pl->leaf_start, L, p, lv, pl->grids, ext ? 1 : 0);   \
+        if (ext)                                                                                             \
+            k_p2m_crowded<PB><<<cwblocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, pl->leaf_start, n, L, p, lv, \
+                                                        pl->grids);                                          \
+        break;
             FMM_P2M(9) FMM_P2M(13) FMM_P2M(17) FMM_P2M(21) FMM_P2M(25) FMM_P2M(33) FMM_P2M(41)
 #undef FMM_P2M
             default: return -2;
         }
-        ++launches;
+        launches += ext ? 2 : 1;
     }
     cudaEventRecord(pl->ev[2], st);
     // Fork after the fine P2M: the near field (stream2) needs only the sort; the coarse levels'

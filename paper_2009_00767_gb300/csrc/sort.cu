@@ -177,17 +177,20 @@ constexpr int kLocalTopMax = 1024;
 template <bool kLocalTop>
 __global__ void k_scan2_down(uint32_t* __restrict__ in, int64_t m, const unsigned long long* __restrict__ sums,
                              uint32_t* __restrict__ leaf_start, uint32_t* __restrict__ bstart,
-                             uint2* __restrict__ map) {
+                             uint2* __restrict__ map, int* __restrict__ crowd_hint) {
     __shared__ unsigned long long wt[kScanThreads / 32 + 1];
     unsigned long long v[kScanItems];
     uint32_t nbk[kScanItems];
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    bool crowded = false;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         v[j] = (base + j < m) ? pop_blocks(in[base + j]) : 0ull;
         nbk[j] = (uint32_t)(v[j] >> 32);
+        crowded |= (uint32_t)v[j] > (uint32_t)FMM_LANE_MAX;
         if (base + j < m) in[base + j] = 0u;   // the populations start the next call at zero
     }
+    if (crowded && crowd_hint) *(volatile int*)crowd_hint = 1;
     block_exclusive_scan(v, wt);
     unsigned long long off;
     if (kLocalTop) {
@@ -289,12 +292,12 @@ int fmm_launch_sort(fmm_plan_s* pl, const double* xy, const double* q, bool with
         k_scan2_reduce<<<nb, kScanThreads, 0, st>>>(pl->counts, m, sums);
         if (nb <= kLocalTopMax) {
             k_scan2_down<true><<<nb, kScanThreads, 0, st>>>(pl->counts, m, sums, pl->leaf_start, pl->leaf_bstart,
-                                                            pl->blk_map);
+                                                            pl->blk_map, pl->crowd_hint_d);
             launches -= 1;
         } else {
             k_scan2_top<<<1, kScanThreads, 0, st>>>(sums, nb);
             k_scan2_down<false><<<nb, kScanThreads, 0, st>>>(pl->counts, m, sums, pl->leaf_start, pl->leaf_bstart,
-                                                             pl->blk_map);
+                                                             pl->blk_map, pl->crowd_hint_d);
         }
     }
     launches += 3;

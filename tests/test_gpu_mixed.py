@@ -131,6 +131,27 @@ def test_crowded_squares_split_over_warps(oracle_mod):
     check_parity(phi, ref, MIXED_TOL, f"clustered N=100000 levels=6 p=16 (max square {st['max_leaf']})")
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2"])
+def test_crowded_fine_moments_either_way(oracle_mod, precision):
+    """A plan's first call sums crowded squares' fine-level moments one warp per square; once a
+    call has seen a crowded square the next ones spread them over the grid (k_p2m_crowded, one
+    more launch).  Both must match the oracle."""
+    import torch
+    from paper_2009_00767_gb300 import binding
+    xy, q = inputs.gmm(60000, inputs.config_seed(2, 11), k=4, sigma_lo=0.01, sigma_hi=0.05)
+    ref = oracle_mod.shiftfree(xy, q, 7, 16)
+    txy, tq = torch.from_numpy(xy).cuda(), torch.from_numpy(q).cuda()
+    with binding.Plan(xy.shape[0], 7, 16, 5.0, precision) as plan:
+        phi1 = plan.potential(txy, tq).cpu().numpy()
+        st1 = plan.stats()
+        phi2 = plan.potential(txy, tq).cpu().numpy()
+        st2 = plan.stats()
+    assert st1["max_leaf"] > 128
+    assert st2["kernel_launches"] == st1["kernel_launches"] + 1
+    check_parity(phi1, ref, MIXED_TOL, f"{precision} crowded squares, one warp each")
+    check_parity(phi2, ref, MIXED_TOL, f"{precision} crowded squares, spread over the grid")
+
+
 @pytest.mark.parametrize("precision", ["fp32", "3xtf32", "bf16x2", "bf16x3"])
 def test_full_size_clustered_16m_sampled(oracle_mod, precision):
     """N = 2^24 in a mixture of 32 Gaussians (sigma log-uniform in [0.01, 0.3]), levels 10,
