@@ -152,6 +152,27 @@ def test_crowded_fine_moments_either_way(oracle_mod, precision):
     check_parity(phi2, ref, MIXED_TOL, f"{precision} crowded squares, spread over the grid")
 
 
+def test_plan_reused_across_block_counts(oracle_mod):
+    """One plan, systems of the same size whose squares split into different numbers of
+    near-field blocks (a clustered system, whose empty squares have none, then a uniform one, and
+    back): every call must rebuild its block map and cover all of them."""
+    import torch
+    from paper_2009_00767_gb300 import binding
+    n = 200000
+    xc, qc = inputs.gmm(n, inputs.config_seed(2, 21))
+    xu, qu = inputs.uniform(n, inputs.config_seed(2, 22))
+    ref_c = oracle_mod.shiftfree(xc, qc, 7, 12)
+    ref_u = oracle_mod.shiftfree(xu, qu, 7, 12)
+    with binding.Plan(n, 7, 12, 5.0, "bf16x2") as plan:
+        out = []
+        for xy, q in ((xc, qc), (xu, qu), (xu, qu), (xc, qc)):
+            out.append(plan.potential(torch.from_numpy(xy).cuda(), torch.from_numpy(q).cuda()).cpu().numpy())
+    check_parity(out[0], ref_c, MIXED_TOL, "clustered, fresh plan")
+    check_parity(out[1], ref_u, MIXED_TOL, "uniform after clustered")
+    check_parity(out[2], ref_u, MIXED_TOL, "uniform after uniform")
+    check_parity(out[3], ref_c, MIXED_TOL, "clustered after uniform")
+
+
 @pytest.mark.parametrize("precision", ["fp32", "3xtf32", "bf16x2", "bf16x3"])
 def test_full_size_clustered_16m_sampled(oracle_mod, precision):
     """N = 2^24 in a mixture of 32 Gaussians (sigma log-uniform in [0.01, 0.3]), levels 10,
