@@ -442,7 +442,9 @@ def run_ours(args):
     xy_h = torch.from_numpy(xy).pin_memory()
     q_h = torch.from_numpy(q).pin_memory()
     phi_h = [torch.empty(w["n"], dtype=torch.float64).pin_memory() for _ in range(2)]
-    e2e_steps = max(3, min(args.steps, 50))
+    # at least 100 calls (about 40 ms): the host clock's jitter and Python's call overhead average
+    # out, where a few calls of 0.4 ms each gave rates that moved by 20% between runs
+    e2e_steps = max(100, min(args.steps, 400))
     for _ in range(2):
         plan.potential_host(xy_h, q_h, phi_h[0])
     barrier()
@@ -458,7 +460,7 @@ def run_ours(args):
     barrier()
     e2e_sync_s = max_over_ranks((time.perf_counter() - te) / e2e_steps, dev)
     e2e = {"value": job_rate(w["n"], ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": w["n"] * 24,
-           "d2h_bytes_per_step": w["n"] * 8, "ms_per_step": e2e_s * 1e3,
+           "d2h_bytes_per_step": w["n"] * 8, "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
            "call": "fmm_potential_host_async per step (pinned host buffers), fmm_sync after the last",
            "one_call_at_a_time": {"value": job_rate(w["n"], ws, e2e_sync_s), "ms_per_step": e2e_sync_s * 1e3,
                                   "call": "fmm_potential_host (waits every step)"}}
