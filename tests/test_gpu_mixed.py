@@ -120,6 +120,17 @@ def test_tensor_core_modes_coarse_levels(oracle_mod, precision, tol, case):
     check_parity(phi, ref, tol, f"{precision} N={n} levels={lev} p={p} {fam}")
 
 
+@pytest.mark.parametrize("precision", ["3xtf32", "bf16x2", "bf16x3"])
+def test_tensor_core_widest_operators(oracle_mod, precision):
+    """p = 28 (K = N = 64 per offset): the widest operators, where the shared-memory plan has the
+    fewest stages (3xTF32: one operator stage and two window stages) and a CTA holds four tiles."""
+    from gpu_util import run_fmm
+    xy, q = inputs.gmm(50000, inputs.config_seed(0, 316))
+    phi, st = run_fmm(xy, q, 7, 28, precision=precision)
+    ref = oracle_mod.shiftfree(xy, q, 7, 28)
+    check_parity(phi, ref, MIXED_TOL, f"{precision} N=50000 levels=7 p=28 gmm")
+
+
 def test_crowded_squares_split_over_warps(oracle_mod):
     """Clustered charges (32 Gaussians, sigma down to 0.01) on a uniform tree: finest squares with
     thousands of particles, whose near field is split into blocks of 24 targets over many warps."""
