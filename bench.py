@@ -551,15 +551,10 @@ def batched_workload(nsys, seed=20094767):
     return ns, levels, np.concatenate(xys), np.concatenate(qs)
 
 
-def run_batched(binding, torch, dev, nsys, steps, warmup, precision):
-    """The batched form: one graph replay per step over all systems (launch shapes picked by the
-    library's autotuner), against a loop of single-system plans of the same precision over the same
-    systems; accuracy against the FP64 direct sum at sampled targets of sampled systems."""
-    ns, levels, xy, q = batched_workload(nsys)
-    total = int(ns.sum())
-    xy_d = torch.from_numpy(xy).to(dev)
-    q_d = torch.from_numpy(q).to(dev)
-    phi = torch.empty(total, dtype=torch.float64, device=dev)
+def _time_batch(binding, torch, ns, levels, xy_d, q_d, steps, warmup, precision):
+    """One batch over the systems (ns, levels), p = 16: autotuned, warmed up, then the median of
+    `steps` graph replays timed with CUDA events."""
+    phi = torch.empty(int(ns.sum()), dtype=torch.float64, device=xy_d.device)
     b = binding.Batch(ns, levels, 16, precision=precision)
     binding.fmm_batch_autotune_cached(b.handle, xy_d, q_d, phi, None)
     tuning = binding.fmm_batch_tuning(b.handle)
@@ -574,16 +569,21 @@ def run_batched(binding, torch, dev, nsys, steps, warmup, precision):
         e1.record()
         torch.cuda.synchronize()
         ms_steps.append(e0.elapsed_time(e1))
-    ms_batch = float(np.median(ms_steps))
     binding.fmm_batch_sync(b.handle)
     launches = binding.fmm_batch_launches(b.handle)
     b.close()
-    # accuracy: 8 systems spread over the size range, 256 sampled targets each
+    return float(np.median(ms_steps)), phi, tuning, launches
+
+
+def _batch_errors(binding, torch, ns, levels, xy_d, q_d, phi):
+    """Relative L2 error of 8 systems spread over the size range, 256 sampled targets each, against
+    the FP64 direct sum."""
     from paper_2009_00767_gb300 import inputs
+    dev = xy_d.device
     off = np.concatenate([[0], np.cumsum(ns)])
     order = np.argsort(ns)
     errs = []
-    for i in order[np.linspace(0, nsys - 1, 8).astype(int)]:
+    for i in order[np.linspace(0, len(ns) - 1, 8).astype(int)]:
         n_i = int(ns[i])
         idx = np.unique((inputs.u01(5150 + int(i), 0, min(256, n_i)) * n_i).astype(np.int64))
         idx_d = torch.from_numpy(idx).to(dev)
@@ -594,6 +594,20 @@ def run_batched(binding, torch, dev, nsys, steps, warmup, precision):
         got = phi[off[i]:off[i + 1]][idx_d]
         errs.append({"system": int(i), "n": n_i, "levels": int(levels[i]),
                      "rel_l2_err": float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))})
+    return errs
+
+
+def run_batched(binding, torch, dev, nsys, steps, warmup, precision):
+    """The batched form: one graph replay per step over all systems (launch shapes picked by the
+    library's autotuner), against a loop of single-system plans of the same precision over the same
+    systems; accuracy against the FP64 direct sum at sampled targets of sampled systems."""
+    ns, levels, xy, q = batched_workload(nsys)
+    total = int(ns.sum())
+    xy_d = torch.from_numpy(xy).to(dev)
+    q_d = torch.from_numpy(q).to(dev)
+    ms_batch, phi, tuning, launches = _time_batch(binding, torch, ns, levels, xy_d, q_d, steps, warmup, precision)
+    errs = _batch_errors(binding, torch, ns, levels, xy_d, q_d, phi)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # the uniform half alone, as its own batch: the particles/s of the same form on the family of
     # the single-system workload (the Gaussian-mixture half fills its leaves unevenly at ~16
     # particles per leaf on average, so its near field dominates the mixed batch)
@@ -601,22 +615,7 @@ def run_batched(binding, torch, dev, nsys, steps, warmup, precision):
     off = np.concatenate([[0], np.cumsum(ns)])
     sel = np.concatenate([np.arange(off[i], off[i + 1]) for i in uni])
     xu, qu = xy_d[torch.from_numpy(sel).to(dev)].contiguous(), q_d[torch.from_numpy(sel).to(dev)].contiguous()
-    phu = torch.empty(sel.shape[0], dtype=torch.float64, device=dev)
-    bu = binding.Batch(ns[uni], levels[uni], 16, precision=precision)
-    binding.fmm_batch_autotune_cached(bu.handle, xu, qu, phu, None)
-    for _ in range(warmup):
-        binding.fmm_batch_potential(bu.handle, xu, qu, phu)
-    torch.cuda.synchronize()
-    msu = []
-    for _ in range(steps):
-        e0.record()
-        binding.fmm_batch_potential(bu.handle, xu, qu, phu)
-        e1.record()
-        torch.cuda.synchronize()
-        msu.append(e0.elapsed_time(e1))
-    binding.fmm_batch_sync(bu.handle)
-    bu.close()
-    ms_uni = float(np.median(msu))
+    ms_uni, phu, _, _ = _time_batch(binding, torch, ns[uni], levels[uni], xu, qu, steps, warmup, precision)
     uniform_subset = {"systems": int(uni.shape[0]), "particles": int(sel.shape[0]), "ms_per_step": ms_uni,
                       "value": sel.shape[0] / (ms_uni * 1e-3), "unit": UNIT}
     del xu, qu, phu
