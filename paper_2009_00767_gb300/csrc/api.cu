@@ -89,7 +89,8 @@ void free_plan(fmm_plan_s* pl) {
     cudaSetDevice(pl->device);
     void* bufs[] = {pl->keys, pl->rank, pl->counts, pl->leaf_start, pl->block_sums, pl->leaf_bstart,
                     pl->blk_map, pl->sorted_key,
-                    pl->sorted64, pl->sorted32, pl->sorted_lo, pl->phi_far, pl->near_grad, pl->T64, pl->T32,
+                    pl->sorted64, pl->sorted32, pl->sorted_lo, pl->phi_far, pl->near_grad, pl->far_part,
+                    pl->T64, pl->T32,
                     pl->d_status,
                     pl->d_counters, pl->d_xy_stage[0], pl->d_q_stage[0], pl->d_phi_stage[0], pl->d_xy_stage[1],
                     pl->d_q_stage[1], pl->d_phi_stage[1]};
@@ -104,11 +105,12 @@ void free_plan(fmm_plan_s* pl) {
     if (pl->h_status) cudaFreeHost(pl->h_status);
     if (pl->h_counters) cudaFreeHost(pl->h_counters);
     if (pl->crowd_hint_h) cudaFreeHost(pl->crowd_hint_h);
-    for (int e = 0; e < 15; ++e)
+    for (int e = 0; e < fmm_plan_s::kEvents; ++e)
         if (pl->ev[e]) cudaEventDestroy(pl->ev[e]);
     if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
     if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     if (pl->ev_join3) cudaEventDestroy(pl->ev_join3);
+    if (pl->ev_a32) cudaEventDestroy(pl->ev_a32);
     if (pl->stream2) cudaStreamDestroy(pl->stream2);
     if (pl->stream3) cudaStreamDestroy(pl->stream3);
     if (pl->s_up) cudaStreamDestroy(pl->s_up);
@@ -249,7 +251,10 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->phi_far, sizeof(double) * n));
     // the field's gradient accumulator (near field in the mixed path, far field in the FP64 path)
     FMM_TRY(dev_alloc(pl, &pl->near_grad, sizeof(double2) * n));
-    if (precision != FMM_FP64) FMM_TRY(dev_alloc(pl, &pl->sorted_lo, sizeof(float2) * n));
+    if (precision != FMM_FP64) {
+        FMM_TRY(dev_alloc(pl, &pl->sorted_lo, sizeof(float2) * n));
+        FMM_TRY(dev_alloc(pl, &pl->far_part, sizeof(float2) * n));
+    }
     const size_t bcplx = precision == FMM_FP64 ? sizeof(double2) : sizeof(float2);
     for (int k = 2; k <= levels; ++k) {
         const size_t W = (size_t)fmm_grid_width(k);
@@ -310,7 +315,7 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
         FMM_TRY(dev_alloc(pl, &pl->d_q_stage[b], sizeof(double) * n));
         FMM_TRY(dev_alloc(pl, &pl->d_phi_stage[b], sizeof(double) * n));
     }
-    for (int e = 0; e < 15; ++e)
+    for (int e = 0; e < fmm_plan_s::kEvents; ++e)
         if (cudaEventCreate(&pl->ev[e]) != cudaSuccess) FMM_TRY(FMM_ERR_CUDA);
     if (precision != FMM_FP64) {
         // the mixed path's near field and coarse levels run on streams of the plan's own
@@ -319,6 +324,7 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
             cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_join3, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev_a32, cudaEventDisableTiming) != cudaSuccess ||
             cudaStreamCreateWithFlags(&pl->s_up, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&pl->s_down, cudaStreamNonBlocking) != cudaSuccess)
             FMM_TRY(FMM_ERR_CUDA);
@@ -463,7 +469,7 @@ fmm_status fmm_sync(fmm_plan_t plan) {
             plan->last.ms_m2l_coarse = (kb & 8) ? span(12, 13) : 0.0;
             plan->last.ms_p2m = plan->last.ms_p2m_fine + plan->last.ms_p2m_coarse;
             plan->last.ms_m2l = plan->last.ms_m2l_fine + plan->last.ms_m2l_coarse;
-            plan->last.ms_l2p = span(4, 5);
+            plan->last.ms_l2p = span(4, 5) + ((kb & 16) ? span(15, 16) : 0.0);
             plan->last.ms_p2p = plan->last.ms_p2p_kernel;
         }
         plan->ev_kernels = 0;

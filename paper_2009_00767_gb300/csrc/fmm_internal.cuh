@@ -105,6 +105,7 @@ struct fmm_plan_s {
     size_t a_bytes[FMM_MAX_LEVELS + 1];
     double* phi_far;                  // FP64 path: far field; mixed path: near-field accumulator per particle
     double2* near_grad;               // mixed path: near-field gradient accumulator (fmm_potential_field)
+    float2* far_part;                 // mixed path: float-float far field of the coarse levels per particle
 
     double2* T64;       // FP64 operators [49][p+1][p+1]
     float2* T32;        // FP32 operators [49][p1b][p1b], zero-padded, [d][0][0] = 0 (mixed SIMT M2L)
@@ -133,18 +134,22 @@ struct fmm_plan_s {
     cudaEvent_t ev_up_done, ev_l2p_done;     // a host call's uploads / compute are complete
     cudaEvent_t ev_down_done[2];             // the set's result was downloaded
 
-    // Mixed path: after the fine P2M the work forks three ways -- the near field on stream2, the
-    // coarse levels' chain (P2M, conversion, M2L of levels 2..5) on stream3, the fine levels' M2L
-    // on the plan's stream -- and joins back before L2P.
+    // Mixed path: after the sort (or, when the coarse M2L reaches a fine level, after the fine P2M)
+    // the work forks three ways -- the near field on stream2, the coarse levels' chain (P2M,
+    // conversion, M2L and L2P of levels 2..5) on stream3, the fine levels' P2M and M2L on the plan's
+    // stream -- and joins back before the fine levels' L2P.
     cudaStream_t stream2, stream3;
     cudaEvent_t ev_fork, ev_join, ev_join3;   // untimed fork / join events
+    cudaEvent_t ev_a32;   // stream3's FP32 moment grids are written (levels 2 .. l-3; from l = 9 on the
+                          // fine levels' M2L on the plan's stream reads some of them)
     // Timing events.  FP64 path: stage boundaries [0..5] (sort, P2M, M2L, L2P, P2P).  Mixed path:
     // [0] start, [1] sort done, [2] fine P2M done, [14] fine M2L start, [3] fine M2L done, [4] L2P
     // start (after the joins), [5] end, all on the plan's stream; [6, 7] the tensor-core M2L
     // kernel; [8, 9] the near-field kernel (stream2); [10, 11] the coarse P2M and its conversion,
-    // [12, 13] the coarse M2L (stream3).
-    cudaEvent_t ev[15];
-    int ev_kernels;       // bits: 1 [6, 7], 2 [8, 9], 4 [10, 11], 8 [12, 13] recorded this call
+    // [12, 13] the coarse M2L, [15, 16] the coarse levels' L2P (stream3).
+    static constexpr int kEvents = 17;
+    cudaEvent_t ev[kEvents];
+    int ev_kernels;       // bits: 1 [6, 7], 2 [8, 9], 4 [10, 11], 8 [12, 13], 16 [15, 16] recorded this call
     int serial;           // fmm_set_concurrency(plan, 1): every stage on the plan's stream
     int events_recorded;
     int launches;

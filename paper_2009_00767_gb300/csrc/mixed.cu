@@ -689,20 +689,25 @@ __device__ __forceinline__ float l2p_split_horner(const float2 (&b)[P1B], float2
     return v;
 }
 
+// Levels k_lo..k_hi.  far_out: the float-float sum of those levels is stored per particle and
+// nothing else (the coarse levels, on the third stream once their M2L is done); otherwise the sum
+// continues from far_in (if given), the near field is added and phi written.  Either way the
+// levels are added in the same order as in one pass over 2..levels, so the result is the same.
 template <int P1B, bool kExact>
 __global__ void __launch_bounds__(128)
-k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int p,
-            MixedLevels lv, FmmLevelPtrs g, const double* __restrict__ near, const unsigned int* __restrict__ status,
+k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int k_lo,
+            int k_hi, int p, MixedLevels lv, FmmLevelPtrs g, const float2* __restrict__ far_in,
+            float2* __restrict__ far_out, const double* __restrict__ near, const unsigned int* __restrict__ status,
             double* __restrict__ phi) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double nd = near[i];
+    const double nd = far_out ? 0.0 : near[i];
     const float4 P = sp[i];
     const uint32_t key = skey[i];
     const uint32_t ix = fmm_compact2(key), iy = fmm_compact2(key >> 1);
     const int p1 = p + 1;
-    float2 far = make_float2(0.f, 0.f);
-    for (int k = 2; k <= levels; ++k) {
+    float2 far = far_in ? far_in[i] : make_float2(0.f, 0.f);
+    for (int k = k_lo; k <= k_hi; ++k) {
         const int sh = levels - k;
         const float2 w = level_w(P.x, P.y, ix, iy, sh, lv.inv_s[k]);
         const size_t t = (size_t)(iy >> sh) * (1u << k) + (ix >> sh);
@@ -714,6 +719,10 @@ k_l2p_mixed(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, in
         // O(z) = sum_{m>=0} b'_{2m+1} z^m: two independent Horner chains of half the length
         const float v = l2p_split_horner<P1B>(b, w);
         far = ff_add(far, ff_add_f(b[0], v));         // b[0] = Re b'_0 as (hi, lo)
+    }
+    if (far_out) {
+        far_out[i] = far;
+        return;
     }
     if (*(volatile const unsigned int*)status != 0u) return;   // inputs failed the device checks
     phi[__float_as_int(P.w)] = p2p_phi(far, fmm_d2ff_bits(nd));
@@ -841,15 +850,17 @@ k_p2p_field(const float4* __restrict__ sp, const uint32_t* __restrict__ leaf_sta
 }  // namespace
 
 // The near field on the plan's second stream: forked from the plan's stream at this point of its
-// work (any point after the sort will do), joined back before L2P.
-int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv, bool with_field) {
+// work (record_fork) or at the fork event recorded earlier (any point after the sort will do),
+// joined back before L2P.
+int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv, bool with_field, bool record_fork) {
     cudaStream_t st = pl->stream, s2 = pl->serial ? pl->stream : pl->stream2;
     // the near-field accumulator starts at zero: cleared on stream2 as soon as the call starts (the
     // start event follows the previous call's L2P, its last reader), beside the sort and fine P2M
     if (s2 != st && cudaStreamWaitEvent(s2, pl->ev[0], 0) != cudaSuccess) return -1;
     if (cudaMemsetAsync(pl->phi_far, 0, sizeof(double) * (size_t)pl->n, s2) != cudaSuccess) return -1;
     if (with_field && cudaMemsetAsync(pl->near_grad, 0, sizeof(double2) * (size_t)pl->n, s2) != cudaSuccess) return -1;
-    if (cudaEventRecord(pl->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(s2, pl->ev_fork, 0) != cudaSuccess)
+    if ((record_fork && cudaEventRecord(pl->ev_fork, st) != cudaSuccess) ||
+        cudaStreamWaitEvent(s2, pl->ev_fork, 0) != cudaSuccess)
         return -1;
     const int L = pl->levels;
     const int64_t n = pl->n;
@@ -886,6 +897,30 @@ void launch_m2l_coarse(const M2LWarpArgs& a, const MixedLevels& lv, int blocks, 
 
 }  // namespace
 
+// L2P of levels k_lo..k_hi on stream s (k_l2p_mixed); -1 if the coefficient bucket is unknown
+static int launch_l2p(fmm_plan_s* pl, const MixedLevels& lv, int k_lo, int k_hi, const float2* far_in, float2* far_out,
+               double* phi, cudaStream_t s) {
+    const int64_t n = pl->n;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    const int p = pl->p, p1 = p + 1;
+    switch (pl->p1b) {
+#define FMM_L2P(PB)                                                                                          \
+    case PB:                                                                                                 \
+        if (p1 == PB)                                                                                        \
+            k_l2p_mixed<PB, true><<<blocks, 128, 0, s>>>(pl->sorted32, pl->sorted_key, n, pl->levels, k_lo, k_hi, \
+                                                         p, lv, pl->grids, far_in, far_out, pl->phi_far,     \
+                                                         pl->d_status, phi);                                 \
+        else                                                                                                 \
+            k_l2p_mixed<PB, false><<<blocks, 128, 0, s>>>(pl->sorted32, pl->sorted_key, n, pl->levels, k_lo, k_hi, \
+                                                          p, lv, pl->grids, far_in, far_out, pl->phi_far,    \
+                                                          pl->d_status, phi);                                \
+        return 0;
+        FMM_L2P(9) FMM_L2P(13) FMM_L2P(17) FMM_L2P(21) FMM_L2P(25) FMM_L2P(33) FMM_L2P(41)
+#undef FMM_L2P
+        default: return -1;
+    }
+}
+
 int fmm_m2l_bucket(int p1) {
     const int b[] = {9, 13, 17, 21, 25, 33, 41};
     for (int v : b)
@@ -910,6 +945,15 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field) {
     const int kf = L - (kFineLevels - 1) > 2 ? L - (kFineLevels - 1) : 2;
     const int kc_max = kf - 1;   // the coarse FP64 grids are zero here (k_prep_a32 re-zeroes them)
     const int kw = L < kM2LWarpMaxLevel ? L : kM2LWarpMaxLevel;   // levels 2..kw: the coarse M2L kernel
+    // The near field needs only the sort; the coarse levels' chain needs the fine P2M only when its
+    // M2L reaches a fine level (kf <= kw).  Otherwise both fork right after the sort and run beside
+    // the fine P2M, which is still launched first, so that its blocks (the head of the longest
+    // chain: fine P2M, tensor-core prep, tensor-core M2L) reach the SMs before the near field's.
+    const bool early_fork = L >= 2 && kf > kw;
+    // Potential calls with levels above kw evaluate the coarse levels' locals on the third stream as
+    // soon as their M2L is done; the final L2P adds the fine levels, the near field and writes phi.
+    const bool split_l2p = field == nullptr && L > kw && kw >= 2;
+    if (early_fork && cudaEventRecord(pl->ev_fork, st) != cudaSuccess) return -1;
     if (L >= 2) {
         // crowded squares (a previous call's scan found a finest square above kLaneMax particles):
         // their fine-level coefficients come from k_p2m_crowded, spread over the grid; the hint is
@@ -933,13 +977,16 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field) {
         launches += ext ? 2 : 1;
     }
     cudaEventRecord(pl->ev[2], st);
-    // Fork after the fine P2M: the near field (stream2) needs only the sort; the coarse levels'
-    // chain (stream3) needs the sort and, for the coarse M2L, the fine levels' moments of levels
-    // up to 5; the fine levels' M2L stays here.  All three join before L2P.  (With
-    // fmm_set_concurrency(plan, 1) they run one after the other on the plan's stream.)
-    const int r = fmm_launch_p2p_concurrent(pl, lv, field != nullptr);   // records ev_fork on the plan's stream
-    if (r < 0) return -1;
-    launches += r;
+    // Otherwise the fork follows the fine P2M: the near field (stream2) on the sort, the coarse
+    // levels' chain (stream3) on the sort and the fine moments of levels up to kw; the fine levels'
+    // M2L stays here.  All three join before L2P.  (With fmm_set_concurrency(plan, 1)
+    // they run one after the other on the plan's stream.)
+    {
+        // records ev_fork on the plan's stream here, unless the fork came after the sort
+        const int r = fmm_launch_p2p_concurrent(pl, lv, field != nullptr, !early_fork);
+        if (r < 0) return -1;
+        launches += r;
+    }
     if (L >= 2) {
         if (cudaStreamWaitEvent(s3, pl->ev_fork, 0) != cudaSuccess) return -1;
         cudaEventRecord(pl->ev[10], s3);
@@ -967,6 +1014,7 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field) {
             pa.p1 = p1;
             k_prep_a32<<<(unsigned)((acc + 255) / 256), 256, 0, s3>>>(pa);
             launches += 2;
+            if (kc_max > kw && cudaEventRecord(pl->ev_a32, s3) != cudaSuccess) return -1;
         }
         cudaEventRecord(pl->ev[11], s3);
         cudaEventRecord(pl->ev[12], s3);
@@ -996,9 +1044,19 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field) {
         ++launches;
         cudaEventRecord(pl->ev[13], s3);
         pl->ev_kernels |= 4 | 8;
+        if (split_l2p) {
+            // the coarse levels' L2P, beside the near field and the fine levels' M2L
+            cudaEventRecord(pl->ev[15], s3);
+            if (launch_l2p(pl, lv, 2, kw, nullptr, pl->far_part, nullptr, s3) < 0) return -2;
+            cudaEventRecord(pl->ev[16], s3);
+            pl->ev_kernels |= 16;
+            ++launches;
+        }
         if (cudaEventRecord(pl->ev_join3, s3) != cudaSuccess) return -1;
 
-        // finer levels on the plan's stream: one thread per target, or the tensor cores
+        // finer levels on the plan's stream: one thread per target, or the tensor cores.  Their
+        // moments of levels kw+1 .. kc_max (l >= 9) come from the third stream's coarse P2M.
+        if (kc_max > kw && s3 != st && cudaStreamWaitEvent(st, pl->ev_a32, 0) != cudaSuccess) return -1;
         cudaEventRecord(pl->ev[14], st);
         M2LMixedArgs a;
         a.g = pl->grids;
@@ -1053,21 +1111,9 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field) {
         }
         ++launches;
     } else {
-        const unsigned blocks = (unsigned)((n + 127) / 128);
-        switch (pl->p1b) {
-#define FMM_L2P(PB)                                                                                          \
-    case PB:                                                                                                 \
-        if (p1 == PB)                                                                                        \
-            k_l2p_mixed<PB, true><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids,    \
-                                                          near, pl->d_status, phi);                          \
-        else                                                                                                 \
-            k_l2p_mixed<PB, false><<<blocks, 128, 0, st>>>(pl->sorted32, pl->sorted_key, n, L, p, lv, pl->grids,   \
-                                                           near, pl->d_status, phi);                         \
-        break;
-            FMM_L2P(9) FMM_L2P(13) FMM_L2P(17) FMM_L2P(21) FMM_L2P(25) FMM_L2P(33) FMM_L2P(41)
-#undef FMM_L2P
-            default: return -2;
-        }
+        if (split_l2p ? launch_l2p(pl, lv, kw + 1, L, pl->far_part, nullptr, phi, st) < 0
+                      : launch_l2p(pl, lv, 2, L, nullptr, nullptr, phi, st) < 0)
+            return -2;
         ++launches;
     }
     cudaEventRecord(pl->ev[5], st);

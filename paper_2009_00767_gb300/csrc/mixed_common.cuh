@@ -93,5 +93,5 @@ int fmm_launch_m2l_tc(fmm_plan_s* pl, const MixedLevels& lv);
 // the FP64 M2L operators T[49][p+1][p+1] (api.cu), real and imaginary parts
 void fmm_build_operators_f64(int p, std::vector<double>& re, std::vector<double>& im);
 // the near field on the plan's second stream (mixed.cu); kernels launched, or -1
-int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv, bool with_field);
+int fmm_launch_p2p_concurrent(fmm_plan_s* pl, const MixedLevels& lv, bool with_field, bool record_fork);
 int fmm_tc_kmin();

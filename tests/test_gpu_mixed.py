@@ -203,6 +203,21 @@ def test_full_size_clustered_16m_sampled(oracle_mod, precision):
                                       f"(max square {st['max_leaf']}, {st['ms_total']:.2f} ms)")
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2", "bf16x3"])
+@pytest.mark.parametrize("lev,p", [(9, 12), (10, 8)])
+def test_deep_trees_on_a_fresh_plan(oracle_mod, precision, lev, p):
+    """Levels 9 and 10: the third stream's coarse P2M forms the moments of levels 2 .. l-3, and
+    the fine levels' M2L on the plan's stream (from level 6) reads those of levels 6 .. l-3, so it
+    has to wait for them.  A fresh plan's grids hold no earlier call's moments that could hide a
+    missing wait; the first call is compared with the oracle element by element."""
+    from gpu_util import run_fmm
+    n = 1 << 16
+    xy, q = inputs.uniform(n, inputs.config_seed(0, 777))
+    phi, _ = run_fmm(xy, q, lev, p, precision=precision)
+    ref = oracle_mod.shiftfree(xy, q, lev, p)
+    check_parity(phi, ref, MIXED_TOL, f"{precision} N={n} levels={lev} p={p} uniform, first call")
+
+
 def test_tensor_core_wait_timeout_is_reported_and_recoverable(oracle_mod):
     """The bounded-wait error path of the tensor-core M2L: with its copy producers switched off
     (fmm_inject_timeout), the first mbarrier wait runs out with nothing in flight, the kernel stores
