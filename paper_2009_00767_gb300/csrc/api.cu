@@ -241,7 +241,10 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     FMM_TRY(dev_alloc(pl, &pl->block_sums, sizeof(unsigned long long) * (pl->scan_blocks + 1)));
     if (precision != FMM_FP64) {
         FMM_TRY(dev_alloc(pl, &pl->leaf_bstart, sizeof(uint32_t) * (m + 1)));
-        FMM_TRY(dev_alloc(pl, &pl->blk_map, sizeof(uint2) * ((size_t)m + (size_t)n / FMM_P2P_BLOCK + 1)));
+        // near-field blocks: at most one partial block per square; the near-field grid has four warps
+        // a CTA and every warp reads its entry, so the map is rounded up to four entries
+        const size_t nblk = ((size_t)m + (size_t)n / FMM_P2P_BLOCK + 1 + 3) & ~(size_t)3;
+        FMM_TRY(dev_alloc(pl, &pl->blk_map, sizeof(uint2) * nblk));
     }
     FMM_TRY(dev_alloc(pl, &pl->sorted_key, sizeof(uint32_t) * n));
     if (precision == FMM_FP64)
