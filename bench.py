@@ -194,19 +194,29 @@ def roofline_for(stage, stats, ms, w, peaks, sm_clock_mhz, precision, traffic):
                    f"{pairs} ordered pairs, one lg2 each (the survey's unit; the symmetric kernel evaluates the "
                    f"forward-neighbour pairs once for both sides, about 0.56 lg2 per ordered pair)",
                    peak_basis=f"MUFU lg2: {N_SMS} SMs x {MUFU_PER_SM}/clk x {sm_clock_mhz:.0f} MHz")
-    if stage in ("p2m_fine", "p2m_coarse", "l2p", "p2m") and precision != "fp64":
+    if stage == "p2m_coarse" and precision != "fp64":
+        # the upward pass: per parent of levels 2 .. l-3, coefficient m sums (m + 1) complex
+        # multiply-adds (8 flop) for each of its four children
+        parents = sum(4 ** k for k in range(2, L - 2))
+        if parents == 0:
+            return None
+        flops = parents * 4 * 8 * sum(m + 1 for m in range(1, p1))
+        nbytes = sum((4 ** (k + 1) + 4 ** k) * p1 * 8 for k in range(2, L - 2))
+        ach_b = nbytes / sec / 1e9
+        return out("k_m2m_f32", "alu", flops / sec / 1e12, fma_peak, "TFLOP/s",
+                   f"{flops:.4g} flop = {parents} parents x 4 children x sum_m (m+1) complex MACs of 8 flop "
+                   f"(levels 2..{L - 3})", peak_basis=fma_basis,
+                   hbm={"achieved": ach_b, "peak": hbm, "unit": "GB/s", "frac": ach_b / hbm, "bytes": nbytes,
+                        "what": "children's FP32 moment grids in, parents' out"})
+    if stage in ("p2m_fine", "l2p", "p2m") and precision != "fp64":
         if stage == "p2m_fine":
             lev = range(max(2, L - 2), L + 1)
             nbytes = 16 * n + grid_bytes(L - 2, L, p1 * 8)
             what = "16 B particle in, FP32 moment grids out"
-        elif stage == "p2m_coarse":
-            lev = range(2, L - 2)
-            nbytes = 20 * n + grid_bytes(2, L - 3, p1 * 24)
-            what = "16 B particle + 4 B key in, FP64 + FP32 moment grids"
         elif stage == "l2p":
             lev = range(2, L + 1)
-            nbytes = 44 * n + grid_bytes(2, L, p1 * 8)
-            what = "16 B particle + 4 B key + 8 B near in, 8 B phi + 8 B near reset out, local grids in"
+            nbytes = 36 * n + grid_bytes(2, L, p1 * 8)
+            what = "16 B particle + 4 B key + 8 B near in, 8 B phi out, local grids in"
         else:
             lev = range(2, L + 1)
             nbytes = 20 * n
@@ -411,9 +421,9 @@ def run_ours(args):
         cands = {k: alone[k] for k in KERNELS_ALONE if alone[k] > 0}
     else:
         cands = {k: stage_avg[k] for k in ("sort", "p2m", "m2l", "l2p", "p2p")}
-    # the dominant kernel: the longest single kernel timed alone (the sort, the coarse P2M and the
-    # fine M2L stage are several kernels each)
-    singles = [k for k in ("p2m_fine", "m2l_coarse", "m2l_tc", "p2p_kernel", "l2p") if k in cands]
+    # the dominant kernel: the longest single kernel timed alone (the sort, the upward pass, the fine
+    # M2L stage and the L2P of the coarse and the fine levels are several kernels each)
+    singles = [k for k in ("p2m_fine", "m2l_coarse", "m2l_tc", "p2p_kernel") if k in cands]
     dom = max(singles or [k for k in cands if k != "sort"], key=cands.get)
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     in_step = dict(stage_avg, m2l_tc=kern_avg["m2l_tc"], p2p_kernel=kern_avg["p2p_kernel"], l2p=stage_avg["l2p"])

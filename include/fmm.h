@@ -98,12 +98,12 @@ typedef struct {
     uint64_t workspace_bytes;  /* device memory the plan owns */
     double ms_m2l_tc;          /* the tensor-core M2L kernel alone (0 when none ran) */
     double ms_p2p_kernel;      /* the mixed path's near-field kernel alone (0 when none ran) */
-    /* Mixed path: after the fine levels' P2M the near field, the coarse levels' chain (P2M of
-     * levels 2..levels-3, its FP32 conversion, M2L of levels 2..5) and the fine levels' M2L run
-     * on three streams at once, so ms_p2m and ms_m2l above are sums of these spans and the
-     * stages overlap in time.  FP64 path: ms_m2l_fine = ms_m2l, the others 0. */
+    /* Mixed path: the near field (from the sort on), the coarse levels' chain (from the fine P2M
+     * on: upward pass to levels levels-3 .. 2, M2L and L2P of levels 2..5) and the fine levels'
+     * P2M and M2L run on three streams at once, so ms_p2m, ms_m2l and ms_l2p above are sums of
+     * these spans and the stages overlap in time.  FP64 path: ms_m2l_fine = ms_m2l, the others 0. */
     double ms_p2m_fine;        /* P2M of the finest three levels */
-    double ms_p2m_coarse;      /* P2M of the coarser levels and their FP32 conversion */
+    double ms_p2m_coarse;      /* the coarser levels' moments by the upward pass (M2M) */
     double ms_m2l_fine;        /* M2L of levels 6 and finer (tensor-core prep + kernel, or FP32) */
     double ms_m2l_coarse;      /* M2L of levels 2..5 on the CUDA cores */
 } fmm_stats;

@@ -90,7 +90,7 @@ void free_plan(fmm_plan_s* pl) {
     void* bufs[] = {pl->keys, pl->rank, pl->counts, pl->leaf_start, pl->block_sums, pl->leaf_bstart,
                     pl->blk_map, pl->sorted_key,
                     pl->sorted64, pl->sorted32, pl->sorted_lo, pl->phi_far, pl->near_grad, pl->far_part,
-                    pl->T64, pl->T32,
+                    pl->T64, pl->T32, pl->U32,
                     pl->d_status,
                     pl->d_counters, pl->d_xy_stage[0], pl->d_q_stage[0], pl->d_phi_stage[0], pl->d_xy_stage[1],
                     pl->d_q_stage[1], pl->d_phi_stage[1]};
@@ -136,12 +136,10 @@ struct DeviceGuard {
     }
 };
 
-// the mixed path's accumulators (square populations, coarse FP64 moment grids) back to zero
+// the mixed path's accumulator (the square populations) back to zero
 fmm_status reset_accumulators(fmm_plan_s* pl, cudaStream_t st) {
     const size_t m = (size_t)1 << (2 * pl->levels);
     if (cudaMemsetAsync(pl->counts, 0, sizeof(uint32_t) * m, st) != cudaSuccess) return FMM_ERR_CUDA;
-    for (int k = 2; k <= pl->levels; ++k)
-        if (cudaMemsetAsync(pl->grids.A[k], 0, pl->a_bytes[k], st) != cudaSuccess) return FMM_ERR_CUDA;
     pl->clean = 1;
     return FMM_OK;
 }
@@ -262,7 +260,8 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     for (int k = 2; k <= levels; ++k) {
         const size_t W = (size_t)fmm_grid_width(k);
         pl->a_bytes[k] = W * W * p1 * sizeof(double2);
-        FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.A[k]), pl->a_bytes[k]));
+        if (precision == FMM_FP64)   // the mixed path's moments live in the FP32 grids only
+            FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.A[k]), pl->a_bytes[k]));
         FMM_TRY(dev_alloc(pl, reinterpret_cast<char**>(&pl->grids.B[k]), ((size_t)1 << (2 * k)) * p1 * bcplx));
         if (precision != FMM_FP64) {
             // the 3-cell halo of the FP32 grid stays zero for the plan's lifetime
@@ -300,6 +299,26 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
         FMM_TRY(dev_alloc(pl, &pl->T32, sizeof(float2) * T32.size()));
         if (cudaMemcpy(pl->T32, T32.data(), sizeof(float2) * T32.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             FMM_TRY(FMM_ERR_CUDA);
+        // the upward pass's translations, one per child position c = cx + 2 cy: a child's moments
+        // about its centre re-expanded about its parent's, M_m(parent) += sum_{j <= m} U_c[m][j] M_j
+        // with U_c[m][j] = C(m, j) 2^-j d_c^(m-j), d_c = ((cx - 1/2) / 2, (cy - 1/2) / 2): w = w'/2 + d_c
+        // between the parent's and the child's scaled offsets (FP64, rounded once to FP32); stored
+        // [c][j][m], so that the threads over m read one j together
+        std::vector<float2> U((size_t)4 * pb * pb, make_float2(0.f, 0.f));
+        for (int c = 0; c < 4; ++c) {
+            const cd d(((c & 1) - 0.5) * 0.5, ((c >> 1) - 0.5) * 0.5);
+            for (int m = 0; m < p1; ++m) {
+                double binom = 1.0;   // C(m, j)
+                for (int j = 0; j <= m; ++j) {
+                    const cd v = binom * std::ldexp(1.0, -j) * std::pow(d, m - j);
+                    U[((size_t)c * pb + j) * pb + m] = make_float2((float)v.real(), (float)v.imag());
+                    binom = binom * (double)(m - j) / (double)(j + 1);
+                }
+            }
+        }
+        FMM_TRY(dev_alloc(pl, &pl->U32, sizeof(float2) * U.size()));
+        if (cudaMemcpy(pl->U32, U.data(), sizeof(float2) * U.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            FMM_TRY(FMM_ERR_CUDA);
     }
     FMM_TRY(dev_alloc(pl, &pl->d_status, sizeof(unsigned int)));
     FMM_TRY(dev_alloc(pl, &pl->d_counters, 2 * FMM_COUNTER_SLOTS * sizeof(unsigned long long)));
@@ -323,13 +342,20 @@ fmm_status fmm_plan(fmm_plan_t* out, int64_t n, int levels, int p, double box, i
     if (precision != FMM_FP64) {
         // the mixed path's near field and coarse levels run on streams of the plan's own
         if (cudaStreamCreateWithFlags(&pl->stream2, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&pl->stream3, cudaStreamNonBlocking) != cudaSuccess ||
+
             cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_join3, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&pl->ev_a32, cudaEventDisableTiming) != cudaSuccess ||
             cudaStreamCreateWithFlags(&pl->s_up, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&pl->s_down, cudaStreamNonBlocking) != cudaSuccess)
+            FMM_TRY(FMM_ERR_CUDA);
+        // The coarse levels' chain (upward pass, coarse M2L and L2P) is a string of small launches
+        // behind the fine P2M; at the device's highest priority its blocks go first whenever the
+        // near field's blocks leave an SM, instead of after all of them.
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&pl->stream3, cudaStreamNonBlocking, greatest) != cudaSuccess)
             FMM_TRY(FMM_ERR_CUDA);
         cudaEvent_t* evs[] = {&pl->ev_sorted, &pl->ev_stage_free[0], &pl->ev_stage_free[1], &pl->ev_up_done,
                               &pl->ev_l2p_done, &pl->ev_down_done[0], &pl->ev_down_done[1]};

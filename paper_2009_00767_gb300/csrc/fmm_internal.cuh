@@ -10,7 +10,8 @@
 //   A[k]  (k = 2..levels)    multipole moments of level k on a (2^k + 6)^2 grid with a 3-square
 //                            zero halo, row-major, p+1 complex coefficients per square
 //   B[k]                     local coefficients of level k, (2^k)^2 row-major, p+1 complex each
-//   A32[k]                   (mixed) FP32 copy of A[k]; slot 0 holds M_0 as a float-float pair
+//   A32[k]                   (mixed) FP32 moments of level k, same layout (the mixed path has no
+//                            FP64 A[k]); slot 0 holds M_0 as a float-float pair
 //   (mixed) B[k] slot 0 holds Re b'_0 as a float-float pair
 //   phi_far[n]               FP64 path: far field summed over levels, box-sorted order; mixed
 //                            path: the near field as float-float pairs (log2 r^2 units)
@@ -73,7 +74,7 @@ __device__ __forceinline__ float2 fmm_d2ff_bits(double d) {
 }
 
 struct FmmLevelPtrs {
-    void* A[FMM_MAX_LEVELS + 1];    // FP64 moments (both paths), double2 [cell][p+1]
+    void* A[FMM_MAX_LEVELS + 1];    // FP64 moments (FP64 path), double2 [cell][p+1]
     void* B[FMM_MAX_LEVELS + 1];    // local coefficients: double2 (FP64 path) or float2 (mixed)
     void* A32[FMM_MAX_LEVELS + 1];  // mixed path: float2 copy of A, coefficient 0 as (hi, lo) of M_0
 };
@@ -95,8 +96,8 @@ struct fmm_plan_s {
     int scan_blocks;
     uint32_t* leaf_bstart;       // near-field target blocks: exclusive scan over the squares, 4^levels + 1
     uint2* blk_map;              // near-field block -> (square, block inside it), mixed path
-    int clean;                   // mixed path: counts and the coarse FP64 moment grids are zero (each
-                                 // call's kernels leave them so; a call that failed to enqueue does not)
+    int clean;                   // mixed path: the square populations are zero (each call's scan
+                                 // leaves them so; a call that failed to enqueue does not)
     uint32_t* sorted_key;
     fmm_p64* sorted64;
     float4* sorted32;
@@ -109,6 +110,7 @@ struct fmm_plan_s {
 
     double2* T64;       // FP64 operators [49][p+1][p+1]
     float2* T32;        // FP32 operators [49][p1b][p1b], zero-padded, [d][0][0] = 0 (mixed SIMT M2L)
+    float2* U32;        // mixed path: upward-pass translations [child position][j][m] (p1b each), zero-padded
     int p1b;            // padded coefficient count of the FP32 M2L kernel instance
     FmmTc* tc;          // tensor-core M2L state (TF32 modes), or null
 

@@ -1,16 +1,16 @@
 // mixed.cu -- the mixed-precision path: FP32 particle stages and FP32 M2L on the CUDA cores,
 // with float-float (two FP32 words) wherever magnitudes are large.  GB300's FP64 pipe is far
 // narrower than its FP32 pipe, so no FP64 arithmetic runs inside the hot loops: FP64 appears
-// only in the atomic moment sums (executed in L2), in the one-off conversion of each moment
-// cell, and in the final phi written for the caller.
+// only in the near field's atomic sums (executed in L2) and in the final phi written for the
+// caller.
 //
 // Scaled form as in fp64.cu (w = (z - c) / s, power-sum moments M_m = sum q w^m):
-//   P2M  every level straight from the particles (U-bar of Sec. 2.2.1): w in FP32 from the
-//        particle's offset to its finest-square centre (an exact dyadic square offset plus an
-//        FP32 product), q w^m in FP32, warp-segmented FP32 sums of at most 32 terms, then FP64
-//        atomics into the level's grid.
-//   prep each moment cell once to FP32; the total charge M_0 (real) is kept as a float-float
-//        pair (hi, lo) in the slot of coefficient 0.
+//   P2M  the finest three levels straight from the particles (U-bar-1 of Sec. 2.2.1): w in FP32
+//        from the particle's offset to its finest-square centre (an exact dyadic square offset
+//        plus an FP32 product), q w^m in FP32, register and shuffle sums; the total charge M_0
+//        (real) is kept as a float-float pair (hi, lo) in the slot of coefficient 0.
+//   M2M  the coarser levels by the upward pass (U-bar-2): each parent the sum of its four
+//        children's moments re-expanded about its centre (exact for truncated expansions).
 //   M2L  (D-bar-1) per target: b'_l = sum_d sum_k T_d[k][l] M[t+d][k] in FP32 (k, l = 0..p),
 //        except the monopole-log term sum_d M_0 (log|w0| + ln s) of b'_0, summed in
 //        float-float; Re b'_0 is stored as a float-float pair in the slot of coefficient 0.
@@ -26,7 +26,7 @@ namespace {
 constexpr int kM2LThreads = 128;
 
 // -------------------------------------------------------------------------------- P2M
-// Every level straight from the particles (U-bar of Sec. 2.2.1).  Squares of a level are
+// The fine levels straight from the particles (U-bar-1 of Sec. 2.2.1).  Squares of a level are
 // contiguous Morton ranges of the sorted particles, so the sums need no global sort of their own.
 //
 // Fine levels (the finest three, l - 2 .. l): two lanes per finest square, 16 consecutive squares
@@ -37,9 +37,7 @@ constexpr int kM2LThreads = 128;
 // group with a share of the coefficients to store: no atomics, coalesced stores.  Squares above
 // kLaneMax particles are summed by the whole warp and added by the owning group before the store.
 //
-// Coarse levels (2 .. l - 3): each warp walks kCoarseChunk consecutive particles; lanes add their
-// particles' terms in registers while the square stays the same and flush (a column sum over the
-// warp's lanes in shared memory, then FP64 atomics into the level's grid) when it changes.
+// Coarse levels (2 .. l - 3): the upward pass from the fine levels' moments (k_m2m_f32).
 constexpr int kFineLevels = 3;
 constexpr int kLaneMax = FMM_LANE_MAX;
 constexpr int kCoarseChunk = 256;
@@ -331,131 +329,92 @@ k_p2m_crowded(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, 
     }
 }
 
+// Upward pass (U-bar-2 of Sec. 2.2.1) for the coarse levels: the parent's moments are the sum of
+// its four children's, each re-expanded about the parent's centre.  With w = (z - c) / s_k per
+// level, a child's w' relates to its parent's as w = w' / 2 + d_c, so
+//     M_m(parent) = sum_c sum_{j <= m} U_c[m][j] M_j(child c),   U_c[m][j] = C(m, j) 2^-j d_c^(m-j),
+// a finite sum, exact for the truncated expansions (the same moments the particles give directly).
+// U comes from the plan ([c][j][m]: FP64 build, one FP32 rounding, zero above the diagonal and
+// past p).  Two
+// parents a CTA, one thread per coefficient m; the total charge (slot 0, a float-float pair) is
+// the children's float-float sum.
+constexpr int kM2MThreads = 64;   // per parent: coefficients 0 .. P1B - 1 (P1B <= 41)
+
 template <int P1B>
-__global__ void __launch_bounds__(128)
-k_p2m_coarse(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, int64_t n, int levels, int kc_max,
-             int p, MixedLevels lv, FmmLevelPtrs g) {
-    __shared__ float red[4][32][2 * P1B + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = ((int64_t)blockIdx.x * 4 + warp) * kCoarseChunk;
-    if (base >= n) return;
-    const int p1 = p + 1, ncol = 2 * p1;
-    float* row = red[warp][lane];
-    for (int k = 2; k <= kc_max; ++k) {
-        const int sh = levels - k;
-        const int W = fmm_grid_width(k);
-        double* A = reinterpret_cast<double*>(g.A[k]);
-        float2 acc[P1B];
+__global__ void __launch_bounds__(2 * kM2MThreads)
+k_m2m_f32(const float2* __restrict__ child, float2* __restrict__ parent, const float2* __restrict__ U, int k,
+          int p1) {
+    static_assert(P1B <= kM2MThreads, "one thread per coefficient");
+    // U is staged in shared memory, all four children's at once where they fit (one round trip to
+    // L2 instead of a chain of dependent loads per thread), else one child's at a time
+    constexpr int UC = 4 * P1B * P1B * (int)sizeof(float2) <= 40 * 1024 ? 4 : 1;
+    __shared__ float2 mom[2][4][P1B];   // the children's moments, slot 0 = M_0 as (hi, lo)
+    __shared__ float2 us[UC * P1B * P1B];
+    const int half = threadIdx.x / kM2MThreads, m = threadIdx.x % kM2MThreads;
+    const uint32_t side = 1u << k;
+    const uint32_t par = blockIdx.x * 2u + (uint32_t)half;   // row-major parent index
+    const bool live = par < side * side;
+    const uint32_t px = par % side, py = par / side;
+    const int Wc = fmm_grid_width(k + 1), Wp = fmm_grid_width(k);
+    if (m < P1B) {
 #pragma unroll
-        for (int m = 0; m < P1B; ++m) acc[m] = make_float2(0.f, 0.f);
-        uint32_t cur = skey[base] >> (2 * sh);
-        auto flush = [&](uint32_t box) {
-#pragma unroll
-            for (int m = 0; m < P1B; ++m) {
-                row[2 * m] = acc[m].x;
-                row[2 * m + 1] = acc[m].y;
-                acc[m] = make_float2(0.f, 0.f);
+        for (int c = 0; c < 4; ++c) {
+            float2 v = make_float2(0.f, 0.f);
+            if (live && m < p1) {
+                const size_t cell = (size_t)(2 * py + (c >> 1) + FMM_HALO) * Wc + 2 * px + (c & 1) + FMM_HALO;
+                v = child[cell * p1 + m];
             }
-            __syncwarp();
-            const size_t cell = (size_t)(fmm_compact2(box >> 1) + FMM_HALO) * W + fmm_compact2(box) + FMM_HALO;
-            for (int col = lane; col < ncol; col += 32) {
-                float s = 0.f;
-#pragma unroll
-                for (int r = 0; r < 32; ++r) s += red[warp][r][col];
-                atomicAdd(A + cell * ncol + col, fmm_f2d_bits(s));
-            }
-            __syncwarp();
-        };
-        // rounds of 64 particles, lane + 32 s (s = 0, 1) of each: when every particle of the
-        // round lies in the current square the pair's power chains run in packed FP32x2; a round
-        // that crosses a square boundary takes its two 32-particle halves in order, adding while
-        // the square is unchanged and flushing when it changes
-        for (int r = 0; r < kCoarseChunk / 64; ++r) {
-            const int64_t j0 = base + 64 * r + lane, j1 = j0 + 32;
-            const bool v0 = j0 < n, v1 = j1 < n;
-            const float4 P0 = v0 ? sp[j0] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 P1 = v1 ? sp[j1] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const uint32_t key0 = v0 ? skey[j0] : 0u, key1 = v1 ? skey[j1] : 0u;
-            const uint32_t bx0 = v0 ? key0 >> (2 * sh) : 0xffffffffu, bx1 = v1 ? key1 >> (2 * sh) : 0xffffffffu;
-            if (__all_sync(0xffffffffu, (!v0 || bx0 == cur) && (!v1 || bx1 == cur))) {
-                const float2 w0 = level_w(P0.x, P0.y, fmm_compact2(key0), fmm_compact2(key0 >> 1), sh, lv.inv_s[k]);
-                const float2 w1 = level_w(P1.x, P1.y, fmm_compact2(key1), fmm_compact2(key1 >> 1), sh, lv.inv_s[k]);
-                const float2 wx = make_float2(w0.x, w1.x), wy = make_float2(w0.y, w1.y);
-                const float2 nwy = make_float2(-w0.y, -w1.y);
-                float2 pr = make_float2(P0.z, P1.z), pi = make_float2(0.f, 0.f);   // q = 0 past the end
-                acc[0].x += pr.x + pr.y;
-#pragma unroll
-                for (int m = 1; m < P1B; ++m) {
-                    const float2 nr = __ffma2_rn(pr, wx, __fmul2_rn(pi, nwy));
-                    const float2 ni = __ffma2_rn(pr, wy, __fmul2_rn(pi, wx));
-                    pr = nr;
-                    pi = ni;
-                    acc[m].x += pr.x + pr.y;
-                    acc[m].y += pi.x + pi.y;
-                }
-            } else {
-#pragma unroll 1
-                for (int half = 0; half < 2; ++half) {
-                    const bool valid = half ? v1 : v0;
-                    const float4 P = half ? P1 : P0;
-                    const uint32_t key = half ? key1 : key0, bx = half ? bx1 : bx0;
-                    float2 c[P1B];
-                    {
-                        const float2 w = level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh, lv.inv_s[k]);
-                        c[0] = make_float2(P.z, 0.f);
-                        float pr = P.z, pi = 0.f;   // q = 0 past the end
-#pragma unroll
-                        for (int m = 1; m < P1B; ++m) {
-                            const float nr = fmaf(pr, w.x, -pi * w.y);
-                            const float ni = fmaf(pr, w.y, pi * w.x);
-                            pr = nr;
-                            pi = ni;
-                            c[m] = make_float2(pr, pi);
-                        }
-                    }
-                    // keys are sorted, so lanes with a square above cur are the ones not yet
-                    // added; each pass adds at least one lane, so at most 32 passes close the half
-                    for (int pass = 0; pass < 33; ++pass) {
-                        if (valid && bx == cur) {
-#pragma unroll
-                            for (int m = 0; m < P1B; ++m) {
-                                acc[m].x += c[m].x;
-                                acc[m].y += c[m].y;
-                            }
-                        }
-                        const unsigned later = __ballot_sync(0xffffffffu, valid && bx > cur);
-                        if (!later) break;
-                        flush(cur);
-                        cur = __shfl_sync(0xffffffffu, bx, __ffs(later) - 1);
-                    }
-                }
-            }
-            if (!__any_sync(0xffffffffu, v1)) break;
+            mom[half][c][m] = v;
         }
-        flush(cur);
     }
-}
-
-// -------------------------------------------------------------------------------- moment prep
-// FP64 moment grids of the coarse levels -> FP32 grids, one thread per coefficient over all the
-// levels; coefficient 0 (the real total charge) becomes a float-float pair.  The FP64 accumulator
-// goes back to zero for the next call.
-struct PrepA32Args {
-    double2* a64[FMM_MAX_LEVELS + 1];
-    float2* a32[FMM_MAX_LEVELS + 1];
-    int64_t base[FMM_MAX_LEVELS + 2];   // first coefficient of each level 2..kmax
-    int kmax, p1;
-};
-
-__global__ void k_prep_a32(const __grid_constant__ PrepA32Args a) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.base[a.kmax + 1]) return;
-    int k = 2;
-    while (g >= a.base[k + 1]) ++k;
-    const int64_t e = g - a.base[k];
-    const double2 v = a.a64[k][e];
-    a.a64[k][e] = make_double2(0.0, 0.0);
-    a.a32[k][e] = (e % a.p1 == 0) ? fmm_d2ff_bits(v.x) : make_float2(fmm_d2ff_bits(v.x).x, fmm_d2ff_bits(v.y).x);
+    const bool work = live && m >= 1 && m < p1;
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int c0 = 0; c0 < 4; c0 += UC) {
+        // every thread's loads issued before its stores: one round trip to L2, not one per element
+        constexpr int NU = UC * P1B * P1B, R = (NU + 2 * kM2MThreads - 1) / (2 * kM2MThreads);
+        float2 stage[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = threadIdx.x + r * 2 * kM2MThreads;
+            stage[r] = i < NU ? __ldg(U + (size_t)c0 * P1B * P1B + i) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = threadIdx.x + r * 2 * kM2MThreads;
+            if (i < NU) us[i] = stage[r];
+        }
+        __syncthreads();
+        if (work) {
+#pragma unroll
+            for (int cc = 0; cc < UC; ++cc) {
+                const float2* u = us + cc * P1B * P1B + m;   // U_c[m][j] at u[j P1B]
+                const float2 m0 = mom[half][c0 + cc][0];
+                const float q0 = m0.x + m0.y;   // M_0 from its float-float pair
+                float r = u[0].x * q0, t = u[0].y * q0;
+#pragma unroll
+                for (int j = 1; j < P1B; ++j) {   // U is zero past m
+                    const float2 uj = u[j * P1B], mj = mom[half][c0 + cc][j];
+                    r = fmaf(uj.x, mj.x, fmaf(-uj.y, mj.y, r));
+                    t = fmaf(uj.x, mj.y, fmaf(uj.y, mj.x, t));
+                }
+                re += r;
+                im += t;
+            }
+        }
+        __syncthreads();
+    }
+    if (!live || m >= p1) return;
+    float2 out;
+    if (m == 0) {
+        out = mom[half][0][0];
+#pragma unroll
+        for (int c = 1; c < 4; ++c) out = ff_add(out, mom[half][c][0]);
+    } else {
+        out = make_float2(re, im);
+    }
+    const size_t pcell = (size_t)(py + FMM_HALO) * Wp + px + FMM_HALO;
+    parent[pcell * p1 + m] = out;
 }
 
 // -------------------------------------------------------------------------------- M2L (FP32 SIMT)
@@ -941,19 +900,18 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field) {
     int launches = 0;
     const double* near = pl->phi_far;   // near-field accumulator per sorted particle
     cudaEventRecord(pl->ev[1], st);
-    // fine levels: the finest kFineLevels; coarser ones by the particle-parallel kernel
+    // fine levels: the finest kFineLevels from the particles; coarser ones by the upward pass
     const int kf = L - (kFineLevels - 1) > 2 ? L - (kFineLevels - 1) : 2;
-    const int kc_max = kf - 1;   // the coarse FP64 grids are zero here (k_prep_a32 re-zeroes them)
+    const int kc_max = kf - 1;
     const int kw = L < kM2LWarpMaxLevel ? L : kM2LWarpMaxLevel;   // levels 2..kw: the coarse M2L kernel
-    // The near field needs only the sort; the coarse levels' chain needs the fine P2M only when its
-    // M2L reaches a fine level (kf <= kw).  Otherwise both fork right after the sort and run beside
-    // the fine P2M, which is still launched first, so that its blocks (the head of the longest
-    // chain: fine P2M, tensor-core prep, tensor-core M2L) reach the SMs before the near field's.
-    const bool early_fork = L >= 2 && kf > kw;
+    // The near field needs only the sort: it forks right after it.  The coarse levels' chain (upward
+    // pass, M2L and L2P of levels 2..kw) needs the fine P2M's moments: it forks after it.  The fine
+    // P2M is launched before the near field, so that its blocks (the head of the longest chain: fine
+    // P2M, tensor-core prep, tensor-core M2L) reach the SMs first.
     // Potential calls with levels above kw evaluate the coarse levels' locals on the third stream as
     // soon as their M2L is done; the final L2P adds the fine levels, the near field and writes phi.
     const bool split_l2p = field == nullptr && L > kw && kw >= 2;
-    if (early_fork && cudaEventRecord(pl->ev_fork, st) != cudaSuccess) return -1;
+    if (cudaEventRecord(pl->ev_fork, st) != cudaSuccess) return -1;
     if (L >= 2) {
         // crowded squares (a previous call's scan found a finest square above kLaneMax particles):
         // their fine-level coefficients come from k_p2m_crowded, spread over the grid; the hint is
@@ -977,45 +935,35 @@ int fmm_launch_mixed(fmm_plan_s* pl, double* phi, double* field) {
         launches += ext ? 2 : 1;
     }
     cudaEventRecord(pl->ev[2], st);
-    // Otherwise the fork follows the fine P2M: the near field (stream2) on the sort, the coarse
-    // levels' chain (stream3) on the sort and the fine moments of levels up to kw; the fine levels'
-    // M2L stays here.  All three join before L2P.  (With fmm_set_concurrency(plan, 1)
-    // they run one after the other on the plan's stream.)
+    // the near field on stream2, from the sort's fork event; all three streams join before the
+    // final L2P (with fmm_set_concurrency(plan, 1) everything runs in turn on the plan's stream)
     {
-        // records ev_fork on the plan's stream here, unless the fork came after the sort
-        const int r = fmm_launch_p2p_concurrent(pl, lv, field != nullptr, !early_fork);
+        const int r = fmm_launch_p2p_concurrent(pl, lv, field != nullptr, false);
         if (r < 0) return -1;
         launches += r;
     }
     if (L >= 2) {
-        if (cudaStreamWaitEvent(s3, pl->ev_fork, 0) != cudaSuccess) return -1;
+        if (s3 != st && cudaStreamWaitEvent(s3, pl->ev[2], 0) != cudaSuccess) return -1;   // the fine P2M is done
         cudaEventRecord(pl->ev[10], s3);
-        if (kc_max >= 2) {
-            const unsigned cblocks = (unsigned)((n + 4 * kCoarseChunk - 1) / (4 * kCoarseChunk));
+        // upward pass, levels kc_max .. 2, each from the level below it
+        for (int k = kc_max; k >= 2; --k) {
+            const unsigned mblocks = (unsigned)(((1u << (2 * k)) + 1u) / 2u);
+            const float2* ch = reinterpret_cast<const float2*>(pl->grids.A32[k + 1]);
+            float2* par = reinterpret_cast<float2*>(pl->grids.A32[k]);
             switch (pl->p1b) {
-#define FMM_P2MC(PB)                                                                                         \
+#define FMM_M2M(PB)                                                                                          \
     case PB:                                                                                                 \
-        k_p2m_coarse<PB><<<cblocks, 128, 0, s3>>>(pl->sorted32, pl->sorted_key, n, L, kc_max, p, lv, pl->grids); \
+        k_m2m_f32<PB><<<mblocks, 2 * kM2MThreads, 0, s3>>>(ch, par, pl->U32, k, p1);                         \
         break;
-                FMM_P2MC(9) FMM_P2MC(13) FMM_P2MC(17) FMM_P2MC(21) FMM_P2MC(25) FMM_P2MC(33) FMM_P2MC(41)
-#undef FMM_P2MC
+                FMM_M2M(9) FMM_M2M(13) FMM_M2M(17) FMM_M2M(21) FMM_M2M(25) FMM_M2M(33) FMM_M2M(41)
+#undef FMM_M2M
                 default: return -2;
             }
-            PrepA32Args pa{};
-            int64_t acc = 0;
-            for (int k = 2; k <= kc_max; ++k) {
-                pa.a64[k] = reinterpret_cast<double2*>(pl->grids.A[k]);
-                pa.a32[k] = reinterpret_cast<float2*>(pl->grids.A32[k]);
-                pa.base[k] = acc;
-                acc += (int64_t)fmm_grid_width(k) * fmm_grid_width(k) * p1;
-            }
-            pa.base[kc_max + 1] = acc;
-            pa.kmax = kc_max;
-            pa.p1 = p1;
-            k_prep_a32<<<(unsigned)((acc + 255) / 256), 256, 0, s3>>>(pa);
-            launches += 2;
-            if (kc_max > kw && cudaEventRecord(pl->ev_a32, s3) != cudaSuccess) return -1;
+            ++launches;
         }
+        // from level 9 on the upward pass forms moments of levels 6 .. l-3, which the fine levels'
+        // M2L on the plan's stream reads
+        if (kc_max > kw && cudaEventRecord(pl->ev_a32, s3) != cudaSuccess) return -1;
         cudaEventRecord(pl->ev[11], s3);
         cudaEventRecord(pl->ev[12], s3);
         // coarse levels: a CTA per 4 x kM2LWarpTargets targets of one class

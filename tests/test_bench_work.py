@@ -45,12 +45,13 @@ def test_roofline_fractions():
     f = bench.roofline_for("l2p", stats, 0.05, w, peaks, 2070.0, "bf16x3", None)
     assert f["bound"] == "alu" and f["unit"] == "TFLOP/s"
     assert f["achieved"] == pytest.approx(8 * 20 * (1 << 20) * 7 / 5e-5 / 1e12)
-    assert f["hbm"]["bytes"] == 44 * (1 << 20) + sum((4 ** k) * 21 * 8 for k in range(2, 9))
+    assert f["hbm"]["bytes"] == 36 * (1 << 20) + sum((4 ** k) * 21 * 8 for k in range(2, 9))
     assert f["hbm"]["frac"] == pytest.approx(f["hbm"]["bytes"] / 5e-5 / 1e9 / 6788.3)
     pf = bench.roofline_for("p2m_fine", stats, 0.03, w, peaks, 2070.0, "bf16x2", None)
     assert pf["achieved"] == pytest.approx(8 * 20 * (1 << 20) * 3 / 3e-5 / 1e12)   # levels 6, 7, 8
-    pc = bench.roofline_for("p2m_coarse", stats, 0.03, w, peaks, 2070.0, "bf16x2", None)
-    assert pc["achieved"] == pytest.approx(8 * 20 * (1 << 20) * 4 / 3e-5 / 1e12)   # levels 2 .. 5
+    pc = bench.roofline_for("p2m_coarse", stats, 0.03, w, peaks, 2070.0, "bf16x2", None)   # upward pass
+    parents = 16 + 64 + 256 + 1024                      # levels 2 .. 5
+    assert pc["achieved"] == pytest.approx(parents * 4 * 8 * sum(range(2, 22)) / 3e-5 / 1e12)
     mc = bench.roofline_for("m2l_coarse", stats, 0.02, w, peaks, 2070.0, "bf16x2", None)
     assert mc["achieved"] == pytest.approx((bench.m2l_pairs(8, 2) - bench.m2l_pairs(8, 6)) * 8 * 441 / 2e-5 / 1e12)
     mf = bench.roofline_for("m2l_fine", stats, 0.06, w, peaks, 2070.0, "bf16x2", None)
