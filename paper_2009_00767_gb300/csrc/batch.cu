@@ -7,7 +7,8 @@
 // grid-stride (persistent) kernel over a flattened work space that spans all systems.  A work
 // item finds its system by binary search over per-system prefix counts held in shared memory.
 // One exclusive scan over the concatenated finest-square populations gives every system's CSR
-// offsets already shifted by the system's first particle.  M2L runs levels 2..5 on the CUDA cores
+// offsets already shifted by the system's first particle.  The coarse levels' moments come from the
+// upward pass over every system's squares of one level per launch.  M2L runs levels 2..5 on the CUDA cores
 // in FP32 and, in the tensor-core precisions, every system's levels 6 and finer in one tcgen05
 // launch whose tiles come from any system (one segment per system and level).  The near field is
 // the symmetric one of the single-system path, on a second branch of the graph beside P2M and M2L;
@@ -27,7 +28,6 @@
 namespace {
 
 constexpr int kT = 128;   // threads per block of every batched kernel
-constexpr int kCoarseChunk = 256;
 constexpr int kLaneMax = 128;
 constexpr int kFineMean = 64;
 constexpr int kP2PBlockMin = 16;   // the smallest near-field block the autotuner tries
@@ -53,8 +53,8 @@ struct BatchArgs {
     const long long* wp_part;     // particles
     const long long* wp_leaf;     // finest squares
     const long long* wp_fine;     // fine-level P2M squares
-    const long long* wp_coarse;   // coarse P2M warps (kCoarseChunk particles each)
     const long long* wp_m2l;      // M2L blocks
+    const long long* wp_m2m;      // upward-pass parents of level 2; level k's prefix is (k - 2) (nsys + 1) further
     int nsys, p;
     double box;
     float2 box_ff;
@@ -67,10 +67,10 @@ struct BatchArgs {
     long long nl;             // concatenated finest squares
     uint32_t* sorted_key;
     float4* sorted32;
-    double* a64;     // coarse moment grids (FP64, atomics)
-    float2* a32;     // all moment grids (FP32; coarse region first, same cells as a64)
+    float2* a32;     // all moment grids (FP32; coarse region first)
     float2* b32;     // local coefficients
     const float2* T; // FP32 operators [49][P1B][P1B]
+    const float2* U; // upward-pass translations [child position][j][m], P1B each (the single-system plan's)
     double* acc;     // near field per sorted particle (log2 r^2 units), zeroed at the start of a call
     unsigned int* status;
     int m2l_kmax;    // levels 2..m2l_kmax of each system run in kb_m2l_f32 (the tensor cores take the rest)
@@ -247,94 +247,103 @@ __global__ void __launch_bounds__(kT) kb_p2m_fine(BatchArgs a, MixedLevels lv) {
     }
 }
 
-// coarse levels: a warp walks kCoarseChunk particles of one system (see mixed.cu)
-template <int P1B>
-__global__ void __launch_bounds__(kT) kb_p2m_coarse(BatchArgs a, MixedLevels lv) {
-    extern __shared__ long long pre[];
-    __shared__ float red[kT / 32][32][2 * P1B + 1];
-    load_prefix(pre, a.wp_coarse, a.nsys);
-    const long long total = pre[a.nsys];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int p1 = a.p + 1, ncol = 2 * p1;
-    float* row = red[warp][lane];
-    for (long long wi = (long long)blockIdx.x * (kT / 32) + warp; wi < total; wi += (long long)gridDim.x * (kT / 32)) {
-        const int s = find_sys(pre, a.nsys, wi);
-        const BatchSys& S = a.sys[s];
-        const long long base = S.p_off + (wi - pre[s]) * kCoarseChunk;
-        const long long end = S.p_off + S.n;
-        for (int k = 2; k < S.kf; ++k) {
-            const int sh = S.levels - k;
-            const int W = fmm_grid_width(k);
-            float2 acc[P1B];
-#pragma unroll
-            for (int m = 0; m < P1B; ++m) acc[m] = make_float2(0.f, 0.f);
-            uint32_t cur = a.sorted_key[base] >> (2 * sh);
-            auto flush = [&](uint32_t box) {
-#pragma unroll
-                for (int m = 0; m < P1B; ++m) {
-                    row[2 * m] = acc[m].x;
-                    row[2 * m + 1] = acc[m].y;
-                    acc[m] = make_float2(0.f, 0.f);
-                }
-                __syncwarp();
-                const long long cell =
-                    S.a_off[k] + (long long)(fmm_compact2(box >> 1) + FMM_HALO) * W + fmm_compact2(box) + FMM_HALO;
-                for (int col = lane; col < ncol; col += 32) {
-                    float sum = 0.f;
-#pragma unroll
-                    for (int r = 0; r < 32; ++r) sum += red[warp][r][col];
-                    atomicAdd(a.a64 + cell * ncol + col, fmm_f2d_bits(sum));
-                }
-                __syncwarp();
-            };
-            for (int r = 0; r < kCoarseChunk / 32; ++r) {
-                const long long j = base + 32 * r + lane;
-                const bool valid = j < end;
-                float2 c[P1B];
-                uint32_t bx = 0xffffffffu;
-                if (valid) {
-                    const float4 P = a.sorted32[j];
-                    const uint32_t key = a.sorted_key[j];
-                    bx = key >> (2 * sh);
-                    const float2 w = level_w(P.x, P.y, fmm_compact2(key), fmm_compact2(key >> 1), sh, lv.inv_s[k]);
-                    c[0] = make_float2(P.z, 0.f);
-                    float pr = P.z, pi = 0.f;
-#pragma unroll
-                    for (int m = 1; m < P1B; ++m) {
-                        const float nr = fmaf(pr, w.x, -pi * w.y);
-                        const float ni = fmaf(pr, w.y, pi * w.x);
-                        pr = nr;
-                        pi = ni;
-                        c[m] = make_float2(pr, pi);
-                    }
-                } else {
-#pragma unroll
-                    for (int m = 0; m < P1B; ++m) c[m] = make_float2(0.f, 0.f);
-                }
-                for (int pass = 0; pass < 33; ++pass) {
-                    if (valid && bx == cur) {
-#pragma unroll
-                        for (int m = 0; m < P1B; ++m) {
-                            acc[m].x += c[m].x;
-                            acc[m].y += c[m].y;
-                        }
-                    }
-                    const unsigned later = __ballot_sync(0xffffffffu, valid && bx > cur);
-                    if (!later) break;
-                    flush(cur);
-                    cur = __shfl_sync(0xffffffffu, bx, __ffs(later) - 1);
-                }
-                if (!__any_sync(0xffffffffu, valid)) break;
-            }
-            flush(cur);
-        }
-    }
-}
+// Upward pass for the coarse levels (U-bar-2, as in mixed.cu's k_m2m_f32): level k of every
+// system whose coarse levels include k, one parent per half-CTA of 64 threads (a thread per
+// coefficient), grid-stride over pairs of parents.  Each parent sums its four children's moments
+// re-expanded about its centre with the tables U; its total charge is a float-float sum.
+constexpr int kM2MHalf = 64;
 
-__global__ void kb_prep_a32(const double2* __restrict__ a64, float2* __restrict__ a32, long long count, int p1) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (long long)gridDim.x * blockDim.x) {
-        const double2 v = a64[e];
-        a32[e] = (e % p1 == 0) ? fmm_d2ff_bits(v.x) : make_float2(fmm_d2ff_bits(v.x).x, fmm_d2ff_bits(v.y).x);
+template <int P1B>
+__global__ void __launch_bounds__(2 * kM2MHalf) kb_m2m(BatchArgs a, int k) {
+    static_assert(P1B <= kM2MHalf, "one thread per coefficient");
+    // the four tables staged at once where they take at most 24 KB (the prefix array shares the
+    // 48 KB of shared memory), else one child's per round
+    constexpr int UC = 4 * P1B * P1B * (int)sizeof(float2) <= 24 * 1024 ? 4 : 1;
+    extern __shared__ long long pre[];
+    __shared__ float2 mom[2][4][P1B];
+    __shared__ float2 us[UC * P1B * P1B];
+    load_prefix(pre, a.wp_m2m + (long long)(k - 2) * (a.nsys + 1), a.nsys);
+    const long long total = pre[a.nsys];
+    const int half = threadIdx.x / kM2MHalf, m = threadIdx.x % kM2MHalf;
+    const int p1 = a.p + 1;
+    auto stage = [&](int c0) {
+        constexpr int NU = UC * P1B * P1B, R = (NU + 2 * kM2MHalf - 1) / (2 * kM2MHalf);
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = threadIdx.x + r * 2 * kM2MHalf;
+            v[r] = i < NU ? __ldg(a.U + (size_t)c0 * P1B * P1B + i) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = threadIdx.x + r * 2 * kM2MHalf;
+            if (i < NU) us[i] = v[r];
+        }
+    };
+    if (UC == 4) stage(0);   // once for all the CTA's parents (load_prefix's barrier came before)
+    for (long long wp = blockIdx.x; 2 * wp < total; wp += gridDim.x) {
+        const long long w = 2 * wp + half;
+        const bool live = w < total;
+        int s = 0;
+        uint32_t px = 0, py = 0;
+        if (live) {
+            s = find_sys(pre, a.nsys, w);
+            const uint32_t par = (uint32_t)(w - pre[s]), side = 1u << k;
+            px = par % side;
+            py = par / side;
+        }
+        const BatchSys& S = a.sys[s];
+        if (m < P1B) {
+            const int Wc = fmm_grid_width(k + 1);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float2 v = make_float2(0.f, 0.f);
+                if (live && m < p1) {
+                    const long long cell =
+                        S.a_off[k + 1] + (long long)(2 * py + (c >> 1) + FMM_HALO) * Wc + 2 * px + (c & 1) + FMM_HALO;
+                    v = a.a32[cell * p1 + m];
+                }
+                mom[half][c][m] = v;
+            }
+        }
+        const bool work = live && m >= 1 && m < p1;
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int c0 = 0; c0 < 4; c0 += UC) {
+            if (UC == 1) stage(c0);
+            __syncthreads();
+            if (work) {
+#pragma unroll
+                for (int cc = 0; cc < UC; ++cc) {
+                    const float2* u = us + cc * P1B * P1B + m;   // U_c[m][j] at u[j P1B]
+                    const float2 m0 = mom[half][c0 + cc][0];
+                    const float q0 = m0.x + m0.y;
+                    float r = u[0].x * q0, t = u[0].y * q0;
+#pragma unroll
+                    for (int j = 1; j < P1B; ++j) {
+                        const float2 uj = u[j * P1B], mj = mom[half][c0 + cc][j];
+                        r = fmaf(uj.x, mj.x, fmaf(-uj.y, mj.y, r));
+                        t = fmaf(uj.x, mj.y, fmaf(uj.y, mj.x, t));
+                    }
+                    re += r;
+                    im += t;
+                }
+            }
+            __syncthreads();
+        }
+        if (live && m < p1) {
+            float2 out;
+            if (m == 0) {
+                out = mom[half][0][0];
+#pragma unroll
+                for (int c = 1; c < 4; ++c) out = ff_add(out, mom[half][c][0]);
+            } else {
+                out = make_float2(re, im);
+            }
+            const int Wp = fmm_grid_width(k);
+            const long long pcell = S.a_off[k] + (long long)(py + FMM_HALO) * Wp + px + FMM_HALO;
+            a.a32[pcell * p1 + m] = out;
+        }
     }
 }
 
@@ -484,7 +493,7 @@ __global__ void __launch_bounds__(kT, 8) kb_p2p(BatchArgs a, MixedLevels lv) {
 struct fmm_batch_s {
     int device, nsys, p, p1b;
     double box;
-    long long nt, nl, coarse_cells, a_cells, b_cells;
+    long long nt, nl, coarse_cells, a_cells, b_cells;   // coarse_cells: the coarse levels' grid cells
     cudaStream_t stream;
     int precision;
     int grid_mult;                    // persistent blocks per SM (autotuned)
@@ -494,16 +503,19 @@ struct fmm_batch_s {
     FmmTc* tc;                        // tensor-core M2L of levels 6 and finer (tensor-core precisions)
     std::vector<BatchSys> host_sys;
     BatchSys* d_sys;
-    long long* d_pre;                 // 5 prefix arrays, (nsys + 1) each
+    long long* d_pre;                 // prefix arrays, (nsys + 1) each: particles, squares, fine P2M
+                                      // squares, M2L blocks, then upward-pass parents of levels 2..max
     BatchCall* d_call;
     BatchCall* h_call;                // pinned
     uint32_t *keys, *rank, *counts, *leaf_start, *block_sums, *sorted_key, *leaf_nb, *bstart;
     uint2* bmap;
     float4* sorted32;
-    double* a64;
     float2 *a32, *b32;
     double* acc;                      // near field per sorted particle
     float2* T32;
+    float2* U32;                      // upward-pass translations (the single-system plan's layout)
+    int m2m_kmax;                     // the highest coarse level of any system (the upward pass runs
+                                      // levels m2m_kmax .. 2), 1 when no system has one
     unsigned int* d_status;
     unsigned int* h_status;
     cudaGraph_t graph;
@@ -521,7 +533,7 @@ void batch_free(fmm_batch_s* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     void* bufs[] = {b->d_sys, b->d_pre, b->d_call, b->keys, b->rank, b->counts, b->leaf_start, b->block_sums,
                     b->leaf_nb, b->bstart, b->bmap,
-                    b->sorted_key, b->sorted32, b->a64, b->a32, b->b32, b->acc, b->T32, b->d_status};
+                    b->sorted_key, b->sorted32, b->a32, b->b32, b->acc, b->T32, b->U32, b->d_status};
     fmm_tc_free(b->tc);
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -557,9 +569,6 @@ int enqueue_batch_kernels(fmm_batch_s* b, const BatchArgs& a, const MixedLevels&
     if (cudaMemsetAsync(b->counts, 0, sizeof(uint32_t) * b->nl, st) != cudaSuccess ||
         cudaMemsetAsync(b->acc, 0, sizeof(double) * b->nt, st) != cudaSuccess)
         return -1;
-    if (b->coarse_cells > 0 &&
-        cudaMemsetAsync(b->a64, 0, sizeof(double2) * b->coarse_cells * (b->p + 1), st) != cudaSuccess)
-        return -1;
     kb_bin<<<grid, kT, pre_bytes, st>>>(a, lv);
     ++launches;
     const int sc = fmm_launch_scan(b->counts, b->nl, b->block_sums, b->leaf_start, (uint32_t)b->nt, st);
@@ -578,11 +587,10 @@ int enqueue_batch_kernels(fmm_batch_s* b, const BatchArgs& a, const MixedLevels&
     if (st2 != st && cudaEventRecord(ev_join, st2) != cudaSuccess) return -1;
     kb_p2m_fine<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
     ++launches;
-    if (b->coarse_cells > 0) {
-        kb_p2m_coarse<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
-        kb_prep_a32<<<grid, 256, 0, st>>>(reinterpret_cast<const double2*>(b->a64), b->a32,
-                                          b->coarse_cells * (b->p + 1), b->p + 1);
-        launches += 2;
+    // upward pass: one launch per coarse level, the finest first
+    for (int k = b->m2m_kmax; k >= 2; --k) {
+        kb_m2m<P1B><<<grid, 2 * kM2MHalf, pre_bytes, st>>>(a, k);
+        ++launches;
     }
     kb_m2l_f32<P1B><<<grid, kT, pre_bytes, st>>>(a, lv);
     ++launches;
@@ -605,8 +613,8 @@ int enqueue_all(fmm_batch_s* b, cudaStream_t st, cudaStream_t st2, cudaEvent_t e
     a.wp_part = b->d_pre;
     a.wp_leaf = b->d_pre + stride;
     a.wp_fine = b->d_pre + 2 * stride;
-    a.wp_coarse = b->d_pre + 3 * stride;
-    a.wp_m2l = b->d_pre + 4 * stride;
+    a.wp_m2l = b->d_pre + 3 * stride;
+    a.wp_m2m = b->d_pre + 4 * stride;
     a.nsys = b->nsys;
     a.p = b->p;
     a.box = b->box;
@@ -621,10 +629,10 @@ int enqueue_all(fmm_batch_s* b, cudaStream_t st, cudaStream_t st2, cudaEvent_t e
     a.nl = b->nl;
     a.sorted_key = b->sorted_key;
     a.sorted32 = b->sorted32;
-    a.a64 = b->a64;
     a.a32 = b->a32;
     a.b32 = b->b32;
     a.T = b->T32;
+    a.U = b->U32;
     a.acc = b->acc;
     a.status = b->d_status;
     a.m2l_kmax = b->tc ? fmm_tc_kmin() - 1 : FMM_MAX_LEVELS;
@@ -782,7 +790,10 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
     const int p1 = p + 1;
     // system layout: particles, leaves, grid cells (all coarse regions first, then the fine ones)
     b->host_sys.resize(nsys);
-    std::vector<long long> pre(5 * (size_t)(nsys + 1), 0);
+    // prefix arrays 0..3, then the upward pass's parents of levels 2 .. FMM_MAX_LEVELS - 1
+    constexpr int kPreArrays = 4 + (FMM_MAX_LEVELS - 2);
+    std::vector<long long> pre(kPreArrays * (size_t)(nsys + 1), 0);
+    b->m2m_kmax = 1;
     long long nl = 0, coarse = 0, cells_fine = 0, bcells = 0;
     nt = 0;
     for (int i = 0; i < nsys; ++i) {
@@ -818,13 +829,18 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
         long long fine = 0;
         for (int k = S.kf; k <= S.levels && S.levels >= 2; ++k) fine += 1ll << (2 * k);
         pre[2 * s1 + i + 1] = pre[2 * s1 + i] + fine;
-        pre[3 * s1 + i + 1] = pre[3 * s1 + i] + (S.kf > 2 && S.levels >= 2 ? (S.n + kCoarseChunk - 1) / kCoarseChunk : 0);
         long long m2l = 0;
         for (int k = 2; k <= S.levels && k <= m2l_kmax; ++k) {
             const long long w2 = 1ll << (k - 1);
             m2l += 4 * ((w2 * w2 + kT - 1) / kT);
         }
-        pre[4 * s1 + i + 1] = pre[4 * s1 + i] + m2l;
+        pre[3 * s1 + i + 1] = pre[3 * s1 + i] + m2l;
+        // the upward pass's parents: level k of this system if k is one of its coarse levels
+        for (int k = 2; k < FMM_MAX_LEVELS; ++k) {
+            const bool coarse_k = S.levels >= 2 && k < S.kf;
+            pre[(size_t)(4 + k - 2) * s1 + i + 1] = pre[(size_t)(4 + k - 2) * s1 + i] + (coarse_k ? (1ll << (2 * k)) : 0);
+            if (coarse_k && k > b->m2m_kmax) b->m2m_kmax = k;
+        }
     }
     b->nt = nt;
     b->nl = nl;
@@ -837,14 +853,15 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
               balloc(b, &b->block_sums, 4 * ((size_t)fmm_scan_blocks(nl) + 1)) && balloc(b, &b->sorted_key, 4 * nt) &&
               balloc(b, &b->leaf_nb, 4 * nl) && balloc(b, &b->bstart, 4 * (nl + 1)) &&
               balloc(b, &b->bmap, sizeof(uint2) * ((size_t)nl + (size_t)nt / kP2PBlockMin + 1)) &&
-              balloc(b, &b->sorted32, 16 * nt) && balloc(b, &b->a64, sizeof(double2) * coarse * p1) &&
+              balloc(b, &b->sorted32, 16 * nt) &&
               balloc(b, &b->a32, sizeof(float2) * b->a_cells * p1) && balloc(b, &b->b32, sizeof(float2) * bcells * p1) &&
               balloc(b, &b->acc, sizeof(double) * nt) && balloc(b, &b->d_status, sizeof(unsigned int));
     if (!ok) {
         batch_free(b);
         return FMM_ERR_OOM;
     }
-    // operators: the plan's FP64 build, rounded to FP32 in the padded layout of the FP32 M2L
+    // operators and the upward pass's tables: the plan's FP64 builds, rounded to FP32 in the padded
+    // layouts of the FP32 kernels
     {
         fmm_plan_t tmp = nullptr;
         fmm_status s = fmm_plan(&tmp, 1, 2, p, box, FMM_MIXED_FP32, stream);
@@ -852,9 +869,11 @@ fmm_status fmm_batch_plan(fmm_batch_t* out, int nsys, const int64_t* n, const in
             batch_free(b);
             return s;
         }
-        const size_t tsz = (size_t)49 * b->p1b * b->p1b;
+        const size_t tsz = (size_t)49 * b->p1b * b->p1b, usz = (size_t)4 * b->p1b * b->p1b;
         ok = balloc(b, &b->T32, sizeof(float2) * tsz) &&
-             cudaMemcpy(b->T32, tmp->T32, sizeof(float2) * tsz, cudaMemcpyDeviceToDevice) == cudaSuccess;
+             cudaMemcpy(b->T32, tmp->T32, sizeof(float2) * tsz, cudaMemcpyDeviceToDevice) == cudaSuccess &&
+             balloc(b, &b->U32, sizeof(float2) * usz) &&
+             cudaMemcpy(b->U32, tmp->U32, sizeof(float2) * usz, cudaMemcpyDeviceToDevice) == cudaSuccess;
         fmm_plan_destroy(tmp);
         if (!ok) {
             batch_free(b);
