@@ -335,9 +335,8 @@ k_p2m_crowded(const float4* __restrict__ sp, const uint32_t* __restrict__ skey, 
 //     M_m(parent) = sum_c sum_{j <= m} U_c[m][j] M_j(child c),   U_c[m][j] = C(m, j) 2^-j d_c^(m-j),
 // a finite sum, exact for the truncated expansions (the same moments the particles give directly).
 // U comes from the plan ([c][j][m]: FP64 build, one FP32 rounding, zero above the diagonal and
-// past p).  Two
-// parents a CTA, one thread per coefficient m; the total charge (slot 0, a float-float pair) is
-// the children's float-float sum.
+// past p).  Two parents a CTA, one thread per coefficient m; the total charge (slot 0, a
+// float-float pair) is the children's float-float sum.
 constexpr int kM2MThreads = 64;   // per parent: coefficients 0 .. P1B - 1 (P1B <= 41)
 
 template <int P1B>
