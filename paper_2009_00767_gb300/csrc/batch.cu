@@ -257,7 +257,7 @@ template <int P1B>
 __global__ void __launch_bounds__(2 * kM2MHalf) kb_m2m(BatchArgs a, int k) {
     static_assert(P1B <= kM2MHalf, "one thread per coefficient");
     // the four tables staged at once where they take at most 24 KB (the prefix array shares the
-    // 48 KB of shared memory), else one child's per round
+    // 48 KB of shared memory), else one child's at a time
     constexpr int UC = 4 * P1B * P1B * (int)sizeof(float2) <= 24 * 1024 ? 4 : 1;
     extern __shared__ long long pre[];
     __shared__ float2 mom[2][4][P1B];
