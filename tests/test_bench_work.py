@@ -70,3 +70,30 @@ def test_cpu_baseline_all_cores_and_one_thread(oracle_mod):
     assert r["kind"] == "oracle" and r["cores"] == threads and r["value"] > 0
     assert r["one_thread"]["cores"] == 1 and r["one_thread"]["value"] > 0
     assert oracle_mod.get_threads() == threads   # the thread count is restored
+
+
+def test_traffic_figures_follow_their_sources(tmp_path, monkeypatch):
+    """profiles/traffic.json's per-stage DRAM bytes count only while the stage's source files hash to
+    the value recorded at capture: a changed kernel source makes the bench report null, not a
+    stale figure."""
+    import hashlib
+    import json
+
+    import bench
+    root = tmp_path / "repo"
+    csrc = root / "paper_2009_00767_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (root / "profiles").mkdir()
+    (csrc / "a.cu").write_text("kernel A\n")
+    (csrc / "b.cuh").write_text("shared header\n")
+    h = hashlib.sha256()
+    for f in ("a.cu", "b.cuh"):
+        h.update((csrc / f).read_bytes())
+    rec = {"stage_x": {"sources": ["a.cu", "b.cuh"], "kernels": ["k_a"], "bytes_per_launch": 1234,
+                       "sha": h.hexdigest()[:16]}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.load_traffic("stage_x") == 1234
+    assert bench.load_traffic("stage_missing") is None
+    (csrc / "b.cuh").write_text("shared header, changed\n")
+    assert bench.load_traffic("stage_x") is None
